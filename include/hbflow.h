@@ -1,0 +1,170 @@
+/* hbflow: one time step of Papanastasiou-regularised Herschel-Bulkley
+ * incompressible flow on a uniform grid, on one GB300 GPU (sm_103a).
+ *
+ * Method: Sverdrup, Nikiforakis & Almgren, "Highly parallelisable simulations
+ * of time-dependent viscoplastic fluid flow with structured adaptive mesh
+ * refinement" (arXiv:1803.00417), Sec. III: the approximate projection method
+ * with a Godunov edge-state predictor, a semi-implicit tensor viscous solve and
+ * a nodal projection (Sec. III A, Eqs. 11-19), and the regularised viscosity
+ * of Sec. III B (Eq. 23).
+ *
+ * Conventions for every entry point:
+ *  - returns an hbf_status (0 on success); on failure hbf_last_error() holds a
+ *    one-line reason.  Outputs are valid only on HBF_OK, except that
+ *    HBF_ERR_NOT_CONVERGED leaves the last iterate and filled stats.
+ *  - work is queued on the CUDA stream given to hbf_init_grid; calls that return
+ *    solver statistics synchronise that stream (they read residual norms).
+ *  - the context owns every device buffer it allocates; pointers passed in by
+ *    the caller stay owned by the caller and are never freed by the library.
+ *  - layouts: cell fields are structure-of-arrays, component-major, x fastest:
+ *    element (c, i, j, k) of a d-component field sits at
+ *    c*ncell + i + nx*(j + ny*k); nodal fields (pressure) have (nx+1)(ny+1)(nz+1)
+ *    points, i + (nx+1)*(j + (ny+1)*k).  In 2D nz = 1 and k = 0.
+ *  - only no-slip walls (with a prescribed tangential wall velocity) are
+ *    supported; every face of the box is a wall.
+ */
+#ifndef HBFLOW_H
+#define HBFLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hbf_ctx hbf_ctx;
+
+enum hbf_status {
+  HBF_OK = 0,
+  HBF_ERR_ARG = -1,           /* invalid argument; nothing was done */
+  HBF_ERR_OOM = -2,           /* device allocation failed */
+  HBF_ERR_CUDA = -3,          /* a CUDA call failed; the message names it */
+  HBF_ERR_NOT_CONVERGED = -4, /* a multigrid solve hit max_cycles */
+  HBF_ERR_TIMEOUT = -5,       /* reserved: a bounded device-side wait gave up */
+  HBF_ERR_NONFINITE = -6      /* a residual norm was NaN or Inf */
+};
+
+enum hbf_precision {
+  HBF_FP64 = 0,  /* every solve in FP64 */
+  HBF_MIXED = 1  /* FP64 defect correction around FP32 V-cycles */
+};
+
+/* Fields that can be copied in or out with hbf_set_field / hbf_get_field.
+ * Sizes in doubles (hbf_field_size): U, USTAR, RHS, GP, LU: d*ncell; P: nnode;
+ * ETA, PHI_MAC: ncell; UADV, UMAC: sum over axes a of nface[a] (axis-major);
+ * UL, UR: sum over axes a of d*nface[a] (axis-major, then component). */
+enum hbf_field {
+  HBF_U = 0,       /* cell velocity u^m (set) / u^{m+1} (after a step) */
+  HBF_P = 1,       /* nodal pressure p^{m-1/2} / p^{m+1/2} */
+  HBF_ETA = 2,     /* cell apparent viscosity eta^m (Eq. 23) */
+  HBF_USTAR = 3,   /* provisional velocity u* (Eq. 16) */
+  HBF_UADV = 4,    /* face advection velocity u^adv (normal component) */
+  HBF_UMAC = 5,    /* MAC-projected face velocity u^MAC */
+  HBF_RHS = 6,     /* right-hand side of the viscous solve (Eq. 16) */
+  HBF_PHI_MAC = 7, /* MAC projection potential */
+  HBF_GP = 8,      /* cell-centred G p^{m-1/2} */
+  HBF_LU = 9,      /* div(eta^m (grad u^m + grad u^m^T)) at cells */
+  HBF_UL = 10,     /* left face states (Eq. 14a) */
+  HBF_UR = 11      /* right face states (Eq. 14b) */
+};
+
+typedef struct {
+  int cycles;      /* V-cycles (outer defect-correction iterations in mixed mode) */
+  int converged;   /* 1 if ||b - A x||_inf <= rtol ||b||_inf */
+  double r0;       /* initial residual norm */
+  double rnorm;    /* final residual norm */
+  double bnorm;    /* ||b||_inf (after removing the mean of a singular rhs) */
+} hbf_solve_stats;
+
+typedef struct {
+  hbf_solve_stats mac, visc, nodal;
+} hbf_step_stats;
+
+/* Create a context for a box of n[0] x n[1] (x n[2]) cells of size h, all
+ * faces no-slip walls.  wall_u[(a*2 + s)*3 + c] is component c of the velocity
+ * of the wall normal to axis a on side s (0 low, 1 high); its normal component
+ * must be 0.  Every n[a] must be even (the multigrid coarsens by two down to at
+ * least two cells per axis).  stream: a cudaStream_t, NULL for the default
+ * stream.  precision: an hbf_precision.  Allocates all device buffers.
+ * (Sec. IV: the lid-driven cavity; Sec. III A: cell-centred velocity, nodal
+ * pressure.) */
+int hbf_init_grid(hbf_ctx** out, int dim, const int64_t n[3], double h, const double wall_u[18],
+                  int precision, void* stream);
+
+/* Regularised Herschel-Bulkley law, Eq. 23 with mu -> K and 1/epsilon -> m:
+ *   eta = (2^(n-1) K g^n + tau_y/2) F(g),  F(g) = (1 - exp(-m g))/g, F(0) = m,
+ * g = |gamma_dot| = sqrt(1/2 tr(D D^T)) (Eq. 1).  reg_power = 0 regularises only
+ * the yield term: eta = 2^(n-1) K g^(n-1) + tau_y/2 F(g) (then n >= 1).
+ * Requires K >= 0, n > 0, tau_y >= 0, m > 0. */
+int hbf_set_rheology(hbf_ctx* ctx, double K, double n, double tau_y, double m, int reg_power);
+
+/* Constant density rho > 0 (Eq. 2b) and body force f (Eq. 2b, f^m in Eq. 15). */
+int hbf_set_density(hbf_ctx* ctx, double rho);
+int hbf_set_body_force(hbf_ctx* ctx, const double f[3]);
+
+/* Include the explicit stress divergence in the edge-state forcing of Eq. 14
+ * (1) or leave it out (0, default; see the library documentation). */
+int hbf_set_predictor_viscous(hbf_ctx* ctx, int on);
+
+/* Multigrid controls: stop when ||b - A x||_inf <= rtol ||b||_inf or after
+ * max_cycles V-cycles; nu1/nu2 pre/post smoothing sweeps; nu_bottom sweeps on
+ * the coarsest level.  Defaults 1e-10, 200, 2, 2, 40. */
+int hbf_set_solver(hbf_ctx* ctx, double rtol, int max_cycles, int nu1, int nu2, int nu_bottom);
+
+/* Number of doubles of a field (see enum hbf_field), or a negative status. */
+int64_t hbf_field_size(const hbf_ctx* ctx, int which);
+
+/* Copy a field in or out.  src/dst may be host or device pointers (unified
+ * addressing); the copy is ordered on the context stream and the host side
+ * must stay valid until hbf_sync. */
+int hbf_set_field(hbf_ctx* ctx, int which, const double* src);
+int hbf_get_field(hbf_ctx* ctx, int which, double* dst);
+
+/* Stage 1 (Sec. III B, Eq. 23): eta^m from U. */
+int hbf_compute_viscosity(hbf_ctx* ctx);
+
+/* Stages 2-3 (Sec. III A, Eqs. 11-14): G p, div tau(u^m), limited slopes,
+ * transverse terms, left/right face states and the advection velocity u^adv.
+ * Needs ETA (hbf_compute_viscosity) for the current U. */
+int hbf_predict(hbf_ctx* ctx, double dt);
+
+/* Stage 4: MAC projection of u^adv: solve the cell-centred Poisson problem
+ * D^MAC G^MAC phi = D^MAC u^adv (Neumann walls, mean-zero phi) and set
+ * u^MAC = u^adv - G^MAC phi.  stats may be NULL. */
+int hbf_mac_project(hbf_ctx* ctx, hbf_solve_stats* stats);
+
+/* Stage 5 (Eqs. 15-16): upwind the face states with u^MAC, form the convective
+ * term and the viscous right-hand side RHS. */
+int hbf_advect_rhs(hbf_ctx* ctx, double dt);
+
+/* Stage 6 (Eq. 16): solve (I - dt/(2 rho) L_eta) u = rhs with the context's
+ * current ETA, L_eta u = div(eta (grad u + grad u^T)), walls at their
+ * velocity.  rhs_dev, u_dev: device arrays of d*ncell doubles; u_dev holds the
+ * initial guess on entry and the solution on exit.  stats may be NULL. */
+int hbf_solve_viscous(hbf_ctx* ctx, double dt, const double* rhs_dev, double* u_dev,
+                      hbf_solve_stats* stats);
+
+/* Stage 7 (Eqs. 17-19): nodal projection.  Solves L phi = rho D(u/dt + G p/rho)
+ * with the finite-element nodal Laplacian (Neumann walls, mean-zero phi), then
+ * u <- u + dt/rho (G p - G phi) and p <- phi.  u_dev: device d*ncell doubles
+ * (u* in, u^{m+1} out); p_dev: device nnode doubles (p^{m-1/2} in, also the
+ * initial guess; p^{m+1/2} out).  stats may be NULL. */
+int hbf_project(hbf_ctx* ctx, double dt, double* u_dev, double* p_dev, hbf_solve_stats* stats);
+
+/* One full step m -> m+1 of stages 1-7 on the context's U and P.  stats may be
+ * NULL.  Returns HBF_ERR_NOT_CONVERGED if any solve did not converge. */
+int hbf_step(hbf_ctx* ctx, double dt, hbf_step_stats* stats);
+
+/* dt = cfl h / max(max|u|, 1) for the current U (synchronises). */
+double hbf_cfl_dt(hbf_ctx* ctx, double cfl);
+
+int hbf_sync(hbf_ctx* ctx);
+const char* hbf_last_error(const hbf_ctx* ctx);
+void hbf_destroy(hbf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HBFLOW_H */

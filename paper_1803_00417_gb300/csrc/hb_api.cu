@@ -1,0 +1,375 @@
+// C-ABI entry points and the step orchestration (Sec. III A: one time step of
+// the approximate projection method; the stage order follows the paper).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "hb_internal.h"
+
+namespace hb {
+
+int fail(hbf_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_check(hbf_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HBF_OK;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? HBF_ERR_OOM : HBF_ERR_CUDA, m);
+}
+
+static Geom make_geom(int dim, const int n[3], double h) {
+  Geom g;
+  std::memset(&g, 0, sizeof g);
+  g.n[0] = n[0];
+  g.n[1] = n[1];
+  g.n[2] = dim == 3 ? n[2] : 1;
+  g.h = h;
+  g.ncell = g.n[0] * g.n[1] * g.n[2];
+  g.nnode = (g.n[0] + 1) * (g.n[1] + 1) * (dim == 3 ? g.n[2] + 1 : 1);
+  g.nface[0] = (g.n[0] + 1) * g.n[1] * g.n[2];
+  g.nface[1] = g.n[0] * (g.n[1] + 1) * g.n[2];
+  g.nface[2] = dim == 3 ? g.n[0] * g.n[1] * (g.n[2] + 1) : 0;
+  return g;
+}
+
+template <typename T>
+static int alloc(hbf_ctx* c, T** p, long long count) {
+  if (count <= 0) {
+    *p = nullptr;
+    return HBF_OK;
+  }
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+  if (e != cudaSuccess) return cuda_check(c, e, "cudaMalloc");
+  c->allocs.push_back(q);
+  *p = (T*)q;
+  return cudaMemsetAsync(q, 0, (size_t)count * sizeof(T), c->stream) == cudaSuccess ? HBF_OK
+                                                                                     : fail(c, HBF_ERR_CUDA, "memset");
+}
+
+static bool can_coarsen(const Geom& g, int dim) {
+  for (int a = 0; a < dim; ++a)
+    if (g.n[a] % 2 != 0 || g.n[a] / 2 < 2) return false;
+  return true;
+}
+
+static int allocate(hbf_ctx* c) {
+  const Geom& g = c->g;
+  const int D = c->dim;
+  int st = 0;
+#define A(ptr, cnt) \
+  if ((st = alloc(c, &(ptr), (cnt)))) return st
+  A(c->u, (long long)D * g.ncell);
+  A(c->ustar, (long long)D * g.ncell);
+  A(c->rhs, (long long)D * g.ncell);
+  A(c->Gp, (long long)D * g.ncell);
+  A(c->Lu, (long long)D * g.ncell);
+  A(c->p, g.nnode);
+  A(c->nrhs, g.nnode);
+  A(c->eta, g.ncell);
+  A(c->phi_mac, g.ncell);
+  A(c->mrhs, g.ncell);
+  A(c->slopes, (long long)D * D * g.ncell);
+  A(c->hats, (long long)D * D * g.ncell);
+  for (int a = 0; a < D; ++a) {
+    A(c->uL[a], (long long)D * g.nface[a]);
+    A(c->uR[a], (long long)D * g.nface[a]);
+    A(c->uadv[a], g.nface[a]);
+    A(c->umac[a], g.nface[a]);
+  }
+  A(c->partial, kRedBlocks);
+  A(c->dres, 8);
+  if (cudaMallocHost((void**)&c->hres, 8 * sizeof(double)) != cudaSuccess)
+    return fail(c, HBF_ERR_OOM, "cudaMallocHost");
+  // multigrid hierarchy
+  Geom gl = g;
+  for (int l = 0;; ++l) {
+    Level L;
+    L.g = gl;
+    if (l > 0) {
+      A(L.vx, (long long)D * gl.ncell);
+      A(L.cx, gl.ncell);
+      A(L.nx, gl.nnode);
+    }
+    A(L.vb, (long long)D * gl.ncell);
+    A(L.vr, (long long)D * gl.ncell);
+    A(L.cb, gl.ncell);
+    A(L.cr, gl.ncell);
+    A(L.nb, gl.nnode);
+    A(L.nr, gl.nnode);
+    for (int a = 0; a < D; ++a) A(L.ef[a], gl.nface[a]);
+    c->lv.push_back(L);
+    if (!can_coarsen(gl, D)) break;
+    gl = D == 3 ? coarse_of<3>(gl) : coarse_of<2>(gl);
+  }
+#undef A
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "allocation");
+}
+
+struct FieldView {
+  double* ptr[3];
+  long long cnt[3];
+  int parts;
+};
+
+static int field_view(hbf_ctx* c, int which, FieldView* v) {
+  const Geom& g = c->g;
+  const int D = c->dim;
+  v->parts = 1;
+  switch (which) {
+    case HBF_U: v->ptr[0] = c->u; v->cnt[0] = (long long)D * g.ncell; return 0;
+    case HBF_P: v->ptr[0] = c->p; v->cnt[0] = g.nnode; return 0;
+    case HBF_ETA: v->ptr[0] = c->eta; v->cnt[0] = g.ncell; return 0;
+    case HBF_USTAR: v->ptr[0] = c->ustar; v->cnt[0] = (long long)D * g.ncell; return 0;
+    case HBF_RHS: v->ptr[0] = c->rhs; v->cnt[0] = (long long)D * g.ncell; return 0;
+    case HBF_PHI_MAC: v->ptr[0] = c->phi_mac; v->cnt[0] = g.ncell; return 0;
+    case HBF_GP: v->ptr[0] = c->Gp; v->cnt[0] = (long long)D * g.ncell; return 0;
+    case HBF_LU: v->ptr[0] = c->Lu; v->cnt[0] = (long long)D * g.ncell; return 0;
+    case HBF_UADV:
+    case HBF_UMAC:
+    case HBF_UL:
+    case HBF_UR:
+      v->parts = D;
+      for (int a = 0; a < D; ++a) {
+        double* src = which == HBF_UADV ? c->uadv[a] : which == HBF_UMAC ? c->umac[a]
+                      : which == HBF_UL ? c->uL[a] : c->uR[a];
+        v->ptr[a] = src;
+        v->cnt[a] = (which == HBF_UL || which == HBF_UR) ? (long long)D * g.nface[a] : g.nface[a];
+      }
+      return 0;
+  }
+  return -1;
+}
+
+}  // namespace hb
+
+using namespace hb;
+
+extern "C" {
+
+int hbf_init_grid(hbf_ctx** out, int dim, const int64_t n[3], double h, const double wall_u[18], int precision,
+                  void* stream) {
+  if (!out) return HBF_ERR_ARG;
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return HBF_ERR_ARG;
+  if (!(h > 0.0) || !n) return HBF_ERR_ARG;
+  if (precision != HBF_FP64 && precision != HBF_MIXED) return HBF_ERR_ARG;
+  int ni[3] = {1, 1, 1};
+  long long tot = 1;
+  for (int a = 0; a < dim; ++a) {
+    if (n[a] < 2 || n[a] > (1 << 20)) return HBF_ERR_ARG;
+    ni[a] = (int)n[a];
+    tot *= (n[a] + 1);
+  }
+  if (tot * dim >= (1LL << 31)) return HBF_ERR_ARG;
+  hbf_ctx* c = new (std::nothrow) hbf_ctx();
+  if (!c) return HBF_ERR_OOM;
+  c->dim = dim;
+  c->precision = precision;
+  c->stream = (cudaStream_t)stream;
+  c->g = make_geom(dim, ni, h);
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 2; ++s)
+      for (int q = 0; q < 3; ++q) c->g.wu[a][s][q] = 0.0;
+  if (wall_u) {
+    for (int a = 0; a < dim; ++a)
+      for (int s = 0; s < 2; ++s)
+        for (int q = 0; q < dim; ++q) c->g.wu[a][s][q] = wall_u[(a * 2 + s) * 3 + q];
+    for (int a = 0; a < dim; ++a)
+      if (c->g.wu[a][0][a] != 0.0 || c->g.wu[a][1][a] != 0.0) {
+        delete c;
+        return HBF_ERR_ARG;
+      }
+  }
+  c->rheo.c2 = 1.0;
+  c->rheo.n = 1.0;
+  c->rheo.tau = 0.0;
+  c->rheo.m = 1e4;
+  c->rheo.reg_power = 1;
+  int st = allocate(c);
+  if (st) {
+    hbf_destroy(c);
+    return st;
+  }
+  *out = c;
+  return HBF_OK;
+}
+
+void hbf_destroy(hbf_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->hres) cudaFreeHost(c->hres);
+  delete c;
+}
+
+const char* hbf_last_error(const hbf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int hbf_sync(hbf_ctx* c) {
+  if (!c) return HBF_ERR_ARG;
+  return cuda_check(c, cudaStreamSynchronize(c->stream), "hbf_sync");
+}
+
+int hbf_set_rheology(hbf_ctx* c, double K, double n, double tau_y, double m, int reg_power) {
+  if (!c) return HBF_ERR_ARG;
+  if (!(K >= 0.0) || !(n > 0.0) || !(tau_y >= 0.0) || !(m > 0.0)) return fail(c, HBF_ERR_ARG, "bad rheology");
+  if (!reg_power && n < 1.0) return fail(c, HBF_ERR_ARG, "reg_power = 0 needs n >= 1 (eta bounded at g = 0)");
+  c->rheo.c2 = std::pow(2.0, n - 1.0) * K;
+  c->rheo.n = n;
+  c->rheo.tau = tau_y;
+  c->rheo.m = m;
+  c->rheo.reg_power = reg_power ? 1 : 0;
+  return HBF_OK;
+}
+
+int hbf_set_density(hbf_ctx* c, double rho) {
+  if (!c) return HBF_ERR_ARG;
+  if (!(rho > 0.0)) return fail(c, HBF_ERR_ARG, "rho must be positive");
+  c->rho = rho;
+  return HBF_OK;
+}
+
+int hbf_set_body_force(hbf_ctx* c, const double f[3]) {
+  if (!c || !f) return HBF_ERR_ARG;
+  for (int a = 0; a < 3; ++a) c->f[a] = a < c->dim ? f[a] : 0.0;
+  return HBF_OK;
+}
+
+int hbf_set_predictor_viscous(hbf_ctx* c, int on) {
+  if (!c) return HBF_ERR_ARG;
+  c->predictor_visc = on ? 1 : 0;
+  return HBF_OK;
+}
+
+int hbf_set_solver(hbf_ctx* c, double rtol, int max_cycles, int nu1, int nu2, int nu_bottom) {
+  if (!c) return HBF_ERR_ARG;
+  if (!(rtol > 0.0) || max_cycles < 1 || nu1 < 0 || nu2 < 0 || nu_bottom < 1)
+    return fail(c, HBF_ERR_ARG, "bad solver settings");
+  c->cfg.rtol = rtol;
+  c->cfg.max_cycles = max_cycles;
+  c->cfg.nu1 = nu1;
+  c->cfg.nu2 = nu2;
+  c->cfg.nu_bottom = nu_bottom;
+  return HBF_OK;
+}
+
+int64_t hbf_field_size(const hbf_ctx* c, int which) {
+  if (!c) return HBF_ERR_ARG;
+  FieldView v;
+  if (field_view(const_cast<hbf_ctx*>(c), which, &v)) return HBF_ERR_ARG;
+  int64_t s = 0;
+  for (int q = 0; q < v.parts; ++q) s += v.cnt[q];
+  return s;
+}
+
+static int copy_field(hbf_ctx* c, int which, double* host_or_dev, bool in) {
+  if (!c || !host_or_dev) return HBF_ERR_ARG;
+  FieldView v;
+  if (field_view(c, which, &v)) return fail(c, HBF_ERR_ARG, "unknown field");
+  long long off = 0;
+  for (int q = 0; q < v.parts; ++q) {
+    size_t bytes = (size_t)v.cnt[q] * sizeof(double);
+    cudaError_t e = in ? cudaMemcpyAsync(v.ptr[q], host_or_dev + off, bytes, cudaMemcpyDefault, c->stream)
+                       : cudaMemcpyAsync(host_or_dev + off, v.ptr[q], bytes, cudaMemcpyDefault, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "field copy");
+    off += v.cnt[q];
+  }
+  return HBF_OK;
+}
+
+int hbf_set_field(hbf_ctx* c, int which, const double* src) {
+  return copy_field(c, which, const_cast<double*>(src), true);
+}
+
+int hbf_get_field(hbf_ctx* c, int which, double* dst) { return copy_field(c, which, dst, false); }
+
+int hbf_compute_viscosity(hbf_ctx* c) {
+  if (!c) return HBF_ERR_ARG;
+  return launch_eta(c);
+}
+
+int hbf_predict(hbf_ctx* c, double dt) {
+  if (!c) return HBF_ERR_ARG;
+  if (!(dt > 0.0)) return fail(c, HBF_ERR_ARG, "dt must be positive");
+  return launch_predict(c, dt);
+}
+
+int hbf_mac_project(hbf_ctx* c, hbf_solve_stats* s) {
+  if (!c) return HBF_ERR_ARG;
+  int st = launch_mac_rhs(c, c->mrhs);
+  if (st) return st;
+  if ((st = cuda_check(c, cudaMemsetAsync(c->phi_mac, 0, (size_t)c->g.ncell * sizeof(double), c->stream),
+                       "memset phi")))
+    return st;
+  int sst = solve_mac(c, c->mrhs, c->phi_mac, s);
+  if (sst && sst != HBF_ERR_NOT_CONVERGED) return sst;
+  st = launch_mac_correct(c, c->phi_mac);
+  return st ? st : sst;
+}
+
+int hbf_advect_rhs(hbf_ctx* c, double dt) {
+  if (!c) return HBF_ERR_ARG;
+  if (!(dt > 0.0)) return fail(c, HBF_ERR_ARG, "dt must be positive");
+  return launch_advect_rhs(c, dt);
+}
+
+int hbf_solve_viscous(hbf_ctx* c, double dt, const double* rhs_dev, double* u_dev, hbf_solve_stats* s) {
+  if (!c || !rhs_dev || !u_dev) return HBF_ERR_ARG;
+  if (!(dt > 0.0)) return fail(c, HBF_ERR_ARG, "dt must be positive");
+  return solve_viscous(c, dt / (2.0 * c->rho), rhs_dev, u_dev, s);
+}
+
+int hbf_project(hbf_ctx* c, double dt, double* u_dev, double* p_dev, hbf_solve_stats* s) {
+  if (!c || !u_dev || !p_dev) return HBF_ERR_ARG;
+  if (!(dt > 0.0)) return fail(c, HBF_ERR_ARG, "dt must be positive");
+  int st = launch_nodal_rhs(c, dt, u_dev, p_dev, c->nrhs);
+  if (st) return st;
+  int sst = solve_nodal(c, c->nrhs, p_dev, s);
+  if (sst && sst != HBF_ERR_NOT_CONVERGED) return sst;
+  st = launch_project_update(c, dt, u_dev, nullptr, p_dev);
+  return st ? st : sst;
+}
+
+int hbf_step(hbf_ctx* c, double dt, hbf_step_stats* stats) {
+  if (!c) return HBF_ERR_ARG;
+  if (!(dt > 0.0)) return fail(c, HBF_ERR_ARG, "dt must be positive");
+  hbf_step_stats local;
+  hbf_step_stats* s = stats ? stats : &local;
+  std::memset(s, 0, sizeof *s);
+  int worst = HBF_OK;
+  int st;
+  if ((st = launch_eta(c))) return st;
+  if ((st = launch_predict(c, dt))) return st;
+  st = hbf_mac_project(c, &s->mac);
+  if (st && st != HBF_ERR_NOT_CONVERGED) return st;
+  if (st) worst = st;
+  if ((st = launch_advect_rhs(c, dt))) return st;
+  if ((st = cuda_check(c, cudaMemcpyAsync(c->ustar, c->u, (size_t)c->dim * c->g.ncell * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, c->stream),
+                       "guess copy")))
+    return st;
+  st = solve_viscous(c, dt / (2.0 * c->rho), c->rhs, c->ustar, &s->visc);
+  if (st && st != HBF_ERR_NOT_CONVERGED) return st;
+  if (st) worst = st;
+  st = hbf_project(c, dt, c->ustar, c->p, &s->nodal);
+  if (st && st != HBF_ERR_NOT_CONVERGED) return st;
+  if (st) worst = st;
+  double* t = c->u;
+  c->u = c->ustar;
+  c->ustar = t;
+  return worst;
+}
+
+double hbf_cfl_dt(hbf_ctx* c, double cfl) {
+  if (!c) return NAN;
+  int st = 0;
+  double umax = reduce_max_abs(c, c->u, (long long)c->dim * c->g.ncell, &st);
+  if (st) return NAN;
+  return cfl * c->g.h / std::fmax(umax, 1.0);
+}
+
+}  // extern "C"

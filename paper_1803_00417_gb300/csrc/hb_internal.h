@@ -1,0 +1,114 @@
+// Host-side internals shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "hb_common.cuh"
+#include "../../include/hbflow.h"
+
+namespace hb {
+
+struct Level {
+  Geom g;
+  // viscous solve (d components each)
+  double* vx = nullptr;
+  double* vb = nullptr;
+  double* vr = nullptr;
+  double* ef[3] = {nullptr, nullptr, nullptr};  // face eta
+  // cell Poisson (MAC)
+  double* cx = nullptr;
+  double* cb = nullptr;
+  double* cr = nullptr;
+  // nodal Poisson
+  double* nx = nullptr;
+  double* nb = nullptr;
+  double* nr = nullptr;
+  // FP32 copies for the mixed-precision V-cycles
+  float* fvx = nullptr;
+  float* fvb = nullptr;
+  float* fvr = nullptr;
+  float* fef[3] = {nullptr, nullptr, nullptr};
+  float* fcx = nullptr;
+  float* fcb = nullptr;
+  float* fcr = nullptr;
+  float* fnx = nullptr;
+  float* fnb = nullptr;
+  float* fnr = nullptr;
+};
+
+struct SolverCfg {
+  double rtol = 1e-10;
+  int max_cycles = 200;
+  int nu1 = 2, nu2 = 2, nu_bottom = 40;
+};
+
+}  // namespace hb
+
+struct hbf_ctx {
+  int dim = 2;
+  int precision = 0;
+  cudaStream_t stream = nullptr;
+  hb::Geom g;
+  hb::Rheo rheo;
+  double rho = 1.0;
+  double f[3] = {0, 0, 0};
+  int predictor_visc = 0;
+  hb::SolverCfg cfg;
+  std::string err;
+
+  // fields (device)
+  double* u = nullptr;      // d*ncell
+  double* p = nullptr;      // nnode
+  double* eta = nullptr;    // ncell
+  double* ustar = nullptr;  // d*ncell
+  double* rhs = nullptr;    // d*ncell
+  double* Gp = nullptr;     // d*ncell
+  double* Lu = nullptr;     // d*ncell
+  double* slopes = nullptr; // d*d*ncell  [a][c]
+  double* hats = nullptr;   // d*d*ncell  [b][c]
+  double* uL[3] = {nullptr, nullptr, nullptr};   // per axis: d*nface[a]
+  double* uR[3] = {nullptr, nullptr, nullptr};
+  double* uadv[3] = {nullptr, nullptr, nullptr}; // per axis: nface[a]
+  double* umac[3] = {nullptr, nullptr, nullptr};
+  double* phi_mac = nullptr;  // ncell
+  double* mrhs = nullptr;     // ncell, MAC right-hand side
+  double* nrhs = nullptr;     // nnode
+  // reductions
+  double* partial = nullptr;  // kRedBlocks doubles
+  double* dres = nullptr;     // device result slot(s)
+  double* hres = nullptr;     // pinned host result
+  std::vector<hb::Level> lv;
+  std::vector<void*> allocs;
+};
+
+namespace hb {
+
+constexpr int kRedBlocks = 1024;
+
+// error helpers
+int fail(hbf_ctx* c, int code, const std::string& msg);
+int cuda_check(hbf_ctx* c, cudaError_t e, const char* what);
+
+// explicit stages (hb_explicit.cu)
+int launch_eta(hbf_ctx* c);
+int launch_predict(hbf_ctx* c, double dt);
+int launch_mac_rhs(hbf_ctx* c, double* rhs);
+int launch_mac_correct(hbf_ctx* c, const double* phi);
+int launch_advect_rhs(hbf_ctx* c, double dt);
+int launch_nodal_rhs(hbf_ctx* c, double dt, const double* ustar, const double* p, double* out);
+int launch_project_update(hbf_ctx* c, double dt, double* u, const double* p_old,
+                          const double* phi);
+int launch_eta_faces(hbf_ctx* c);
+
+// reductions (hb_mg.cu)
+double reduce_max_abs(hbf_ctx* c, const double* x, long long n, int* st);
+double reduce_sum(hbf_ctx* c, const double* x, long long n, int* st);
+
+// solves (hb_mg.cu)
+int solve_mac(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
+int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s);
+int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
+
+}  // namespace hb

@@ -1,0 +1,551 @@
+// Multigrid kernels for the three solves of the step, templated on the space
+// dimension D and the arithmetic type T (double for the FP64 path, float for
+// the FP32 V-cycles of the mixed-precision defect correction).
+//
+//  * tensor viscous: (I - beta L_eta) u = b, red-black Gauss-Seidel on one
+//    component at a time with the other components frozen in the cross terms
+//  * cell Poisson (MAC potential): red-black Gauss-Seidel, Neumann walls
+//  * nodal FE Poisson: 2^D-colour Gauss-Seidel (the 3^D stencil couples
+//    diagonal neighbours), Neumann walls by even reflection
+//  * transfers: cell averaging / cell-centred multilinear interpolation,
+//    full weighting / multilinear interpolation on nodes, coarse face eta as
+//    the mean of the fine faces tiling each coarse face
+#pragma once
+#include "hb_common.cuh"
+
+namespace hb {
+
+// ---------------------------------------------------------------------------
+// tensor viscous operator pieces (mirrors the explicit-stage operator)
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
+                                  bool hom) {
+  if (L[a] < 0 || L[a] >= g.n[a] - 1) return T(0);
+  T two_h = T(2) * T(g.h);
+  int p1[3] = {L[0], L[1], L[2]}, p0[3] = {L[0], L[1], L[2]};
+  p1[c] += 1;
+  p0[c] -= 1;
+  T dL = (uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom)) / two_h;
+  p1[a] += 1;
+  p0[a] += 1;
+  T dR = (uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom)) / two_h;
+  return T(0.5) * (dL + dR);
+}
+
+template <int D, typename T>
+__device__ inline T mg_tensor_point(const T* __restrict__ u, const T* const* ef, const Geom& g, int c,
+                                    const int* p, bool hom) {
+  const T* uc = u + (size_t)c * g.ncell;
+  T acc = T(0);
+  T h = T(g.h);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    T flux[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      int L[3] = {p[0], p[1], p[2]};
+      L[a] += s - 1;
+      int R[3] = {L[0], L[1], L[2]};
+      R[a] += 1;
+      T e = ef[a][fidx(g, a, R[0], R[1], R[2])];
+      T nrm = (uget<D>(uc, g, c, R[0], R[1], R[2], hom) - uget<D>(uc, g, c, L[0], L[1], L[2], hom)) / h;
+      if (a == c)
+        flux[s] = e * (T(2) * nrm);
+      else
+        flux[s] = e * (nrm + mg_face_cross<D, T>(u + (size_t)a * g.ncell, g, a, c, L, hom));
+    }
+    acc += (flux[1] - flux[0]) / h;
+  }
+  return acc;
+}
+
+// Gauss-Seidel update of component c at cell p (all other values frozen)
+template <int D, typename T>
+__device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
+                                  const Geom& g, int c, const int* p, T beta, bool hom) {
+  const T* uc = u + (size_t)c * g.ncell;
+  T h = T(g.h);
+  T hh = h * h;
+  T offd = T(0), diag = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    T kappa = (a == c) ? T(2) : T(1);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      int q[3] = {p[0], p[1], p[2]};
+      int fq[3] = {p[0], p[1], p[2]};
+      if (s == 0) {
+        q[a] -= 1;
+      } else {
+        q[a] += 1;
+        fq[a] += 1;
+      }
+      T wf = kappa * ef[a][fidx(g, a, fq[0], fq[1], fq[2])] / hh;
+      bool wall = (s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1);
+      if (wall) {
+        T ub = hom ? T(0) : T(g.wu[a][s][c]);
+        offd += T(2) * wf * ub;
+        diag += T(2) * wf;
+      } else {
+        offd += wf * uc[cidx<D>(g, q[0], q[1], q[2])];
+        diag += wf;
+      }
+    }
+  }
+  T cross = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (a == c) continue;
+    const T* ua = u + (size_t)a * g.ncell;
+    int Llo[3] = {p[0], p[1], p[2]};
+    Llo[a] -= 1;
+    int fhi[3] = {p[0], p[1], p[2]};
+    fhi[a] += 1;
+    T fluxhi = ef[a][fidx(g, a, fhi[0], fhi[1], fhi[2])] * mg_face_cross<D, T>(ua, g, a, c, p, hom);
+    T fluxlo = ef[a][fidx(g, a, p[0], p[1], p[2])] * mg_face_cross<D, T>(ua, g, a, c, Llo, hom);
+    cross += (fluxhi - fluxlo) / h;
+  }
+  return (b[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] + beta * (offd + cross)) /
+         (T(1) + beta * diag);
+}
+
+// thread t -> cell of red-black colour col (x index stride 2)
+template <int D>
+__device__ inline bool rb_cell(const Geom& g, int t, int col, int* p) {
+  int nxh = (g.n[0] + 1) / 2;
+  int ih = t % nxh;
+  int r = t / nxh;
+  int j, k;
+  if (D == 3) {
+    j = r % g.n[1];
+    k = r / g.n[1];
+  } else {
+    j = r;
+    k = 0;
+  }
+  int i = 2 * ih + ((j + k + col) & 1);
+  p[0] = i;
+  p[1] = j;
+  p[2] = k;
+  return i < g.n[0];
+}
+
+template <int D>
+__host__ __device__ inline int rb_count(const Geom& g) {
+  return ((g.n[0] + 1) / 2) * g.n[1] * (D == 3 ? g.n[2] : 1);
+}
+
+template <int D, typename T>
+__global__ void k_visc_smooth(T* __restrict__ u, const T* __restrict__ b, const T* ef0, const T* ef1,
+                              const T* ef2, Geom g, int c, int col, T beta, int hom) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  int nt = rb_count<D>(g);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    int p[3];
+    if (!rb_cell<D>(g, t, col, p)) continue;
+    T v = visc_gs_point<D, T>(u, b, ef, g, c, p, beta, hom != 0);
+    u[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
+  }
+}
+
+template <int D, typename T>
+__global__ void k_visc_resid(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ r,
+                             const T* ef0, const T* ef1, const T* ef2, Geom g, T beta, int hom) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    int p[3];
+    cell_coords<D>(g, t, p[0], p[1], p[2]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      size_t o = (size_t)c * g.ncell + t;
+      T Lu = mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+      r[o] = b[o] - (u[o] - beta * Lu);
+    }
+  }
+}
+
+// coarsest level: all sweeps in one block
+template <int D, typename T>
+__global__ void k_visc_bottom(T* __restrict__ u, const T* __restrict__ b, const T* ef0, const T* ef1,
+                              const T* ef2, Geom g, T beta, int nsweep, int hom) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  int nt = rb_count<D>(g);
+  for (int sw = 0; sw < nsweep; ++sw)
+    for (int c = 0; c < D; ++c)
+      for (int col = 0; col < 2; ++col) {
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+          int p[3];
+          if (!rb_cell<D>(g, t, col, p)) continue;
+          T v = visc_gs_point<D, T>(u, b, ef, g, c, p, beta, hom != 0);
+          u[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
+        }
+        __syncthreads();
+      }
+}
+
+// ---------------------------------------------------------------------------
+// cell-centred Poisson (MAC potential), Neumann walls
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ inline T cell_gs_point(const T* __restrict__ x, const T* __restrict__ b, const Geom& g,
+                                  const int* p) {
+  T s = T(0);
+  int cnt = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    T lo = T(0), hi = T(0);
+    if (p[a] > 0) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[a] -= 1;
+      lo = x[cidx<D>(g, q[0], q[1], q[2])];
+      ++cnt;
+    }
+    if (p[a] < g.n[a] - 1) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[a] += 1;
+      hi = x[cidx<D>(g, q[0], q[1], q[2])];
+      ++cnt;
+    }
+    s += lo + hi;
+  }
+  T h = T(g.h);
+  return (s - h * h * b[cidx<D>(g, p[0], p[1], p[2])]) / T(cnt);
+}
+
+template <int D, typename T>
+__global__ void k_cell_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g, int col) {
+  int nt = rb_count<D>(g);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    int p[3];
+    if (!rb_cell<D>(g, t, col, p)) continue;
+    x[cidx<D>(g, p[0], p[1], p[2])] = cell_gs_point<D, T>(x, b, g, p);
+  }
+}
+
+template <int D, typename T>
+__global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
+  T h = T(g.h);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    int p[3];
+    cell_coords<D>(g, t, p[0], p[1], p[2]);
+    T xc = x[t];
+    T acc = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      T glo = T(0), ghi = T(0);
+      if (p[a] > 0) {
+        int q[3] = {p[0], p[1], p[2]};
+        q[a] -= 1;
+        glo = (xc - x[cidx<D>(g, q[0], q[1], q[2])]) / h;
+      }
+      if (p[a] < g.n[a] - 1) {
+        int q[3] = {p[0], p[1], p[2]};
+        q[a] += 1;
+        ghi = (x[cidx<D>(g, q[0], q[1], q[2])] - xc) / h;
+      }
+      acc += (ghi - glo) / h;
+    }
+    r[t] = b[t] - acc;
+  }
+}
+
+template <int D, typename T>
+__global__ void k_cell_bottom(T* __restrict__ x, const T* __restrict__ b, Geom g, int nsweep) {
+  int nt = rb_count<D>(g);
+  for (int sw = 0; sw < nsweep; ++sw)
+    for (int col = 0; col < 2; ++col) {
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        int p[3];
+        if (!rb_cell<D>(g, t, col, p)) continue;
+        x[cidx<D>(g, p[0], p[1], p[2])] = cell_gs_point<D, T>(x, b, g, p);
+      }
+      __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// nodal FE Poisson, Neumann walls
+// ---------------------------------------------------------------------------
+// stencil weight (times h^2) of offset o in {-1,0,1}^D
+template <int D, typename T>
+__device__ inline T fe_weight(int nz) {
+  if (nz == 0) return T(-8.0 / 3.0);
+  if (D == 2) return T(1.0 / 3.0);
+  return nz == 1 ? T(0) : (nz == 2 ? T(1.0 / 6.0) : T(1.0 / 12.0));
+}
+
+template <int D, typename T>
+__device__ inline T nodal_lap_point(const T* __restrict__ x, const Geom& g, const int* p, bool skip_centre) {
+  T s = T(0);
+  const int K = D == 3 ? 27 : 9;
+#pragma unroll
+  for (int o = 0; o < K; ++o) {
+    int oo[3];
+    if (D == 3) {
+      oo[0] = o / 9 - 1;
+      oo[1] = (o / 3) % 3 - 1;
+      oo[2] = o % 3 - 1;
+    } else {
+      oo[0] = o / 3 - 1;
+      oo[1] = o % 3 - 1;
+      oo[2] = 0;
+    }
+    int nz = (oo[0] != 0) + (oo[1] != 0) + (oo[2] != 0);
+    if (nz == 0 && skip_centre) continue;
+    if (D == 3 && nz == 1) continue;
+    T w = fe_weight<D, T>(nz);
+    s += w * ndget<D>(x, g, p[0] + oo[0], p[1] + oo[1], p[2] + oo[2]);
+  }
+  return s;
+}
+
+template <int D>
+__device__ inline bool mc_node(const Geom& g, int t, int col, int* p) {
+  int e[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
+  int cnt[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int bit = (a < D) ? ((col >> a) & 1) : 0;
+    cnt[a] = (a < D) ? (e[a] - bit + 1) / 2 : 1;
+  }
+  int i0 = t % cnt[0];
+  int r = t / cnt[0];
+  int i1 = r % cnt[1];
+  int i2 = r / cnt[1];
+  p[0] = 2 * i0 + (col & 1);
+  p[1] = 2 * i1 + ((col >> 1) & 1);
+  p[2] = D == 3 ? 2 * i2 + ((col >> 2) & 1) : 0;
+  return i2 < cnt[2];
+}
+
+template <int D>
+__host__ __device__ inline int mc_count(const Geom& g, int col) {
+  int e[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
+  int c = 1;
+  for (int a = 0; a < D; ++a) c *= (e[a] - ((col >> a) & 1) + 1) / 2;
+  return c;
+}
+
+template <int D, typename T>
+__global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g, int col) {
+  int nt = mc_count<D>(g, col);
+  T hh = T(g.h) * T(g.h);
+  T s0 = fe_weight<D, T>(0);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    int p[3];
+    if (!mc_node<D>(g, t, col, p)) continue;
+    int id = nidx(g, p[0], p[1], p[2]);
+    T s = nodal_lap_point<D, T>(x, g, p, true);
+    x[id] = (hh * b[id] - s) / s0;
+  }
+}
+
+template <int D, typename T>
+__global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
+  int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
+  T hh = T(g.h) * T(g.h);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
+    int p[3];
+    p[0] = t % e0;
+    int q = t / e0;
+    p[1] = q % e1;
+    p[2] = q / e1;
+    r[t] = b[t] - nodal_lap_point<D, T>(x, g, p, false) / hh;
+  }
+}
+
+template <int D, typename T>
+__global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom g, int nsweep) {
+  T hh = T(g.h) * T(g.h);
+  T s0 = fe_weight<D, T>(0);
+  const int ncol = 1 << D;
+  for (int sw = 0; sw < nsweep; ++sw)
+    for (int col = 0; col < ncol; ++col) {
+      int nt = mc_count<D>(g, col);
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        int p[3];
+        if (!mc_node<D>(g, t, col, p)) continue;
+        int id = nidx(g, p[0], p[1], p[2]);
+        T s = nodal_lap_point<D, T>(x, g, p, true);
+        x[id] = (hh * b[id] - s) / s0;
+      }
+      __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// transfers
+// ---------------------------------------------------------------------------
+// mean of the 2^D children, averaged axis by axis (x, then y, then z)
+template <int D, typename T>
+__global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, Geom gf, Geom gc, int ncomp) {
+  long long tot = (long long)gc.ncell * ncomp;
+  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
+       tt += (long long)gridDim.x * blockDim.x) {
+    int comp = (int)(tt / gc.ncell);
+    int t = (int)(tt % gc.ncell);
+    int I, J, K;
+    cell_coords<D>(gc, t, I, J, K);
+    const T* fc = f + (size_t)comp * gf.ncell;
+    T v[2][2];
+    for (int kk = 0; kk < (D == 3 ? 2 : 1); ++kk)
+      for (int jj = 0; jj < 2; ++jj) {
+        int j = 2 * J + jj, k = D == 3 ? 2 * K + kk : 0;
+        v[kk][jj] = T(0.5) * (fc[cidx<D>(gf, 2 * I, j, k)] + fc[cidx<D>(gf, 2 * I + 1, j, k)]);
+      }
+    T w0 = T(0.5) * (v[0][0] + v[0][1]);
+    T out = w0;
+    if (D == 3) {
+      T w1 = T(0.5) * (v[1][0] + v[1][1]);
+      out = T(0.5) * (w0 + w1);
+    }
+    c[(size_t)comp * gc.ncell + t] = out;
+  }
+}
+
+// coarse a-face eta: mean of the fine a-faces tiling it (pairwise, axis order)
+template <int D, typename T>
+__global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, int a, Geom gf, Geom gc) {
+  int ex[3] = {gc.n[0] + (a == 0), gc.n[1] + (a == 1), gc.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    int P[3];
+    P[0] = t % ex[0];
+    int r = t / ex[0];
+    P[1] = r % ex[1];
+    P[2] = r / ex[1];
+    // the two tangential axes in increasing order
+    int o1 = -1, o2 = -1;
+    for (int b = 0; b < D; ++b)
+      if (b != a) {
+        if (o1 < 0)
+          o1 = b;
+        else
+          o2 = b;
+      }
+    T v[2][2];
+    for (int s2 = 0; s2 < (D == 3 ? 2 : 1); ++s2)
+      for (int s1 = 0; s1 < 2; ++s1) {
+        int q[3] = {2 * P[0], 2 * P[1], D == 3 ? 2 * P[2] : 0};
+        q[o1] += s1;
+        if (D == 3) q[o2] += s2;
+        v[s2][s1] = ff[fidx(gf, a, q[0], q[1], q[2])];
+      }
+    T w0 = T(0.5) * (v[0][0] + v[0][1]);
+    T out = w0;
+    if (D == 3) {
+      T w1 = T(0.5) * (v[1][0] + v[1][1]);
+      out = T(0.5) * (w0 + w1);
+    }
+    fc[t] = out;
+  }
+}
+
+// coarse cell value with ghost by reflection: sign -1 (Dirichlet error), +1 (Neumann)
+template <int D, typename T>
+__device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, int i, int j, int k, T sign) {
+  T s = T(1);
+  if (i < 0) { i = 0; s *= sign; }
+  if (i >= g.n[0]) { i = g.n[0] - 1; s *= sign; }
+  if (j < 0) { j = 0; s *= sign; }
+  if (j >= g.n[1]) { j = g.n[1] - 1; s *= sign; }
+  if (D == 3) {
+    if (k < 0) { k = 0; s *= sign; }
+    if (k >= g.n[2]) { k = g.n[2] - 1; s *= sign; }
+  }
+  return s * e[cidx<D>(g, i, j, k)];
+}
+
+// x_f += P e_c, cell-centred multilinear (3/4, 1/4 per axis), axis by axis
+template <int D, typename T>
+__global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc,
+                                    int ncomp, T sign) {
+  long long tot = (long long)gf.ncell * ncomp;
+  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
+       tt += (long long)gridDim.x * blockDim.x) {
+    int comp = (int)(tt / gf.ncell);
+    int t = (int)(tt % gf.ncell);
+    int i, j, k;
+    cell_coords<D>(gf, t, i, j, k);
+    const T* e = ec + (size_t)comp * gc.ncell;
+    int I = i >> 1, J = j >> 1, K = k >> 1;
+    int In = (i & 1) ? I + 1 : I - 1;
+    int Jn = (j & 1) ? J + 1 : J - 1;
+    int Kn = (k & 1) ? K + 1 : K - 1;
+    T tz[2];
+    for (int kk = 0; kk < (D == 3 ? 2 : 1); ++kk) {
+      int kc = kk ? Kn : K;
+      T ty[2];
+      for (int jj = 0; jj < 2; ++jj) {
+        int jc = jj ? Jn : J;
+        ty[jj] = T(0.75) * cget_refl<D>(e, gc, I, jc, kc, sign) + T(0.25) * cget_refl<D>(e, gc, In, jc, kc, sign);
+      }
+      tz[kk] = T(0.75) * ty[0] + T(0.25) * ty[1];
+    }
+    T v = D == 3 ? T(0.75) * tz[0] + T(0.25) * tz[1] : tz[0];
+    xf[(size_t)comp * gf.ncell + t] += v;
+  }
+}
+
+// full weighting onto coarse nodes (even reflection), axis by axis
+template <int D, typename T>
+__global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, Geom gf, Geom gc) {
+  int e0 = gc.n[0] + 1, e1 = gc.n[1] + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gc.nnode; t += gridDim.x * blockDim.x) {
+    int I = t % e0;
+    int q = t / e0;
+    int J = q % e1;
+    int K = q / e1;
+    T zr[3];
+    for (int kk = 0; kk < (D == 3 ? 3 : 1); ++kk) {
+      int k = D == 3 ? 2 * K + kk - 1 : 0;
+      T yr[3];
+      for (int jj = 0; jj < 3; ++jj) {
+        int j = 2 * J + jj - 1;
+        T cen = ndget<D>(rf, gf, 2 * I, j, k);
+        T lo = ndget<D>(rf, gf, 2 * I - 1, j, k);
+        T hi = ndget<D>(rf, gf, 2 * I + 1, j, k);
+        yr[jj] = T(0.5) * cen + T(0.25) * (lo + hi);
+      }
+      zr[kk] = T(0.5) * yr[1] + T(0.25) * (yr[0] + yr[2]);
+    }
+    rc[t] = D == 3 ? T(0.5) * zr[1] + T(0.25) * (zr[0] + zr[2]) : zr[0];
+  }
+}
+
+// x_f += P e_c, nodal multilinear, axis by axis
+template <int D, typename T>
+__global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc) {
+  int e0 = gf.n[0] + 1, e1 = gf.n[1] + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gf.nnode; t += gridDim.x * blockDim.x) {
+    int i = t % e0;
+    int q = t / e0;
+    int j = q % e1;
+    int k = q / e1;
+    int I = i >> 1, J = j >> 1, K = k >> 1;
+    T tz[2];
+    for (int kk = 0; kk < (D == 3 ? 2 : 1); ++kk) {
+      int kc = K + kk;
+      if (D == 3 && kk == 1 && !(k & 1)) {
+        tz[1] = T(0);
+        continue;
+      }
+      T ty[2];
+      for (int jj = 0; jj < 2; ++jj) {
+        int jc = J + jj;
+        if (jj == 1 && !(j & 1)) {
+          ty[1] = T(0);
+          continue;
+        }
+        T a0 = ec[nidx(gc, I, jc, D == 3 ? kc : 0)];
+        ty[jj] = (i & 1) ? T(0.5) * (a0 + ec[nidx(gc, I + 1, jc, D == 3 ? kc : 0)]) : a0;
+      }
+      tz[kk] = (j & 1) ? T(0.5) * (ty[0] + ty[1]) : ty[0];
+    }
+    T v = (D == 3 && (k & 1)) ? T(0.5) * (tz[0] + tz[1]) : tz[0];
+    xf[t] += v;
+  }
+}
+
+}  // namespace hb

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of the hbflow C-ABI (include/hbflow.h).
+
+Argument marshalling only: every stage of the step runs in the CUDA library.
+Device memory and streams come from PyTorch.  The library must have been built
+(``paper_1803_00417_gb300.build.build()``); there is no CPU fallback and
+loading fails loudly without it.
+
+Array layout helpers convert between the x-fastest, component-major device
+layout and numpy arrays indexed ``[i, j(, k)]`` (axis a = direction a).
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhbflow.so")
+
+HBF_OK = 0
+HBF_ERR_NOT_CONVERGED = -4
+FIELDS = dict(U=0, P=1, ETA=2, USTAR=3, UADV=4, UMAC=5, RHS=6, PHI_MAC=7, GP=8, LU=9, UL=10, UR=11)
+FP64, MIXED = 0, 1
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("converged", ctypes.c_int), ("r0", ctypes.c_double),
+                ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(cycles=self.cycles, converged=bool(self.converged), r0=self.r0, rnorm=self.rnorm,
+                    bnorm=self.bnorm)
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("mac", SolveStats), ("visc", SolveStats), ("nodal", SolveStats)]
+
+    def as_dict(self):
+        return dict(mac=self.mac.as_dict(), visc=self.visc.as_dict(), nodal=self.nodal.as_dict())
+
+
+_lib = None
+
+SIGNATURES = {
+    "hbf_init_grid": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]),
+    "hbf_set_rheology": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int]),
+    "hbf_set_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "hbf_set_body_force": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "hbf_set_predictor_viscous": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hbf_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int]),
+    "hbf_field_size": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
+    "hbf_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "hbf_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "hbf_compute_viscosity": (ctypes.c_int, [ctypes.c_void_p]),
+    "hbf_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "hbf_mac_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SolveStats)]),
+    "hbf_advect_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "hbf_solve_viscous": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(SolveStats)]),
+    "hbf_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(SolveStats)]),
+    "hbf_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(StepStats)]),
+    "hbf_cfl_dt": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_double]),
+    "hbf_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "hbf_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "hbf_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def load(path=LIB_PATH):
+    """Load the shared library and declare every exported signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"hbflow CUDA library not built ({path}); run paper_1803_00417_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class HBFlowError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hbflow error {code}: {msg}")
+        self.code = code
+
+
+def to_device_layout(arrs):
+    """List of numpy arrays indexed [i, j(, k)] -> flat x-fastest array."""
+    if isinstance(arrs, np.ndarray):
+        arrs = [arrs]
+    return np.concatenate([np.ascontiguousarray(np.asarray(a, dtype=np.float64).T).ravel() for a in arrs])
+
+
+def from_device_layout(flat, shape, ncomp):
+    """Flat x-fastest array -> list of ``ncomp`` numpy arrays of ``shape``."""
+    n = int(np.prod(shape))
+    return [np.ascontiguousarray(flat[c * n:(c + 1) * n].reshape(shape[::-1]).T) for c in range(ncomp)]
+
+
+def _ptr(x):
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags.c_contiguous
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(int(x))
+
+
+class HBFlow:
+    """One context of the library: a box of ``n`` cells of size ``h`` with wall
+    velocities ``wall_u[a][s][c]`` (all faces are no-slip walls)."""
+
+    def __init__(self, n, h, wall_u=None, precision=FP64, stream=None):
+        self.lib = load()
+        self.n = tuple(int(v) for v in n)
+        self.d = len(self.n)
+        self.h = float(h)
+        nn = (ctypes.c_int64 * 3)(*(list(self.n) + [1] * (3 - self.d)))
+        wu = np.zeros((3, 2, 3))
+        if wall_u is not None:
+            w = np.asarray(wall_u, dtype=np.float64).reshape(self.d, 2, self.d)
+            wu[:self.d, :, :self.d] = w
+        wuc = (ctypes.c_double * 18)(*wu.ravel())
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._stream = stream
+        ctx = ctypes.c_void_p()
+        st = self.lib.hbf_init_grid(ctypes.byref(ctx), self.d, nn, self.h, wuc, int(precision),
+                                    ctypes.c_void_p(stream))
+        if st != HBF_OK:
+            raise HBFlowError(st, "hbf_init_grid failed")
+        self.ctx = ctx
+        self.ncell = int(np.prod(self.n))
+        self.node_shape = tuple(v + 1 for v in self.n)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.hbf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow_nc=False):
+        if st == HBF_OK or (allow_nc and st == HBF_ERR_NOT_CONVERGED):
+            return st
+        raise HBFlowError(st, self.lib.hbf_last_error(self.ctx).decode())
+
+    # ---- configuration ------------------------------------------------------------
+    def set_rheology(self, K, n, tau_y, m, reg_power=True):
+        self._check(self.lib.hbf_set_rheology(self.ctx, K, n, tau_y, m, int(bool(reg_power))))
+
+    def set_density(self, rho):
+        self._check(self.lib.hbf_set_density(self.ctx, rho))
+
+    def set_body_force(self, f):
+        ff = (ctypes.c_double * 3)(*(list(f) + [0.0] * (3 - len(f))))
+        self._check(self.lib.hbf_set_body_force(self.ctx, ff))
+
+    def set_predictor_viscous(self, on):
+        self._check(self.lib.hbf_set_predictor_viscous(self.ctx, int(bool(on))))
+
+    def set_solver(self, rtol=1e-10, max_cycles=200, nu1=2, nu2=2, nu_bottom=40):
+        self._check(self.lib.hbf_set_solver(self.ctx, rtol, max_cycles, nu1, nu2, nu_bottom))
+
+    # ---- fields -------------------------------------------------------------------
+    def field_size(self, which):
+        return int(self.lib.hbf_field_size(self.ctx, FIELDS[which]))
+
+    def set_field(self, which, src):
+        """src: flat float64 numpy array (host) or torch CUDA tensor (device)."""
+        self._check(self.lib.hbf_set_field(self.ctx, FIELDS[which], _ptr(src)))
+        self.sync()
+
+    def get_field(self, which, dst=None):
+        if dst is None:
+            dst = np.empty(self.field_size(which), dtype=np.float64)
+        self._check(self.lib.hbf_get_field(self.ctx, FIELDS[which], _ptr(dst)))
+        self.sync()
+        return dst
+
+    def set_velocity(self, u):
+        self.set_field("U", to_device_layout(u))
+
+    def set_pressure(self, p):
+        self.set_field("P", to_device_layout(p))
+
+    def velocity(self, which="U"):
+        return from_device_layout(self.get_field(which), self.n, self.d)
+
+    def pressure(self):
+        return from_device_layout(self.get_field("P"), self.node_shape, 1)[0]
+
+    def cell_scalar(self, which):
+        return from_device_layout(self.get_field(which), self.n, 1)[0]
+
+    def face_field(self, which, ncomp):
+        """Face arrays per axis a (list over a of lists over components)."""
+        flat = self.get_field(which)
+        out, off = [], 0
+        for a in range(self.d):
+            shape = tuple(self.n[b] + (1 if b == a else 0) for b in range(self.d))
+            cnt = int(np.prod(shape)) * ncomp
+            out.append(from_device_layout(flat[off:off + cnt], shape, ncomp))
+            off += cnt
+        return out
+
+    # ---- stages -------------------------------------------------------------------
+    def compute_viscosity(self):
+        self._check(self.lib.hbf_compute_viscosity(self.ctx))
+
+    def predict(self, dt):
+        self._check(self.lib.hbf_predict(self.ctx, dt))
+
+    def mac_project(self):
+        s = SolveStats()
+        self._check(self.lib.hbf_mac_project(self.ctx, ctypes.byref(s)), allow_nc=True)
+        return s.as_dict()
+
+    def advect_rhs(self, dt):
+        self._check(self.lib.hbf_advect_rhs(self.ctx, dt))
+
+    def solve_viscous(self, dt, rhs_dev, u_dev):
+        s = SolveStats()
+        self._check(self.lib.hbf_solve_viscous(self.ctx, dt, _ptr(rhs_dev), _ptr(u_dev), ctypes.byref(s)),
+                    allow_nc=True)
+        return s.as_dict()
+
+    def project(self, dt, u_dev, p_dev):
+        s = SolveStats()
+        self._check(self.lib.hbf_project(self.ctx, dt, _ptr(u_dev), _ptr(p_dev), ctypes.byref(s)), allow_nc=True)
+        return s.as_dict()
+
+    def step(self, dt):
+        s = StepStats()
+        self._check(self.lib.hbf_step(self.ctx, dt, ctypes.byref(s)), allow_nc=True)
+        return s.as_dict()
+
+    def cfl_dt(self, cfl):
+        return float(self.lib.hbf_cfl_dt(self.ctx, cfl))
+
+    def sync(self):
+        self._check(self.lib.hbf_sync(self.ctx))

@@ -1,0 +1,159 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle on the
+same seeded inputs, stage by stage and for whole steps.
+
+Tolerance: relative L2 <= 1e-10 per step (FP64 path).  Stages without an
+iterative solve agree to rounding (<= 1e-12)."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle.grid import Grid  # noqa: E402
+from oracle.multigrid import SolverParams  # noqa: E402
+from oracle.step import Rheology, step  # noqa: E402
+from paper_1803_00417_gb300.inputs import cavity, random_state  # noqa: E402
+
+TOL_STEP = 1e-10
+TOL_EXPLICIT = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1803_00417_gb300 import build
+
+    build.build()
+
+
+def rel_l2(a, b):
+    a = [np.asarray(x) for x in (a if isinstance(a, (list, tuple)) else [a])]
+    b = [np.asarray(x) for x in (b if isinstance(b, (list, tuple)) else [b])]
+    num = sum(float(np.sum((x - y) ** 2)) for x, y in zip(a, b))
+    den = sum(float(np.sum(y ** 2)) for y in b)
+    return np.sqrt(num / den) if den > 0 else np.sqrt(num)
+
+
+def setup(n, seed, amp=1.0, **over):
+    from paper_1803_00417_gb300.hbflow import HBFlow
+
+    cfg = cavity(n, **over)
+    u, p = random_state(cfg["n"], seed=seed, amp=amp)
+    sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"])
+    sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+    sim.set_velocity(u)
+    sim.set_pressure(p)
+    g = Grid(cfg["n"], cfg["h"], wall_u=cfg["wall_u"])
+    rh = Rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+    return sim, g, rh, cfg, u, p
+
+
+CASES = [((40, 24), 1), ((64, 64), 2), ((18, 10), 3), ((16, 12, 10), 4), ((12, 12, 12), 5)]
+
+
+@pytest.mark.parametrize("n,seed", CASES)
+def test_stages_match_oracle(n, seed):
+    sim, g, rh, cfg, u, p = setup(n, seed, Re=1.0, Bi=2.0, Pa=1e4, nexp=1.0)
+    dt = cfg["dt"]
+    ref = step(g, u, p, dt, rh, keep=True)
+    d = g.d
+    sim.compute_viscosity()
+    assert rel_l2(sim.cell_scalar("ETA"), ref.eta) < 1e-13
+    sim.predict(dt)
+    assert rel_l2(sim.velocity("GP"), ref.Gp) < TOL_EXPLICIT
+    assert rel_l2(sim.velocity("LU"), ref.Lu) < TOL_EXPLICIT
+    uL = sim.face_field("UL", d)
+    uR = sim.face_field("UR", d)
+    for a in range(d):
+        assert rel_l2(uL[a], ref.uL[a]) < TOL_EXPLICIT
+        assert rel_l2(uR[a], ref.uR[a]) < TOL_EXPLICIT
+    uadv = sim.face_field("UADV", 1)
+    assert rel_l2([x[0] for x in uadv], ref.uadv) < TOL_EXPLICIT
+    st = sim.mac_project()
+    assert st["converged"]
+    assert st["cycles"] == ref.stats["mac"].cycles
+    assert rel_l2(sim.cell_scalar("PHI_MAC"), ref.phi_mac) < TOL_STEP
+    umac = sim.face_field("UMAC", 1)
+    assert rel_l2([x[0] for x in umac], ref.umac) < TOL_STEP
+    sim.advect_rhs(dt)
+    assert rel_l2(sim.velocity("RHS"), ref.rhs) < TOL_STEP
+    # viscous solve from the oracle's own right-hand side (isolates the solve)
+    from paper_1803_00417_gb300.hbflow import to_device_layout
+
+    rhs_d = torch.tensor(to_device_layout(ref.rhs), device="cuda")
+    u_d = torch.tensor(to_device_layout(u), device="cuda")
+    st = sim.solve_viscous(dt, rhs_d, u_d)
+    assert st["converged"]
+    from paper_1803_00417_gb300.hbflow import from_device_layout
+
+    ustar = from_device_layout(u_d.cpu().numpy(), g.n, d)
+    assert rel_l2(ustar, ref.ustar) < TOL_STEP
+    # nodal projection from the oracle's u*
+    us_d = torch.tensor(to_device_layout(ref.ustar), device="cuda")
+    p_d = torch.tensor(to_device_layout(p), device="cuda")
+    st = sim.project(dt, us_d, p_d)
+    assert st["converged"]
+    unew = from_device_layout(us_d.cpu().numpy(), g.n, d)
+    pnew = from_device_layout(p_d.cpu().numpy(), tuple(v + 1 for v in g.n), 1)[0]
+    assert rel_l2(unew, ref.u) < TOL_STEP
+    assert rel_l2(pnew, ref.p) < TOL_STEP
+    sim.close()
+
+
+@pytest.mark.parametrize("n,seed,over", [
+    ((64, 64), 11, dict(Re=1.0, Bi=2.0, Pa=1e4, nexp=1.0)),          # Bingham cavity workload
+    ((48, 32), 12, dict(Re=1000.0, Bi=5.0, Pa=1e5, nexp=0.5)),       # HB shear-thinning
+    ((16, 16, 16), 13, dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)),   # 3D HB shear-thickening
+])
+def test_full_step_matches_oracle(n, seed, over):
+    sim, g, rh, cfg, u, p = setup(n, seed, **over)
+    dt = cfg["dt"]
+    for _ in range(2):
+        ref = step(g, u, p, dt, rh)
+        stats = sim.step(dt)
+        ug, pg = sim.velocity(), sim.pressure()
+        assert stats["visc"]["cycles"] == ref.stats["visc"].cycles
+        assert rel_l2(ug, ref.u) < TOL_STEP, rel_l2(ug, ref.u)
+        assert rel_l2(pg, ref.p) < 10 * TOL_STEP
+        # next step from the oracle's state, so each step is checked on its own
+        u, p = ref.u, ref.p
+        sim.set_velocity(u)
+        sim.set_pressure(p)
+    sim.close()
+
+
+def test_start_from_rest_several_steps():
+    # the 64^2 Bingham cavity from rest: zero state, lid impulsively started
+    cfg = cavity((32, 32), Re=1.0, Bi=2.0, Pa=1e4, nexp=1.0)
+    from paper_1803_00417_gb300.hbflow import HBFlow
+
+    sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"])
+    sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+    g = Grid(cfg["n"], cfg["h"], wall_u=cfg["wall_u"])
+    rh = Rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+    u = [np.zeros(cfg["n"]) for _ in range(2)]
+    p = np.zeros(tuple(v + 1 for v in cfg["n"]))
+    sim.set_velocity(u)
+    sim.set_pressure(p)
+    for _ in range(4):
+        ref = step(g, u, p, cfg["dt"], rh)
+        sim.step(cfg["dt"])
+        assert rel_l2(sim.velocity(), ref.u) < TOL_STEP
+        u, p = ref.u, ref.p
+        sim.set_velocity(u)
+        sim.set_pressure(p)
+    sim.close()
+
+
+def test_smallest_grid_and_odd_sizes():
+    # 2x2 cells (single multigrid level) and a size that stops coarsening on an
+    # odd count (10 -> 5)
+    for n in [(2, 2), (10, 6), (4, 4, 4)]:
+        sim, g, rh, cfg, u, p = setup(n, 21, Re=10.0, Bi=1.0, Pa=1e3, nexp=1.0)
+        ref = step(g, u, p, cfg["dt"], rh)
+        sim.step(cfg["dt"])
+        assert rel_l2(sim.velocity(), ref.u) < TOL_STEP
+        sim.close()
