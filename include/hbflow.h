@@ -53,7 +53,8 @@ enum hbf_precision {
 /* Fields that can be copied in or out with hbf_set_field / hbf_get_field.
  * Sizes in doubles (hbf_field_size): U, USTAR, RHS, GP, LU: d*ncell; P: nnode;
  * ETA, PHI_MAC: ncell; UADV, UMAC: sum over axes a of nface[a] (axis-major);
- * UL, UR: sum over axes a of d*nface[a] (axis-major, then component). */
+ * UL, UR: sum over axes a of d*nface[a] (axis-major, then component);
+ * ETA_FACES: sum over axes of nface[a]; SLOPES, HATS: d*d*ncell. */
 enum hbf_field {
   HBF_U = 0,       /* cell velocity u^m (set) / u^{m+1} (after a step) */
   HBF_P = 1,       /* nodal pressure p^{m-1/2} / p^{m+1/2} */
@@ -66,7 +67,10 @@ enum hbf_field {
   HBF_GP = 8,      /* cell-centred G p^{m-1/2} */
   HBF_LU = 9,      /* div(eta^m (grad u^m + grad u^m^T)) at cells */
   HBF_UL = 10,     /* left face states (Eq. 14a) */
-  HBF_UR = 11      /* right face states (Eq. 14b) */
+  HBF_UR = 11,     /* right face states (Eq. 14b) */
+  HBF_ETA_FACES = 12, /* face eta of the finest level (axis-major) */
+  HBF_SLOPES = 13, /* limited slopes, d*d*ncell, [axis][component] */
+  HBF_HATS = 14    /* transverse terms, d*d*ncell, [axis][component] */
 };
 
 typedef struct {

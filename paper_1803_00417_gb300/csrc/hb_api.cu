@@ -128,6 +128,15 @@ static int field_view(hbf_ctx* c, int which, FieldView* v) {
     case HBF_PHI_MAC: v->ptr[0] = c->phi_mac; v->cnt[0] = g.ncell; return 0;
     case HBF_GP: v->ptr[0] = c->Gp; v->cnt[0] = (long long)D * g.ncell; return 0;
     case HBF_LU: v->ptr[0] = c->Lu; v->cnt[0] = (long long)D * g.ncell; return 0;
+    case HBF_SLOPES: v->ptr[0] = c->slopes; v->cnt[0] = (long long)D * D * g.ncell; return 0;
+    case HBF_HATS: v->ptr[0] = c->hats; v->cnt[0] = (long long)D * D * g.ncell; return 0;
+    case HBF_ETA_FACES:
+      v->parts = D;
+      for (int a = 0; a < D; ++a) {
+        v->ptr[a] = c->lv[0].ef[a];
+        v->cnt[a] = g.nface[a];
+      }
+      return 0;
     case HBF_UADV:
     case HBF_UMAC:
     case HBF_UL:

@@ -48,7 +48,7 @@ __host__ __device__ inline int fidx(const Geom& g, int a, int i, int j, int k) {
 }
 
 template <int D>
-__device__ inline void cell_coords(const Geom& g, int t, int& i, int& j, int& k) {
+__host__ __device__ inline void cell_coords(const Geom& g, int t, int& i, int& j, int& k) {
   i = t % g.n[0];
   int r = t / g.n[0];
   if (D == 3) {
@@ -64,30 +64,32 @@ __device__ inline void cell_coords(const Geom& g, int t, int& i, int& j, int& k)
 // by one or two cells: odd reflection about the wall value of that face,
 // g = 2 u_b - u_mirror (homogeneous: u_b = 0).
 template <int D, typename T>
-__device__ inline T uget(const T* __restrict__ uc, const Geom& g, int c, int i, int j, int k,
-                         bool hom) {
-  int p[3] = {i, j, k};
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if (p[a] < 0) {
-      int q[3] = {p[0], p[1], p[2]};
-      q[a] = -p[a] - 1;
-      T ub = hom ? T(0) : T(g.wu[a][0][c]);
-      return T(2) * ub - uc[cidx<D>(g, q[0], q[1], q[2])];
-    }
-    if (p[a] >= g.n[a]) {
-      int q[3] = {p[0], p[1], p[2]};
-      q[a] = 2 * g.n[a] - 1 - p[a];
-      T ub = hom ? T(0) : T(g.wu[a][1][c]);
-      return T(2) * ub - uc[cidx<D>(g, q[0], q[1], q[2])];
-    }
+__host__ __device__ inline T uget(const T* __restrict__ uc, const Geom& g, int c, int i, int j, int k,
+                                  bool hom) {
+  // the first out-of-range axis (x, then y, then z) selects the reflection
+  int ax = -1, side = 0;
+  if (i < 0) {
+    ax = 0; side = 0; i = -i - 1;
+  } else if (i >= g.n[0]) {
+    ax = 0; side = 1; i = 2 * g.n[0] - 1 - i;
+  } else if (j < 0) {
+    ax = 1; side = 0; j = -j - 1;
+  } else if (j >= g.n[1]) {
+    ax = 1; side = 1; j = 2 * g.n[1] - 1 - j;
+  } else if (D == 3 && k < 0) {
+    ax = 2; side = 0; k = -k - 1;
+  } else if (D == 3 && k >= g.n[2]) {
+    ax = 2; side = 1; k = 2 * g.n[2] - 1 - k;
   }
-  return uc[cidx<D>(g, i, j, k)];
+  T v = uc[cidx<D>(g, i, j, k)];
+  if (ax < 0) return v;
+  T ub = hom ? T(0) : T(g.wu[ax][side][c]);
+  return T(2) * ub - v;
 }
 
 // Scalar with even reflection across walls (Neumann ghosts; one layer).
 template <int D, typename T>
-__device__ inline T nget(const T* __restrict__ x, const Geom& g, int i, int j, int k) {
+__host__ __device__ inline T nget(const T* __restrict__ x, const Geom& g, int i, int j, int k) {
   i = i < 0 ? -i - 1 : (i >= g.n[0] ? 2 * g.n[0] - 1 - i : i);
   j = j < 0 ? -j - 1 : (j >= g.n[1] ? 2 * g.n[1] - 1 - j : j);
   if (D == 3) k = k < 0 ? -k - 1 : (k >= g.n[2] ? 2 * g.n[2] - 1 - k : k);
@@ -96,7 +98,7 @@ __device__ inline T nget(const T* __restrict__ x, const Geom& g, int i, int j, i
 
 // Node value with even reflection across walls (node -1 -> 1, n+1 -> n-1).
 template <int D, typename T>
-__device__ inline T ndget(const T* __restrict__ x, const Geom& g, int i, int j, int k) {
+__host__ __device__ inline T ndget(const T* __restrict__ x, const Geom& g, int i, int j, int k) {
   i = i < 0 ? -i : (i > g.n[0] ? 2 * g.n[0] - i : i);
   j = j < 0 ? -j : (j > g.n[1] ? 2 * g.n[1] - j : j);
   if (D == 3) k = k < 0 ? -k : (k > g.n[2] ? 2 * g.n[2] - k : k);

@@ -15,7 +15,7 @@ namespace hb {
 // ---------------------------------------------------------------------------
 // Stage 1: strain rate and regularised viscosity (Eqs. 1, 21-23)
 // ---------------------------------------------------------------------------
-__device__ inline double viscosity(double g, const Rheo& r) {
+__host__ __device__ inline double viscosity(double g, const Rheo& r) {
   double x = r.m * g;
   double F;
   if (x < 1.0e-3) {
@@ -85,7 +85,7 @@ __global__ void k_eta_faces(const double* __restrict__ eta, double* __restrict__
 // Stage 2: cell G p from nodes and L_eta u = div(eta (grad u + grad u^T))
 // ---------------------------------------------------------------------------
 template <int D>
-__device__ inline double grad_nodal(const double* __restrict__ p, const Geom& g, int a, int i, int j,
+__host__ __device__ inline double grad_nodal(const double* __restrict__ p, const Geom& g, int a, int i, int j,
                                     int k) {
   // (p_+ - p_-)/h on each node pair along a, averaged over the other axes in order
   int c[3] = {i, j, k};
@@ -127,7 +127,7 @@ __global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, 
 // Tangential derivative (d_c u_a) on the a-face between cell L and L + e_a:
 // mean of the two cells' central c-differences; zero on a wall face.
 template <int D, typename T>
-__device__ inline T face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
+__host__ __device__ inline T face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
                                bool hom) {
   if (L[a] < 0 || L[a] >= g.n[a] - 1) return T(0);
   int q[3];
@@ -154,7 +154,7 @@ __device__ inline T face_cross(const T* __restrict__ ua, const Geom& g, int a, i
 
 // (L_eta u)_c at cell p with face eta arrays ef[a]
 template <int D, typename T>
-__device__ inline T tensor_op_point(const T* __restrict__ u, const T* const* ef, const Geom& g, int c,
+__host__ __device__ inline T tensor_op_point(const T* __restrict__ u, const T* const* ef, const Geom& g, int c,
                                     const int* p, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
   T acc = T(0);
@@ -195,7 +195,7 @@ __global__ void k_tensor_op(const double* __restrict__ u, const double* ef0, con
 // ---------------------------------------------------------------------------
 // Stage 3: Godunov edge states (Eqs. 11-14)
 // ---------------------------------------------------------------------------
-__device__ inline double sgn_min(double v, double lim) {
+__host__ __device__ inline double sgn_min(double v, double lim) {
   // sign(v) * min(|v|, lim) with sign(0) = 0
   if (v == 0.0) return 0.0;
   double m = fmin(fabs(v), lim);
@@ -204,7 +204,7 @@ __device__ inline double sgn_min(double v, double lim) {
 
 // Colella's fourth-order limited slope along axis a for component c
 template <int D>
-__device__ inline double limited_slope(const double* __restrict__ uc, const Geom& g, int c, int a,
+__host__ __device__ inline double limited_slope(const double* __restrict__ uc, const Geom& g, int c, int a,
                                        const int* p) {
   double w[5];
 #pragma unroll
@@ -239,14 +239,14 @@ __global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slop
   }
 }
 
-__device__ inline double riemann(double uL, double uR) {
+__host__ __device__ inline double riemann(double uL, double uR) {
   double s = uL + uR;
   if (uL > 0.0 && s > 0.0) return uL;
   if (uR < 0.0 && s < 0.0) return uR;
   return 0.0;
 }
 
-__device__ inline double upwind(double uL, double uR, double v) {
+__host__ __device__ inline double upwind(double uL, double uR, double v) {
   if (v > 0.0) return uL;
   if (v < 0.0) return uR;
   return 0.5 * (uL + uR);
@@ -255,7 +255,7 @@ __device__ inline double upwind(double uL, double uR, double v) {
 // Slope-only pre-states on the b-face between L and L+e_b (or wall values);
 // st[c] returns the upwinded state of each component, vb the normal velocity.
 template <int D>
-__device__ inline void prestate_face(const double* __restrict__ u, const double* __restrict__ slopes,
+__host__ __device__ inline void prestate_face(const double* __restrict__ u, const double* __restrict__ slopes,
                                      const Geom& g, double dt, int b, const int* L, double* st,
                                      double& vb) {
   int R[3] = {L[0], L[1], L[2]};
@@ -304,7 +304,7 @@ __global__ void k_hats(const double* __restrict__ u, const double* __restrict__ 
 // one-sided extrapolation of component c from cell q to its face along a,
 // side = -1 (left state: face above q) or +1 (right state: face below q)
 template <int D>
-__device__ inline double trace(const double* __restrict__ u, const double* __restrict__ slopes,
+__host__ __device__ inline double trace(const double* __restrict__ u, const double* __restrict__ slopes,
                                const double* __restrict__ hats, const double* __restrict__ Gp,
                                const double* __restrict__ Lu, const double* f, double rho, int pv,
                                const Geom& g, double dt, int a, int c, int tq, bool left) {

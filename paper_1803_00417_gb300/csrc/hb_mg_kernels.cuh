@@ -19,7 +19,7 @@ namespace hb {
 // tensor viscous operator pieces (mirrors the explicit-stage operator)
 // ---------------------------------------------------------------------------
 template <int D, typename T>
-__device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
+__host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
                                   bool hom) {
   if (L[a] < 0 || L[a] >= g.n[a] - 1) return T(0);
   T two_h = T(2) * T(g.h);
@@ -34,7 +34,7 @@ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a
 }
 
 template <int D, typename T>
-__device__ inline T mg_tensor_point(const T* __restrict__ u, const T* const* ef, const Geom& g, int c,
+__host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const T* const* ef, const Geom& g, int c,
                                     const int* p, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
   T acc = T(0);
@@ -62,7 +62,7 @@ __device__ inline T mg_tensor_point(const T* __restrict__ u, const T* const* ef,
 
 // Gauss-Seidel update of component c at cell p (all other values frozen)
 template <int D, typename T>
-__device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
+__host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
                                   const Geom& g, int c, const int* p, T beta, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
   T h = T(g.h);
@@ -112,7 +112,7 @@ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__
 
 // thread t -> cell of red-black colour col (x index stride 2)
 template <int D>
-__device__ inline bool rb_cell(const Geom& g, int t, int col, int* p) {
+__host__ __device__ inline bool rb_cell(const Geom& g, int t, int col, int* p) {
   int nxh = (g.n[0] + 1) / 2;
   int ih = t % nxh;
   int r = t / nxh;
@@ -188,7 +188,7 @@ __global__ void k_visc_bottom(T* __restrict__ u, const T* __restrict__ b, const 
 // cell-centred Poisson (MAC potential), Neumann walls
 // ---------------------------------------------------------------------------
 template <int D, typename T>
-__device__ inline T cell_gs_point(const T* __restrict__ x, const T* __restrict__ b, const Geom& g,
+__host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __restrict__ b, const Geom& g,
                                   const int* p) {
   T s = T(0);
   int cnt = 0;
@@ -269,14 +269,14 @@ __global__ void k_cell_bottom(T* __restrict__ x, const T* __restrict__ b, Geom g
 // ---------------------------------------------------------------------------
 // stencil weight (times h^2) of offset o in {-1,0,1}^D
 template <int D, typename T>
-__device__ inline T fe_weight(int nz) {
+__host__ __device__ inline T fe_weight(int nz) {
   if (nz == 0) return T(-8.0 / 3.0);
   if (D == 2) return T(1.0 / 3.0);
   return nz == 1 ? T(0) : (nz == 2 ? T(1.0 / 6.0) : T(1.0 / 12.0));
 }
 
 template <int D, typename T>
-__device__ inline T nodal_lap_point(const T* __restrict__ x, const Geom& g, const int* p, bool skip_centre) {
+__host__ __device__ inline T nodal_lap_point(const T* __restrict__ x, const Geom& g, const int* p, bool skip_centre) {
   T s = T(0);
   const int K = D == 3 ? 27 : 9;
 #pragma unroll
@@ -301,7 +301,7 @@ __device__ inline T nodal_lap_point(const T* __restrict__ x, const Geom& g, cons
 }
 
 template <int D>
-__device__ inline bool mc_node(const Geom& g, int t, int col, int* p) {
+__host__ __device__ inline bool mc_node(const Geom& g, int t, int col, int* p) {
   int e[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
   int cnt[3];
 #pragma unroll
@@ -444,7 +444,7 @@ __global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, i
 
 // coarse cell value with ghost by reflection: sign -1 (Dirichlet error), +1 (Neumann)
 template <int D, typename T>
-__device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, int i, int j, int k, T sign) {
+__host__ __device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, int i, int j, int k, T sign) {
   T s = T(1);
   if (i < 0) { i = 0; s *= sign; }
   if (i >= g.n[0]) { i = g.n[0] - 1; s *= sign; }

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libhbflow.so")
 
 HBF_OK = 0
 HBF_ERR_NOT_CONVERGED = -4
-FIELDS = dict(U=0, P=1, ETA=2, USTAR=3, UADV=4, UMAC=5, RHS=6, PHI_MAC=7, GP=8, LU=9, UL=10, UR=11)
+FIELDS = dict(U=0, P=1, ETA=2, USTAR=3, UADV=4, UMAC=5, RHS=6, PHI_MAC=7, GP=8, LU=9, UL=10, UR=11,
+              ETA_FACES=12, SLOPES=13, HATS=14)
 FP64, MIXED = 0, 1
 
 
