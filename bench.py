@@ -1,0 +1,317 @@
+"""Benchmark: cell-steps/s of the regularised Herschel-Bulkley time step on the
+3D lid-driven cavity (256^3 cells, n=1.5, Bi=10, Re=100, Pa=1e5), every
+multigrid solve to a 1e-10 relative residual.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference ...   # the CPU oracle on this host's cores
+
+Prints one JSON line (rank 0).  A step is one full pass of the method (all
+stages and solves) over the whole grid; the state evolves from rest with a
+constant dt (the paper's timing protocol: fixed time step, warm-up steps
+before the timed ones).  Inputs live in HBM before the timed region; every
+field is larger than L2, so no L2 flush is needed between steps.
+With several GPUs each rank runs an independent replica (the single-cavity
+step does not shard); value = all ranks' cell-steps / the slowest rank's time.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s at 256³ 3D HB cavity, mixed+learned vs plain FP64, same residual"
+UNIT = "cell-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="cavity256_3d_hb")
+    ap.add_argument("--n", type=int, default=0, help="override cells per axis (testing only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--profile-only", action="store_true", help="run warm-up + steps, print nothing else")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg_full, nsample, steps, warmup=0):
+    """Time the CPU oracle on the same cavity at nsample^3 cells (a bounded
+    sample of the workload: same physics and dt rule).  Returns cell-steps/s."""
+    from oracle.grid import Grid
+    from oracle.step import Rheology, step
+    from paper_1803_00417_gb300.inputs import cavity
+
+    name = cfg_full["name"]
+    d = cfg_full["d"]
+    cfg = cavity(name, n=(nsample,) * d)
+    g = Grid(cfg["n"], cfg["h"], wall_u=cfg["wall_u"])
+    rh = Rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+    u = [np.zeros(cfg["n"]) for _ in range(d)]
+    p = np.zeros(tuple(v + 1 for v in cfg["n"]))
+    for _ in range(warmup):
+        r = step(g, u, p, cfg["dt"], rh)
+        u, p = r.u, r.p
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r = step(g, u, p, cfg["dt"], rh)
+        u, p = r.u, r.p
+    dt = time.perf_counter() - t0
+    return int(np.prod(cfg["n"])) * steps / dt, dt
+
+
+def cpu_cores_used():
+    # numpy runs the oracle's array arithmetic on one thread (no BLAS calls)
+    return 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1803_00417_gb300.inputs import cavity
+
+    cfg = cavity(args.workload)
+    cfg["name"] = args.workload
+    nsample = 32 if cfg["d"] == 3 else 128
+    val, secs = oracle_sample(cfg, nsample, args.steps, args.warmup)
+    sample = f"{nsample}^{cfg['d']} cells of the same cavity, {args.steps} timed steps after {args.warmup}"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": list(cfg["n"]), "sample_n": [nsample] * cfg["d"],
+                       "precision": "fp64", "parallelism": "replicas"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+def visc_smoother_bytes(d, ncell, elem):
+    """Algorithmic bytes of one finest-level launch of the viscous smoother
+    (one component, one colour): reads the other colour of u_c (ncell/2), the
+    other components for the cross terms ((d-1) ncell), b_c of the colour
+    (ncell/2) and every face eta once (d ncell); writes u_c of the colour
+    (ncell/2)."""
+    return elem * ncell * (0.5 + (d - 1) + 0.5 + d + 0.5)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1803_00417_gb300 import build
+    from paper_1803_00417_gb300.hbflow import FP64, MIXED, HBFlow
+    from paper_1803_00417_gb300.inputs import cavity
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+
+    over = {"n": (args.n,) * 3} if args.n else {}
+    cfg = cavity(args.workload, **over)
+    cfg["name"] = args.workload
+    d = cfg["d"]
+    ncell = int(np.prod(cfg["n"]))
+    prec = MIXED if args.precision == "mixed" else FP64
+    sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=prec)
+    sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+    sim.set_solver(rtol=1e-10, max_cycles=200)
+    zeros_u = np.zeros(d * ncell)
+    zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
+    sim.set_field("U", zeros_u)
+    sim.set_field("P", zeros_p)
+    dt = cfg["dt"]
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        sim.step(dt)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+    clocks = Clocks(local)
+    sim.profile_enable(True)
+    n_launch0 = sim.launch_count()
+    cycles = {"mac": 0, "visc": 0, "nodal": 0}
+    converged = True
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st = sim.step(dt)
+        for k in cycles:
+            cycles[k] += st[k]["cycles"]
+            converged &= st[k]["converged"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.launch_count() - n_launch0
+    prof = {k: sim.profile_read(k) for k in sim.PROFILE_SLOTS}
+    sim.profile_enable(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ncell * args.steps / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.empty(d * ncell, dtype=torch.float64, pin_memory=True).numpy()
+        hp = torch.empty(zeros_p.size, dtype=torch.float64, pin_memory=True).numpy()
+        sim.get_field("U", hu)
+        sim.get_field("P", hp)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.set_field("U", hu)
+            sim.set_field("P", hp)
+            sim.step(dt)
+            sim.get_field("U", hu)
+            sim.get_field("P", hp)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([secs], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            secs = float(t.item())
+        e2e = {"value": world * ncell * args.e2e_steps / secs, "unit": UNIT,
+               "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    elem = 4 if prec == MIXED else 8
+    sm_ms, sm_n = prof["visc_smooth"]
+    roofline = None
+    if sm_n > 0:
+        per_launch_s = sm_ms / sm_n / 1e3
+        algo = visc_smoother_bytes(d, ncell, elem)
+        ach = algo / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                    "traffic": None, "kernel": "k_visc_smooth (finest level)",
+                    "launches": sm_n, "avg_launch_us": per_launch_s * 1e6,
+                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    cpu = None
+    if not args.no_cpu:
+        nsample = 32 if d == 3 else 128
+        val, secs = oracle_sample(cfg, nsample, 2)
+        cpu = {"value": val, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": f"2 steps from rest of the same cavity at {nsample}^{d} cells ({secs:.1f} s)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == FP64 else "f64+f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": list(cfg["n"]), "precision": args.precision,
+                       "rtol": 1e-10, "dt": dt, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "no flush: every field (>= 134 MB) exceeds the 129 MB L2",
+                       "cycles_per_step": {k: v / args.steps for k, v in cycles.items()},
+                       "converged": bool(converged)},
+            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk,
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

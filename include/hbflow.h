@@ -163,6 +163,18 @@ int hbf_step(hbf_ctx* ctx, double dt, hbf_step_stats* stats);
 /* dt = cfl h / max(max|u|, 1) for the current U (synchronises). */
 double hbf_cfl_dt(hbf_ctx* ctx, double cfl);
 
+/* Event timing of finest-level launches, per kernel class (slot):
+ *   0 viscous smoother, 1 viscous residual, 2 nodal smoother, 3 nodal residual,
+ *   4 MAC smoother, 5 MAC residual, 6 explicit stages (all levels).
+ * hbf_profile_enable(ctx, 1) synchronises, clears the accumulators and starts
+ * recording; hbf_profile_read synchronises and returns the summed device time
+ * in milliseconds and the number of launches recorded for a slot. */
+int hbf_profile_enable(hbf_ctx* ctx, int on);
+int hbf_profile_read(hbf_ctx* ctx, int slot, double* total_ms, int64_t* launches);
+
+/* Number of kernels the context has launched since it was created. */
+int64_t hbf_launch_count(const hbf_ctx* ctx);
+
 int hbf_sync(hbf_ctx* ctx);
 const char* hbf_last_error(const hbf_ctx* ctx);
 void hbf_destroy(hbf_ctx* ctx);

@@ -20,6 +20,26 @@ int cuda_check(hbf_ctx* c, cudaError_t e, const char* what) {
   return fail(c, e == cudaErrorMemoryAllocation ? HBF_ERR_OOM : HBF_ERR_CUDA, m);
 }
 
+void prof_mark(hbf_ctx* c, int slot, bool start) {
+  Prof& P = c->prof;
+  if (P.used[slot] + 2 > P.ev[slot].size()) {
+    if (P.ev[slot].size() >= 2 * kProfPairs) return;  // pool full: stop recording this slot
+    size_t old = P.ev[slot].size();
+    P.ev[slot].resize(old + 256);
+    for (size_t q = old; q < P.ev[slot].size(); ++q) cudaEventCreate(&P.ev[slot][q]);
+  }
+  if (!start && (P.used[slot] & 1) == 0) return;  // unmatched stop (start was dropped)
+  cudaEventRecord(P.ev[slot][P.used[slot]++], c->stream);
+}
+
+static void prof_release(hbf_ctx* c) {
+  for (int s = 0; s < kSlotCount; ++s) {
+    for (cudaEvent_t e : c->prof.ev[s]) cudaEventDestroy(e);
+    c->prof.ev[s].clear();
+    c->prof.used[s] = 0;
+  }
+}
+
 static Geom make_geom(int dim, const int n[3], double h) {
   Geom g;
   std::memset(&g, 0, sizeof g);
@@ -213,8 +233,37 @@ void hbf_destroy(hbf_ctx* c) {
   else cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
   if (c->hres) cudaFreeHost(c->hres);
+  prof_release(c);
   delete c;
 }
+
+int hbf_profile_enable(hbf_ctx* c, int on) {
+  if (!c) return HBF_ERR_ARG;
+  int st = cuda_check(c, cudaStreamSynchronize(c->stream), "profile sync");
+  if (st) return st;
+  for (int s = 0; s < kSlotCount; ++s) c->prof.used[s] = 0;
+  c->prof.on = on != 0;
+  return HBF_OK;
+}
+
+int hbf_profile_read(hbf_ctx* c, int slot, double* total_ms, int64_t* launches) {
+  if (!c || slot < 0 || slot >= kSlotCount || !total_ms || !launches) return HBF_ERR_ARG;
+  int st = cuda_check(c, cudaStreamSynchronize(c->stream), "profile sync");
+  if (st) return st;
+  double tot = 0.0;
+  size_t pairs = c->prof.used[slot] / 2;
+  for (size_t q = 0; q < pairs; ++q) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, c->prof.ev[slot][2 * q], c->prof.ev[slot][2 * q + 1]);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaEventElapsedTime");
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = (int64_t)pairs;
+  return HBF_OK;
+}
+
+int64_t hbf_launch_count(const hbf_ctx* c) { return c ? (int64_t)c->nlaunch : HBF_ERR_ARG; }
 
 const char* hbf_last_error(const hbf_ctx* c) { return c ? c->err.c_str() : "null context"; }
 

@@ -523,12 +523,12 @@ __global__ void k_project_update(double* __restrict__ u, const double* __restric
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-#define HB_DISPATCH(dim, KERNEL, GRID, ...)                                       \
-  do {                                                                           \
-    if ((dim) == 2)                                                              \
-      KERNEL<2><<<(GRID), kThreads, 0, c->stream>>>(__VA_ARGS__);                \
-    else                                                                         \
-      KERNEL<3><<<(GRID), kThreads, 0, c->stream>>>(__VA_ARGS__);                \
+#define HB_DISPATCH(dim, KERNEL, GRID, ...)                            \
+  do {                                                                \
+    if ((dim) == 2)                                                   \
+      launch(c, kSlotExplicit, KERNEL<2>, (GRID), kThreads, __VA_ARGS__); \
+    else                                                              \
+      launch(c, kSlotExplicit, KERNEL<3>, (GRID), kThreads, __VA_ARGS__); \
   } while (0)
 
 int launch_eta(hbf_ctx* c) {

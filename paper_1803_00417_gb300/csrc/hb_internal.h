@@ -38,6 +38,28 @@ struct Level {
   float* fnr = nullptr;
 };
 
+// profiling slots: device time of every launch of one kernel class on the
+// finest level, recorded with CUDA events on the context stream
+enum ProfSlot {
+  kSlotViscSmooth = 0,
+  kSlotViscResid = 1,
+  kSlotNodalSmooth = 2,
+  kSlotNodalResid = 3,
+  kSlotCellSmooth = 4,
+  kSlotCellResid = 5,
+  kSlotExplicit = 6,
+  kSlotCount = 7,
+  kSlotNone = -1
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev[kSlotCount];  // start/stop pairs
+  size_t used[kSlotCount] = {0, 0, 0, 0, 0, 0, 0};
+};
+
+constexpr size_t kProfPairs = 16384;
+
 struct SolverCfg {
   double rtol = 1e-10;
   int max_cycles = 200;
@@ -81,11 +103,25 @@ struct hbf_ctx {
   double* hres = nullptr;     // pinned host result
   std::vector<hb::Level> lv;
   std::vector<void*> allocs;
+  hb::Prof prof;
+  long long nlaunch = 0;
 };
 
 namespace hb {
 
 constexpr int kRedBlocks = 1024;
+
+void prof_mark(hbf_ctx* c, int slot, bool start);
+
+// every kernel launch of the library goes through here: counts it and, when
+// profiling is on, brackets finest-level launches of a slot with events
+template <typename K, typename... Args>
+inline void launch(hbf_ctx* c, int slot, K kern, int grid, int block, Args... args) {
+  if (slot >= 0 && c->prof.on) prof_mark(c, slot, true);
+  kern<<<grid, block, 0, c->stream>>>(args...);
+  if (slot >= 0 && c->prof.on) prof_mark(c, slot, false);
+  ++c->nlaunch;
+}
 
 // error helpers
 int fail(hbf_ctx* c, int code, const std::string& msg);

@@ -101,8 +101,8 @@ __global__ void k_zero(T* __restrict__ x, long long n) {
 
 template <int MODE>
 static int reduce_to_device(hbf_ctx* c, const double* x, long long n, double* out) {
-  k_reduce_partial<MODE><<<kRedBlocks, kThreads, 0, c->stream>>>(x, n, c->partial, c->g, c->dim);
-  k_reduce_final<MODE><<<1, 1024, 0, c->stream>>>(c->partial, kRedBlocks, out);
+  launch(c, kSlotNone, k_reduce_partial<MODE>, kRedBlocks, kThreads, x, n, c->partial, c->g, c->dim);
+  launch(c, kSlotNone, k_reduce_final<MODE>, 1, 1024, c->partial, kRedBlocks, out);
   return cuda_check(c, cudaGetLastError(), "reduction");
 }
 
@@ -163,28 +163,28 @@ struct ViscProblem : Problem {
     int nb = grid_for(rb_count<D>(L.g));
     for (int comp = 0; comp < D; ++comp)
       for (int col = 0; col < 2; ++col)
-        k_visc_smooth<D, double><<<nb, kThreads, 0, c->stream>>>(x(l), L.vb, L.ef[0], L.ef[1], L.ef[2], L.g,
+        launch(c, l == 0 ? kSlotViscSmooth : kSlotNone, k_visc_smooth<D, double>, nb, kThreads, x(l), L.vb, L.ef[0], L.ef[1], L.ef[2], L.g,
                                                                   comp, col, beta, l > 0);
   }
   void resid(int l) override {
     const Level& L = c->lv[l];
-    k_visc_resid<D, double><<<grid_for(L.g.ncell), kThreads, 0, c->stream>>>(x(l), L.vb, L.vr, L.ef[0], L.ef[1],
+    launch(c, l == 0 ? kSlotViscResid : kSlotNone, k_visc_resid<D, double>, grid_for(L.g.ncell), kThreads, x(l), L.vb, L.vr, L.ef[0], L.ef[1],
                                                                              L.ef[2], L.g, beta, l > 0);
   }
   void restrict_to(int l) override {
     const Level &F = c->lv[l], &C = c->lv[l + 1];
-    k_restrict_cells<D, double><<<grid_for((long long)D * C.g.ncell), kThreads, 0, c->stream>>>(F.vr, C.vb, F.g,
+    launch(c, kSlotNone, k_restrict_cells<D, double>, grid_for((long long)D * C.g.ncell), kThreads, F.vr, C.vb, F.g,
                                                                                               C.g, D);
-    k_zero<double><<<grid_for((long long)D * C.g.ncell), kThreads, 0, c->stream>>>(C.vx, (long long)D * C.g.ncell);
+    launch(c, kSlotNone, k_zero<double>, grid_for((long long)D * C.g.ncell), kThreads, C.vx, (long long)D * C.g.ncell);
   }
   void prolong_add(int l) override {
     const Level &F = c->lv[l], &C = c->lv[l + 1];
-    k_prolong_cells_add<D, double><<<grid_for((long long)D * F.g.ncell), kThreads, 0, c->stream>>>(
+    launch(c, kSlotNone, k_prolong_cells_add<D, double>, grid_for((long long)D * F.g.ncell), kThreads, 
         x(l), C.vx, F.g, C.g, D, -1.0);
   }
   void bottom(int l) override {
     const Level& L = c->lv[l];
-    k_visc_bottom<D, double><<<1, 1024, 0, c->stream>>>(x(l), L.vb, L.ef[0], L.ef[1], L.ef[2], L.g, beta,
+    launch(c, kSlotNone, k_visc_bottom<D, double>, 1, 1024, x(l), L.vb, L.ef[0], L.ef[1], L.ef[2], L.g, beta,
                                                          c->cfg.nu_bottom, l > 0);
   }
 };
@@ -201,30 +201,30 @@ struct MacProblem : Problem {
     const Level& L = c->lv[l];
     int nb = grid_for(rb_count<D>(L.g));
     for (int col = 0; col < 2; ++col)
-      k_cell_smooth<D, double><<<nb, kThreads, 0, c->stream>>>(x(l), L.cb, L.g, col);
+      launch(c, l == 0 ? kSlotCellSmooth : kSlotNone, k_cell_smooth<D, double>, nb, kThreads, x(l), L.cb, L.g, col);
   }
   void resid(int l) override {
     const Level& L = c->lv[l];
-    k_cell_resid<D, double><<<grid_for(L.g.ncell), kThreads, 0, c->stream>>>(x(l), L.cb, L.cr, L.g);
+    launch(c, l == 0 ? kSlotCellResid : kSlotNone, k_cell_resid<D, double>, grid_for(L.g.ncell), kThreads, x(l), L.cb, L.cr, L.g);
   }
   void restrict_to(int l) override {
     const Level &F = c->lv[l], &C = c->lv[l + 1];
-    k_restrict_cells<D, double><<<grid_for(C.g.ncell), kThreads, 0, c->stream>>>(F.cr, C.cb, F.g, C.g, 1);
-    k_zero<double><<<grid_for(C.g.ncell), kThreads, 0, c->stream>>>(C.cx, C.g.ncell);
+    launch(c, kSlotNone, k_restrict_cells<D, double>, grid_for(C.g.ncell), kThreads, F.cr, C.cb, F.g, C.g, 1);
+    launch(c, kSlotNone, k_zero<double>, grid_for(C.g.ncell), kThreads, C.cx, C.g.ncell);
   }
   void prolong_add(int l) override {
     const Level &F = c->lv[l], &C = c->lv[l + 1];
-    k_prolong_cells_add<D, double><<<grid_for(F.g.ncell), kThreads, 0, c->stream>>>(x(l), C.cx, F.g, C.g, 1, 1.0);
+    launch(c, kSlotNone, k_prolong_cells_add<D, double>, grid_for(F.g.ncell), kThreads, x(l), C.cx, F.g, C.g, 1, 1.0);
   }
   void bottom(int l) override {
     const Level& L = c->lv[l];
-    k_cell_bottom<D, double><<<1, 1024, 0, c->stream>>>(x(l), L.cb, L.g, c->cfg.nu_bottom);
+    launch(c, kSlotNone, k_cell_bottom<D, double>, 1, 1024, x(l), L.cb, L.g, c->cfg.nu_bottom);
   }
   int sub_mean(int l, double* v) override {
     const Level& L = c->lv[l];
     int st = reduce_to_device<1>(c, v, L.g.ncell, c->dres + 1);
     if (st) return st;
-    k_sub_mean<double><<<grid_for(L.g.ncell), kThreads, 0, c->stream>>>(v, L.g.ncell, c->dres + 1,
+    launch(c, kSlotNone, k_sub_mean<double>, grid_for(L.g.ncell), kThreads, v, L.g.ncell, c->dres + 1,
                                                                        1.0 / (double)L.g.ncell);
     return cuda_check(c, cudaGetLastError(), "k_sub_mean");
   }
@@ -241,24 +241,25 @@ struct NodalProblem : Problem {
   void smooth(int l) override {
     const Level& L = c->lv[l];
     for (int col = 0; col < (1 << D); ++col)
-      k_nodal_smooth<D, double><<<grid_for(mc_count<D>(L.g, col)), kThreads, 0, c->stream>>>(x(l), L.nb, L.g, col);
+      launch(c, l == 0 ? kSlotNodalSmooth : kSlotNone, k_nodal_smooth<D, double>, grid_for(mc_count<D>(L.g, col)),
+             kThreads, x(l), L.nb, L.g, col);
   }
   void resid(int l) override {
     const Level& L = c->lv[l];
-    k_nodal_resid<D, double><<<grid_for(L.g.nnode), kThreads, 0, c->stream>>>(x(l), L.nb, L.nr, L.g);
+    launch(c, l == 0 ? kSlotNodalResid : kSlotNone, k_nodal_resid<D, double>, grid_for(L.g.nnode), kThreads, x(l), L.nb, L.nr, L.g);
   }
   void restrict_to(int l) override {
     const Level &F = c->lv[l], &C = c->lv[l + 1];
-    k_restrict_nodes<D, double><<<grid_for(C.g.nnode), kThreads, 0, c->stream>>>(F.nr, C.nb, F.g, C.g);
-    k_zero<double><<<grid_for(C.g.nnode), kThreads, 0, c->stream>>>(C.nx, C.g.nnode);
+    launch(c, kSlotNone, k_restrict_nodes<D, double>, grid_for(C.g.nnode), kThreads, F.nr, C.nb, F.g, C.g);
+    launch(c, kSlotNone, k_zero<double>, grid_for(C.g.nnode), kThreads, C.nx, C.g.nnode);
   }
   void prolong_add(int l) override {
     const Level &F = c->lv[l], &C = c->lv[l + 1];
-    k_prolong_nodes_add<D, double><<<grid_for(F.g.nnode), kThreads, 0, c->stream>>>(x(l), C.nx, F.g, C.g);
+    launch(c, kSlotNone, k_prolong_nodes_add<D, double>, grid_for(F.g.nnode), kThreads, x(l), C.nx, F.g, C.g);
   }
   void bottom(int l) override {
     const Level& L = c->lv[l];
-    k_nodal_bottom<D, double><<<1, 1024, 0, c->stream>>>(x(l), L.nb, L.g, c->cfg.nu_bottom);
+    launch(c, kSlotNone, k_nodal_bottom<D, double>, 1, 1024, x(l), L.nb, L.g, c->cfg.nu_bottom);
   }
   int sub_mean(int l, double* v) override {
     const Level& L = c->lv[l];
@@ -268,7 +269,7 @@ struct NodalProblem : Problem {
     c->g = gsave;
     if (st) return st;
     double wsum = (double)L.g.n[0] * L.g.n[1] * (D == 3 ? L.g.n[2] : 1);
-    k_sub_mean<double><<<grid_for(L.g.nnode), kThreads, 0, c->stream>>>(v, L.g.nnode, c->dres + 1, 1.0 / wsum);
+    launch(c, kSlotNone, k_sub_mean<double>, grid_for(L.g.nnode), kThreads, v, L.g.nnode, c->dres + 1, 1.0 / wsum);
     return cuda_check(c, cudaGetLastError(), "k_sub_mean");
   }
 };
@@ -339,7 +340,7 @@ static void build_eta_levels(hbf_ctx* c) {
   for (size_t l = 1; l < c->lv.size(); ++l) {
     const Level &F = c->lv[l - 1], &C = c->lv[l];
     for (int a = 0; a < D; ++a)
-      k_restrict_faces<D, double><<<grid_for(C.g.nface[a]), kThreads, 0, c->stream>>>(F.ef[a], C.ef[a], a, F.g,
+      launch(c, kSlotNone, k_restrict_faces<D, double>, grid_for(C.g.nface[a]), kThreads, F.ef[a], C.ef[a], a, F.g,
                                                                                        C.g);
   }
 }

@@ -66,6 +66,10 @@ SIGNATURES = {
                                    ctypes.POINTER(SolveStats)]),
     "hbf_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(StepStats)]),
     "hbf_cfl_dt": (ctypes.c_double, [ctypes.c_void_p, ctypes.c_double]),
+    "hbf_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hbf_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "hbf_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "hbf_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hbf_destroy": (None, [ctypes.c_void_p]),
@@ -252,6 +256,21 @@ class HBFlow:
 
     def cfl_dt(self, cfl):
         return float(self.lib.hbf_cfl_dt(self.ctx, cfl))
+
+    PROFILE_SLOTS = dict(visc_smooth=0, visc_resid=1, nodal_smooth=2, nodal_resid=3, mac_smooth=4,
+                         mac_resid=5, explicit=6)
+
+    def profile_enable(self, on=True):
+        self._check(self.lib.hbf_profile_enable(self.ctx, int(bool(on))))
+
+    def profile_read(self, slot):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self.lib.hbf_profile_read(self.ctx, self.PROFILE_SLOTS[slot], ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self):
+        return int(self.lib.hbf_launch_count(self.ctx))
 
     def sync(self):
         self._check(self.lib.hbf_sync(self.ctx))
