@@ -109,10 +109,22 @@ static int allocate(hbf_ctx* c) {
   for (int l = 0;; ++l) {
     Level L;
     L.g = gl;
-    if (l > 0) {
+    if (l > 0 || c->precision == HBF_MIXED) {
       A(L.vx, (long long)D * gl.ncell);
       A(L.cx, gl.ncell);
       A(L.nx, gl.nnode);
+    }
+    if (c->precision == HBF_MIXED) {
+      A(L.fvx, (long long)D * gl.ncell);
+      A(L.fvb, (long long)D * gl.ncell);
+      A(L.fvr, (long long)D * gl.ncell);
+      A(L.fcx, gl.ncell);
+      A(L.fcb, gl.ncell);
+      A(L.fcr, gl.ncell);
+      A(L.fnx, gl.nnode);
+      A(L.fnb, gl.nnode);
+      A(L.fnr, gl.nnode);
+      for (int a = 0; a < D; ++a) A(L.fef[a], gl.nface[a]);
     }
     A(L.vb, (long long)D * gl.ncell);
     A(L.vr, (long long)D * gl.ncell);

@@ -10,6 +10,7 @@
 // bottom solve.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "hb_internal.h"
 #include "hb_mg_kernels.cuh"
@@ -129,156 +130,252 @@ double reduce_sum(hbf_ctx* c, const double* x, long long n, int* st) {
 }
 
 // ---------------------------------------------------------------------------
+// small elementwise kernels
+// ---------------------------------------------------------------------------
+template <typename TO, typename TI>
+__global__ void k_convert(TO* __restrict__ out, const TI* __restrict__ in, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = TO(in[t]);
+}
+
+// x (FP64) += e (FP32): the defect-correction update
+__global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ e, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    x[t] += (double)e[t];
+}
+
+// ---------------------------------------------------------------------------
+// per-precision views of a level's arrays
+// ---------------------------------------------------------------------------
+template <typename T>
+struct View;
+template <>
+struct View<double> {
+  static double* vx(Level& L) { return L.vx; }
+  static double* vb(Level& L) { return L.vb; }
+  static double* vr(Level& L) { return L.vr; }
+  static double* ef(Level& L, int a) { return L.ef[a]; }
+  static double* cx(Level& L) { return L.cx; }
+  static double* cb(Level& L) { return L.cb; }
+  static double* cr(Level& L) { return L.cr; }
+  static double* nx(Level& L) { return L.nx; }
+  static double* nb(Level& L) { return L.nb; }
+  static double* nr(Level& L) { return L.nr; }
+};
+template <>
+struct View<float> {
+  static float* vx(Level& L) { return L.fvx; }
+  static float* vb(Level& L) { return L.fvb; }
+  static float* vr(Level& L) { return L.fvr; }
+  static float* ef(Level& L, int a) { return L.fef[a]; }
+  static float* cx(Level& L) { return L.fcx; }
+  static float* cb(Level& L) { return L.fcb; }
+  static float* cr(Level& L) { return L.fcr; }
+  static float* nx(Level& L) { return L.fnx; }
+  static float* nb(Level& L) { return L.fnb; }
+  static float* nr(Level& L) { return L.fnr; }
+};
+
+// ---------------------------------------------------------------------------
 // problem interface for the generic driver
 // ---------------------------------------------------------------------------
+// One linear problem on the level hierarchy in arithmetic T.  hom0: level 0
+// carries homogeneous boundary values (the error equation of the mixed
+// solve); coarse levels are always homogeneous.
+template <typename T>
 struct Problem {
   hbf_ctx* c;
   int nlev;
   bool singular;
-  explicit Problem(hbf_ctx* ctx, bool sing) : c(ctx), nlev((int)ctx->lv.size()), singular(sing) {}
+  bool hom0;
+  Problem(hbf_ctx* ctx, bool sing, bool h0) : c(ctx), nlev((int)ctx->lv.size()), singular(sing), hom0(h0) {}
   virtual ~Problem() {}
-  virtual double* x(int l) = 0;
-  virtual double* b(int l) = 0;
-  virtual double* r(int l) = 0;
+  bool hom(int l) const { return l > 0 || hom0; }
+  virtual T* x(int l) = 0;
+  virtual T* b(int l) = 0;
+  virtual T* r(int l) = 0;
   virtual long long count(int l) = 0;
   virtual void smooth(int l) = 0;
   virtual void resid(int l) = 0;
-  virtual void restrict_to(int l) = 0;   // b(l+1) = R r(l)
-  virtual void prolong_add(int l) = 0;   // x(l) += P x(l+1)
-  virtual void bottom(int l) = 0;
+  virtual void restrict_to(int l) = 0;  // b(l+1) = R r(l), x(l+1) = 0
+  virtual void prolong_add(int l) = 0;  // x(l) += P x(l+1)
+  virtual void bottom(int l) = 0;       // FP64 sweeps on the coarsest level
   virtual int sub_mean(int l, double* v) { (void)l; (void)v; return 0; }
 };
 
-template <int D>
-struct ViscProblem : Problem {
-  double* x0;
+// coarsest level in FP64 for either precision: the FP32 path converts in and out
+template <typename T>
+static void bottom_fp64(Problem<T>& P, int l, double* xd, double* bd, void (*run)(Problem<T>&, int, double*, double*)) {
+  hbf_ctx* c = P.c;
+  long long n = P.count(l);
+  if (!std::is_same<T, double>::value) {
+    launch(c, kSlotNone, k_convert<double, T>, grid_for(n), kThreads, bd, (const T*)P.b(l), n);
+    launch(c, kSlotNone, k_zero<double>, grid_for(n), kThreads, xd, n);
+  }
+  if (P.singular) P.sub_mean(l, bd);
+  run(P, l, xd, bd);
+  if (P.singular) P.sub_mean(l, xd);
+  if (!std::is_same<T, double>::value)
+    launch(c, kSlotNone, k_convert<T, double>, grid_for(n), kThreads, P.x(l), (const double*)xd, n);
+}
+
+template <int D, typename T>
+struct ViscProblem : Problem<T> {
+  using Problem<T>::c;
+  T* x0;
   double beta;
-  ViscProblem(hbf_ctx* ctx, double* x_in, double bt) : Problem(ctx, false), x0(x_in), beta(bt) {}
-  double* x(int l) override { return l == 0 ? x0 : c->lv[l].vx; }
-  double* b(int l) override { return c->lv[l].vb; }
-  double* r(int l) override { return c->lv[l].vr; }
+  ViscProblem(hbf_ctx* ctx, T* x_in, double bt, bool h0) : Problem<T>(ctx, false, h0), x0(x_in), beta(bt) {}
+  T* x(int l) override { return l == 0 ? x0 : View<T>::vx(c->lv[l]); }
+  T* b(int l) override { return View<T>::vb(c->lv[l]); }
+  T* r(int l) override { return View<T>::vr(c->lv[l]); }
   long long count(int l) override { return (long long)D * c->lv[l].g.ncell; }
   void smooth(int l) override {
-    const Level& L = c->lv[l];
+    Level& L = c->lv[l];
     int nb = grid_for(rb_count<D>(L.g));
     for (int comp = 0; comp < D; ++comp)
       for (int col = 0; col < 2; ++col)
-        launch(c, l == 0 ? kSlotViscSmooth : kSlotNone, k_visc_smooth<D, double>, nb, kThreads, x(l), L.vb, L.ef[0], L.ef[1], L.ef[2], L.g,
-                                                                  comp, col, beta, l > 0);
+        launch(c, l == 0 ? kSlotViscSmooth : kSlotNone, k_visc_smooth<D, T>, nb, kThreads, x(l), b(l),
+               View<T>::ef(L, 0), View<T>::ef(L, 1), View<T>::ef(L, 2), L.g, comp, col, (T)beta, (int)this->hom(l));
   }
   void resid(int l) override {
-    const Level& L = c->lv[l];
-    launch(c, l == 0 ? kSlotViscResid : kSlotNone, k_visc_resid<D, double>, grid_for(L.g.ncell), kThreads, x(l), L.vb, L.vr, L.ef[0], L.ef[1],
-                                                                             L.ef[2], L.g, beta, l > 0);
+    Level& L = c->lv[l];
+    launch(c, l == 0 ? kSlotViscResid : kSlotNone, k_visc_resid<D, T>, grid_for(L.g.ncell), kThreads, x(l), b(l),
+           r(l), View<T>::ef(L, 0), View<T>::ef(L, 1), View<T>::ef(L, 2), L.g, (T)beta, (int)this->hom(l));
   }
   void restrict_to(int l) override {
-    const Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_restrict_cells<D, double>, grid_for((long long)D * C.g.ncell), kThreads, F.vr, C.vb, F.g,
-                                                                                              C.g, D);
-    launch(c, kSlotNone, k_zero<double>, grid_for((long long)D * C.g.ncell), kThreads, C.vx, (long long)D * C.g.ncell);
+    Level &F = c->lv[l], &C = c->lv[l + 1];
+    long long n = (long long)D * C.g.ncell;
+    launch(c, kSlotNone, k_restrict_cells<D, T>, grid_for(n), kThreads, r(l), b(l + 1), F.g, C.g, D);
+    launch(c, kSlotNone, k_zero<T>, grid_for(n), kThreads, x(l + 1), n);
   }
   void prolong_add(int l) override {
-    const Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_prolong_cells_add<D, double>, grid_for((long long)D * F.g.ncell), kThreads, 
-        x(l), C.vx, F.g, C.g, D, -1.0);
+    Level &F = c->lv[l], &C = c->lv[l + 1];
+    launch(c, kSlotNone, k_prolong_cells_add<D, T>, grid_for((long long)D * F.g.ncell), kThreads, x(l), x(l + 1),
+           F.g, C.g, D, T(-1));
+  }
+  static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
+    auto& S = static_cast<ViscProblem&>(P);
+    Level& L = S.c->lv[l];
+    launch(S.c, kSlotNone, k_visc_bottom<D, double>, 1, 1024, xd, (const double*)bd, (const double*)L.ef[0],
+           (const double*)L.ef[1], (const double*)L.ef[2], L.g, S.beta, S.c->cfg.nu_bottom, (int)S.hom(l));
   }
   void bottom(int l) override {
-    const Level& L = c->lv[l];
-    launch(c, kSlotNone, k_visc_bottom<D, double>, 1, 1024, x(l), L.vb, L.ef[0], L.ef[1], L.ef[2], L.g, beta,
-                                                         c->cfg.nu_bottom, l > 0);
+    Level& L = c->lv[l];
+    double* xd = std::is_same<T, double>::value ? (double*)x(l) : L.vx;
+    double* bd = std::is_same<T, double>::value ? (double*)b(l) : L.vb;
+    bottom_fp64<T>(*this, l, xd, bd, &run_bottom);
   }
 };
 
-template <int D>
-struct MacProblem : Problem {
-  double* x0;
-  MacProblem(hbf_ctx* ctx, double* x_in) : Problem(ctx, true), x0(x_in) {}
-  double* x(int l) override { return l == 0 ? x0 : c->lv[l].cx; }
-  double* b(int l) override { return c->lv[l].cb; }
-  double* r(int l) override { return c->lv[l].cr; }
+template <int D, typename T>
+struct MacProblem : Problem<T> {
+  using Problem<T>::c;
+  T* x0;
+  MacProblem(hbf_ctx* ctx, T* x_in) : Problem<T>(ctx, true, true), x0(x_in) {}
+  T* x(int l) override { return l == 0 ? x0 : View<T>::cx(c->lv[l]); }
+  T* b(int l) override { return View<T>::cb(c->lv[l]); }
+  T* r(int l) override { return View<T>::cr(c->lv[l]); }
   long long count(int l) override { return c->lv[l].g.ncell; }
   void smooth(int l) override {
-    const Level& L = c->lv[l];
+    Level& L = c->lv[l];
     int nb = grid_for(rb_count<D>(L.g));
     for (int col = 0; col < 2; ++col)
-      launch(c, l == 0 ? kSlotCellSmooth : kSlotNone, k_cell_smooth<D, double>, nb, kThreads, x(l), L.cb, L.g, col);
+      launch(c, l == 0 ? kSlotCellSmooth : kSlotNone, k_cell_smooth<D, T>, nb, kThreads, x(l), b(l), L.g, col);
   }
   void resid(int l) override {
-    const Level& L = c->lv[l];
-    launch(c, l == 0 ? kSlotCellResid : kSlotNone, k_cell_resid<D, double>, grid_for(L.g.ncell), kThreads, x(l), L.cb, L.cr, L.g);
+    Level& L = c->lv[l];
+    launch(c, l == 0 ? kSlotCellResid : kSlotNone, k_cell_resid<D, T>, grid_for(L.g.ncell), kThreads, x(l), b(l),
+           r(l), L.g);
   }
   void restrict_to(int l) override {
-    const Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_restrict_cells<D, double>, grid_for(C.g.ncell), kThreads, F.cr, C.cb, F.g, C.g, 1);
-    launch(c, kSlotNone, k_zero<double>, grid_for(C.g.ncell), kThreads, C.cx, C.g.ncell);
+    Level &F = c->lv[l], &C = c->lv[l + 1];
+    launch(c, kSlotNone, k_restrict_cells<D, T>, grid_for(C.g.ncell), kThreads, r(l), b(l + 1), F.g, C.g, 1);
+    launch(c, kSlotNone, k_zero<T>, grid_for(C.g.ncell), kThreads, x(l + 1), (long long)C.g.ncell);
   }
   void prolong_add(int l) override {
-    const Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_prolong_cells_add<D, double>, grid_for(F.g.ncell), kThreads, x(l), C.cx, F.g, C.g, 1, 1.0);
+    Level &F = c->lv[l], &C = c->lv[l + 1];
+    launch(c, kSlotNone, k_prolong_cells_add<D, T>, grid_for(F.g.ncell), kThreads, x(l), x(l + 1), F.g, C.g, 1,
+           T(1));
+  }
+  static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
+    Level& L = P.c->lv[l];
+    launch(P.c, kSlotNone, k_cell_bottom<D, double>, 1, 1024, xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
   }
   void bottom(int l) override {
-    const Level& L = c->lv[l];
-    launch(c, kSlotNone, k_cell_bottom<D, double>, 1, 1024, x(l), L.cb, L.g, c->cfg.nu_bottom);
+    Level& L = c->lv[l];
+    double* xd = std::is_same<T, double>::value ? (double*)x(l) : L.cx;
+    double* bd = std::is_same<T, double>::value ? (double*)b(l) : L.cb;
+    bottom_fp64<T>(*this, l, xd, bd, &run_bottom);
   }
   int sub_mean(int l, double* v) override {
-    const Level& L = c->lv[l];
+    Level& L = c->lv[l];
     int st = reduce_to_device<1>(c, v, L.g.ncell, c->dres + 1);
     if (st) return st;
-    launch(c, kSlotNone, k_sub_mean<double>, grid_for(L.g.ncell), kThreads, v, L.g.ncell, c->dres + 1,
-                                                                       1.0 / (double)L.g.ncell);
+    launch(c, kSlotNone, k_sub_mean<double>, grid_for(L.g.ncell), kThreads, v, (long long)L.g.ncell,
+           (const double*)(c->dres + 1), 1.0 / (double)L.g.ncell);
     return cuda_check(c, cudaGetLastError(), "k_sub_mean");
   }
 };
 
-template <int D>
-struct NodalProblem : Problem {
-  double* x0;
-  NodalProblem(hbf_ctx* ctx, double* x_in) : Problem(ctx, true), x0(x_in) {}
-  double* x(int l) override { return l == 0 ? x0 : c->lv[l].nx; }
-  double* b(int l) override { return c->lv[l].nb; }
-  double* r(int l) override { return c->lv[l].nr; }
+template <int D, typename T>
+struct NodalProblem : Problem<T> {
+  using Problem<T>::c;
+  T* x0;
+  NodalProblem(hbf_ctx* ctx, T* x_in) : Problem<T>(ctx, true, true), x0(x_in) {}
+  T* x(int l) override { return l == 0 ? x0 : View<T>::nx(c->lv[l]); }
+  T* b(int l) override { return View<T>::nb(c->lv[l]); }
+  T* r(int l) override { return View<T>::nr(c->lv[l]); }
   long long count(int l) override { return c->lv[l].g.nnode; }
   void smooth(int l) override {
-    const Level& L = c->lv[l];
+    Level& L = c->lv[l];
     for (int col = 0; col < (1 << D); ++col)
-      launch(c, l == 0 ? kSlotNodalSmooth : kSlotNone, k_nodal_smooth<D, double>, grid_for(mc_count<D>(L.g, col)),
-             kThreads, x(l), L.nb, L.g, col);
+      launch(c, l == 0 ? kSlotNodalSmooth : kSlotNone, k_nodal_smooth<D, T>, grid_for(mc_count<D>(L.g, col)),
+             kThreads, x(l), b(l), L.g, col);
   }
   void resid(int l) override {
-    const Level& L = c->lv[l];
-    launch(c, l == 0 ? kSlotNodalResid : kSlotNone, k_nodal_resid<D, double>, grid_for(L.g.nnode), kThreads, x(l), L.nb, L.nr, L.g);
+    Level& L = c->lv[l];
+    launch(c, l == 0 ? kSlotNodalResid : kSlotNone, k_nodal_resid<D, T>, grid_for(L.g.nnode), kThreads, x(l), b(l),
+           r(l), L.g);
   }
   void restrict_to(int l) override {
-    const Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_restrict_nodes<D, double>, grid_for(C.g.nnode), kThreads, F.nr, C.nb, F.g, C.g);
-    launch(c, kSlotNone, k_zero<double>, grid_for(C.g.nnode), kThreads, C.nx, C.g.nnode);
+    Level &F = c->lv[l], &C = c->lv[l + 1];
+    launch(c, kSlotNone, k_restrict_nodes<D, T>, grid_for(C.g.nnode), kThreads, r(l), b(l + 1), F.g, C.g);
+    launch(c, kSlotNone, k_zero<T>, grid_for(C.g.nnode), kThreads, x(l + 1), (long long)C.g.nnode);
   }
   void prolong_add(int l) override {
-    const Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_prolong_nodes_add<D, double>, grid_for(F.g.nnode), kThreads, x(l), C.nx, F.g, C.g);
+    Level &F = c->lv[l], &C = c->lv[l + 1];
+    launch(c, kSlotNone, k_prolong_nodes_add<D, T>, grid_for(F.g.nnode), kThreads, x(l), x(l + 1), F.g, C.g);
+  }
+  static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
+    Level& L = P.c->lv[l];
+    launch(P.c, kSlotNone, k_nodal_bottom<D, double>, 1, 1024, xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
   }
   void bottom(int l) override {
-    const Level& L = c->lv[l];
-    launch(c, kSlotNone, k_nodal_bottom<D, double>, 1, 1024, x(l), L.nb, L.g, c->cfg.nu_bottom);
+    Level& L = c->lv[l];
+    double* xd = std::is_same<T, double>::value ? (double*)x(l) : L.nx;
+    double* bd = std::is_same<T, double>::value ? (double*)b(l) : L.nb;
+    bottom_fp64<T>(*this, l, xd, bd, &run_bottom);
   }
   int sub_mean(int l, double* v) override {
-    const Level& L = c->lv[l];
+    Level& L = c->lv[l];
     Geom gsave = c->g;
     c->g = L.g;  // the weighted reduction reads the level geometry from the context
     int st = reduce_to_device<2>(c, v, L.g.nnode, c->dres + 1);
     c->g = gsave;
     if (st) return st;
     double wsum = (double)L.g.n[0] * L.g.n[1] * (D == 3 ? L.g.n[2] : 1);
-    launch(c, kSlotNone, k_sub_mean<double>, grid_for(L.g.nnode), kThreads, v, L.g.nnode, c->dres + 1, 1.0 / wsum);
+    launch(c, kSlotNone, k_sub_mean<double>, grid_for(L.g.nnode), kThreads, v, (long long)L.g.nnode,
+           (const double*)(c->dres + 1), 1.0 / wsum);
     return cuda_check(c, cudaGetLastError(), "k_sub_mean");
   }
 };
 
-static void vcycle(Problem& P, int l, const SolverCfg& cfg) {
+template <typename T>
+static void vcycle(Problem<T>& P, int l, const SolverCfg& cfg) {
   if (l == P.nlev - 1) {
-    if (P.singular) P.sub_mean(l, P.b(l));
     P.bottom(l);
-    if (P.singular) P.sub_mean(l, P.x(l));
     return;
   }
   for (int s = 0; s < cfg.nu1; ++s) P.smooth(l);
@@ -289,7 +386,27 @@ static void vcycle(Problem& P, int l, const SolverCfg& cfg) {
   for (int s = 0; s < cfg.nu2; ++s) P.smooth(l);
 }
 
-static int mg_solve(Problem& P, const double* b_in, hbf_solve_stats* out) {
+static int finish(hbf_ctx* c, int cycles, double r0, double rn, double bnorm, double tol, hbf_solve_stats* out) {
+  hbf_solve_stats s;
+  s.cycles = cycles;
+  s.r0 = r0;
+  s.rnorm = rn;
+  s.bnorm = bnorm;
+  s.converged = rn <= tol;
+  if (out) *out = s;
+  if (!std::isfinite(rn) || !std::isfinite(bnorm)) return fail(c, HBF_ERR_NONFINITE, "non-finite residual norm");
+  if (!s.converged) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "multigrid did not converge: %d cycles, residual %.3e > tol %.3e", cycles, rn, tol);
+    return fail(c, HBF_ERR_NOT_CONVERGED, buf);
+  }
+  return HBF_OK;
+}
+
+// Plain FP64 multigrid (P64 only) or FP64 defect correction around FP32
+// V-cycles (P32 given): r = b - A x in FP64; solve A e = r by one FP32
+// V-cycle from e = 0; x += e in FP64; repeat to the same FP64 tolerance.
+static int mg_solve(Problem<double>& P, Problem<float>* P32, const double* b_in, hbf_solve_stats* out) {
   hbf_ctx* c = P.c;
   const SolverCfg& cfg = c->cfg;
   long long n0 = P.count(0);
@@ -310,7 +427,14 @@ static int mg_solve(Problem& P, const double* b_in, hbf_solve_stats* out) {
   double tol = cfg.rtol * bnorm;
   int cycles = 0;
   while (rn > tol && cycles < cfg.max_cycles && std::isfinite(rn)) {
-    vcycle(P, 0, cfg);
+    if (P32) {
+      launch(c, kSlotNone, k_convert<float, double>, grid_for(n0), kThreads, P32->b(0), (const double*)P.r(0), n0);
+      launch(c, kSlotNone, k_zero<float>, grid_for(n0), kThreads, P32->x(0), n0);
+      vcycle(*P32, 0, cfg);
+      launch(c, kSlotNone, k_add_f32, grid_for(n0), kThreads, P.x(0), (const float*)P32->x(0), n0);
+    } else {
+      vcycle(P, 0, cfg);
+    }
     ++cycles;
     if (P.singular && (st = P.sub_mean(0, P.x(0)))) return st;
     P.resid(0);
@@ -318,62 +442,68 @@ static int mg_solve(Problem& P, const double* b_in, hbf_solve_stats* out) {
     if (st) return st;
   }
   if ((st = cuda_check(c, cudaGetLastError(), "multigrid kernels"))) return st;
-  hbf_solve_stats s;
-  s.cycles = cycles;
-  s.r0 = r0;
-  s.rnorm = rn;
-  s.bnorm = bnorm;
-  s.converged = rn <= tol;
-  if (out) *out = s;
-  if (!std::isfinite(rn) || !std::isfinite(bnorm)) return fail(c, HBF_ERR_NONFINITE, "non-finite residual norm");
-  if (!s.converged) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "multigrid did not converge: %d cycles, residual %.3e > tol %.3e", cycles, rn, tol);
-    return fail(c, HBF_ERR_NOT_CONVERGED, buf);
-  }
-  return HBF_OK;
+  return finish(c, cycles, r0, rn, bnorm, tol, out);
 }
 
-// coarse-level face eta from the level-0 faces
+// coarse-level face eta from the level-0 faces (and FP32 copies when mixed)
 template <int D>
 static void build_eta_levels(hbf_ctx* c) {
   for (size_t l = 1; l < c->lv.size(); ++l) {
-    const Level &F = c->lv[l - 1], &C = c->lv[l];
+    Level &F = c->lv[l - 1], &C = c->lv[l];
     for (int a = 0; a < D; ++a)
-      launch(c, kSlotNone, k_restrict_faces<D, double>, grid_for(C.g.nface[a]), kThreads, F.ef[a], C.ef[a], a, F.g,
-                                                                                       C.g);
+      launch(c, kSlotNone, k_restrict_faces<D, double>, grid_for(C.g.nface[a]), kThreads, (const double*)F.ef[a],
+             C.ef[a], a, F.g, C.g);
   }
+  if (c->precision == HBF_MIXED)
+    for (auto& L : c->lv)
+      for (int a = 0; a < D; ++a)
+        launch(c, kSlotNone, k_convert<float, double>, grid_for(L.g.nface[a]), kThreads, L.fef[a],
+               (const double*)L.ef[a], (long long)L.g.nface[a]);
+}
+
+template <int D>
+static int solve_viscous_d(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s) {
+  build_eta_levels<D>(c);
+  ViscProblem<D, double> P(c, u, beta, false);
+  if (c->precision == HBF_MIXED) {
+    ViscProblem<D, float> P32(c, c->lv[0].fvx, beta, true);
+    return mg_solve(P, &P32, rhs, s);
+  }
+  return mg_solve(P, nullptr, rhs, s);
 }
 
 int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s) {
   int st = launch_eta_faces(c);
   if (st) return st;
-  if (c->dim == 2) {
-    build_eta_levels<2>(c);
-    ViscProblem<2> P(c, u, beta);
-    return mg_solve(P, rhs, s);
+  return c->dim == 2 ? solve_viscous_d<2>(c, beta, rhs, u, s) : solve_viscous_d<3>(c, beta, rhs, u, s);
+}
+
+template <int D>
+static int solve_mac_d(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s) {
+  MacProblem<D, double> P(c, phi);
+  if (c->precision == HBF_MIXED) {
+    MacProblem<D, float> P32(c, c->lv[0].fcx);
+    return mg_solve(P, &P32, rhs, s);
   }
-  build_eta_levels<3>(c);
-  ViscProblem<3> P(c, u, beta);
-  return mg_solve(P, rhs, s);
+  return mg_solve(P, nullptr, rhs, s);
 }
 
 int solve_mac(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s) {
-  if (c->dim == 2) {
-    MacProblem<2> P(c, phi);
-    return mg_solve(P, rhs, s);
+  return c->dim == 2 ? solve_mac_d<2>(c, rhs, phi, s) : solve_mac_d<3>(c, rhs, phi, s);
+}
+
+template <int D>
+static int solve_nodal_d(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s) {
+  NodalProblem<D, double> P(c, phi);
+  if (c->precision == HBF_MIXED) {
+    NodalProblem<D, float> P32(c, c->lv[0].fnx);
+    return mg_solve(P, &P32, rhs, s);
   }
-  MacProblem<3> P(c, phi);
-  return mg_solve(P, rhs, s);
+  return mg_solve(P, nullptr, rhs, s);
 }
 
 int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s) {
-  if (c->dim == 2) {
-    NodalProblem<2> P(c, phi);
-    return mg_solve(P, rhs, s);
-  }
-  NodalProblem<3> P(c, phi);
-  return mg_solve(P, rhs, s);
+  return c->dim == 2 ? solve_nodal_d<2>(c, rhs, phi, s) : solve_nodal_d<3>(c, rhs, phi, s);
 }
 
 }  // namespace hb

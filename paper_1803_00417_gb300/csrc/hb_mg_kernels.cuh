@@ -21,16 +21,16 @@ namespace hb {
 template <int D, typename T>
 __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
                                   bool hom) {
+  // mean of the two cells' central differences, (dL + dR)/2 with dL, dR over 2h
   if (L[a] < 0 || L[a] >= g.n[a] - 1) return T(0);
-  T two_h = T(2) * T(g.h);
   int p1[3] = {L[0], L[1], L[2]}, p0[3] = {L[0], L[1], L[2]};
   p1[c] += 1;
   p0[c] -= 1;
-  T dL = (uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom)) / two_h;
+  T dL = uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom);
   p1[a] += 1;
   p0[a] += 1;
-  T dR = (uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom)) / two_h;
-  return T(0.5) * (dL + dR);
+  T dR = uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom);
+  return (dL + dR) * T(0.25 / g.h);
 }
 
 template <int D, typename T>
@@ -38,7 +38,7 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const T* c
                                     const int* p, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
   T acc = T(0);
-  T h = T(g.h);
+  const T ih = T(1.0 / g.h);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T flux[2];
@@ -49,13 +49,13 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const T* c
       int R[3] = {L[0], L[1], L[2]};
       R[a] += 1;
       T e = ef[a][fidx(g, a, R[0], R[1], R[2])];
-      T nrm = (uget<D>(uc, g, c, R[0], R[1], R[2], hom) - uget<D>(uc, g, c, L[0], L[1], L[2], hom)) / h;
+      T nrm = (uget<D>(uc, g, c, R[0], R[1], R[2], hom) - uget<D>(uc, g, c, L[0], L[1], L[2], hom)) * ih;
       if (a == c)
         flux[s] = e * (T(2) * nrm);
       else
         flux[s] = e * (nrm + mg_face_cross<D, T>(u + (size_t)a * g.ncell, g, a, c, L, hom));
     }
-    acc += (flux[1] - flux[0]) / h;
+    acc += (flux[1] - flux[0]) * ih;
   }
   return acc;
 }
@@ -65,8 +65,8 @@ template <int D, typename T>
 __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
                                   const Geom& g, int c, const int* p, T beta, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
-  T h = T(g.h);
-  T hh = h * h;
+  const T ih = T(1.0 / g.h);
+  const T ihh = T(1.0 / (g.h * g.h));
   T offd = T(0), diag = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -81,7 +81,7 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
         q[a] += 1;
         fq[a] += 1;
       }
-      T wf = kappa * ef[a][fidx(g, a, fq[0], fq[1], fq[2])] / hh;
+      T wf = kappa * ef[a][fidx(g, a, fq[0], fq[1], fq[2])] * ihh;
       bool wall = (s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1);
       if (wall) {
         T ub = hom ? T(0) : T(g.wu[a][s][c]);
@@ -104,7 +104,7 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
     fhi[a] += 1;
     T fluxhi = ef[a][fidx(g, a, fhi[0], fhi[1], fhi[2])] * mg_face_cross<D, T>(ua, g, a, c, p, hom);
     T fluxlo = ef[a][fidx(g, a, p[0], p[1], p[2])] * mg_face_cross<D, T>(ua, g, a, c, Llo, hom);
-    cross += (fluxhi - fluxlo) / h;
+    cross += (fluxhi - fluxlo) * ih;
   }
   return (b[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] + beta * (offd + cross)) /
          (T(1) + beta * diag);
@@ -209,8 +209,8 @@ __host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __r
     }
     s += lo + hi;
   }
-  T h = T(g.h);
-  return (s - h * h * b[cidx<D>(g, p[0], p[1], p[2])]) / T(cnt);
+  T hh = T(g.h * g.h);
+  return (s - hh * b[cidx<D>(g, p[0], p[1], p[2])]) / T(cnt);
 }
 
 template <int D, typename T>
@@ -225,7 +225,7 @@ __global__ void k_cell_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g
 
 template <int D, typename T>
 __global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
-  T h = T(g.h);
+  const T ih = T(1.0 / g.h);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
@@ -237,14 +237,14 @@ __global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T
       if (p[a] > 0) {
         int q[3] = {p[0], p[1], p[2]};
         q[a] -= 1;
-        glo = (xc - x[cidx<D>(g, q[0], q[1], q[2])]) / h;
+        glo = (xc - x[cidx<D>(g, q[0], q[1], q[2])]) * ih;
       }
       if (p[a] < g.n[a] - 1) {
         int q[3] = {p[0], p[1], p[2]};
         q[a] += 1;
-        ghi = (x[cidx<D>(g, q[0], q[1], q[2])] - xc) / h;
+        ghi = (x[cidx<D>(g, q[0], q[1], q[2])] - xc) * ih;
       }
-      acc += (ghi - glo) / h;
+      acc += (ghi - glo) * ih;
     }
     r[t] = b[t] - acc;
   }
@@ -330,35 +330,35 @@ __host__ __device__ inline int mc_count(const Geom& g, int col) {
 template <int D, typename T>
 __global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g, int col) {
   int nt = mc_count<D>(g, col);
-  T hh = T(g.h) * T(g.h);
-  T s0 = fe_weight<D, T>(0);
+  const T hh = T(g.h * g.h);
+  const T is0 = T(-3.0 / 8.0);  // 1 / centre weight
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     int p[3];
     if (!mc_node<D>(g, t, col, p)) continue;
     int id = nidx(g, p[0], p[1], p[2]);
     T s = nodal_lap_point<D, T>(x, g, p, true);
-    x[id] = (hh * b[id] - s) / s0;
+    x[id] = (hh * b[id] - s) * is0;
   }
 }
 
 template <int D, typename T>
 __global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
   int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
-  T hh = T(g.h) * T(g.h);
+  const T ihh = T(1.0 / (g.h * g.h));
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
     int p[3];
     p[0] = t % e0;
     int q = t / e0;
     p[1] = q % e1;
     p[2] = q / e1;
-    r[t] = b[t] - nodal_lap_point<D, T>(x, g, p, false) / hh;
+    r[t] = b[t] - nodal_lap_point<D, T>(x, g, p, false) * ihh;
   }
 }
 
 template <int D, typename T>
 __global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom g, int nsweep) {
-  T hh = T(g.h) * T(g.h);
-  T s0 = fe_weight<D, T>(0);
+  const T hh = T(g.h * g.h);
+  const T is0 = T(-3.0 / 8.0);
   const int ncol = 1 << D;
   for (int sw = 0; sw < nsweep; ++sw)
     for (int col = 0; col < ncol; ++col) {
@@ -368,7 +368,7 @@ __global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom 
         if (!mc_node<D>(g, t, col, p)) continue;
         int id = nidx(g, p[0], p[1], p[2]);
         T s = nodal_lap_point<D, T>(x, g, p, true);
-        x[id] = (hh * b[id] - s) / s0;
+        x[id] = (hh * b[id] - s) * is0;
       }
       __syncthreads();
     }
