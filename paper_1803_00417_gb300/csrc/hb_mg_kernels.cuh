@@ -110,6 +110,107 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
          (T(1) + beta * diag);
 }
 
+// Strides of the cell array and of the face arrays (face array a, axis b).
+struct Strides {
+  int s[3];
+  int fs[3][3];
+};
+
+__host__ __device__ inline Strides make_strides(const Geom& g) {
+  Strides st;
+  st.s[0] = 1;
+  st.s[1] = g.n[0];
+  st.s[2] = g.n[0] * g.n[1];
+  for (int a = 0; a < 3; ++a) {
+    int ex = g.n[0] + (a == 0), ey = g.n[1] + (a == 1);
+    st.fs[a][0] = 1;
+    st.fs[a][1] = ex;
+    st.fs[a][2] = ex * ey;
+  }
+  return st;
+}
+
+template <int D>
+__host__ __device__ inline bool interior(const Geom& g, const int* p) {
+  bool in = p[0] >= 1 && p[0] <= g.n[0] - 2 && p[1] >= 1 && p[1] <= g.n[1] - 2;
+  if (D == 3) in = in && p[2] >= 1 && p[2] <= g.n[2] - 2;
+  return in;
+}
+
+// The same Gauss-Seidel update as visc_gs_point for a cell whose whole
+// stencil is inside the domain: direct strided indexing, no ghost logic.
+template <int D, typename T>
+__host__ __device__ inline T visc_gs_interior(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
+                                              const Geom& g, const Strides& S, int c, const int* p, T beta) {
+  const int id = cidx<D>(g, p[0], p[1], p[2]);
+  const T* uc = u + (size_t)c * g.ncell;
+  const T ih = T(1.0 / g.h);
+  const T ihh = T(1.0 / (g.h * g.h));
+  const T q = T(0.25 / g.h);
+  int fid[3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) fid[a] = fidx(g, a, p[0], p[1], p[2]);
+  T offd = T(0), diag = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    T kappa = (a == c) ? T(2) : T(1);
+    T wlo = kappa * ef[a][fid[a]] * ihh;
+    offd += wlo * uc[id - S.s[a]];
+    diag += wlo;
+    T whi = kappa * ef[a][fid[a] + S.fs[a][a]] * ihh;
+    offd += whi * uc[id + S.s[a]];
+    diag += whi;
+  }
+  T cross = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (a == c) continue;
+    const T* ua = u + (size_t)a * g.ncell;
+    const int sa = S.s[a], sc = S.s[c];
+    T mid = ua[id + sc] - ua[id - sc];
+    T xhi = (mid + (ua[id + sa + sc] - ua[id + sa - sc])) * q;
+    T xlo = ((ua[id - sa + sc] - ua[id - sa - sc]) + mid) * q;
+    T fluxhi = ef[a][fid[a] + S.fs[a][a]] * xhi;
+    T fluxlo = ef[a][fid[a]] * xlo;
+    cross += (fluxhi - fluxlo) * ih;
+  }
+  return (b[(size_t)c * g.ncell + id] + beta * (offd + cross)) / (T(1) + beta * diag);
+}
+
+// (L_eta u)_c for an interior cell, same arithmetic as mg_tensor_point
+template <int D, typename T>
+__host__ __device__ inline T tensor_interior(const T* __restrict__ u, const T* const* ef, const Geom& g,
+                                             const Strides& S, int c, const int* p) {
+  const int id = cidx<D>(g, p[0], p[1], p[2]);
+  const T* uc = u + (size_t)c * g.ncell;
+  const T ih = T(1.0 / g.h);
+  const T q = T(0.25 / g.h);
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int fid = fidx(g, a, p[0], p[1], p[2]);
+    const int sa = S.s[a];
+    T u0 = uc[id];
+    T nlo = (u0 - uc[id - sa]) * ih;
+    T nhi = (uc[id + sa] - u0) * ih;
+    T flo, fhi;
+    if (a == c) {
+      flo = ef[a][fid] * (T(2) * nlo);
+      fhi = ef[a][fid + S.fs[a][a]] * (T(2) * nhi);
+    } else {
+      const T* ua = u + (size_t)a * g.ncell;
+      const int sc = S.s[c];
+      T mid = ua[id + sc] - ua[id - sc];
+      T xhi = (mid + (ua[id + sa + sc] - ua[id + sa - sc])) * q;
+      T xlo = ((ua[id - sa + sc] - ua[id - sa - sc]) + mid) * q;
+      flo = ef[a][fid] * (nlo + xlo);
+      fhi = ef[a][fid + S.fs[a][a]] * (nhi + xhi);
+    }
+    acc += (fhi - flo) * ih;
+  }
+  return acc;
+}
+
 // thread t -> cell of red-black colour col (x index stride 2)
 template <int D>
 __host__ __device__ inline bool rb_cell(const Geom& g, int t, int col, int* p) {
@@ -140,11 +241,13 @@ template <int D, typename T>
 __global__ void k_visc_smooth(T* __restrict__ u, const T* __restrict__ b, const T* ef0, const T* ef1,
                               const T* ef2, Geom g, int c, int col, T beta, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
+  const Strides S = make_strides(g);
   int nt = rb_count<D>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     int p[3];
     if (!rb_cell<D>(g, t, col, p)) continue;
-    T v = visc_gs_point<D, T>(u, b, ef, g, c, p, beta, hom != 0);
+    T v = interior<D>(g, p) ? visc_gs_interior<D, T>(u, b, ef, g, S, c, p, beta)
+                            : visc_gs_point<D, T>(u, b, ef, g, c, p, beta, hom != 0);
     u[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
   }
 }
@@ -153,13 +256,15 @@ template <int D, typename T>
 __global__ void k_visc_resid(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ r,
                              const T* ef0, const T* ef1, const T* ef2, Geom g, T beta, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
+  const Strides S = make_strides(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
+    const bool in = interior<D>(g, p);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       size_t o = (size_t)c * g.ncell + t;
-      T Lu = mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+      T Lu = in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
       r[o] = b[o] - (u[o] - beta * Lu);
     }
   }
