@@ -215,13 +215,15 @@ def _nb(d, a, s):
 class TensorViscous:
     """(I - beta L_eta) u = b, beta = dt / (2 rho), all d components coupled
     through the cross terms of L_eta (Eq. 16).  Level 0 carries the wall
-    velocities, coarse levels the homogeneous error equation."""
+    velocities (unless ``hom0``), coarse levels the homogeneous error
+    equation."""
 
     singular = False
 
-    def __init__(self, grid, eta, beta):
+    def __init__(self, grid, eta, beta, hom0=False):
         self.levels = build_levels(grid)
         self.beta = beta
+        self.hom0 = hom0
         self.etas = [face_eta_all(eta, grid)]
         for l in range(1, len(self.levels)):
             self.etas.append(restrict_faces(self.etas[-1], self.levels[l - 1]))
@@ -230,14 +232,14 @@ class TensorViscous:
 
     def apply(self, l, u):
         g = self.levels[l]
-        Lu = tensor_op(u, self.etas[l], g, homogeneous=(l > 0))
+        Lu = tensor_op(u, self.etas[l], g, homogeneous=(l > 0 or self.hom0))
         return [u[c] - self.beta * Lu[c] for c in range(g.d)]
 
     def smooth(self, l, u, b):
         g = self.levels[l]
         d, h = g.d, g.h
         eta = self.etas[l]
-        hom = l > 0
+        hom = l > 0 or self.hom0
         for c in range(d):
             cross = tensor_cross_part(u, eta, g, c, homogeneous=hom)
             for col in (0, 1):
@@ -370,3 +372,72 @@ def mg_solve(prob, x, b, params):
             prob.sub_mean(0, x)
         rn = _max_abs(_residual(prob, 0, x, b))
     return x, SolveStats(cycles, r0, rn, bnorm, rn <= tol)
+
+
+def _dot(a, b):
+    return sum(float(np.sum(x * y)) for x, y in zip(a, b))
+
+
+def bicgstab_solve(prob, x, b, params):
+    """BiCGStab (van der Vorst 1992) on (I - beta L_eta) u = b, right-
+    preconditioned by one V-cycle of the homogeneous operator from a zero
+    guess.  The V-cycle alone is not a convergent iteration for every
+    viscosity field the regularised law produces (at large contrast the
+    component-wise smoother with frozen cross terms can diverge), but it is a
+    good preconditioner.  Stops when the recursive residual meets
+    ||r||_inf <= rtol ||b||_inf and the true residual confirms it; otherwise
+    restarts from the true residual.  ``cycles`` counts BiCGStab iterations
+    (two V-cycles each)."""
+    b = [np.array(bc, dtype=np.float64) for bc in b]
+    pre = TensorViscous.__new__(TensorViscous)
+    pre.__dict__.update(prob.__dict__)
+    pre.hom0 = True
+    d = len(b)
+
+    def A0(e):
+        return pre.apply(0, e)
+
+    def M(r):
+        e = pre.zeros(0)
+        vcycle(pre, 0, e, [rc.copy() for rc in r], params)
+        return e
+
+    bnorm = _max_abs(b)
+    r = _residual(prob, 0, x, b)
+    rn = _max_abs(r)
+    r0 = rn
+    if bnorm == 0.0:
+        bnorm = rn
+    tol = params.rtol * bnorm
+    it = 0
+    while rn > tol and it < params.max_cycles:
+        rhat = [rc.copy() for rc in r]
+        rho = alpha = omega = 1.0
+        v = [np.zeros_like(rc) for rc in r]
+        p = [np.zeros_like(rc) for rc in r]
+        while it < params.max_cycles:
+            rho1 = _dot(rhat, r)
+            if rho1 == 0.0:
+                break
+            beta = (rho1 / rho) * (alpha / omega)
+            p = [r[c] + beta * (p[c] - omega * v[c]) for c in range(d)]
+            phat = M(p)
+            v = A0(phat)
+            den = _dot(rhat, v)
+            if den == 0.0:
+                break
+            alpha = rho1 / den
+            s = [r[c] - alpha * v[c] for c in range(d)]
+            shat = M(s)
+            t = A0(shat)
+            tt = _dot(t, t)
+            omega = _dot(t, s) / tt if tt > 0.0 else 0.0
+            x = [x[c] + alpha * phat[c] + omega * shat[c] for c in range(d)]
+            r = [s[c] - omega * t[c] for c in range(d)]
+            rho = rho1
+            it += 1
+            if _max_abs(r) <= tol or omega == 0.0:
+                break
+        r = _residual(prob, 0, x, b)
+        rn = _max_abs(r)
+    return x, SolveStats(it, r0, rn, bnorm, rn <= tol)

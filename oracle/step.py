@@ -12,7 +12,8 @@ Order of the step:
  5. upwinding by u^MAC and the convective term; right-hand side of Eq. 16:
     b = u^m - dt [u^MAC . grad u~] + dt/rho (-G p + 1/2 L_eta u^m + f).
  6. (I - dt/(2 rho) L_eta^m) u* = b, walls at their (constant) velocity
-    (Eq. 16; L_eta u = 2 div(eta gamma_dot)).
+    (Eq. 16; L_eta u = 2 div(eta gamma_dot)), by V-cycle-preconditioned
+    BiCGStab (the paper leaves the solver to AMReX).
  7. nodal projection L phi = rho D(u*/dt + G p^{m-1/2}/rho) (Eq. 17),
     u^{m+1} = u* + dt/rho (G p^{m-1/2} - G phi), p^{m+1/2} = phi.
     Eq. 18 prints u^{m+1} = u* - dt/rho G phi, which is inconsistent with the
@@ -24,7 +25,7 @@ import numpy as np
 from .godunov import advective_term, face_states
 from .grid import node_weights, nodes_full, nodes_unique, sl
 from .multigrid import (CellPoisson, NodalPoisson, SolveStats, SolverParams, TensorViscous,
-                        mg_solve)
+                        bicgstab_solve, mg_solve)
 from .operators import (cell_grad_nodal, face_eta_all, mac_div, mac_grad, nodal_div, tensor_op)
 from .rheology import cell_viscosity
 
@@ -80,7 +81,7 @@ def step(grid, u, p, dt, rheo, rho=1.0, f=None, params=None, keep=False, predict
     rhs = [u[c] - dt * A[c] + (dt / rho) * (-Gp[c] + 0.5 * Lu[c] + f[c]) for c in range(d)]
 
     visc = TensorViscous(grid, eta, dt / (2.0 * rho))
-    ustar, st_visc = mg_solve(visc, [uc.copy() for uc in u], rhs, params)
+    ustar, st_visc = bicgstab_solve(visc, [uc.copy() for uc in u], rhs, params)
 
     w = node_weights(grid)
     v = [ustar[c] / dt + Gp[c] / rho for c in range(d)]

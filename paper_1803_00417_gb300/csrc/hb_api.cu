@@ -100,6 +100,15 @@ static int allocate(hbf_ctx* c) {
     A(c->uadv[a], g.nface[a]);
     A(c->umac[a], g.nface[a]);
   }
+  A(c->kb, (long long)D * g.ncell);
+  A(c->kr, (long long)D * g.ncell);
+  A(c->krh, (long long)D * g.ncell);
+  A(c->kp, (long long)D * g.ncell);
+  A(c->kv, (long long)D * g.ncell);
+  A(c->ks, (long long)D * g.ncell);
+  A(c->kt, (long long)D * g.ncell);
+  A(c->kph, (long long)D * g.ncell);
+  A(c->ksh, (long long)D * g.ncell);
   A(c->partial, kRedBlocks);
   A(c->dres, 8);
   if (cudaMallocHost((void**)&c->hres, 8 * sizeof(double)) != cudaSuccess)

@@ -97,6 +97,9 @@ struct hbf_ctx {
   double* phi_mac = nullptr;  // ncell
   double* mrhs = nullptr;     // ncell, MAC right-hand side
   double* nrhs = nullptr;     // nnode
+  // BiCGStab vectors of the viscous solve (d*ncell each)
+  double *kb = nullptr, *kr = nullptr, *krh = nullptr, *kp = nullptr, *kv = nullptr, *ks = nullptr,
+         *kt = nullptr, *kph = nullptr, *ksh = nullptr;
   // reductions
   double* partial = nullptr;  // kRedBlocks doubles
   double* dres = nullptr;     // device result slot(s)
@@ -141,6 +144,7 @@ int launch_eta_faces(hbf_ctx* c);
 // reductions (hb_mg.cu)
 double reduce_max_abs(hbf_ctx* c, const double* x, long long n, int* st);
 double reduce_sum(hbf_ctx* c, const double* x, long long n, int* st);
+double reduce_dot(hbf_ctx* c, const double* a, const double* b, long long n, int* st);
 
 // solves (hb_mg.cu)
 int solve_mac(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);

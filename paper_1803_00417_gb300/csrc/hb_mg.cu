@@ -100,6 +100,23 @@ __global__ void k_zero(T* __restrict__ x, long long n) {
     x[t] = T(0);
 }
 
+__global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                              double* __restrict__ part) {
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    acc += a[t] * b[t];
+  __shared__ double sh[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
 template <int MODE>
 static int reduce_to_device(hbf_ctx* c, const double* x, long long n, double* out) {
   launch(c, kSlotNone, k_reduce_partial<MODE>, kRedBlocks, kThreads, x, n, c->partial, c->g, c->dim);
@@ -119,6 +136,14 @@ static double read_result(hbf_ctx* c, const double* dev, int* st) {
 
 double reduce_max_abs(hbf_ctx* c, const double* x, long long n, int* st) {
   *st = reduce_to_device<0>(c, x, n, c->dres);
+  if (*st) return NAN;
+  return read_result(c, c->dres, st);
+}
+
+double reduce_dot(hbf_ctx* c, const double* a, const double* b, long long n, int* st) {
+  launch(c, kSlotNone, k_dot_partial, kRedBlocks, kThreads, a, b, n, c->partial);
+  launch(c, kSlotNone, k_reduce_final<1>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
+  *st = cuda_check(c, cudaGetLastError(), "dot");
   if (*st) return NAN;
   return read_result(c, c->dres, st);
 }
@@ -144,6 +169,30 @@ __global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ e, l
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
     x[t] += (double)e[t];
+}
+
+// p = r + beta (p - omega v)
+__global__ void k_bicg_p(double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ v,
+                         double beta, double omega, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    p[t] = r[t] + beta * (p[t] - omega * v[t]);
+}
+
+// out = x - a y
+__global__ void k_axmy(double* __restrict__ out, const double* __restrict__ x, double a,
+                       const double* __restrict__ y, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = x[t] - a * y[t];
+}
+
+// x = x + alpha ph + omega sh
+__global__ void k_bicg_x(double* __restrict__ x, const double* __restrict__ ph, const double* __restrict__ sh,
+                         double alpha, double omega, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    x[t] = x[t] + alpha * ph[t] + omega * sh[t];
 }
 
 // ---------------------------------------------------------------------------
@@ -386,6 +435,8 @@ static void vcycle(Problem<T>& P, int l, const SolverCfg& cfg) {
   for (int s = 0; s < cfg.nu2; ++s) P.smooth(l);
 }
 
+static inline int l0slot() { return kSlotViscResid; }
+
 static int finish(hbf_ctx* c, int cycles, double r0, double rn, double bnorm, double tol, hbf_solve_stats* out) {
   hbf_solve_stats s;
   s.cycles = cycles;
@@ -461,15 +512,98 @@ static void build_eta_levels(hbf_ctx* c) {
                (const double*)L.ef[a], (long long)L.g.nface[a]);
 }
 
+// BiCGStab (van der Vorst 1992) on (I - beta L_eta) u = b, right-preconditioned
+// by one V-cycle of the homogeneous operator from a zero guess (FP64, or FP32
+// in mixed mode).  The V-cycle alone does not converge for every viscosity
+// field of the regularised law; as a preconditioner it does.  Stops when the
+// recursive residual meets the tolerance and the true FP64 residual confirms
+// it; otherwise restarts from the true residual.  cycles = iterations.
 template <int D>
-static int solve_viscous_d(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s) {
+static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* x, hbf_solve_stats* out) {
   build_eta_levels<D>(c);
-  ViscProblem<D, double> P(c, u, beta, false);
-  if (c->precision == HBF_MIXED) {
-    ViscProblem<D, float> P32(c, c->lv[0].fvx, beta, true);
-    return mg_solve(P, &P32, rhs, s);
+  const SolverCfg& cfg = c->cfg;
+  Level& L0 = c->lv[0];
+  const long long n = (long long)D * L0.g.ncell;
+  const size_t bytes = (size_t)n * sizeof(double);
+  const int nb = grid_for(n);
+  double *kb = c->kb, *r = c->kr, *rh = c->krh, *p = c->kp, *v = c->kv, *s = c->ks, *t = c->kt, *ph = c->kph,
+         *sh = c->ksh;
+  ViscProblem<D, double> P(c, x, beta, false);
+  ViscProblem<D, float> Pre32(c, L0.fvx, beta, true);
+  const bool mixed = c->precision == HBF_MIXED;
+  int st;
+  auto true_residual = [&]() -> double {
+    cudaMemcpyAsync(L0.vb, kb, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    P.resid(0);
+    cudaMemcpyAsync(r, L0.vr, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    return reduce_max_abs(c, r, n, &st);
+  };
+  // z = M^{-1} q
+  auto precond = [&](const double* q, double* z) {
+    if (mixed) {
+      launch(c, kSlotNone, k_convert<float, double>, nb, kThreads, L0.fvb, q, n);
+      launch(c, kSlotNone, k_zero<float>, nb, kThreads, L0.fvx, n);
+      vcycle(Pre32, 0, cfg);
+      launch(c, kSlotNone, k_convert<double, float>, nb, kThreads, z, (const float*)L0.fvx, n);
+    } else {
+      ViscProblem<D, double> Pz(c, z, beta, true);
+      cudaMemcpyAsync(L0.vb, q, bytes, cudaMemcpyDeviceToDevice, c->stream);
+      launch(c, kSlotNone, k_zero<double>, nb, kThreads, z, n);
+      vcycle(Pz, 0, cfg);
+    }
+  };
+  auto apply0 = [&](const double* q, double* out_) {
+    launch(c, l0slot(), k_visc_apply<D, double>, grid_for(L0.g.ncell), kThreads, q, out_, (const double*)L0.ef[0],
+           (const double*)L0.ef[1], (const double*)L0.ef[2], L0.g, beta, 1);
+  };
+  if ((st = cuda_check(c, cudaMemcpyAsync(kb, b_in, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy rhs")))
+    return st;
+  double bnorm = reduce_max_abs(c, kb, n, &st);
+  if (st) return st;
+  double rn = true_residual();
+  if (st) return st;
+  double r0 = rn;
+  if (bnorm == 0.0) bnorm = rn;
+  const double tol = cfg.rtol * bnorm;
+  int it = 0;
+  while (rn > tol && it < cfg.max_cycles && std::isfinite(rn)) {
+    cudaMemcpyAsync(rh, r, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    launch(c, kSlotNone, k_zero<double>, nb, kThreads, v, n);
+    launch(c, kSlotNone, k_zero<double>, nb, kThreads, p, n);
+    while (it < cfg.max_cycles) {
+      double rho1 = reduce_dot(c, rh, r, n, &st);
+      if (st) return st;
+      if (rho1 == 0.0 || !std::isfinite(rho1)) break;
+      double bt = (rho1 / rho) * (alpha / omega);
+      launch(c, kSlotNone, k_bicg_p, nb, kThreads, p, (const double*)r, (const double*)v, bt, omega, n);
+      precond(p, ph);
+      apply0(ph, v);
+      double den = reduce_dot(c, rh, v, n, &st);
+      if (st) return st;
+      if (den == 0.0 || !std::isfinite(den)) break;
+      alpha = rho1 / den;
+      launch(c, kSlotNone, k_axmy, nb, kThreads, s, (const double*)r, alpha, (const double*)v, n);
+      precond(s, sh);
+      apply0(sh, t);
+      double tt = reduce_dot(c, t, t, n, &st);
+      if (st) return st;
+      double ts = reduce_dot(c, t, s, n, &st);
+      if (st) return st;
+      omega = tt > 0.0 ? ts / tt : 0.0;
+      launch(c, kSlotNone, k_bicg_x, nb, kThreads, x, (const double*)ph, (const double*)sh, alpha, omega, n);
+      launch(c, kSlotNone, k_axmy, nb, kThreads, r, (const double*)s, omega, (const double*)t, n);
+      rho = rho1;
+      ++it;
+      double rr = reduce_max_abs(c, r, n, &st);
+      if (st) return st;
+      if (rr <= tol || omega == 0.0 || !std::isfinite(rr)) break;
+    }
+    rn = true_residual();
+    if (st) return st;
   }
-  return mg_solve(P, nullptr, rhs, s);
+  if ((st = cuda_check(c, cudaGetLastError(), "viscous solve"))) return st;
+  return finish(c, it, r0, rn, bnorm, tol, out);
 }
 
 int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s) {

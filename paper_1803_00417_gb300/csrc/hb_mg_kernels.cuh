@@ -270,6 +270,25 @@ __global__ void k_visc_resid(const T* __restrict__ u, const T* __restrict__ b, T
   }
 }
 
+// out = u - beta L_eta u (the operator itself, for the Krylov iteration)
+template <int D, typename T>
+__global__ void k_visc_apply(const T* __restrict__ u, T* __restrict__ out, const T* ef0, const T* ef1,
+                             const T* ef2, Geom g, T beta, int hom) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  const Strides S = make_strides(g);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    int p[3];
+    cell_coords<D>(g, t, p[0], p[1], p[2]);
+    const bool in = interior<D>(g, p);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      size_t o = (size_t)c * g.ncell + t;
+      T Lu = in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+      out[o] = u[o] - beta * Lu;
+    }
+  }
+}
+
 // coarsest level: all sweeps in one block
 template <int D, typename T>
 __global__ void k_visc_bottom(T* __restrict__ u, const T* __restrict__ b, const T* ef0, const T* ef1,

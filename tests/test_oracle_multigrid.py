@@ -168,3 +168,23 @@ def test_singular_solve_mean_and_zero_rhs():
     b = rng.normal(size=(8, 8))
     x, st = mg_solve(prob, [np.zeros((8, 8))], [b], SolverParams())
     assert st.converged and abs(np.mean(x[0])) < 1e-14
+
+
+@pytest.mark.parametrize("n", [(8, 8), (4, 4, 4)])
+def test_tensor_viscous_bicgstab_matches_dense(n):
+    from oracle.multigrid import bicgstab_solve
+
+    d = len(n)
+    wall = np.zeros((d, 2, d))
+    wall[d - 1, 1, 0] = 1.0
+    g = Grid(n, 1.0 / max(n), wall_u=wall)
+    rng = np.random.default_rng(8)
+    # strong contrast, as the regularised law produces
+    eta = np.exp(rng.uniform(-4, 4, size=n))
+    prob = TensorViscous(g, eta, beta=0.05)
+    b = [rng.normal(size=n) for _ in range(d)]
+    M, b0, unflat, flat = _dense(lambda x: prob.apply(0, x), [n] * d)
+    ref = np.linalg.solve(M, flat(b) - b0)
+    x, st = bicgstab_solve(prob, [np.zeros(n) for _ in range(d)], b, P)
+    assert st.converged
+    np.testing.assert_allclose(flat(x), ref, atol=1e-10 * np.max(np.abs(ref)))
