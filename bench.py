@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--profile-only", action="store_true", help="run warm-up + steps, print nothing else")
+    ap.add_argument("--profiler-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -214,6 +215,8 @@ def run_ours(args):
     clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    if args.profiler_range:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     for _ in range(args.steps):
         st = sim.step(dt)
@@ -222,6 +225,8 @@ def run_ours(args):
             converged &= st[k]["converged"]
     ev1.record(stream)
     torch.cuda.synchronize()
+    if args.profiler_range:
+        torch.cuda.profiler.stop()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     launches = sim.launch_count() - n_launch0
