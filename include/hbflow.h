@@ -175,6 +175,31 @@ int hbf_profile_read(hbf_ctx* ctx, int slot, double* total_ms, int64_t* launches
 /* Number of kernels the context has launched since it was created. */
 int64_t hbf_launch_count(const hbf_ctx* ctx);
 
+/* Allocation-free variant of hbf_cfl_dt for callers that cannot allocate
+ * device memory: code recorded inside a CUDA graph capture (cudaMalloc is not
+ * permitted there), hosts whose device memory belongs to another runtime's pool
+ * allocator, or drivers that reserve every byte up front.  The paper has no
+ * counterpart; it is a service of this library.
+ *
+ * Computes dt = cfl h / max(max_i |u_dev[i]|, 1) on the device and writes it to
+ * dt_dev (one double in device memory).  u_dev: n doubles in device memory
+ * (any layout, e.g. all velocity components).  stream: a cudaStream_t or NULL.
+ * The work is queued on the stream; nothing is allocated and nothing
+ * synchronises.
+ *
+ * Scratch: a file-scope device array of 32768 doubles (256 KiB), present on
+ * every GPU that loads the library until the process exits, so
+ * n <= HBF_NOALLOC_MAX_N (32768 * 2048 = 67,108,864 doubles); larger n returns
+ * HBF_ERR_ARG without touching the GPU, as do null pointers or h, cfl <= 0.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one array and each overwrites the slots it
+ * reads, so nothing carries over between calls, but calls whose GPU work
+ * overlaps (different streams, or concurrent host threads) race on it.
+ * Returns HBF_OK, HBF_ERR_ARG or HBF_ERR_CUDA. */
+#define HBF_NOALLOC_MAX_N 67108864LL
+int hbf_cfl_dt_noalloc(const double* u_dev, int64_t n, double h, double cfl, double* dt_dev, void* stream);
+
 int hbf_sync(hbf_ctx* ctx);
 const char* hbf_last_error(const hbf_ctx* ctx);
 void hbf_destroy(hbf_ctx* ctx);

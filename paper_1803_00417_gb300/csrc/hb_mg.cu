@@ -155,6 +155,85 @@ double reduce_sum(hbf_ctx* c, const double* x, long long n, int* st) {
 }
 
 // ---------------------------------------------------------------------------
+// CFL time step without any device allocation (hbf_cfl_dt_noalloc)
+// ---------------------------------------------------------------------------
+// Callers that cannot allocate device memory -- code running inside a CUDA
+// graph capture (where cudaMalloc is not allowed), hosts whose device memory is
+// owned by another runtime's pool allocator, or embedded drivers that reserve
+// all memory up front -- still need the time-step rule.  This variant of the
+// max-|u| reduction keeps its per-block partials in a file-scope device array
+// instead of the context's allocated scratch.  Every GPU that loads the
+// library holds this array (256 KiB) until the process exits.
+constexpr int kNoAllocBlocks = 32768;                       // partial slots
+constexpr long long kNoAllocPerBlock = (long long)kThreads * 8;  // elements per block
+constexpr long long kNoAllocMaxN = (long long)kNoAllocBlocks * kNoAllocPerBlock;
+static __device__ __align__(256) double g_noalloc_partial[kNoAllocBlocks];
+
+// one block per kNoAllocPerBlock elements: max |x| of its chunk (non-finite -> +inf)
+__global__ void k_noalloc_maxabs_partial(const double* __restrict__ x, long long n, double* __restrict__ part) {
+  long long base = (long long)blockIdx.x * kNoAllocPerBlock;
+  double acc = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    long long t = base + (long long)q * kThreads + threadIdx.x;
+    if (t < n) {
+      double a = fabs(x[t]);
+      if (!isfinite(a)) a = INFINITY;
+      acc = fmax(acc, a);
+    }
+  }
+  __shared__ double sh[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+// reduce the nb partials written by this call and write dt
+__global__ void k_noalloc_cfl_final(const double* __restrict__ part, int nb, double h, double cfl,
+                                    double* __restrict__ dt_out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) acc = fmax(acc, part[t]);
+  for (int off = 16; off > 0; off >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (int)(blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (threadIdx.x == 0) *dt_out = cfl * h / fmax(v, 1.0);
+  }
+}
+
+// Device address of g_noalloc_partial per device, looked up once per device
+// (with that device current) and cached; the name itself is only a host-side
+// stand-in and must never be handed to a kernel.
+static double* noalloc_scratch(int* st) {
+  constexpr int kMaxDevices = 64;
+  static double* addr[kMaxDevices] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    *st = HBF_ERR_CUDA;
+    return nullptr;
+  }
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+    if (e != cudaSuccess || !p) {
+      *st = HBF_ERR_CUDA;
+      return nullptr;
+    }
+    addr[dev] = (double*)p;
+  }
+  *st = HBF_OK;
+  return addr[dev];
+}
+
+// ---------------------------------------------------------------------------
 // small elementwise kernels
 // ---------------------------------------------------------------------------
 template <typename TO, typename TI>
@@ -641,3 +720,18 @@ int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s) 
 }
 
 }  // namespace hb
+
+extern "C" int hbf_cfl_dt_noalloc(const double* u_dev, int64_t n, double h, double cfl, double* dt_dev,
+                                  void* stream) {
+  using namespace hb;
+  if (!u_dev || !dt_dev || n < 1 || !(h > 0.0) || !(cfl > 0.0)) return HBF_ERR_ARG;
+  if (n > kNoAllocMaxN) return HBF_ERR_ARG;  // more elements than the static partial array covers
+  int st = 0;
+  double* part = noalloc_scratch(&st);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int nb = (int)((n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+  k_noalloc_maxabs_partial<<<nb, kThreads, 0, s>>>(u_dev, (long long)n, part);
+  k_noalloc_cfl_final<<<1, 1024, 0, s>>>(part, nb, h, cfl, dt_dev);
+  return cudaGetLastError() == cudaSuccess ? HBF_OK : HBF_ERR_CUDA;
+}

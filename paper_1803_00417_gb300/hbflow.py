@@ -70,6 +70,8 @@ SIGNATURES = {
     "hbf_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64)]),
     "hbf_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "hbf_cfl_dt_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "hbf_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hbf_destroy": (None, [ctypes.c_void_p]),
