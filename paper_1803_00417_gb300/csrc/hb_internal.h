@@ -126,6 +126,14 @@ inline void launch(hbf_ctx* c, int slot, K kern, int grid, int block, Args... ar
   ++c->nlaunch;
 }
 
+template <typename K, typename... Args>
+inline void launch3(hbf_ctx* c, int slot, K kern, dim3 grid, dim3 block, Args... args) {
+  if (slot >= 0 && c->prof.on) prof_mark(c, slot, true);
+  kern<<<grid, block, 0, c->stream>>>(args...);
+  if (slot >= 0 && c->prof.on) prof_mark(c, slot, false);
+  ++c->nlaunch;
+}
+
 // error helpers
 int fail(hbf_ctx* c, int code, const std::string& msg);
 int cuda_check(hbf_ctx* c, cudaError_t e, const char* what);

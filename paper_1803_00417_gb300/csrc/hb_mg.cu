@@ -274,6 +274,13 @@ __global__ void k_bicg_x(double* __restrict__ x, const double* __restrict__ ph, 
     x[t] = x[t] + alpha * ph[t] + omega * sh[t];
 }
 
+// threads of the single-block coarsest-level solver: enough for the largest
+// colour class, in whole warps (fewer threads make each barrier cheaper)
+static inline int bottom_threads(int colour_count) {
+  int t = ((colour_count + 31) / 32) * 32;
+  return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+}
+
 // ---------------------------------------------------------------------------
 // per-precision views of a level's arrays
 // ---------------------------------------------------------------------------
@@ -361,16 +368,29 @@ struct ViscProblem : Problem<T> {
   long long count(int l) override { return (long long)D * c->lv[l].g.ncell; }
   void smooth(int l) override {
     Level& L = c->lv[l];
-    int nb = grid_for(rb_count<D>(L.g));
-    for (int comp = 0; comp < D; ++comp)
+    const int slot = l == 0 ? kSlotViscSmooth : kSlotNone;
+    const dim3 blk(32, 8, 1);
+    const dim3 grd((unsigned)((L.g.n[0] + 1) / 2 + 31) / 32, (unsigned)(L.g.n[1] + 7) / 8, (unsigned)L.g.n[2]);
+    const T* e0 = View<T>::ef(L, 0);
+    const T* e1 = View<T>::ef(L, 1);
+    const T* e2 = View<T>::ef(L, 2);
+    const int hm = (int)this->hom(l);
+    for (int col = 0; col < 2; ++col)
+      launch3(c, slot, k_visc_smooth_c<D, T, 0>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
+    for (int col = 0; col < 2; ++col)
+      launch3(c, slot, k_visc_smooth_c<D, T, 1>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
+    if (D == 3)
       for (int col = 0; col < 2; ++col)
-        launch(c, l == 0 ? kSlotViscSmooth : kSlotNone, k_visc_smooth<D, T>, nb, kThreads, x(l), b(l),
-               View<T>::ef(L, 0), View<T>::ef(L, 1), View<T>::ef(L, 2), L.g, comp, col, (T)beta, (int)this->hom(l));
+        launch3(c, slot, k_visc_smooth_c<D, T, 2>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta,
+                hm);
   }
   void resid(int l) override {
     Level& L = c->lv[l];
-    launch(c, l == 0 ? kSlotViscResid : kSlotNone, k_visc_resid<D, T>, grid_for(L.g.ncell), kThreads, x(l), b(l),
-           r(l), View<T>::ef(L, 0), View<T>::ef(L, 1), View<T>::ef(L, 2), L.g, (T)beta, (int)this->hom(l));
+    const dim3 blk(32, 8, 1);
+    const dim3 grd((unsigned)(L.g.n[0] + 31) / 32, (unsigned)(L.g.n[1] + 7) / 8, (unsigned)L.g.n[2]);
+    launch3(c, l == 0 ? kSlotViscResid : kSlotNone, k_visc_op3<D, T>, grd, blk, (const T*)x(l), (const T*)b(l), r(l),
+            (const T*)View<T>::ef(L, 0), (const T*)View<T>::ef(L, 1), (const T*)View<T>::ef(L, 2), L.g, (T)beta,
+            (int)this->hom(l));
   }
   void restrict_to(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
@@ -386,7 +406,7 @@ struct ViscProblem : Problem<T> {
   static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
     auto& S = static_cast<ViscProblem&>(P);
     Level& L = S.c->lv[l];
-    launch(S.c, kSlotNone, k_visc_bottom<D, double>, 1, 1024, xd, (const double*)bd, (const double*)L.ef[0],
+    launch(S.c, kSlotNone, k_visc_bottom<D, double>, 1, bottom_threads(rb_count<D>(L.g)), xd, (const double*)bd, (const double*)L.ef[0],
            (const double*)L.ef[1], (const double*)L.ef[2], L.g, S.beta, S.c->cfg.nu_bottom, (int)S.hom(l));
   }
   void bottom(int l) override {
@@ -429,7 +449,7 @@ struct MacProblem : Problem<T> {
   }
   static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
     Level& L = P.c->lv[l];
-    launch(P.c, kSlotNone, k_cell_bottom<D, double>, 1, 1024, xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
+    launch(P.c, kSlotNone, k_cell_bottom<D, double>, 1, bottom_threads(rb_count<D>(L.g)), xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
   }
   void bottom(int l) override {
     Level& L = c->lv[l];
@@ -478,7 +498,7 @@ struct NodalProblem : Problem<T> {
   }
   static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
     Level& L = P.c->lv[l];
-    launch(P.c, kSlotNone, k_nodal_bottom<D, double>, 1, 1024, xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
+    launch(P.c, kSlotNone, k_nodal_bottom<D, double>, 1, bottom_threads(mc_count<D>(L.g, 0)), xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
   }
   void bottom(int l) override {
     Level& L = c->lv[l];
@@ -632,8 +652,10 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
     }
   };
   auto apply0 = [&](const double* q, double* out_) {
-    launch(c, l0slot(), k_visc_apply<D, double>, grid_for(L0.g.ncell), kThreads, q, out_, (const double*)L0.ef[0],
-           (const double*)L0.ef[1], (const double*)L0.ef[2], L0.g, beta, 1);
+    const dim3 blk(32, 8, 1);
+    const dim3 grd((unsigned)(L0.g.n[0] + 31) / 32, (unsigned)(L0.g.n[1] + 7) / 8, (unsigned)L0.g.n[2]);
+    launch3(c, l0slot(), k_visc_op3<D, double>, grd, blk, q, (const double*)nullptr, out_, (const double*)L0.ef[0],
+            (const double*)L0.ef[1], (const double*)L0.ef[2], L0.g, beta, 1);
   };
   if ((st = cuda_check(c, cudaMemcpyAsync(kb, b_in, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy rhs")))
     return st;

@@ -140,7 +140,7 @@ __host__ __device__ inline bool interior(const Geom& g, const int* p) {
 // The same Gauss-Seidel update as visc_gs_point for a cell whose whole
 // stencil is inside the domain: direct strided indexing, no ghost logic.
 template <int D, typename T>
-__host__ __device__ inline T visc_gs_interior(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
+__host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
                                               const Geom& g, const Strides& S, int c, const int* p, T beta) {
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
@@ -179,7 +179,7 @@ __host__ __device__ inline T visc_gs_interior(const T* __restrict__ u, const T* 
 
 // (L_eta u)_c for an interior cell, same arithmetic as mg_tensor_point
 template <int D, typename T>
-__host__ __device__ inline T tensor_interior(const T* __restrict__ u, const T* const* ef, const Geom& g,
+__host__ __device__ __forceinline__ T tensor_interior(const T* __restrict__ u, const T* const* ef, const Geom& g,
                                              const Strides& S, int c, const int* p) {
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
@@ -249,6 +249,53 @@ __global__ void k_visc_smooth(T* __restrict__ u, const T* __restrict__ b, const 
     T v = interior<D>(g, p) ? visc_gs_interior<D, T>(u, b, ef, g, S, c, p, beta)
                             : visc_gs_point<D, T>(u, b, ef, g, c, p, beta, hom != 0);
     u[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
+  }
+}
+
+// 3D launch grid: x over pairs of cells of a row (one of each colour), y over
+// rows, z over planes; no integer division, the component is a template
+// parameter so every a == C decision folds at compile time.
+template <int D, typename T, int C>
+__global__ void __launch_bounds__(256) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
+                                                      const T* ef1, const T* ef2, Geom g, int col, T beta, int hom) {
+  const int ih = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (j >= g.n[1]) return;
+  const int i = 2 * ih + ((j + k + col) & 1);
+  if (i >= g.n[0]) return;
+  int p[3] = {i, j, k};
+  const T* ef[3] = {ef0, ef1, ef2};
+  T v;
+  if (interior<D>(g, p)) {
+    const Strides S = make_strides(g);
+    v = visc_gs_interior<D, T>(u, b, ef, g, S, C, p, beta);
+  } else {
+    v = visc_gs_point<D, T>(u, b, ef, g, C, p, beta, hom != 0);
+  }
+  u[(size_t)C * g.ncell + cidx<D>(g, i, j, k)] = v;
+}
+
+// out = u - beta L u, or r = b - (u - beta L u) when b != nullptr; 3D grid over cells
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_visc_op3(const T* __restrict__ u, const T* __restrict__ b,
+                                                 T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
+                                                 Geom g, T beta, int hom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  int p[3] = {i, j, k};
+  const T* ef[3] = {ef0, ef1, ef2};
+  const int t = cidx<D>(g, i, j, k);
+  const bool in = interior<D>(g, p);
+  const Strides S = make_strides(g);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    size_t o = (size_t)c * g.ncell + t;
+    T Lu = in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+    T Au = u[o] - beta * Lu;
+    out[o] = b ? b[o] - Au : Au;
   }
 }
 
