@@ -109,6 +109,17 @@ static int allocate(hbf_ctx* c) {
   A(c->kt, (long long)D * g.ncell);
   A(c->kph, (long long)D * g.ncell);
   A(c->ksh, (long long)D * g.ncell);
+  if (c->precision == HBF_MIXED) {
+    A(c->fkr, (long long)D * g.ncell);
+    A(c->fkrh, (long long)D * g.ncell);
+    A(c->fkp, (long long)D * g.ncell);
+    A(c->fkv, (long long)D * g.ncell);
+    A(c->fks, (long long)D * g.ncell);
+    A(c->fkt, (long long)D * g.ncell);
+    A(c->fkph, (long long)D * g.ncell);
+    A(c->fksh, (long long)D * g.ncell);
+    A(c->fke, (long long)D * g.ncell);
+  }
   A(c->partial, kRedBlocks);
   A(c->dres, 8);
   if (cudaMallocHost((void**)&c->hres, 8 * sizeof(double)) != cudaSuccess)

@@ -100,6 +100,9 @@ struct hbf_ctx {
   // BiCGStab vectors of the viscous solve (d*ncell each)
   double *kb = nullptr, *kr = nullptr, *krh = nullptr, *kp = nullptr, *kv = nullptr, *ks = nullptr,
          *kt = nullptr, *kph = nullptr, *ksh = nullptr;
+  // FP32 BiCGStab vectors of the mixed-precision viscous solve
+  float *fkr = nullptr, *fkrh = nullptr, *fkp = nullptr, *fkv = nullptr, *fks = nullptr, *fkt = nullptr,
+        *fkph = nullptr, *fksh = nullptr, *fke = nullptr;
   // reductions
   double* partial = nullptr;  // kRedBlocks doubles
   double* dres = nullptr;     // device result slot(s)

@@ -251,27 +251,83 @@ __global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ e, l
 }
 
 // p = r + beta (p - omega v)
-__global__ void k_bicg_p(double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ v,
-                         double beta, double omega, long long n) {
+template <typename T>
+__global__ void k_bicg_p(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ v, T beta, T omega,
+                         long long n) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
     p[t] = r[t] + beta * (p[t] - omega * v[t]);
 }
 
 // out = x - a y
-__global__ void k_axmy(double* __restrict__ out, const double* __restrict__ x, double a,
-                       const double* __restrict__ y, long long n) {
+template <typename T>
+__global__ void k_axmy(T* __restrict__ out, const T* __restrict__ x, T a, const T* __restrict__ y, long long n) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
     out[t] = x[t] - a * y[t];
 }
 
 // x = x + alpha ph + omega sh
-__global__ void k_bicg_x(double* __restrict__ x, const double* __restrict__ ph, const double* __restrict__ sh,
-                         double alpha, double omega, long long n) {
+template <typename T>
+__global__ void k_bicg_x(T* __restrict__ x, const T* __restrict__ ph, const T* __restrict__ sh, T alpha, T omega,
+                         long long n) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
     x[t] = x[t] + alpha * ph[t] + omega * sh[t];
+}
+
+// sum of a*b over float arrays, accumulated in FP64
+__global__ void k_dot_partial_f(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                                double* __restrict__ part) {
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    acc += (double)a[t] * (double)b[t];
+  __shared__ double sh[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+// max |x| over a float array (non-finite -> +inf)
+__global__ void k_maxabs_partial_f(const float* __restrict__ x, long long n, double* __restrict__ part) {
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    double a = fabs((double)x[t]);
+    if (!isfinite(a)) a = INFINITY;
+    acc = fmax(acc, a);
+  }
+  __shared__ double sh[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+static double reduce_dot_f(hbf_ctx* c, const float* a, const float* b, long long n, int* st) {
+  launch(c, kSlotNone, k_dot_partial_f, kRedBlocks, kThreads, a, b, n, c->partial);
+  launch(c, kSlotNone, k_reduce_final<1>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
+  *st = cuda_check(c, cudaGetLastError(), "dot");
+  if (*st) return NAN;
+  return read_result(c, c->dres, st);
+}
+
+static double reduce_max_abs_f(hbf_ctx* c, const float* x, long long n, int* st) {
+  launch(c, kSlotNone, k_maxabs_partial_f, kRedBlocks, kThreads, x, n, c->partial);
+  launch(c, kSlotNone, k_reduce_final<0>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
+  *st = cuda_check(c, cudaGetLastError(), "max");
+  if (*st) return NAN;
+  return read_result(c, c->dres, st);
 }
 
 // threads of the single-block coarsest-level solver: enough for the largest
@@ -369,8 +425,8 @@ struct ViscProblem : Problem<T> {
   void smooth(int l) override {
     Level& L = c->lv[l];
     const int slot = l == 0 ? kSlotViscSmooth : kSlotNone;
-    const dim3 blk(32, 8, 1);
-    const dim3 grd((unsigned)((L.g.n[0] + 1) / 2 + 31) / 32, (unsigned)(L.g.n[1] + 7) / 8, (unsigned)L.g.n[2]);
+    const dim3 blk(kThreads, 1, 1);
+    const dim3 grd((unsigned)grid_for(rb_count<D>(L.g), 152 * 24), 1, 1);
     const T* e0 = View<T>::ef(L, 0);
     const T* e1 = View<T>::ef(L, 1);
     const T* e2 = View<T>::ef(L, 2);
@@ -617,9 +673,107 @@ static void build_eta_levels(hbf_ctx* c) {
 // field of the regularised law; as a preconditioner it does.  Stops when the
 // recursive residual meets the tolerance and the true FP64 residual confirms
 // it; otherwise restarts from the true residual.  cycles = iterations.
+// Mixed precision: FP64 defect correction (r = b - A x and x += e in FP64)
+// around an FP32 BiCGStab on A e = r, itself preconditioned by FP32 V-cycles,
+// run until its residual drops by kInnerRtol (or kInnerMax iterations).
+// cycles = total inner iterations.
+constexpr double kInnerRtol = 1e-4;
+constexpr int kInnerMax = 40;
+
+template <int D>
+static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, double* x, hbf_solve_stats* out) {
+  const SolverCfg& cfg = c->cfg;
+  Level& L0 = c->lv[0];
+  const long long n = (long long)D * L0.g.ncell;
+  const size_t bytes = (size_t)n * sizeof(double);
+  const size_t fbytes = (size_t)n * sizeof(float);
+  const int nb = grid_for(n);
+  double *kb = c->kb, *r = c->kr;
+  float *fr = c->fkr, *frh = c->fkrh, *fp = c->fkp, *fv = c->fkv, *fs = c->fks, *ft = c->fkt, *fph = c->fkph,
+        *fsh = c->fksh, *fe = c->fke;
+  ViscProblem<D, double> P(c, x, beta, false);
+  const float fbeta = (float)beta;
+  int st = 0;
+  auto true_residual = [&]() -> double {
+    cudaMemcpyAsync(L0.vb, kb, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    P.resid(0);
+    cudaMemcpyAsync(r, L0.vr, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    return reduce_max_abs(c, r, n, &st);
+  };
+  auto precond = [&](const float* q, float* z) {
+    ViscProblem<D, float> Pz(c, z, beta, true);
+    cudaMemcpyAsync(L0.fvb, q, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    launch(c, kSlotNone, k_zero<float>, nb, kThreads, z, n);
+    vcycle(Pz, 0, cfg);
+  };
+  const dim3 blk(32, 8, 1);
+  const dim3 grd((unsigned)(L0.g.n[0] + 31) / 32, (unsigned)(L0.g.n[1] + 7) / 8, (unsigned)L0.g.n[2]);
+  auto apply0 = [&](const float* q, float* o) {
+    launch3(c, kSlotNone, k_visc_op3<D, float>, grd, blk, q, (const float*)nullptr, o, (const float*)L0.fef[0],
+            (const float*)L0.fef[1], (const float*)L0.fef[2], L0.g, fbeta, 1);
+  };
+  if ((st = cuda_check(c, cudaMemcpyAsync(kb, b_in, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy rhs")))
+    return st;
+  double bnorm = reduce_max_abs(c, kb, n, &st);
+  if (st) return st;
+  double rn = true_residual();
+  if (st) return st;
+  double r0 = rn;
+  if (bnorm == 0.0) bnorm = rn;
+  const double tol = cfg.rtol * bnorm;
+  int it = 0;
+  while (rn > tol && it < cfg.max_cycles && std::isfinite(rn)) {
+    launch(c, kSlotNone, k_convert<float, double>, nb, kThreads, fr, (const double*)r, n);
+    launch(c, kSlotNone, k_zero<float>, nb, kThreads, fe, n);
+    cudaMemcpyAsync(frh, fr, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    launch(c, kSlotNone, k_zero<float>, nb, kThreads, fv, n);
+    launch(c, kSlotNone, k_zero<float>, nb, kThreads, fp, n);
+    double in_norm = reduce_max_abs_f(c, fr, n, &st);
+    if (st) return st;
+    const double in_tol = kInnerRtol * in_norm;
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    for (int k = 0; k < kInnerMax && it < cfg.max_cycles; ++k) {
+      double rho1 = reduce_dot_f(c, frh, fr, n, &st);
+      if (st) return st;
+      if (rho1 == 0.0 || !std::isfinite(rho1)) break;
+      double bt = (rho1 / rho) * (alpha / omega);
+      launch(c, kSlotNone, k_bicg_p<float>, nb, kThreads, fp, (const float*)fr, (const float*)fv, (float)bt,
+             (float)omega, n);
+      precond(fp, fph);
+      apply0(fph, fv);
+      double den = reduce_dot_f(c, frh, fv, n, &st);
+      if (st) return st;
+      if (den == 0.0 || !std::isfinite(den)) break;
+      alpha = rho1 / den;
+      launch(c, kSlotNone, k_axmy<float>, nb, kThreads, fs, (const float*)fr, (float)alpha, (const float*)fv, n);
+      precond(fs, fsh);
+      apply0(fsh, ft);
+      double tt = reduce_dot_f(c, ft, ft, n, &st);
+      if (st) return st;
+      double ts = reduce_dot_f(c, ft, fs, n, &st);
+      if (st) return st;
+      omega = tt > 0.0 ? ts / tt : 0.0;
+      launch(c, kSlotNone, k_bicg_x<float>, nb, kThreads, fe, (const float*)fph, (const float*)fsh, (float)alpha,
+             (float)omega, n);
+      launch(c, kSlotNone, k_axmy<float>, nb, kThreads, fr, (const float*)fs, (float)omega, (const float*)ft, n);
+      rho = rho1;
+      ++it;
+      double rr = reduce_max_abs_f(c, fr, n, &st);
+      if (st) return st;
+      if (rr <= in_tol || omega == 0.0 || !std::isfinite(rr)) break;
+    }
+    launch(c, kSlotNone, k_add_f32, nb, kThreads, x, (const float*)fe, n);
+    rn = true_residual();
+    if (st) return st;
+  }
+  if ((st = cuda_check(c, cudaGetLastError(), "viscous solve"))) return st;
+  return finish(c, it, r0, rn, bnorm, tol, out);
+}
+
 template <int D>
 static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* x, hbf_solve_stats* out) {
   build_eta_levels<D>(c);
+  if (c->precision == HBF_MIXED) return solve_viscous_mixed<D>(c, beta, b_in, x, out);
   const SolverCfg& cfg = c->cfg;
   Level& L0 = c->lv[0];
   const long long n = (long long)D * L0.g.ncell;
@@ -677,14 +831,14 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
       if (st) return st;
       if (rho1 == 0.0 || !std::isfinite(rho1)) break;
       double bt = (rho1 / rho) * (alpha / omega);
-      launch(c, kSlotNone, k_bicg_p, nb, kThreads, p, (const double*)r, (const double*)v, bt, omega, n);
+      launch(c, kSlotNone, k_bicg_p<double>, nb, kThreads, p, (const double*)r, (const double*)v, bt, omega, n);
       precond(p, ph);
       apply0(ph, v);
       double den = reduce_dot(c, rh, v, n, &st);
       if (st) return st;
       if (den == 0.0 || !std::isfinite(den)) break;
       alpha = rho1 / den;
-      launch(c, kSlotNone, k_axmy, nb, kThreads, s, (const double*)r, alpha, (const double*)v, n);
+      launch(c, kSlotNone, k_axmy<double>, nb, kThreads, s, (const double*)r, alpha, (const double*)v, n);
       precond(s, sh);
       apply0(sh, t);
       double tt = reduce_dot(c, t, t, n, &st);
@@ -692,8 +846,8 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
       double ts = reduce_dot(c, t, s, n, &st);
       if (st) return st;
       omega = tt > 0.0 ? ts / tt : 0.0;
-      launch(c, kSlotNone, k_bicg_x, nb, kThreads, x, (const double*)ph, (const double*)sh, alpha, omega, n);
-      launch(c, kSlotNone, k_axmy, nb, kThreads, r, (const double*)s, omega, (const double*)t, n);
+      launch(c, kSlotNone, k_bicg_x<double>, nb, kThreads, x, (const double*)ph, (const double*)sh, alpha, omega, n);
+      launch(c, kSlotNone, k_axmy<double>, nb, kThreads, r, (const double*)s, omega, (const double*)t, n);
       rho = rho1;
       ++it;
       double rr = reduce_max_abs(c, r, n, &st);
