@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--breakdown", action="store_true",
+                    help="also time bottom solves, transfers, reductions, vector updates and coarse levels")
     ap.add_argument("--profiler-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -207,7 +209,7 @@ def run_ours(args):
         dist.barrier()
 
     clocks = Clocks(local)
-    sim.profile_enable(True)
+    sim.profile_enable(2 if args.breakdown else 1)
     n_launch0 = sim.launch_count()
     cycles = {"mac": 0, "visc": 0, "nodal": 0}
     converged = True
@@ -231,7 +233,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     launches = sim.launch_count() - n_launch0
     prof = {k: sim.profile_read(k) for k in sim.PROFILE_SLOTS}
-    sim.profile_enable(False)
+    sim.profile_enable(0)
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -304,7 +306,7 @@ def run_ours(args):
                        "converged": bool(converged)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk,
-            "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

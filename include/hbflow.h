@@ -163,12 +163,16 @@ int hbf_step(hbf_ctx* ctx, double dt, hbf_step_stats* stats);
 /* dt = cfl h / max(max|u|, 1) for the current U (synchronises). */
 double hbf_cfl_dt(hbf_ctx* ctx, double cfl);
 
-/* Event timing of finest-level launches, per kernel class (slot):
- *   0 viscous smoother, 1 viscous residual, 2 nodal smoother, 3 nodal residual,
- *   4 MAC smoother, 5 MAC residual, 6 explicit stages (all levels).
- * hbf_profile_enable(ctx, 1) synchronises, clears the accumulators and starts
- * recording; hbf_profile_read synchronises and returns the summed device time
- * in milliseconds and the number of launches recorded for a slot. */
+/* Event timing of launches, per kernel class (slot):
+ *   0 viscous smoother, 1 viscous residual/operator, 2 nodal smoother,
+ *   3 nodal residual, 4 MAC smoother, 5 MAC residual (slots 0-5: finest level
+ *   only), 6 explicit stages; with level 2 also 7 coarsest-level solves,
+ *   8 transfers and conversions, 9 reductions, 10 Krylov vector updates,
+ *   11 smoothing and residuals on coarse levels.
+ * hbf_profile_enable(ctx, level) synchronises, clears the accumulators and
+ * records at that level (0 off, 1 slots 0-6, 2 all); hbf_profile_read
+ * synchronises and returns the summed device time in milliseconds and the
+ * number of launches recorded for a slot. */
 int hbf_profile_enable(hbf_ctx* ctx, int on);
 int hbf_profile_read(hbf_ctx* ctx, int slot, double* total_ms, int64_t* launches);
 

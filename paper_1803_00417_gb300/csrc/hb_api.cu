@@ -274,7 +274,7 @@ int hbf_profile_enable(hbf_ctx* c, int on) {
   int st = cuda_check(c, cudaStreamSynchronize(c->stream), "profile sync");
   if (st) return st;
   for (int s = 0; s < kSlotCount; ++s) c->prof.used[s] = 0;
-  c->prof.on = on != 0;
+  c->prof.level = on < 0 ? 0 : (on > 2 ? 2 : on);
   return HBF_OK;
 }
 

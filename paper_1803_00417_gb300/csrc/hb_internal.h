@@ -48,15 +48,25 @@ enum ProfSlot {
   kSlotCellSmooth = 4,
   kSlotCellResid = 5,
   kSlotExplicit = 6,
-  kSlotCount = 7,
+  // detail slots (recorded only at profiling level 2)
+  kSlotBottom = 7,
+  kSlotTransfer = 8,
+  kSlotReduce = 9,
+  kSlotVector = 10,
+  kSlotCoarse = 11,
+  kSlotCount = 12,
   kSlotNone = -1
 };
 
 struct Prof {
-  bool on = false;
+  int level = 0;  // 0 off, 1 main slots, 2 main + detail slots
   std::vector<cudaEvent_t> ev[kSlotCount];  // start/stop pairs
-  size_t used[kSlotCount] = {0, 0, 0, 0, 0, 0, 0};
+  size_t used[kSlotCount] = {};
 };
+
+inline bool prof_wants(const Prof& P, int slot) {
+  return slot >= 0 && P.level > 0 && (slot < kSlotBottom || P.level > 1);
+}
 
 constexpr size_t kProfPairs = 16384;
 
@@ -123,17 +133,19 @@ void prof_mark(hbf_ctx* c, int slot, bool start);
 // profiling is on, brackets finest-level launches of a slot with events
 template <typename K, typename... Args>
 inline void launch(hbf_ctx* c, int slot, K kern, int grid, int block, Args... args) {
-  if (slot >= 0 && c->prof.on) prof_mark(c, slot, true);
+  const bool rec = prof_wants(c->prof, slot);
+  if (rec) prof_mark(c, slot, true);
   kern<<<grid, block, 0, c->stream>>>(args...);
-  if (slot >= 0 && c->prof.on) prof_mark(c, slot, false);
+  if (rec) prof_mark(c, slot, false);
   ++c->nlaunch;
 }
 
 template <typename K, typename... Args>
 inline void launch3(hbf_ctx* c, int slot, K kern, dim3 grid, dim3 block, Args... args) {
-  if (slot >= 0 && c->prof.on) prof_mark(c, slot, true);
+  const bool rec = prof_wants(c->prof, slot);
+  if (rec) prof_mark(c, slot, true);
   kern<<<grid, block, 0, c->stream>>>(args...);
-  if (slot >= 0 && c->prof.on) prof_mark(c, slot, false);
+  if (rec) prof_mark(c, slot, false);
   ++c->nlaunch;
 }
 

@@ -119,8 +119,8 @@ __global__ void k_dot_partial(const double* __restrict__ a, const double* __rest
 
 template <int MODE>
 static int reduce_to_device(hbf_ctx* c, const double* x, long long n, double* out) {
-  launch(c, kSlotNone, k_reduce_partial<MODE>, kRedBlocks, kThreads, x, n, c->partial, c->g, c->dim);
-  launch(c, kSlotNone, k_reduce_final<MODE>, 1, 1024, c->partial, kRedBlocks, out);
+  launch(c, kSlotReduce, k_reduce_partial<MODE>, kRedBlocks, kThreads, x, n, c->partial, c->g, c->dim);
+  launch(c, kSlotReduce, k_reduce_final<MODE>, 1, 1024, c->partial, kRedBlocks, out);
   return cuda_check(c, cudaGetLastError(), "reduction");
 }
 
@@ -141,8 +141,8 @@ double reduce_max_abs(hbf_ctx* c, const double* x, long long n, int* st) {
 }
 
 double reduce_dot(hbf_ctx* c, const double* a, const double* b, long long n, int* st) {
-  launch(c, kSlotNone, k_dot_partial, kRedBlocks, kThreads, a, b, n, c->partial);
-  launch(c, kSlotNone, k_reduce_final<1>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
+  launch(c, kSlotReduce, k_dot_partial, kRedBlocks, kThreads, a, b, n, c->partial);
+  launch(c, kSlotReduce, k_reduce_final<1>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
   *st = cuda_check(c, cudaGetLastError(), "dot");
   if (*st) return NAN;
   return read_result(c, c->dres, st);
@@ -315,16 +315,16 @@ __global__ void k_maxabs_partial_f(const float* __restrict__ x, long long n, dou
 }
 
 static double reduce_dot_f(hbf_ctx* c, const float* a, const float* b, long long n, int* st) {
-  launch(c, kSlotNone, k_dot_partial_f, kRedBlocks, kThreads, a, b, n, c->partial);
-  launch(c, kSlotNone, k_reduce_final<1>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
+  launch(c, kSlotReduce, k_dot_partial_f, kRedBlocks, kThreads, a, b, n, c->partial);
+  launch(c, kSlotReduce, k_reduce_final<1>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
   *st = cuda_check(c, cudaGetLastError(), "dot");
   if (*st) return NAN;
   return read_result(c, c->dres, st);
 }
 
 static double reduce_max_abs_f(hbf_ctx* c, const float* x, long long n, int* st) {
-  launch(c, kSlotNone, k_maxabs_partial_f, kRedBlocks, kThreads, x, n, c->partial);
-  launch(c, kSlotNone, k_reduce_final<0>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
+  launch(c, kSlotReduce, k_maxabs_partial_f, kRedBlocks, kThreads, x, n, c->partial);
+  launch(c, kSlotReduce, k_reduce_final<0>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
   *st = cuda_check(c, cudaGetLastError(), "max");
   if (*st) return NAN;
   return read_result(c, c->dres, st);
@@ -402,14 +402,14 @@ static void bottom_fp64(Problem<T>& P, int l, double* xd, double* bd, void (*run
   hbf_ctx* c = P.c;
   long long n = P.count(l);
   if (!std::is_same<T, double>::value) {
-    launch(c, kSlotNone, k_convert<double, T>, grid_for(n), kThreads, bd, (const T*)P.b(l), n);
-    launch(c, kSlotNone, k_zero<double>, grid_for(n), kThreads, xd, n);
+    launch(c, kSlotTransfer, k_convert<double, T>, grid_for(n), kThreads, bd, (const T*)P.b(l), n);
+    launch(c, kSlotTransfer, k_zero<double>, grid_for(n), kThreads, xd, n);
   }
   if (P.singular) P.sub_mean(l, bd);
   run(P, l, xd, bd);
   if (P.singular) P.sub_mean(l, xd);
   if (!std::is_same<T, double>::value)
-    launch(c, kSlotNone, k_convert<T, double>, grid_for(n), kThreads, P.x(l), (const double*)xd, n);
+    launch(c, kSlotTransfer, k_convert<T, double>, grid_for(n), kThreads, P.x(l), (const double*)xd, n);
 }
 
 template <int D, typename T>
@@ -424,7 +424,7 @@ struct ViscProblem : Problem<T> {
   long long count(int l) override { return (long long)D * c->lv[l].g.ncell; }
   void smooth(int l) override {
     Level& L = c->lv[l];
-    const int slot = l == 0 ? kSlotViscSmooth : kSlotNone;
+    const int slot = l == 0 ? kSlotViscSmooth : kSlotCoarse;
     const dim3 blk(kThreads, 1, 1);
     const dim3 grd((unsigned)grid_for(rb_count<D>(L.g), 152 * 24), 1, 1);
     const T* e0 = View<T>::ef(L, 0);
@@ -444,25 +444,25 @@ struct ViscProblem : Problem<T> {
     Level& L = c->lv[l];
     const dim3 blk(32, 8, 1);
     const dim3 grd((unsigned)(L.g.n[0] + 31) / 32, (unsigned)(L.g.n[1] + 7) / 8, (unsigned)L.g.n[2]);
-    launch3(c, l == 0 ? kSlotViscResid : kSlotNone, k_visc_op3<D, T>, grd, blk, (const T*)x(l), (const T*)b(l), r(l),
+    launch3(c, l == 0 ? kSlotViscResid : kSlotCoarse, k_visc_op3<D, T>, grd, blk, (const T*)x(l), (const T*)b(l), r(l),
             (const T*)View<T>::ef(L, 0), (const T*)View<T>::ef(L, 1), (const T*)View<T>::ef(L, 2), L.g, (T)beta,
             (int)this->hom(l));
   }
   void restrict_to(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
     long long n = (long long)D * C.g.ncell;
-    launch(c, kSlotNone, k_restrict_cells<D, T>, grid_for(n), kThreads, r(l), b(l + 1), F.g, C.g, D);
-    launch(c, kSlotNone, k_zero<T>, grid_for(n), kThreads, x(l + 1), n);
+    launch(c, kSlotTransfer, k_restrict_cells<D, T>, grid_for(n), kThreads, r(l), b(l + 1), F.g, C.g, D);
+    launch(c, kSlotTransfer, k_zero<T>, grid_for(n), kThreads, x(l + 1), n);
   }
   void prolong_add(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_prolong_cells_add<D, T>, grid_for((long long)D * F.g.ncell), kThreads, x(l), x(l + 1),
+    launch(c, kSlotTransfer, k_prolong_cells_add<D, T>, grid_for((long long)D * F.g.ncell), kThreads, x(l), x(l + 1),
            F.g, C.g, D, T(-1));
   }
   static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
     auto& S = static_cast<ViscProblem&>(P);
     Level& L = S.c->lv[l];
-    launch(S.c, kSlotNone, k_visc_bottom<D, double>, 1, bottom_threads(rb_count<D>(L.g)), xd, (const double*)bd, (const double*)L.ef[0],
+    launch(S.c, kSlotBottom, k_visc_bottom<D, double>, 1, bottom_threads(rb_count<D>(L.g)), xd, (const double*)bd, (const double*)L.ef[0],
            (const double*)L.ef[1], (const double*)L.ef[2], L.g, S.beta, S.c->cfg.nu_bottom, (int)S.hom(l));
   }
   void bottom(int l) override {
@@ -486,26 +486,26 @@ struct MacProblem : Problem<T> {
     Level& L = c->lv[l];
     int nb = grid_for(rb_count<D>(L.g));
     for (int col = 0; col < 2; ++col)
-      launch(c, l == 0 ? kSlotCellSmooth : kSlotNone, k_cell_smooth<D, T>, nb, kThreads, x(l), b(l), L.g, col);
+      launch(c, l == 0 ? kSlotCellSmooth : kSlotCoarse, k_cell_smooth<D, T>, nb, kThreads, x(l), b(l), L.g, col);
   }
   void resid(int l) override {
     Level& L = c->lv[l];
-    launch(c, l == 0 ? kSlotCellResid : kSlotNone, k_cell_resid<D, T>, grid_for(L.g.ncell), kThreads, x(l), b(l),
+    launch(c, l == 0 ? kSlotCellResid : kSlotCoarse, k_cell_resid<D, T>, grid_for(L.g.ncell), kThreads, x(l), b(l),
            r(l), L.g);
   }
   void restrict_to(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_restrict_cells<D, T>, grid_for(C.g.ncell), kThreads, r(l), b(l + 1), F.g, C.g, 1);
-    launch(c, kSlotNone, k_zero<T>, grid_for(C.g.ncell), kThreads, x(l + 1), (long long)C.g.ncell);
+    launch(c, kSlotTransfer, k_restrict_cells<D, T>, grid_for(C.g.ncell), kThreads, r(l), b(l + 1), F.g, C.g, 1);
+    launch(c, kSlotTransfer, k_zero<T>, grid_for(C.g.ncell), kThreads, x(l + 1), (long long)C.g.ncell);
   }
   void prolong_add(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_prolong_cells_add<D, T>, grid_for(F.g.ncell), kThreads, x(l), x(l + 1), F.g, C.g, 1,
+    launch(c, kSlotTransfer, k_prolong_cells_add<D, T>, grid_for(F.g.ncell), kThreads, x(l), x(l + 1), F.g, C.g, 1,
            T(1));
   }
   static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
     Level& L = P.c->lv[l];
-    launch(P.c, kSlotNone, k_cell_bottom<D, double>, 1, bottom_threads(rb_count<D>(L.g)), xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
+    launch(P.c, kSlotBottom, k_cell_bottom<D, double>, 1, bottom_threads(rb_count<D>(L.g)), xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
   }
   void bottom(int l) override {
     Level& L = c->lv[l];
@@ -517,7 +517,7 @@ struct MacProblem : Problem<T> {
     Level& L = c->lv[l];
     int st = reduce_to_device<1>(c, v, L.g.ncell, c->dres + 1);
     if (st) return st;
-    launch(c, kSlotNone, k_sub_mean<double>, grid_for(L.g.ncell), kThreads, v, (long long)L.g.ncell,
+    launch(c, kSlotTransfer, k_sub_mean<double>, grid_for(L.g.ncell), kThreads, v, (long long)L.g.ncell,
            (const double*)(c->dres + 1), 1.0 / (double)L.g.ncell);
     return cuda_check(c, cudaGetLastError(), "k_sub_mean");
   }
@@ -535,26 +535,26 @@ struct NodalProblem : Problem<T> {
   void smooth(int l) override {
     Level& L = c->lv[l];
     for (int col = 0; col < (1 << D); ++col)
-      launch(c, l == 0 ? kSlotNodalSmooth : kSlotNone, k_nodal_smooth<D, T>, grid_for(mc_count<D>(L.g, col)),
+      launch(c, l == 0 ? kSlotNodalSmooth : kSlotCoarse, k_nodal_smooth<D, T>, grid_for(mc_count<D>(L.g, col)),
              kThreads, x(l), b(l), L.g, col);
   }
   void resid(int l) override {
     Level& L = c->lv[l];
-    launch(c, l == 0 ? kSlotNodalResid : kSlotNone, k_nodal_resid<D, T>, grid_for(L.g.nnode), kThreads, x(l), b(l),
+    launch(c, l == 0 ? kSlotNodalResid : kSlotCoarse, k_nodal_resid<D, T>, grid_for(L.g.nnode), kThreads, x(l), b(l),
            r(l), L.g);
   }
   void restrict_to(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_restrict_nodes<D, T>, grid_for(C.g.nnode), kThreads, r(l), b(l + 1), F.g, C.g);
-    launch(c, kSlotNone, k_zero<T>, grid_for(C.g.nnode), kThreads, x(l + 1), (long long)C.g.nnode);
+    launch(c, kSlotTransfer, k_restrict_nodes<D, T>, grid_for(C.g.nnode), kThreads, r(l), b(l + 1), F.g, C.g);
+    launch(c, kSlotTransfer, k_zero<T>, grid_for(C.g.nnode), kThreads, x(l + 1), (long long)C.g.nnode);
   }
   void prolong_add(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotNone, k_prolong_nodes_add<D, T>, grid_for(F.g.nnode), kThreads, x(l), x(l + 1), F.g, C.g);
+    launch(c, kSlotTransfer, k_prolong_nodes_add<D, T>, grid_for(F.g.nnode), kThreads, x(l), x(l + 1), F.g, C.g);
   }
   static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
     Level& L = P.c->lv[l];
-    launch(P.c, kSlotNone, k_nodal_bottom<D, double>, 1, bottom_threads(mc_count<D>(L.g, 0)), xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
+    launch(P.c, kSlotBottom, k_nodal_bottom<D, double>, 1, bottom_threads(mc_count<D>(L.g, 0)), xd, (const double*)bd, L.g, P.c->cfg.nu_bottom);
   }
   void bottom(int l) override {
     Level& L = c->lv[l];
@@ -570,7 +570,7 @@ struct NodalProblem : Problem<T> {
     c->g = gsave;
     if (st) return st;
     double wsum = (double)L.g.n[0] * L.g.n[1] * (D == 3 ? L.g.n[2] : 1);
-    launch(c, kSlotNone, k_sub_mean<double>, grid_for(L.g.nnode), kThreads, v, (long long)L.g.nnode,
+    launch(c, kSlotTransfer, k_sub_mean<double>, grid_for(L.g.nnode), kThreads, v, (long long)L.g.nnode,
            (const double*)(c->dres + 1), 1.0 / wsum);
     return cuda_check(c, cudaGetLastError(), "k_sub_mean");
   }
@@ -634,10 +634,10 @@ static int mg_solve(Problem<double>& P, Problem<float>* P32, const double* b_in,
   int cycles = 0;
   while (rn > tol && cycles < cfg.max_cycles && std::isfinite(rn)) {
     if (P32) {
-      launch(c, kSlotNone, k_convert<float, double>, grid_for(n0), kThreads, P32->b(0), (const double*)P.r(0), n0);
-      launch(c, kSlotNone, k_zero<float>, grid_for(n0), kThreads, P32->x(0), n0);
+      launch(c, kSlotTransfer, k_convert<float, double>, grid_for(n0), kThreads, P32->b(0), (const double*)P.r(0), n0);
+      launch(c, kSlotTransfer, k_zero<float>, grid_for(n0), kThreads, P32->x(0), n0);
       vcycle(*P32, 0, cfg);
-      launch(c, kSlotNone, k_add_f32, grid_for(n0), kThreads, P.x(0), (const float*)P32->x(0), n0);
+      launch(c, kSlotTransfer, k_add_f32, grid_for(n0), kThreads, P.x(0), (const float*)P32->x(0), n0);
     } else {
       vcycle(P, 0, cfg);
     }
@@ -657,13 +657,13 @@ static void build_eta_levels(hbf_ctx* c) {
   for (size_t l = 1; l < c->lv.size(); ++l) {
     Level &F = c->lv[l - 1], &C = c->lv[l];
     for (int a = 0; a < D; ++a)
-      launch(c, kSlotNone, k_restrict_faces<D, double>, grid_for(C.g.nface[a]), kThreads, (const double*)F.ef[a],
+      launch(c, kSlotTransfer, k_restrict_faces<D, double>, grid_for(C.g.nface[a]), kThreads, (const double*)F.ef[a],
              C.ef[a], a, F.g, C.g);
   }
   if (c->precision == HBF_MIXED)
     for (auto& L : c->lv)
       for (int a = 0; a < D; ++a)
-        launch(c, kSlotNone, k_convert<float, double>, grid_for(L.g.nface[a]), kThreads, L.fef[a],
+        launch(c, kSlotTransfer, k_convert<float, double>, grid_for(L.g.nface[a]), kThreads, L.fef[a],
                (const double*)L.ef[a], (long long)L.g.nface[a]);
 }
 
@@ -703,13 +703,13 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
   auto precond = [&](const float* q, float* z) {
     ViscProblem<D, float> Pz(c, z, beta, true);
     cudaMemcpyAsync(L0.fvb, q, fbytes, cudaMemcpyDeviceToDevice, c->stream);
-    launch(c, kSlotNone, k_zero<float>, nb, kThreads, z, n);
+    launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, z, n);
     vcycle(Pz, 0, cfg);
   };
   const dim3 blk(32, 8, 1);
   const dim3 grd((unsigned)(L0.g.n[0] + 31) / 32, (unsigned)(L0.g.n[1] + 7) / 8, (unsigned)L0.g.n[2]);
   auto apply0 = [&](const float* q, float* o) {
-    launch3(c, kSlotNone, k_visc_op3<D, float>, grd, blk, q, (const float*)nullptr, o, (const float*)L0.fef[0],
+    launch3(c, kSlotViscResid, k_visc_op3<D, float>, grd, blk, q, (const float*)nullptr, o, (const float*)L0.fef[0],
             (const float*)L0.fef[1], (const float*)L0.fef[2], L0.g, fbeta, 1);
   };
   if ((st = cuda_check(c, cudaMemcpyAsync(kb, b_in, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy rhs")))
@@ -723,11 +723,11 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
   const double tol = cfg.rtol * bnorm;
   int it = 0;
   while (rn > tol && it < cfg.max_cycles && std::isfinite(rn)) {
-    launch(c, kSlotNone, k_convert<float, double>, nb, kThreads, fr, (const double*)r, n);
-    launch(c, kSlotNone, k_zero<float>, nb, kThreads, fe, n);
+    launch(c, kSlotTransfer, k_convert<float, double>, nb, kThreads, fr, (const double*)r, n);
+    launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, fe, n);
     cudaMemcpyAsync(frh, fr, fbytes, cudaMemcpyDeviceToDevice, c->stream);
-    launch(c, kSlotNone, k_zero<float>, nb, kThreads, fv, n);
-    launch(c, kSlotNone, k_zero<float>, nb, kThreads, fp, n);
+    launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, fv, n);
+    launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, fp, n);
     double in_norm = reduce_max_abs_f(c, fr, n, &st);
     if (st) return st;
     const double in_tol = kInnerRtol * in_norm;
@@ -737,7 +737,7 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
       if (st) return st;
       if (rho1 == 0.0 || !std::isfinite(rho1)) break;
       double bt = (rho1 / rho) * (alpha / omega);
-      launch(c, kSlotNone, k_bicg_p<float>, nb, kThreads, fp, (const float*)fr, (const float*)fv, (float)bt,
+      launch(c, kSlotVector, k_bicg_p<float>, nb, kThreads, fp, (const float*)fr, (const float*)fv, (float)bt,
              (float)omega, n);
       precond(fp, fph);
       apply0(fph, fv);
@@ -745,7 +745,7 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
       if (st) return st;
       if (den == 0.0 || !std::isfinite(den)) break;
       alpha = rho1 / den;
-      launch(c, kSlotNone, k_axmy<float>, nb, kThreads, fs, (const float*)fr, (float)alpha, (const float*)fv, n);
+      launch(c, kSlotVector, k_axmy<float>, nb, kThreads, fs, (const float*)fr, (float)alpha, (const float*)fv, n);
       precond(fs, fsh);
       apply0(fsh, ft);
       double tt = reduce_dot_f(c, ft, ft, n, &st);
@@ -753,16 +753,16 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
       double ts = reduce_dot_f(c, ft, fs, n, &st);
       if (st) return st;
       omega = tt > 0.0 ? ts / tt : 0.0;
-      launch(c, kSlotNone, k_bicg_x<float>, nb, kThreads, fe, (const float*)fph, (const float*)fsh, (float)alpha,
+      launch(c, kSlotVector, k_bicg_x<float>, nb, kThreads, fe, (const float*)fph, (const float*)fsh, (float)alpha,
              (float)omega, n);
-      launch(c, kSlotNone, k_axmy<float>, nb, kThreads, fr, (const float*)fs, (float)omega, (const float*)ft, n);
+      launch(c, kSlotVector, k_axmy<float>, nb, kThreads, fr, (const float*)fs, (float)omega, (const float*)ft, n);
       rho = rho1;
       ++it;
       double rr = reduce_max_abs_f(c, fr, n, &st);
       if (st) return st;
       if (rr <= in_tol || omega == 0.0 || !std::isfinite(rr)) break;
     }
-    launch(c, kSlotNone, k_add_f32, nb, kThreads, x, (const float*)fe, n);
+    launch(c, kSlotTransfer, k_add_f32, nb, kThreads, x, (const float*)fe, n);
     rn = true_residual();
     if (st) return st;
   }
@@ -794,14 +794,14 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
   // z = M^{-1} q
   auto precond = [&](const double* q, double* z) {
     if (mixed) {
-      launch(c, kSlotNone, k_convert<float, double>, nb, kThreads, L0.fvb, q, n);
-      launch(c, kSlotNone, k_zero<float>, nb, kThreads, L0.fvx, n);
+      launch(c, kSlotTransfer, k_convert<float, double>, nb, kThreads, L0.fvb, q, n);
+      launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, L0.fvx, n);
       vcycle(Pre32, 0, cfg);
-      launch(c, kSlotNone, k_convert<double, float>, nb, kThreads, z, (const float*)L0.fvx, n);
+      launch(c, kSlotTransfer, k_convert<double, float>, nb, kThreads, z, (const float*)L0.fvx, n);
     } else {
       ViscProblem<D, double> Pz(c, z, beta, true);
       cudaMemcpyAsync(L0.vb, q, bytes, cudaMemcpyDeviceToDevice, c->stream);
-      launch(c, kSlotNone, k_zero<double>, nb, kThreads, z, n);
+      launch(c, kSlotTransfer, k_zero<double>, nb, kThreads, z, n);
       vcycle(Pz, 0, cfg);
     }
   };
@@ -824,21 +824,21 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
   while (rn > tol && it < cfg.max_cycles && std::isfinite(rn)) {
     cudaMemcpyAsync(rh, r, bytes, cudaMemcpyDeviceToDevice, c->stream);
     double rho = 1.0, alpha = 1.0, omega = 1.0;
-    launch(c, kSlotNone, k_zero<double>, nb, kThreads, v, n);
-    launch(c, kSlotNone, k_zero<double>, nb, kThreads, p, n);
+    launch(c, kSlotTransfer, k_zero<double>, nb, kThreads, v, n);
+    launch(c, kSlotTransfer, k_zero<double>, nb, kThreads, p, n);
     while (it < cfg.max_cycles) {
       double rho1 = reduce_dot(c, rh, r, n, &st);
       if (st) return st;
       if (rho1 == 0.0 || !std::isfinite(rho1)) break;
       double bt = (rho1 / rho) * (alpha / omega);
-      launch(c, kSlotNone, k_bicg_p<double>, nb, kThreads, p, (const double*)r, (const double*)v, bt, omega, n);
+      launch(c, kSlotVector, k_bicg_p<double>, nb, kThreads, p, (const double*)r, (const double*)v, bt, omega, n);
       precond(p, ph);
       apply0(ph, v);
       double den = reduce_dot(c, rh, v, n, &st);
       if (st) return st;
       if (den == 0.0 || !std::isfinite(den)) break;
       alpha = rho1 / den;
-      launch(c, kSlotNone, k_axmy<double>, nb, kThreads, s, (const double*)r, alpha, (const double*)v, n);
+      launch(c, kSlotVector, k_axmy<double>, nb, kThreads, s, (const double*)r, alpha, (const double*)v, n);
       precond(s, sh);
       apply0(sh, t);
       double tt = reduce_dot(c, t, t, n, &st);
@@ -846,8 +846,8 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
       double ts = reduce_dot(c, t, s, n, &st);
       if (st) return st;
       omega = tt > 0.0 ? ts / tt : 0.0;
-      launch(c, kSlotNone, k_bicg_x<double>, nb, kThreads, x, (const double*)ph, (const double*)sh, alpha, omega, n);
-      launch(c, kSlotNone, k_axmy<double>, nb, kThreads, r, (const double*)s, omega, (const double*)t, n);
+      launch(c, kSlotVector, k_bicg_x<double>, nb, kThreads, x, (const double*)ph, (const double*)sh, alpha, omega, n);
+      launch(c, kSlotVector, k_axmy<double>, nb, kThreads, r, (const double*)s, omega, (const double*)t, n);
       rho = rho1;
       ++it;
       double rr = reduce_max_abs(c, r, n, &st);

@@ -260,10 +260,12 @@ class HBFlow:
         return float(self.lib.hbf_cfl_dt(self.ctx, cfl))
 
     PROFILE_SLOTS = dict(visc_smooth=0, visc_resid=1, nodal_smooth=2, nodal_resid=3, mac_smooth=4,
-                         mac_resid=5, explicit=6)
+                         mac_resid=5, explicit=6, bottom=7, transfer=8, reduce=9, vector=10, coarse=11)
 
-    def profile_enable(self, on=True):
-        self._check(self.lib.hbf_profile_enable(self.ctx, int(bool(on))))
+    def profile_enable(self, level=1):
+        """0 off, 1 finest-level solver kernels and explicit stages, 2 also
+        bottom solves, transfers, reductions, vector updates, coarse levels."""
+        self._check(self.lib.hbf_profile_enable(self.ctx, int(level)))
 
     def profile_read(self, slot):
         ms = ctypes.c_double()
