@@ -37,7 +37,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the plain FP64 method on the same workload")
     ap.add_argument("--workload", default="cavity256_3d_hb")
     ap.add_argument("--n", type=int, default=0, help="override cells per axis (testing only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -202,42 +204,46 @@ def run_ours(args):
     dt = cfg["dt"]
     stream = torch.cuda.current_stream()
 
-    for _ in range(args.warmup):
-        sim.step(dt)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
+    def timed(sim_, level, clocks_=None, profiler_range=False):
+        for _ in range(args.warmup):
+            sim_.step(dt)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        sim_.profile_enable(level)
+        n0 = sim_.launch_count()
+        cyc = {"mac": 0, "visc": 0, "nodal": 0}
+        conv = True
+        torch.cuda.synchronize()
+        if clocks_ is not None:
+            clocks_.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if profiler_range:
+            torch.cuda.profiler.start()
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = sim_.step(dt)
+            for k in cyc:
+                cyc[k] += st[k]["cycles"]
+                conv &= st[k]["converged"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if profiler_range:
+            torch.cuda.profiler.stop()
+        clk_ = clocks_.stop() if clocks_ is not None else None
+        ms_ = e0.elapsed_time(e1)
+        nl = sim_.launch_count() - n0
+        prof_ = {k: sim_.profile_read(k) for k in sim_.PROFILE_SLOTS}
+        sim_.profile_enable(0)
+        if dist is not None:
+            t = torch.tensor([ms_], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_ = float(t.item())
+        return ms_, cyc, conv, nl, prof_, clk_
 
     clocks = Clocks(local)
-    sim.profile_enable(2 if args.breakdown else 1)
-    n_launch0 = sim.launch_count()
-    cycles = {"mac": 0, "visc": 0, "nodal": 0}
-    converged = True
-    torch.cuda.synchronize()
-    clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    if args.profiler_range:
-        torch.cuda.profiler.start()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        st = sim.step(dt)
-        for k in cycles:
-            cycles[k] += st[k]["cycles"]
-            converged &= st[k]["converged"]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if args.profiler_range:
-        torch.cuda.profiler.stop()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    launches = sim.launch_count() - n_launch0
-    prof = {k: sim.profile_read(k) for k in sim.PROFILE_SLOTS}
-    sim.profile_enable(0)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, cycles, converged, launches, prof, clk = timed(sim, 2 if args.breakdown else 1, clocks, args.profiler_range)
     value = world * ncell * args.steps / (ms / 1e3)
 
     # ---- end to end through the public API with host buffers ----
@@ -265,6 +271,22 @@ def run_ours(args):
             secs = float(t.item())
         e2e = {"value": world * ncell * args.e2e_steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
+
+    fp64 = None
+    if prec == MIXED and not args.no_fp64_compare:
+        sim.close()
+        ref = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=FP64)
+        ref.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+        ref.set_solver(rtol=1e-10, max_cycles=200)
+        ref.set_field("U", zeros_u)
+        ref.set_field("P", zeros_p)
+        ms64, cyc64, conv64, _, _, _ = timed(ref, 0)
+        ref.close()
+        v64 = world * ncell * args.steps / (ms64 / 1e3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.steps,
+                "cycles_per_step": {k: v / args.steps for k, v in cyc64.items()}, "converged": bool(conv64),
+                "speedup_of_value": value / v64,
+                "note": "plain FP64 method (FP64 V-cycles, FP64 BiCGStab), same workload, residual and protocol"}
 
     if rank != 0:
         if dist is not None:
@@ -305,6 +327,7 @@ def run_ours(args):
                        "cycles_per_step": {k: v / args.steps for k, v in cycles.items()},
                        "converged": bool(converged)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "fp64_method": fp64,
             "clocks": clk,
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0}}
     print(json.dumps(line), flush=True)
