@@ -54,7 +54,7 @@ enum hbf_precision {
  * Sizes in doubles (hbf_field_size): U, USTAR, RHS, GP, LU: d*ncell; P: nnode;
  * ETA, PHI_MAC: ncell; UADV, UMAC: sum over axes a of nface[a] (axis-major);
  * UL, UR: sum over axes a of d*nface[a] (axis-major, then component);
- * ETA_FACES: sum over axes of nface[a]; SLOPES, HATS: d*d*ncell. */
+ * ETA_FACES: sum over axes of nface[a]; SLOPES, HATS: d*d*ncell; NRES0: nnode. */
 enum hbf_field {
   HBF_U = 0,       /* cell velocity u^m (set) / u^{m+1} (after a step) */
   HBF_P = 1,       /* nodal pressure p^{m-1/2} / p^{m+1/2} */
@@ -70,7 +70,8 @@ enum hbf_field {
   HBF_UR = 11,     /* right face states (Eq. 14b) */
   HBF_ETA_FACES = 12, /* face eta of the finest level (axis-major) */
   HBF_SLOPES = 13, /* limited slopes, d*d*ncell, [axis][component] */
-  HBF_HATS = 14    /* transverse terms, d*d*ncell, [axis][component] */
+  HBF_HATS = 14,   /* transverse terms, d*d*ncell, [axis][component] */
+  HBF_NRES0 = 15   /* nodal projection: warm-start residual b - L p of the last hbf_project */
 };
 
 typedef struct {
@@ -79,6 +80,7 @@ typedef struct {
   double r0;       /* initial residual norm */
   double rnorm;    /* final residual norm */
   double bnorm;    /* ||b||_inf (after removing the mean of a singular rhs) */
+  int guess;       /* nodal projection: 1 if the learned initial guess was used */
 } hbf_solve_stats;
 
 typedef struct {
@@ -203,6 +205,51 @@ int64_t hbf_launch_count(const hbf_ctx* ctx);
  * Returns HBF_OK, HBF_ERR_ARG or HBF_ERR_CUDA. */
 #define HBF_NOALLOC_MAX_N 67108864LL
 int hbf_cfl_dt_noalloc(const double* u_dev, int64_t n, double h, double cfl, double* dt_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned initial guess for the nodal projection solve (Eq. 17).  The paper
+ * has no learned part; this network is an addition whose output only changes
+ * the multigrid's starting point: the solve still runs to the same tolerance.
+ *
+ * A 4-level U-Net (16-32-64-128 channels, 3^d convolutions, ReLU, 2^d average
+ * pooling, nearest upsampling with skip concatenation, 1x1 head) on a box of
+ * n[0] x n[1] (x n[2]) points, each a multiple of 8.  BF16 weights and
+ * activations, FP32 accumulation on the tensor cores, FP32 master weights.
+ * Parameters are a flat FP32 vector, layer by layer: W[tap][c_out][c_in] then
+ * b[c_out] for the 14 convolutions (taps in lexicographic order over
+ * {-1,0,1}^d, x slowest; the first layer has c_in = 16 of which only channel 0
+ * is used), then the head's 16 weights and 1 bias.  Arrays x, y, t, mask are
+ * FP32 on the device, one value per point, x fastest.
+ * ------------------------------------------------------------------------- */
+typedef struct hbf_unet hbf_unet;
+
+/* train = 0 allocates only what inference needs.  seed: He-normal init. */
+int hbf_unet_create(hbf_unet** out, int dim, const int64_t n[3], int train, uint64_t seed, void* stream);
+void hbf_unet_destroy(hbf_unet* net);
+const char* hbf_unet_last_error(const hbf_unet* net);
+int64_t hbf_unet_param_count(const hbf_unet* net);
+/* copy the FP32 parameters (or, after backward, their gradients) out/in;
+ * host or device pointers; synchronises */
+int hbf_unet_get_params(hbf_unet* net, float* dst);
+int hbf_unet_set_params(hbf_unet* net, const float* src);
+int hbf_unet_get_grads(hbf_unet* net, float* dst);
+/* y = net(x); y_dev may be NULL (the output stays inside the network) */
+int hbf_unet_forward(hbf_unet* net, const float* x_dev, float* y_dev);
+/* masked mean squared error of the last forward output against t; writes the
+ * output gradient to gy_dev and the loss to *loss (synchronises) */
+int hbf_unet_loss(hbf_unet* net, const float* t_dev, const float* mask_dev, float* gy_dev, double* loss);
+/* accumulate parameter gradients of the last forward for output gradient gy */
+int hbf_unet_backward(hbf_unet* net, const float* gy_dev);
+int hbf_unet_zero_grads(hbf_unet* net);
+/* one Adam step on the accumulated gradients, which it then clears */
+int hbf_unet_adam(hbf_unet* net, double lr, double beta1, double beta2, double eps);
+
+/* Use net (NULL disables) for the initial guess of every nodal projection
+ * solve of ctx: with r0 = b - L p the warm-start residual, the candidate guess
+ * is p + |r0|_inf net(r0 / |r0|_inf); it is kept only if its residual is
+ * smaller than |r0|_inf, otherwise the solve starts from p.  The network's
+ * box must hold the (n+1)^d nodes: each of its sizes >= n[a] + 1. */
+int hbf_set_guess_model(hbf_ctx* ctx, hbf_unet* net);
 
 int hbf_sync(hbf_ctx* ctx);
 const char* hbf_last_error(const hbf_ctx* ctx);

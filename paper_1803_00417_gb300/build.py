@@ -20,6 +20,7 @@ UNITS = {
     "hb_api.cu": [],
     "hb_explicit.cu": ["-fmad=false"],
     "hb_mg.cu": [],
+    "hb_unet.cu": [],
 }
 
 

@@ -89,6 +89,7 @@ static int allocate(hbf_ctx* c) {
   A(c->Lu, (long long)D * g.ncell);
   A(c->p, g.nnode);
   A(c->nrhs, g.nnode);
+  A(c->nres0, g.nnode);
   A(c->eta, g.ncell);
   A(c->phi_mac, g.ncell);
   A(c->mrhs, g.ncell);
@@ -182,6 +183,7 @@ static int field_view(hbf_ctx* c, int which, FieldView* v) {
     case HBF_LU: v->ptr[0] = c->Lu; v->cnt[0] = (long long)D * g.ncell; return 0;
     case HBF_SLOPES: v->ptr[0] = c->slopes; v->cnt[0] = (long long)D * D * g.ncell; return 0;
     case HBF_HATS: v->ptr[0] = c->hats; v->cnt[0] = (long long)D * D * g.ncell; return 0;
+    case HBF_NRES0: v->ptr[0] = c->nres0; v->cnt[0] = g.nnode; return 0;
     case HBF_ETA_FACES:
       v->parts = D;
       for (int a = 0; a < D; ++a) {
@@ -263,6 +265,7 @@ void hbf_destroy(hbf_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  release_guess(c);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hres) cudaFreeHost(c->hres);
   prof_release(c);
@@ -418,7 +421,11 @@ int hbf_project(hbf_ctx* c, double dt, double* u_dev, double* p_dev, hbf_solve_s
   if (!(dt > 0.0)) return fail(c, HBF_ERR_ARG, "dt must be positive");
   int st = launch_nodal_rhs(c, dt, u_dev, p_dev, c->nrhs);
   if (st) return st;
+  if ((st = nodal_residual(c, c->nrhs, p_dev, c->nres0))) return st;
+  int used = 0;
+  if (c->guess && (st = apply_guess(c, c->nrhs, p_dev, &used))) return st;
   int sst = solve_nodal(c, c->nrhs, p_dev, s);
+  if (s) s->guess = used;
   if (sst && sst != HBF_ERR_NOT_CONVERGED) return sst;
   st = launch_project_update(c, dt, u_dev, nullptr, p_dev);
   return st ? st : sst;

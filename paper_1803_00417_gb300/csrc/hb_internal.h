@@ -107,6 +107,11 @@ struct hbf_ctx {
   double* phi_mac = nullptr;  // ncell
   double* mrhs = nullptr;     // ncell, MAC right-hand side
   double* nrhs = nullptr;     // nnode
+  double* nres0 = nullptr;    // nnode: warm-start residual of the last nodal solve
+  // learned initial guess (optional)
+  hbf_unet* guess = nullptr;
+  double* ntry = nullptr;     // nnode: candidate guess
+  float* net_x = nullptr;     // network input, one value per network point
   // BiCGStab vectors of the viscous solve (d*ncell each)
   double *kb = nullptr, *kr = nullptr, *krh = nullptr, *kp = nullptr, *kv = nullptr, *ks = nullptr,
          *kt = nullptr, *kph = nullptr, *ksh = nullptr;
@@ -173,5 +178,11 @@ double reduce_dot(hbf_ctx* c, const double* a, const double* b, long long n, int
 int solve_mac(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
 int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s);
 int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
+int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r);
+
+// learned initial guess (hb_unet.cu): replaces p by the network's guess when
+// that lowers the residual; *used tells which
+int apply_guess(hbf_ctx* c, const double* b, double* p, int* used);
+void release_guess(hbf_ctx* c);
 
 }  // namespace hb

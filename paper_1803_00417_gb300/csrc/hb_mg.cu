@@ -599,6 +599,7 @@ static int finish(hbf_ctx* c, int cycles, double r0, double rn, double bnorm, do
   s.rnorm = rn;
   s.bnorm = bnorm;
   s.converged = rn <= tol;
+  s.guess = 0;
   if (out) *out = s;
   if (!std::isfinite(rn) || !std::isfinite(bnorm)) return fail(c, HBF_ERR_NONFINITE, "non-finite residual norm");
   if (!s.converged) {
@@ -893,6 +894,14 @@ static int solve_nodal_d(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_s
 
 int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s) {
   return c->dim == 2 ? solve_nodal_d<2>(c, rhs, phi, s) : solve_nodal_d<3>(c, rhs, phi, s);
+}
+
+int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r) {
+  if (c->dim == 2)
+    launch(c, kSlotNodalResid, k_nodal_resid<2, double>, grid_for(c->g.nnode), kThreads, x, b, r, c->g);
+  else
+    launch(c, kSlotNodalResid, k_nodal_resid<3, double>, grid_for(c->g.nnode), kThreads, x, b, r, c->g);
+  return cuda_check(c, cudaGetLastError(), "nodal residual");
 }
 
 }  // namespace hb

@@ -20,17 +20,17 @@ LIB_PATH = os.path.join(HERE, "_build", "libhbflow.so")
 HBF_OK = 0
 HBF_ERR_NOT_CONVERGED = -4
 FIELDS = dict(U=0, P=1, ETA=2, USTAR=3, UADV=4, UMAC=5, RHS=6, PHI_MAC=7, GP=8, LU=9, UL=10, UR=11,
-              ETA_FACES=12, SLOPES=13, HATS=14)
+              ETA_FACES=12, SLOPES=13, HATS=14, NRES0=15)
 FP64, MIXED = 0, 1
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("converged", ctypes.c_int), ("r0", ctypes.c_double),
-                ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double)]
+                ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double), ("guess", ctypes.c_int)]
 
     def as_dict(self):
         return dict(cycles=self.cycles, converged=bool(self.converged), r0=self.r0, rnorm=self.rnorm,
-                    bnorm=self.bnorm)
+                    bnorm=self.bnorm, guess=bool(self.guess))
 
 
 class StepStats(ctypes.Structure):
@@ -72,6 +72,22 @@ SIGNATURES = {
     "hbf_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "hbf_cfl_dt_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_unet_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p]),
+    "hbf_unet_destroy": (None, [ctypes.c_void_p]),
+    "hbf_unet_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "hbf_unet_param_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "hbf_unet_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_unet_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_unet_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_unet_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_unet_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "hbf_unet_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_unet_zero_grads": (ctypes.c_int, [ctypes.c_void_p]),
+    "hbf_unet_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double]),
+    "hbf_set_guess_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hbf_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hbf_destroy": (None, [ctypes.c_void_p]),
@@ -278,3 +294,80 @@ class HBFlow:
 
     def sync(self):
         self._check(self.lib.hbf_sync(self.ctx))
+
+
+class UNet:
+    """The learned initial-guess network (hbf_unet_*): a box of ``n`` points
+    (each a multiple of 8).  Arrays passed in are torch CUDA float32 tensors of
+    one value per point, x fastest."""
+
+    def __init__(self, n, train=False, seed=0, stream=None):
+        self.lib = load()
+        self.n = tuple(int(v) for v in n)
+        self.d = len(self.n)
+        nn = (ctypes.c_int64 * 3)(*(list(self.n) + [1] * (3 - self.d)))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        net = ctypes.c_void_p()
+        st = self.lib.hbf_unet_create(ctypes.byref(net), self.d, nn, int(bool(train)), int(seed),
+                                      ctypes.c_void_p(stream))
+        if st != HBF_OK:
+            raise HBFlowError(st, "hbf_unet_create failed")
+        self.net = net
+        self.points = int(np.prod(self.n))
+
+    def close(self):
+        if getattr(self, "net", None):
+            self.lib.hbf_unet_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != HBF_OK:
+            raise HBFlowError(st, self.lib.hbf_unet_last_error(self.net).decode())
+
+    def param_count(self):
+        return int(self.lib.hbf_unet_param_count(self.net))
+
+    def get_params(self):
+        out = np.empty(self.param_count(), dtype=np.float32)
+        self._check(self.lib.hbf_unet_get_params(self.net, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self.lib.hbf_unet_set_params(self.net, ctypes.c_void_p(flat.ctypes.data)))
+
+    def get_grads(self):
+        out = np.empty(self.param_count(), dtype=np.float32)
+        self._check(self.lib.hbf_unet_get_grads(self.net, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def forward(self, x_dev, y_dev=None):
+        self._check(self.lib.hbf_unet_forward(self.net, _ptr(x_dev), _ptr(y_dev) if y_dev is not None else None))
+
+    def loss(self, t_dev, mask_dev, gy_dev):
+        v = ctypes.c_double()
+        self._check(self.lib.hbf_unet_loss(self.net, _ptr(t_dev), _ptr(mask_dev), _ptr(gy_dev), ctypes.byref(v)))
+        return v.value
+
+    def backward(self, gy_dev):
+        self._check(self.lib.hbf_unet_backward(self.net, _ptr(gy_dev)))
+
+    def zero_grads(self):
+        self._check(self.lib.hbf_unet_zero_grads(self.net))
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self.lib.hbf_unet_adam(self.net, lr, beta1, beta2, eps))
+
+
+def set_guess_model(sim, net):
+    """Use ``net`` (a UNet, or None) for the nodal projection's initial guess."""
+    st = sim.lib.hbf_set_guess_model(sim.ctx, net.net if net is not None else None)
+    sim._check(st)

@@ -1,0 +1,95 @@
+"""Training driver of the learned initial guess (marshalling only: the data
+come from the library's solver, the network runs in the library's kernels).
+
+Pairs (x, y) for the nodal projection solve of Eq. 17: x = r0 / |r0|_inf with
+r0 = b - L p^{m-1/2} the warm-start residual, y = (phi - p^{m-1/2}) / |r0|_inf
+the correction the multigrid found.  Both live on the (n+1)^d nodes and are
+zero-padded to the network's box (multiples of 8)."""
+
+import numpy as np
+
+from .hbflow import HBFlow, UNet, from_device_layout
+from .inputs import cavity, rheology_params
+
+
+def net_box(n):
+    """Smallest box of multiples of 8 holding the (n+1)^d nodes."""
+    return tuple(((v + 1 + 7) // 8) * 8 for v in n)
+
+
+def nodes_to_box(a_nodes, n, box):
+    """Flat node array (x fastest, (n+1)^d) -> flat box array (x fastest)."""
+    d = len(n)
+    shp = tuple(v + 1 for v in n)
+    arr = np.asarray(a_nodes, dtype=np.float64).reshape(shp[::-1])
+    out = np.zeros(box[::-1], dtype=np.float32)
+    out[tuple(slice(0, s) for s in shp[::-1])] = arr
+    return out.ravel()
+
+
+def box_mask(n, box):
+    return nodes_to_box(np.ones(int(np.prod([v + 1 for v in n]))), n, box)
+
+
+def sample_params(rng, bi_max=20.0):
+    """Bi ~ U[0, bi_max], n ~ U[0.5, 1.5], Re = 10^U[0,3] (dimensionless groups
+    of Sec. IV), Pa = 1e4."""
+    return dict(Re=10.0 ** rng.uniform(0, 3), nexp=rng.uniform(0.5, 1.5), Bi=rng.uniform(0, bi_max), Pa=1e4)
+
+
+def generate_pairs(n, seeds, steps, skip=1, precision=0, stream=None):
+    """Run cavities from rest with seeded random rheology and collect the
+    nodal-solve pairs of every ``skip``-th step after the first."""
+    import torch
+
+    box = net_box(n)
+    xs, ys, info = [], [], []
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+        cfg = cavity(tuple(n), **sample_params(rng))
+        sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=precision, stream=stream)
+        sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+        d = len(n)
+        nn = int(np.prod(cfg["n"]))
+        sim.set_field("U", np.zeros(d * nn))
+        sim.set_field("P", np.zeros(int(np.prod([v + 1 for v in cfg["n"]]))))
+        for s in range(steps):
+            p_old = sim.get_field("P").copy()
+            st = sim.step(cfg["dt"])
+            if s >= 1 and (s - 1) % skip == 0:
+                r0 = sim.get_field("NRES0")
+                p_new = sim.get_field("P")
+                nrm = float(np.max(np.abs(r0)))
+                if nrm > 0:
+                    xs.append(nodes_to_box(r0 / nrm, n, box))
+                    ys.append(nodes_to_box((p_new - p_old) / nrm, n, box))
+                    info.append(dict(seed=seed, step=s, cycles=st["nodal"]["cycles"]))
+        sim.close()
+    return np.array(xs), np.array(ys), info
+
+
+def train(net, xs, ys, mask, epochs=20, lr=1e-3, batch=4, seed=0, log=None):
+    """Adam on the masked MSE; returns the loss history (mean per epoch)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    dev = "cuda"
+    m = torch.tensor(mask, device=dev)
+    gy = torch.empty(net.points, dtype=torch.float32, device=dev)
+    X = torch.tensor(xs, device=dev)
+    Y = torch.tensor(ys, device=dev)
+    hist = []
+    net.zero_grads()
+    for ep in range(epochs):
+        order = rng.permutation(len(xs))
+        tot = 0.0
+        for q, i in enumerate(order):
+            net.forward(X[i])
+            tot += net.loss(Y[i], m, gy)
+            net.backward(gy)
+            if (q + 1) % batch == 0 or q == len(order) - 1:
+                net.adam(lr=lr)
+        hist.append(tot / len(xs))
+        if log:
+            log(ep, hist[-1])
+    return hist
