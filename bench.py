@@ -38,6 +38,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-learned", action="store_true", help="time the mixed method without the learned guess")
+    ap.add_argument("--learn-n", type=int, default=48, help="cells per axis of the training cavities")
+    ap.add_argument("--learn-epochs", type=int, default=6)
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 method on the same workload")
     ap.add_argument("--workload", default="cavity256_3d_hb")
@@ -194,9 +197,34 @@ def run_ours(args):
     d = cfg["d"]
     ncell = int(np.prod(cfg["n"]))
     prec = MIXED if args.precision == "mixed" else FP64
+    learned = None
+    model = None
+    if prec == MIXED and not args.no_learned:
+        # offline part of the learned guess: solver-generated pairs on small
+        # cavities of the same family, trained by the library's kernels
+        from paper_1803_00417_gb300.hbflow import UNet
+        from paper_1803_00417_gb300.learned import box_mask, generate_pairs, net_box, train
+
+        t0 = time.perf_counter()
+        ln = (args.learn_n,) * d
+        xs, ys, _ = generate_pairs(ln, seeds=range(4), steps=9, precision=MIXED)
+        lbox = net_box(ln)
+        tnet = UNet(lbox, train=True, seed=0)
+        hist = train(tnet, xs, ys, box_mask(ln, lbox), epochs=args.learn_epochs, lr=1e-3, batch=4)
+        params = tnet.get_params()
+        tnet.close()
+        model = UNet(net_box(cfg["n"]), train=False)
+        model.set_params(params)
+        learned = {"train_cavities": f"4 x {args.learn_n}^{d}, random Bi/n/Re", "train_pairs": int(len(xs)),
+                   "epochs": args.learn_epochs, "loss_first": hist[0], "loss_last": hist[-1],
+                   "offline_seconds": time.perf_counter() - t0, "box": list(net_box(cfg["n"]))}
     sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=prec)
     sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
     sim.set_solver(rtol=1e-10, max_cycles=200)
+    if model is not None:
+        from paper_1803_00417_gb300.hbflow import set_guess_model
+
+        set_guess_model(sim, model)
     zeros_u = np.zeros(d * ncell)
     zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
     sim.set_field("U", zeros_u)
@@ -214,6 +242,7 @@ def run_ours(args):
         n0 = sim_.launch_count()
         cyc = {"mac": 0, "visc": 0, "nodal": 0}
         conv = True
+        used = 0
         torch.cuda.synchronize()
         if clocks_ is not None:
             clocks_.start()
@@ -227,6 +256,7 @@ def run_ours(args):
             for k in cyc:
                 cyc[k] += st[k]["cycles"]
                 conv &= st[k]["converged"]
+            used += int(st["nodal"]["guess"])
         e1.record(stream)
         torch.cuda.synchronize()
         if profiler_range:
@@ -240,11 +270,14 @@ def run_ours(args):
             t = torch.tensor([ms_], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_ = float(t.item())
+        timed.guess_used = used
         return ms_, cyc, conv, nl, prof_, clk_
 
     clocks = Clocks(local)
     ms, cycles, converged, launches, prof, clk = timed(sim, 2 if args.breakdown else 1, clocks, args.profiler_range)
     value = world * ncell * args.steps / (ms / 1e3)
+    if learned is not None:
+        learned["guess_accepted_steps"] = f"{timed.guess_used}/{args.steps}"
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -271,6 +304,18 @@ def run_ours(args):
             secs = float(t.item())
         e2e = {"value": world * ncell * args.e2e_steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
+
+    mixed_only = None
+    if model is not None:
+        # the same method without the learned guess, for the V-cycles saved
+        set_guess_model(sim, None)
+        sim.set_field("U", zeros_u)
+        sim.set_field("P", zeros_p)
+        msm, cycm, convm, _, _, _ = timed(sim, 0)
+        mixed_only = {"value": world * ncell * args.steps / (msm / 1e3), "unit": UNIT,
+                      "ms_per_step": msm / args.steps, "converged": bool(convm),
+                      "cycles_per_step": {k: v / args.steps for k, v in cycm.items()}}
+        model.close()
 
     fp64 = None
     if prec == MIXED and not args.no_fp64_compare:
@@ -320,14 +365,15 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == FP64 else "f64+f32", "data": "synthetic",
-            "config": {"workload": args.workload, "n": list(cfg["n"]), "precision": args.precision,
+            "vs_baseline": None, "dtype": "f64" if prec == FP64 else ("f64+f32+bf16" if learned else "f64+f32"), "data": "synthetic",
+            "config": {"workload": args.workload, "n": list(cfg["n"]),
+                       "precision": args.precision + ("+learned" if learned else ""),
                        "rtol": 1e-10, "dt": dt, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "no flush: every field (>= 134 MB) exceeds the 129 MB L2",
                        "cycles_per_step": {k: v / args.steps for k, v in cycles.items()},
                        "converged": bool(converged)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "fp64_method": fp64,
+            "fp64_method": fp64, "learned_guess": learned, "mixed_without_learned": mixed_only,
             "clocks": clk,
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0}}
     print(json.dumps(line), flush=True)

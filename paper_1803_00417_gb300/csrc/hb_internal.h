@@ -110,7 +110,8 @@ struct hbf_ctx {
   double* nres0 = nullptr;    // nnode: warm-start residual of the last nodal solve
   // learned initial guess (optional)
   hbf_unet* guess = nullptr;
-  double* ntry = nullptr;     // nnode: candidate guess
+  double* ntry = nullptr;     // nnode: network correction on the nodes
+  double* nzero = nullptr;    // nnode zeros
   float* net_x = nullptr;     // network input, one value per network point
   // BiCGStab vectors of the viscous solve (d*ncell each)
   double *kb = nullptr, *kr = nullptr, *krh = nullptr, *kp = nullptr, *kv = nullptr, *ks = nullptr,
@@ -179,6 +180,7 @@ int solve_mac(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
 int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s);
 int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
 int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r);
+void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, long long n);  // out = x - a y
 
 // learned initial guess (hb_unet.cu): replaces p by the network's guess when
 // that lowers the residual; *used tells which

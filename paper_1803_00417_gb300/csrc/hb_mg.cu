@@ -904,6 +904,10 @@ int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r) {
   return cuda_check(c, cudaGetLastError(), "nodal residual");
 }
 
+void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, long long n) {
+  launch(c, kSlotVector, k_axmy<double>, grid_for(n), kThreads, out, x, a, y, n);
+}
+
 }  // namespace hb
 
 extern "C" int hbf_cfl_dt_noalloc(const double* u_dev, int64_t n, double h, double cfl, double* dt_dev,

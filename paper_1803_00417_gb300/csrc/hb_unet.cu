@@ -280,6 +280,7 @@ struct hbf_unet {
   double* part = nullptr;
   double* hpart = nullptr;
   long long step = 0;
+  long long nlaunch_fwd = 0;  // kernel launches of one forward pass
   std::vector<void*> allocs;
   std::string err;
 };
@@ -459,15 +460,14 @@ __global__ void k_nodes_to_net(const double* __restrict__ r, double scale, int e
   }
 }
 
-// out[node] = p[node] + scale * y[point]
-__global__ void k_net_to_nodes(const float* __restrict__ y, double scale, const double* __restrict__ p, int e0, int e1,
-                               int e2, Box box, double* __restrict__ out) {
+// delta[node] = y[point]
+__global__ void k_net_to_nodes(const float* __restrict__ y, int e0, int e1, int e2, Box box, double* __restrict__ out) {
   const long long n = (long long)e0 * e1 * e2;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % e0);
     const long long r = t / e0;
     const int j = (int)(r % e1), k = (int)(r / e1);
-    out[t] = p[t] + scale * (double)y[i + (long long)box.X * (j + (long long)box.Y * k)];
+    out[t] = (double)y[i + (long long)box.X * (j + (long long)box.Y * k)];
   }
 }
 
@@ -477,17 +477,24 @@ namespace hb {
 
 void release_guess(hbf_ctx* c) {
   if (c->ntry) cudaFree(c->ntry);
+  if (c->nzero) cudaFree(c->nzero);
   if (c->net_x) cudaFree(c->net_x);
   c->ntry = nullptr;
+  c->nzero = nullptr;
   c->net_x = nullptr;
   c->guess = nullptr;
 }
 
+// Candidate p + alpha delta, delta = the network's correction for the
+// normalised warm-start residual r0, alpha the least-squares step
+// argmin |r0 - alpha L delta|_2; kept only if its max-norm residual is smaller.
 int apply_guess(hbf_ctx* c, const double* b, double* p, int* used) {
+  (void)b;
   *used = 0;
   hbf_unet* N = c->guess;
   int st = 0;
-  const double n0 = reduce_max_abs(c, c->nres0, c->g.nnode, &st);
+  const long long nn = c->g.nnode;
+  const double n0 = reduce_max_abs(c, c->nres0, nn, &st);
   if (st) return st;
   if (!(n0 > 0.0) || !std::isfinite(n0)) return HBF_OK;
   const int e0 = c->g.n[0] + 1, e1 = c->g.n[1] + 1, e2 = c->dim == 3 ? c->g.n[2] + 1 : 1;
@@ -496,21 +503,27 @@ int apply_guess(hbf_ctx* c, const double* b, double* p, int* used) {
   k_nodes_to_net<<<grid(N->P[0]), kThreads, 0, c->stream>>>(c->nres0, 1.0 / n0, e0, e1, e2, N->box[0], c->net_x);
   forward(N, c->net_x);
   N->stream = saved;
-  k_net_to_nodes<<<grid((long long)e0 * e1 * e2), kThreads, 0, c->stream>>>(N->y, n0, p, e0, e1, e2, N->box[0],
-                                                                           c->ntry);
-  c->nlaunch += 40;
+  k_net_to_nodes<<<grid(nn), kThreads, 0, c->stream>>>(N->y, e0, e1, e2, N->box[0], c->ntry);
+  c->nlaunch += N->nlaunch_fwd + 2;
   if ((st = cuda_check(c, cudaGetLastError(), "learned guess"))) return st;
-  // keep the candidate only if its residual is smaller
-  if ((st = nodal_residual(c, b, c->ntry, c->lv[0].nr))) return st;
-  const double n1 = reduce_max_abs(c, c->lv[0].nr, c->g.nnode, &st);
+  // w = -L delta, alpha = -(r0, w)/(w, w), candidate residual r0 + alpha w
+  double* w = c->lv[0].nr;
+  double* rtry = c->lv[0].nb;
+  if ((st = nodal_residual(c, c->nzero, c->ntry, w))) return st;
+  const double rw = reduce_dot(c, c->nres0, w, nn, &st);
+  if (st) return st;
+  const double ww = reduce_dot(c, w, w, nn, &st);
+  if (st) return st;
+  if (!(ww > 0.0) || !std::isfinite(rw)) return HBF_OK;
+  const double alpha = -rw / ww;
+  axmy(c, rtry, c->nres0, -alpha, w, nn);
+  const double n1 = reduce_max_abs(c, rtry, nn, &st);
   if (st) return st;
   if (n1 < n0) {
-    if ((st = cuda_check(c, cudaMemcpyAsync(p, c->ntry, (size_t)c->g.nnode * sizeof(double), cudaMemcpyDeviceToDevice,
-                                            c->stream), "guess copy")))
-      return st;
+    axmy(c, p, p, -alpha, c->ntry, nn);
     *used = 1;
   }
-  return HBF_OK;
+  return cuda_check(c, cudaGetLastError(), "learned guess");
 }
 
 }  // namespace hb
@@ -529,6 +542,7 @@ int hbf_unet_create(hbf_unet** out, int dim, const int64_t n[3], int train, uint
   if (!N) return HBF_ERR_OOM;
   N->d = dim;
   N->train = train != 0;
+  N->nlaunch_fwd = 25;  // pack, 14 convolutions, 3 pools, 3 upsamples, 3 copies, head
   N->stream = (cudaStream_t)stream;
   for (int l = 0; l < 4; ++l) {
     const int s = 1 << l;
@@ -728,6 +742,8 @@ int hbf_set_guess_model(hbf_ctx* c, hbf_unet* N) {
   for (int a = 0; a < c->dim; ++a)
     if (b[a] < e[a]) return hb::fail(c, HBF_ERR_ARG, "guess model box is smaller than the node grid");
   if (cudaMalloc((void**)&c->ntry, (size_t)c->g.nnode * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->nzero, (size_t)c->g.nnode * sizeof(double)) != cudaSuccess ||
+      cudaMemset(c->nzero, 0, (size_t)c->g.nnode * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&c->net_x, (size_t)N->P[0] * sizeof(float)) != cudaSuccess) {
     hb::release_guess(c);
     return hb::fail(c, HBF_ERR_OOM, "guess buffers");

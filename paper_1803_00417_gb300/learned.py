@@ -2,8 +2,9 @@
 come from the library's solver, the network runs in the library's kernels).
 
 Pairs (x, y) for the nodal projection solve of Eq. 17: x = r0 / |r0|_inf with
-r0 = b - L p^{m-1/2} the warm-start residual, y = (phi - p^{m-1/2}) / |r0|_inf
-the correction the multigrid found.  Both live on the (n+1)^d nodes and are
+r0 = b - L p^{m-1/2} the warm-start residual, y = d / |d|_inf with
+d = phi - p^{m-1/2} the correction the multigrid found.  The network learns the
+direction of the correction; the library scales it by a least-squares step.  Both live on the (n+1)^d nodes and are
 zero-padded to the network's box (multiples of 8)."""
 
 import numpy as np
@@ -60,9 +61,11 @@ def generate_pairs(n, seeds, steps, skip=1, precision=0, stream=None):
                 r0 = sim.get_field("NRES0")
                 p_new = sim.get_field("P")
                 nrm = float(np.max(np.abs(r0)))
-                if nrm > 0:
+                dphi = p_new - p_old
+                dn = float(np.max(np.abs(dphi)))
+                if nrm > 0 and dn > 0:
                     xs.append(nodes_to_box(r0 / nrm, n, box))
-                    ys.append(nodes_to_box((p_new - p_old) / nrm, n, box))
+                    ys.append(nodes_to_box(dphi / dn, n, box))
                     info.append(dict(seed=seed, step=s, cycles=st["nodal"]["cycles"]))
         sim.close()
     return np.array(xs), np.array(ys), info
