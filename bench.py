@@ -39,8 +39,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-learned", action="store_true", help="time the mixed method without the learned guess")
-    ap.add_argument("--learn-n", type=int, default=48, help="cells per axis of the training cavities")
-    ap.add_argument("--learn-epochs", type=int, default=6)
+    ap.add_argument("--learn-n", type=int, default=64, help="cells per axis of the training cavities")
+    ap.add_argument("--learn-seeds", type=int, default=6)
+    ap.add_argument("--learn-steps", type=int, default=10)
+    ap.add_argument("--learn-epochs", type=int, default=15)
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 method on the same workload")
     ap.add_argument("--workload", default="cavity256_3d_hb")
@@ -207,7 +209,7 @@ def run_ours(args):
 
         t0 = time.perf_counter()
         ln = (args.learn_n,) * d
-        xs, ys, _ = generate_pairs(ln, seeds=range(4), steps=9, precision=MIXED)
+        xs, ys, _ = generate_pairs(ln, seeds=range(args.learn_seeds), steps=args.learn_steps, precision=MIXED)
         lbox = net_box(ln)
         tnet = UNet(lbox, train=True, seed=0)
         hist = train(tnet, xs, ys, box_mask(ln, lbox), epochs=args.learn_epochs, lr=1e-3, batch=4)
@@ -215,7 +217,8 @@ def run_ours(args):
         tnet.close()
         model = UNet(net_box(cfg["n"]), train=False)
         model.set_params(params)
-        learned = {"train_cavities": f"4 x {args.learn_n}^{d}, random Bi/n/Re", "train_pairs": int(len(xs)),
+        learned = {"train_cavities": f"{args.learn_seeds} x {args.learn_n}^{d}, random Bi/n/Re",
+                   "train_pairs": int(len(xs)),
                    "epochs": args.learn_epochs, "loss_first": hist[0], "loss_last": hist[-1],
                    "offline_seconds": time.perf_counter() - t0, "box": list(net_box(cfg["n"]))}
     sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=prec)
