@@ -6,7 +6,8 @@ V-cycle, written the textbook way:
 
     V(l): nu1 smoothing sweeps; r = b - A x; restrict r; solve the coarse error
           equation by V(l+1) from zero; prolong and add; nu2 sweeps.
-    coarsest level: ``nu_bottom`` smoothing sweeps.
+    coarsest level: an exact dense solve when it has at most DENSE_MAX
+    unknowns (the usual case: 2^d cells), else ``nu_bottom`` smoothing sweeps.
     stop when ||b - A x||_inf <= rtol ||b||_inf (||b|| after removing the mean
     of a singular problem's right-hand side).
 
@@ -330,13 +331,65 @@ def _residual(prob, l, x, b):
     return [b[c] - Ax[c] for c in range(len(b))]
 
 
+DENSE_MAX = 128
+
+
+def _flat(xs):
+    return np.concatenate([x.ravel() for x in xs])
+
+
+def _unflat(v, like):
+    out, k = [], 0
+    for a in like:
+        out.append(v[k:k + a.size].reshape(a.shape))
+        k += a.size
+    return out
+
+
+def _bottom_dense(prob, l, x, b):
+    """x = exact solution of the level-l problem for right-hand side b (the
+    affine part of a level with wall values is moved to the right).  Singular
+    problems are solved with their (weighted) mean-zero constraint appended as
+    a bordered row and column."""
+    cache = prob.__dict__.setdefault("_dense_cache", {})
+    key = (l, bool(getattr(prob, "hom0", False)))
+    like = prob.zeros(l)
+    if key not in cache:
+        z = prob.zeros(l)
+        a0 = _flat(prob.apply(l, z))
+        n = a0.size
+        M = np.zeros((n, n))
+        for k in range(n):
+            e = np.zeros(n)
+            e[k] = 1.0
+            M[:, k] = _flat(prob.apply(l, _unflat(e, like))) - a0
+        if prob.singular:
+            w = _flat([prob.weights[l]]) if isinstance(prob, NodalPoisson) else np.ones(n)
+            B = np.zeros((n + 1, n + 1))
+            B[:n, :n] = M
+            B[:n, n] = w
+            B[n, :n] = w
+            M = B
+        cache[key] = (M, a0)
+    M, a0 = cache[key]
+    rhs = _flat(b) - a0
+    if prob.singular:
+        rhs = np.concatenate([rhs, [0.0]])
+    sol = np.linalg.solve(M, rhs)[:a0.size]
+    for xc, sc in zip(x, _unflat(sol, like)):
+        xc[...] = sc
+
+
 def vcycle(prob, l, x, b, params):
     if l == len(prob.levels) - 1:
         if prob.singular:
             b = [bc.copy() for bc in b]
             prob.sub_mean(l, b)
-        for _ in range(params.nu_bottom):
-            prob.smooth(l, x, b)
+        if sum(a.size for a in x) <= DENSE_MAX:
+            _bottom_dense(prob, l, x, b)
+        else:
+            for _ in range(params.nu_bottom):
+                prob.smooth(l, x, b)
         if prob.singular:
             prob.sub_mean(l, x)
         return

@@ -121,6 +121,10 @@ static int allocate(hbf_ctx* c) {
     A(c->fksh, (long long)D * g.ncell);
     A(c->fke, (long long)D * g.ncell);
   }
+  for (int q = 0; q < 3; ++q) A(c->dense[q].Minv, (long long)(kDenseMax + 1) * (kDenseMax + 1));
+  A(c->dX, (long long)kDenseMax * kDenseMax);
+  A(c->dM, (long long)(kDenseMax + 1) * (kDenseMax + 1));
+  A(c->dA, (long long)(kDenseMax + 1) * 2 * (kDenseMax + 1));
   A(c->partial, kRedBlocks);
   A(c->dres, 8);
   if (cudaMallocHost((void**)&c->hres, 8 * sizeof(double)) != cudaSuccess)

@@ -82,7 +82,8 @@ __global__ void k_eta_faces(const double* __restrict__ eta, double* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Stage 2: cell G p from nodes and L_eta u = div(eta (grad u + grad u^T))
+// Stage 2: cell G p from nodes (L_eta u itself is evaluated by the
+// multigrid unit's operator kernel, k_tensor_lu)
 // ---------------------------------------------------------------------------
 template <int D>
 __host__ __device__ inline double grad_nodal(const double* __restrict__ p, const Geom& g, int a, int i, int j,
@@ -124,74 +125,6 @@ __global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, 
   }
 }
 
-// Tangential derivative (d_c u_a) on the a-face between cell L and L + e_a:
-// mean of the two cells' central c-differences; zero on a wall face.
-template <int D, typename T>
-__host__ __device__ inline T face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
-                               bool hom) {
-  if (L[a] < 0 || L[a] >= g.n[a] - 1) return T(0);
-  int q[3];
-  T dL, dR;
-  {
-    int p1[3] = {L[0], L[1], L[2]}, p0[3] = {L[0], L[1], L[2]};
-    p1[c] += 1;
-    p0[c] -= 1;
-    dL = (uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom)) /
-         (T(2) * T(g.h));
-  }
-  {
-    int p1[3] = {L[0], L[1], L[2]}, p0[3] = {L[0], L[1], L[2]};
-    p1[a] += 1;
-    p0[a] += 1;
-    p1[c] += 1;
-    p0[c] -= 1;
-    dR = (uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom)) /
-         (T(2) * T(g.h));
-  }
-  (void)q;
-  return T(0.5) * (dL + dR);
-}
-
-// (L_eta u)_c at cell p with face eta arrays ef[a]
-template <int D, typename T>
-__host__ __device__ inline T tensor_op_point(const T* __restrict__ u, const T* const* ef, const Geom& g, int c,
-                                    const int* p, bool hom) {
-  const T* uc = u + (size_t)c * g.ncell;
-  T acc = T(0);
-  T h = T(g.h);
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    T flux[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      int L[3] = {p[0], p[1], p[2]};
-      L[a] += s - 1;  // face between L and L + e_a
-      int R[3] = {L[0], L[1], L[2]};
-      R[a] += 1;
-      T ef_ = ef[a][fidx(g, a, R[0], R[1], R[2])];
-      T nrm = (uget<D>(uc, g, c, R[0], R[1], R[2], hom) - uget<D>(uc, g, c, L[0], L[1], L[2], hom)) / h;
-      if (a == c)
-        flux[s] = ef_ * (T(2) * nrm);
-      else
-        flux[s] = ef_ * (nrm + face_cross<D, T>(u + (size_t)a * g.ncell, g, a, c, L, hom));
-    }
-    acc += (flux[1] - flux[0]) / h;
-  }
-  return acc;
-}
-
-template <int D>
-__global__ void k_tensor_op(const double* __restrict__ u, const double* ef0, const double* ef1,
-                            const double* ef2, double* __restrict__ out, Geom g) {
-  const double* ef[3] = {ef0, ef1, ef2};
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    int p[3];
-    cell_coords<D>(g, t, p[0], p[1], p[2]);
-#pragma unroll
-    for (int c = 0; c < D; ++c) out[(size_t)c * g.ncell + t] = tensor_op_point<D, double>(u, ef, g, c, p, false);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Stage 3: Godunov edge states (Eqs. 11-14)
 // ---------------------------------------------------------------------------
@@ -202,17 +135,8 @@ __host__ __device__ inline double sgn_min(double v, double lim) {
   return v > 0.0 ? m : -m;
 }
 
-// Colella's fourth-order limited slope along axis a for component c
-template <int D>
-__host__ __device__ inline double limited_slope(const double* __restrict__ uc, const Geom& g, int c, int a,
-                                       const int* p) {
-  double w[5];
-#pragma unroll
-  for (int o = -2; o <= 2; ++o) {
-    int q[3] = {p[0], p[1], p[2]};
-    q[a] += o;
-    w[o + 2] = uget<D>(uc, g, c, q[0], q[1], q[2], false);
-  }
+// Colella's slope from the five values w[0..4] at offsets -2..2
+__host__ __device__ inline double slope5(const double* w) {
   double dlim[3], dC[3], df[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) {  // cells p-1, p, p+1
@@ -228,14 +152,31 @@ __host__ __device__ inline double limited_slope(const double* __restrict__ uc, c
 
 template <int D>
 __global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slopes, Geom g) {
+  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+    for (int a = 0; a < D; ++a) {
+      const bool inner = p[a] >= 2 && p[a] <= g.n[a] - 3;
 #pragma unroll
-      for (int c = 0; c < D; ++c)
-        slopes[(size_t)(a * D + c) * g.ncell + t] = limited_slope<D>(u + (size_t)c * g.ncell, g, c, a, p);
+      for (int c = 0; c < D; ++c) {
+        const double* uc = u + (size_t)c * g.ncell;
+        double w[5];
+        if (inner) {
+#pragma unroll
+          for (int o = -2; o <= 2; ++o) w[o + 2] = uc[t + o * st[a]];
+        } else {
+#pragma unroll
+          for (int o = -2; o <= 2; ++o) {
+            int q[3] = {p[0], p[1], p[2]};
+            q[a] += o;
+            w[o + 2] = uget<D>(uc, g, c, q[0], q[1], q[2], false);
+          }
+        }
+        slopes[(size_t)(a * D + c) * g.ncell + t] = slope5(w);
+      }
+    }
   }
 }
 
@@ -548,8 +489,7 @@ int launch_predict(hbf_ctx* c, double dt) {
   HB_DISPATCH(c->dim, k_grad_p, grid_for(g.ncell), c->p, c->Gp, g);
   int st = launch_eta_faces(c);
   if (st) return st;
-  HB_DISPATCH(c->dim, k_tensor_op, grid_for(g.ncell), c->u, c->lv[0].ef[0], c->lv[0].ef[1],
-              c->lv[0].ef[2], c->Lu, g);
+  if ((st = tensor_lu(c, c->u, c->Lu))) return st;
   HB_DISPATCH(c->dim, k_slopes, grid_for(g.ncell), c->u, c->slopes, g);
   HB_DISPATCH(c->dim, k_hats, grid_for(g.ncell), c->u, c->slopes, c->hats, g, dt);
   for (int a = 0; a < c->dim; ++a)

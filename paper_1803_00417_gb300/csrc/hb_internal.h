@@ -70,6 +70,15 @@ inline bool prof_wants(const Prof& P, int slot) {
 
 constexpr size_t kProfPairs = 16384;
 
+// exact coarsest-level solve: inverse of the (bordered, for singular
+// problems) dense operator of the bottom level
+constexpr int kDenseMax = 128;  // unknowns
+struct Dense {
+  double* Minv = nullptr;  // (kDenseMax+1)^2
+  int n = 0;               // matrix size (unknowns, +1 when bordered)
+  bool valid = false;
+};
+
 struct SolverCfg {
   double rtol = 1e-10;
   int max_cycles = 200;
@@ -127,6 +136,8 @@ struct hbf_ctx {
   std::vector<void*> allocs;
   hb::Prof prof;
   long long nlaunch = 0;
+  hb::Dense dense[3];  // viscous, MAC, nodal
+  double *dX = nullptr, *dM = nullptr, *dA = nullptr;  // build scratch
 };
 
 namespace hb {
@@ -180,6 +191,7 @@ int solve_mac(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
 int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s);
 int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
 int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r);
+int tensor_lu(hbf_ctx* c, const double* u, double* out);  // out = L_eta u, finest level
 void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, long long n);  // out = x - a y
 
 // learned initial guess (hb_unet.cu): replaces p by the network's guess when

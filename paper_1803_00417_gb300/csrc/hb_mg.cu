@@ -392,12 +392,29 @@ struct Problem {
   virtual void resid(int l) = 0;
   virtual void restrict_to(int l) = 0;  // b(l+1) = R r(l), x(l+1) = 0
   virtual void prolong_add(int l) = 0;  // x(l) += P x(l+1)
-  virtual void bottom(int l) = 0;       // FP64 sweeps on the coarsest level
+  virtual void bottom(int l) = 0;       // FP64 solve on the coarsest level
   virtual int sub_mean(int l, double* v) { (void)l; (void)v; return 0; }
+  virtual int kind() const = 0;         // 0 viscous, 1 MAC, 2 nodal
+  virtual double dense_beta() const { return 0.0; }
 };
 
-// coarsest level in FP64 for either precision: the FP32 path converts in and out
-template <typename T>
+// dense inverse of the bottom operator of problem kind `kind` at level l
+template <int D>
+static void build_dense(hbf_ctx* c, int kind, int l, long long n, double beta) {
+  Level& L = c->lv[l];
+  Dense& Dn = c->dense[kind];
+  const int m = kind == 0 ? (int)n : (int)n + 1;
+  launch(c, kSlotBottom, k_dense_build<D>, (int)n, 128, kind, c->dX, c->dM, (int)n, m, (const double*)L.ef[0],
+         (const double*)L.ef[1], (const double*)L.ef[2], L.g, beta);
+  launch(c, kSlotBottom, k_gauss_jordan, 1, 256, (const double*)c->dM, m, c->dA, Dn.Minv);
+  Dn.n = m;
+  Dn.valid = true;
+}
+
+// coarsest level in FP64 for either precision (the FP32 path converts in and
+// out): exact dense solve when it has at most kDenseMax unknowns, else
+// nu_bottom smoothing sweeps
+template <int D, typename T>
 static void bottom_fp64(Problem<T>& P, int l, double* xd, double* bd, void (*run)(Problem<T>&, int, double*, double*)) {
   hbf_ctx* c = P.c;
   long long n = P.count(l);
@@ -406,7 +423,13 @@ static void bottom_fp64(Problem<T>& P, int l, double* xd, double* bd, void (*run
     launch(c, kSlotTransfer, k_zero<double>, grid_for(n), kThreads, xd, n);
   }
   if (P.singular) P.sub_mean(l, bd);
-  run(P, l, xd, bd);
+  if (n <= kDenseMax) {
+    Dense& Dn = c->dense[P.kind()];
+    if (!Dn.valid) build_dense<D>(c, P.kind(), l, n, P.dense_beta());
+    launch(c, kSlotBottom, k_dense_apply, 1, 256, (const double*)Dn.Minv, Dn.n, (const double*)bd, (int)n, xd);
+  } else {
+    run(P, l, xd, bd);
+  }
   if (P.singular) P.sub_mean(l, xd);
   if (!std::is_same<T, double>::value)
     launch(c, kSlotTransfer, k_convert<T, double>, grid_for(n), kThreads, P.x(l), (const double*)xd, n);
@@ -418,6 +441,8 @@ struct ViscProblem : Problem<T> {
   T* x0;
   double beta;
   ViscProblem(hbf_ctx* ctx, T* x_in, double bt, bool h0) : Problem<T>(ctx, false, h0), x0(x_in), beta(bt) {}
+  int kind() const override { return 0; }
+  double dense_beta() const override { return beta; }
   T* x(int l) override { return l == 0 ? x0 : View<T>::vx(c->lv[l]); }
   T* b(int l) override { return View<T>::vb(c->lv[l]); }
   T* r(int l) override { return View<T>::vr(c->lv[l]); }
@@ -469,7 +494,7 @@ struct ViscProblem : Problem<T> {
     Level& L = c->lv[l];
     double* xd = std::is_same<T, double>::value ? (double*)x(l) : L.vx;
     double* bd = std::is_same<T, double>::value ? (double*)b(l) : L.vb;
-    bottom_fp64<T>(*this, l, xd, bd, &run_bottom);
+    bottom_fp64<D, T>(*this, l, xd, bd, &run_bottom);
   }
 };
 
@@ -478,6 +503,7 @@ struct MacProblem : Problem<T> {
   using Problem<T>::c;
   T* x0;
   MacProblem(hbf_ctx* ctx, T* x_in) : Problem<T>(ctx, true, true), x0(x_in) {}
+  int kind() const override { return 1; }
   T* x(int l) override { return l == 0 ? x0 : View<T>::cx(c->lv[l]); }
   T* b(int l) override { return View<T>::cb(c->lv[l]); }
   T* r(int l) override { return View<T>::cr(c->lv[l]); }
@@ -511,7 +537,7 @@ struct MacProblem : Problem<T> {
     Level& L = c->lv[l];
     double* xd = std::is_same<T, double>::value ? (double*)x(l) : L.cx;
     double* bd = std::is_same<T, double>::value ? (double*)b(l) : L.cb;
-    bottom_fp64<T>(*this, l, xd, bd, &run_bottom);
+    bottom_fp64<D, T>(*this, l, xd, bd, &run_bottom);
   }
   int sub_mean(int l, double* v) override {
     Level& L = c->lv[l];
@@ -528,6 +554,7 @@ struct NodalProblem : Problem<T> {
   using Problem<T>::c;
   T* x0;
   NodalProblem(hbf_ctx* ctx, T* x_in) : Problem<T>(ctx, true, true), x0(x_in) {}
+  int kind() const override { return 2; }
   T* x(int l) override { return l == 0 ? x0 : View<T>::nx(c->lv[l]); }
   T* b(int l) override { return View<T>::nb(c->lv[l]); }
   T* r(int l) override { return View<T>::nr(c->lv[l]); }
@@ -560,7 +587,7 @@ struct NodalProblem : Problem<T> {
     Level& L = c->lv[l];
     double* xd = std::is_same<T, double>::value ? (double*)x(l) : L.nx;
     double* bd = std::is_same<T, double>::value ? (double*)b(l) : L.nb;
-    bottom_fp64<T>(*this, l, xd, bd, &run_bottom);
+    bottom_fp64<D, T>(*this, l, xd, bd, &run_bottom);
   }
   int sub_mean(int l, double* v) override {
     Level& L = c->lv[l];
@@ -774,6 +801,7 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
 template <int D>
 static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* x, hbf_solve_stats* out) {
   build_eta_levels<D>(c);
+  c->dense[0].valid = false;  // new viscosity and dt: rebuild the bottom inverse
   if (c->precision == HBF_MIXED) return solve_viscous_mixed<D>(c, beta, b_in, x, out);
   const SolverCfg& cfg = c->cfg;
   Level& L0 = c->lv[0];
@@ -906,6 +934,17 @@ int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r) {
 
 void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, long long n) {
   launch(c, kSlotVector, k_axmy<double>, grid_for(n), kThreads, out, x, a, y, n);
+}
+
+int tensor_lu(hbf_ctx* c, const double* u, double* out) {
+  const Level& L = c->lv[0];
+  if (c->dim == 2)
+    launch(c, kSlotExplicit, k_tensor_lu<2, double>, grid_for(L.g.ncell, 152 * 24), kThreads, u, out,
+           (const double*)L.ef[0], (const double*)L.ef[1], (const double*)L.ef[2], L.g, 0);
+  else
+    launch(c, kSlotExplicit, k_tensor_lu<3, double>, grid_for(L.g.ncell, 152 * 24), kThreads, u, out,
+           (const double*)L.ef[0], (const double*)L.ef[1], (const double*)L.ef[2], L.g, 0);
+  return cuda_check(c, cudaGetLastError(), "k_tensor_lu");
 }
 
 }  // namespace hb

@@ -334,6 +334,23 @@ __global__ void k_visc_apply(const T* __restrict__ u, T* __restrict__ out, const
   }
 }
 
+// out = L_eta u (the stress divergence alone), grid-stride over cells
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_tensor_lu(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
+                                                  const T* ef1, const T* ef2, Geom g, int hom) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  const Strides S = make_strides(g);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    int p[3];
+    cell_coords<D>(g, t, p[0], p[1], p[2]);
+    const bool in = interior<D>(g, p);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      out[(size_t)c * g.ncell + t] =
+          in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+  }
+}
+
 // coarsest level: all sweeps in one block
 template <int D, typename T>
 __global__ void k_visc_bottom(T* __restrict__ u, const T* __restrict__ b, const T* ef0, const T* ef1,
@@ -714,6 +731,151 @@ __global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec
     }
     T v = (D == 3 && (k & 1)) ? T(0.5) * (tz[0] + tz[1]) : tz[0];
     xf[t] += v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// exact coarsest-level solve: dense operator, Gauss-Jordan inverse, product
+// ---------------------------------------------------------------------------
+// cell Laplacian of x at p (Neumann walls), as k_cell_resid
+template <int D, typename T>
+__device__ inline T cell_lap_point(const T* __restrict__ x, const Geom& g, const int* p) {
+  const T ih = T(1.0 / g.h);
+  const T xc = x[cidx<D>(g, p[0], p[1], p[2])];
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    T glo = T(0), ghi = T(0);
+    if (p[a] > 0) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[a] -= 1;
+      glo = (xc - x[cidx<D>(g, q[0], q[1], q[2])]) * ih;
+    }
+    if (p[a] < g.n[a] - 1) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[a] += 1;
+      ghi = (x[cidx<D>(g, q[0], q[1], q[2])] - xc) * ih;
+    }
+    acc += (ghi - glo) * ih;
+  }
+  return acc;
+}
+
+// Column k of the bottom operator (kind 0 viscous, 1 MAC, 2 nodal), applied to
+// the unit vector e_k held in X[k*n ..]; M is row-major with leading size ld.
+// Singular problems get the constraint row/column of weights w (1 for cells,
+// the dual-cell fraction for nodes).
+template <int D>
+__global__ void k_dense_build(int kind, double* __restrict__ X, double* __restrict__ M, int n, int ld,
+                              const double* ef0, const double* ef1, const double* ef2, Geom g, double beta) {
+  const int k = blockIdx.x;
+  double* e = X + (size_t)k * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) e[i] = (i == k) ? 1.0 : 0.0;
+  __syncthreads();
+  const double* ef[3] = {ef0, ef1, ef2};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v;
+    int p[3];
+    if (kind == 0) {
+      const int c = i / g.ncell, t = i % g.ncell;
+      cell_coords<D>(g, t, p[0], p[1], p[2]);
+      v = e[i] - beta * mg_tensor_point<D, double>(e, ef, g, c, p, true);
+    } else if (kind == 1) {
+      cell_coords<D>(g, i, p[0], p[1], p[2]);
+      v = cell_lap_point<D, double>(e, g, p);
+    } else {
+      const int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
+      p[0] = i % e0;
+      p[1] = (i / e0) % e1;
+      p[2] = i / (e0 * e1);
+      v = nodal_lap_point<D, double>(e, g, p, false) * (1.0 / (g.h * g.h));
+    }
+    M[(size_t)i * ld + k] = v;
+  }
+  if (kind != 0 && threadIdx.x == 0) {
+    // constraint entries of column k and (for the last block) the border
+    double w = 1.0;
+    if (kind == 2) {
+      const int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
+      const int pi = k % e0, pj = (k / e0) % e1, pk = k / (e0 * e1);
+      if (pi == 0 || pi == g.n[0]) w *= 0.5;
+      if (pj == 0 || pj == g.n[1]) w *= 0.5;
+      if (D == 3 && (pk == 0 || pk == g.n[2])) w *= 0.5;
+    }
+    M[(size_t)n * ld + k] = w;
+    M[(size_t)k * ld + n] = w;
+    if (k == 0) M[(size_t)n * ld + n] = 0.0;
+  }
+}
+
+// Gauss-Jordan with partial pivoting on [M | I] (m x 2m, A), one block;
+// writes the inverse to Minv (m x m).  Returns with Minv = 0 if singular.
+__global__ void k_gauss_jordan(const double* __restrict__ M, int m, double* __restrict__ A, double* __restrict__ Minv) {
+  __shared__ double fcol[kDenseMax + 1];
+  __shared__ double sv[256];
+  __shared__ int si[256];
+  __shared__ int piv;
+  const int w2 = 2 * m;
+  for (int t = threadIdx.x; t < m * w2; t += blockDim.x) {
+    const int i = t / w2, j = t % w2;
+    A[t] = j < m ? M[(size_t)i * m + j] : (j - m == i ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+      const double a = fabs(A[(size_t)i * w2 + k]);
+      if (a > best) {
+        best = a;
+        bi = i;
+      }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = -1.0;
+      int ib = k;
+      for (int q = 0; q < (int)blockDim.x; ++q)
+        if (sv[q] > b) {
+          b = sv[q];
+          ib = si[q];
+        }
+      piv = ib;
+    }
+    __syncthreads();
+    const int pr = piv;
+    if (pr != k)
+      for (int j = threadIdx.x; j < w2; j += blockDim.x) {
+        const double t0 = A[(size_t)k * w2 + j];
+        A[(size_t)k * w2 + j] = A[(size_t)pr * w2 + j];
+        A[(size_t)pr * w2 + j] = t0;
+      }
+    __syncthreads();
+    const double d = A[(size_t)k * w2 + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < w2; j += blockDim.x) A[(size_t)k * w2 + j] /= d;
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) fcol[i] = A[(size_t)i * w2 + k];
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * w2; t += blockDim.x) {
+      const int i = t / w2, j = t % w2;
+      if (i != k) A[t] -= fcol[i] * A[(size_t)k * w2 + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) Minv[t] = A[(size_t)(t / m) * w2 + m + t % m];
+}
+
+// x[i] = sum_j Minv[i][j] b[j] over the n unknowns (the bordered row/column,
+// when present, multiplies a zero constraint value)
+__global__ void k_dense_apply(const double* __restrict__ Minv, int m, const double* __restrict__ b, int n,
+                              double* __restrict__ x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc += Minv[(size_t)i * m + j] * b[j];
+    x[i] = acc;
   }
 }
 
