@@ -29,8 +29,8 @@ __host__ __device__ inline double viscosity(double g, const Rheo& r) {
 }
 
 template <int D>
-__global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, Geom g, Rheo r) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+__host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, double* __restrict__ eta, Geom g, Rheo r, int t) {
+  
     int i, j, k;
     cell_coords<D>(g, t, i, j, k);
     int p[3] = {i, j, k};
@@ -60,14 +60,20 @@ __global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, Ge
     double gn = sqrt(0.5 * s);
     eta[t] = viscosity(gn, r);
   }
+
+template <int D>
+__global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, Geom g, Rheo r) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_eta_at<D>(u, eta, g, r, t);
+  }
 }
 
 // face eta on level 0: mean of the two cells, wall faces take the interior cell
 template <int D>
-__global__ void k_eta_faces(const double* __restrict__ eta, double* __restrict__ ef, int a, Geom g) {
+__host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict__ eta, double* __restrict__ ef, int a, Geom g, int t) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+  
     int p[3];
     p[0] = t % ex[0];
     int r = t / ex[0];
@@ -78,6 +84,14 @@ __global__ void k_eta_faces(const double* __restrict__ eta, double* __restrict__
     if (L[a] < 0) L[a] = 0;
     if (R[a] >= g.n[a]) R[a] = g.n[a] - 1;
     ef[t] = 0.5 * (eta[cidx<D>(g, L[0], L[1], L[2])] + eta[cidx<D>(g, R[0], R[1], R[2])]);
+  }
+
+template <int D>
+__global__ void k_eta_faces(const double* __restrict__ eta, double* __restrict__ ef, int a, Geom g) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    k_eta_faces_at<D>(eta, ef, a, g, t);
   }
 }
 
@@ -116,12 +130,18 @@ __host__ __device__ inline double grad_nodal(const double* __restrict__ p, const
 }
 
 template <int D>
-__global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, Geom g) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+__host__ __device__ __forceinline__ void k_grad_p_at(const double* __restrict__ p, double* __restrict__ Gp, Geom g, int t) {
+  
     int i, j, k;
     cell_coords<D>(g, t, i, j, k);
 #pragma unroll
     for (int a = 0; a < D; ++a) Gp[(size_t)a * g.ncell + t] = grad_nodal<D>(p, g, a, i, j, k);
+  }
+
+template <int D>
+__global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, Geom g) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_grad_p_at<D>(p, Gp, g, t);
   }
 }
 
@@ -151,9 +171,9 @@ __host__ __device__ inline double slope5(const double* w) {
 }
 
 template <int D>
-__global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slopes, Geom g) {
+__host__ __device__ __forceinline__ void k_slopes_at(const double* __restrict__ u, double* __restrict__ slopes, Geom g, int t) {
   const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+  
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
 #pragma unroll
@@ -177,6 +197,13 @@ __global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slop
         slopes[(size_t)(a * D + c) * g.ncell + t] = slope5(w);
       }
     }
+  }
+
+template <int D>
+__global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slopes, Geom g) {
+  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_slopes_at<D>(u, slopes, g, t);
   }
 }
 
@@ -223,9 +250,9 @@ __host__ __device__ inline void prestate_face(const double* __restrict__ u, cons
 }
 
 template <int D>
-__global__ void k_hats(const double* __restrict__ u, const double* __restrict__ slopes,
-                       double* __restrict__ hats, Geom g, double dt) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+__host__ __device__ __forceinline__ void k_hats_at(const double* __restrict__ u, const double* __restrict__ slopes,
+                       double* __restrict__ hats, Geom g, double dt, int t) {
+  
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
 #pragma unroll
@@ -239,6 +266,13 @@ __global__ void k_hats(const double* __restrict__ u, const double* __restrict__ 
       for (int c = 0; c < D; ++c)
         hats[(size_t)(b * D + c) * g.ncell + t] = 0.5 * (vHi + vLo) * (stHi[c] - stLo[c]) / g.h;
     }
+  }
+
+template <int D>
+__global__ void k_hats(const double* __restrict__ u, const double* __restrict__ slopes,
+                       double* __restrict__ hats, Geom g, double dt) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_hats_at<D>(u, slopes, hats, g, dt, t);
   }
 }
 
@@ -271,14 +305,14 @@ struct Force {
 };
 
 template <int D>
-__global__ void k_traces(const double* __restrict__ u, const double* __restrict__ slopes,
+__host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ u, const double* __restrict__ slopes,
                          const double* __restrict__ hats, const double* __restrict__ Gp,
                          const double* __restrict__ Lu, Force fo, double rho, int pv, int a,
                          double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
-                         Geom g, double dt) {
+                         Geom g, double dt, int t) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+  
     int R[3];
     R[0] = t % ex[0];
     int r = t / ex[0];
@@ -294,7 +328,7 @@ __global__ void k_traces(const double* __restrict__ u, const double* __restrict_
         uR[(size_t)c * nf + t] = g.wu[a][side][c];
       }
       uadv[t] = 0.0;
-      continue;
+      return;
     }
     int tl = cidx<D>(g, L[0], L[1], L[2]), tr = cidx<D>(g, R[0], R[1], R[2]);
     double vl = 0, vr = 0;
@@ -311,16 +345,28 @@ __global__ void k_traces(const double* __restrict__ u, const double* __restrict_
     }
     uadv[t] = riemann(vl, vr);
   }
+
+template <int D>
+__global__ void k_traces(const double* __restrict__ u, const double* __restrict__ slopes,
+                         const double* __restrict__ hats, const double* __restrict__ Gp,
+                         const double* __restrict__ Lu, Force fo, double rho, int pv, int a,
+                         double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
+                         Geom g, double dt) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    k_traces_at<D>(u, slopes, hats, Gp, Lu, fo, rho, pv, a, uL, uR, uadv, g, dt, t);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Stage 4: MAC divergence and correction
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void k_mac_rhs(const double* ua0, const double* ua1, const double* ua2,
-                          double* __restrict__ rhs, Geom g) {
+__host__ __device__ __forceinline__ void k_mac_rhs_at(const double* ua0, const double* ua1, const double* ua2,
+                          double* __restrict__ rhs, Geom g, int t) {
   const double* ua[3] = {ua0, ua1, ua2};
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+  
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
     double acc = 0.0;
@@ -334,14 +380,22 @@ __global__ void k_mac_rhs(const double* ua0, const double* ua1, const double* ua
     }
     rhs[t] = acc;
   }
+
+template <int D>
+__global__ void k_mac_rhs(const double* ua0, const double* ua1, const double* ua2,
+                          double* __restrict__ rhs, Geom g) {
+  const double* ua[3] = {ua0, ua1, ua2};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_mac_rhs_at<D>(ua0, ua1, ua2, rhs, g, t);
+  }
 }
 
 template <int D>
-__global__ void k_mac_correct(const double* __restrict__ uadv, const double* __restrict__ phi,
-                              double* __restrict__ umac, int a, Geom g) {
+__host__ __device__ __forceinline__ void k_mac_correct_at(const double* __restrict__ uadv, const double* __restrict__ phi,
+                              double* __restrict__ umac, int a, Geom g, int t) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+  
     int R[3];
     R[0] = t % ex[0];
     int r = t / ex[0];
@@ -349,12 +403,21 @@ __global__ void k_mac_correct(const double* __restrict__ uadv, const double* __r
     R[2] = r / ex[1];
     if (R[a] == 0 || R[a] == g.n[a]) {
       umac[t] = 0.0;
-      continue;
+      return;
     }
     int L[3] = {R[0], R[1], R[2]};
     L[a] -= 1;
     double gr = (phi[cidx<D>(g, R[0], R[1], R[2])] - phi[cidx<D>(g, L[0], L[1], L[2])]) / g.h;
     umac[t] = uadv[t] - gr;
+  }
+
+template <int D>
+__global__ void k_mac_correct(const double* __restrict__ uadv, const double* __restrict__ phi,
+                              double* __restrict__ umac, int a, Geom g) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    k_mac_correct_at<D>(uadv, phi, umac, a, g, t);
   }
 }
 
@@ -362,16 +425,16 @@ __global__ void k_mac_correct(const double* __restrict__ uadv, const double* __r
 // Stage 5: upwinding with u^MAC, convective term, viscous right-hand side
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, const double* uL1,
+__host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restrict__ u, const double* uL0, const double* uL1,
                              const double* uL2, const double* uR0, const double* uR1,
                              const double* uR2, const double* um0, const double* um1,
                              const double* um2, const double* __restrict__ Gp,
                              const double* __restrict__ Lu, Force fo, double rho,
-                             double* __restrict__ rhs, Geom g, double dt) {
+                             double* __restrict__ rhs, Geom g, double dt, int t) {
   const double* uL[3] = {uL0, uL1, uL2};
   const double* uR[3] = {uR0, uR1, uR2};
   const double* um[3] = {um0, um1, um2};
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+  
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
     double A[3] = {0.0, 0.0, 0.0};
@@ -397,16 +460,30 @@ __global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, co
       rhs[o] = u[o] - dt * A[c] + (dt / rho) * (-Gp[o] + 0.5 * Lu[o] + fo.f[c]);
     }
   }
+
+template <int D>
+__global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, const double* uL1,
+                             const double* uL2, const double* uR0, const double* uR1,
+                             const double* uR2, const double* um0, const double* um1,
+                             const double* um2, const double* __restrict__ Gp,
+                             const double* __restrict__ Lu, Force fo, double rho,
+                             double* __restrict__ rhs, Geom g, double dt) {
+  const double* uL[3] = {uL0, uL1, uL2};
+  const double* uR[3] = {uR0, uR1, uR2};
+  const double* um[3] = {um0, um1, um2};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_advect_rhs_at<D>(u, uL0, uL1, uL2, uR0, uR1, uR2, um0, um1, um2, Gp, Lu, fo, rho, rhs, g, dt, t);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Stage 7: nodal divergence of u*/dt + G p/rho, projection update
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __restrict__ Gp,
-                            double* __restrict__ out, Geom g, double dt, double rho) {
+__host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict__ ustar, const double* __restrict__ Gp,
+                            double* __restrict__ out, Geom g, double dt, double rho, int t) {
   int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
+  
     int p[3];
     p[0] = t % ex[0];
     int r = t / ex[0];
@@ -432,7 +509,7 @@ __global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __re
         int q[3] = {p[0] - 1 + cb[0], p[1] - 1 + cb[1], D == 3 ? p[2] - 1 + cb[2] : 0};
         bool in = q[0] >= 0 && q[0] < g.n[0] && q[1] >= 0 && q[1] < g.n[1] &&
                   (D == 2 || (q[2] >= 0 && q[2] < g.n[2]));
-        if (!in) continue;
+        if (!in) return;
         size_t o = (size_t)a * g.ncell + cidx<D>(g, q[0], q[1], q[2]);
         double v = ustar[o] / dt + Gp[o] / rho;
         acc += cb[a] ? v : -v;
@@ -444,12 +521,20 @@ __global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __re
       if (p[a] == 0 || p[a] == g.n[a]) w *= 0.5;
     out[t] = rho * (acc / (w * (double)(1 << (D - 1)) * g.h));
   }
+
+template <int D>
+__global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __restrict__ Gp,
+                            double* __restrict__ out, Geom g, double dt, double rho) {
+  int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
+    k_nodal_rhs_at<D>(ustar, Gp, out, g, dt, rho, t);
+  }
 }
 
 template <int D>
-__global__ void k_project_update(double* __restrict__ u, const double* __restrict__ Gp,
-                                 const double* __restrict__ phi, Geom g, double dt, double rho) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+__host__ __device__ __forceinline__ void k_project_update_at(double* __restrict__ u, const double* __restrict__ Gp,
+                                 const double* __restrict__ phi, Geom g, double dt, double rho, int t) {
+  
     int i, j, k;
     cell_coords<D>(g, t, i, j, k);
 #pragma unroll
@@ -458,6 +543,13 @@ __global__ void k_project_update(double* __restrict__ u, const double* __restric
       double gphi = grad_nodal<D>(phi, g, a, i, j, k);
       u[o] = u[o] + (dt / rho) * (Gp[o] - gphi);
     }
+  }
+
+template <int D>
+__global__ void k_project_update(double* __restrict__ u, const double* __restrict__ Gp,
+                                 const double* __restrict__ phi, Geom g, double dt, double rho) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_project_update_at<D>(u, Gp, phi, g, dt, rho, t);
   }
 }
 

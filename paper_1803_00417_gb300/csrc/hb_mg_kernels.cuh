@@ -256,13 +256,13 @@ __global__ void k_visc_smooth(T* __restrict__ u, const T* __restrict__ b, const 
 // parameter so every a == C decision folds at compile time.  (A grid-stride
 // launch of about 24 blocks per SM measured faster than one thread per cell.)
 template <int D, typename T, int C>
-__global__ void __launch_bounds__(256) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
-                                                      const T* ef1, const T* ef2, Geom g, int col, T beta, int hom) {
+__host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
+                                                      const T* ef1, const T* ef2, Geom g, int col, T beta, int hom, int t) {
   const T* ef[3] = {ef0, ef1, ef2};
   const int nt = rb_count<D>(g);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+  
     int p[3];
-    if (!rb_cell<D>(g, t, col, p)) continue;
+    if (!rb_cell<D>(g, t, col, p)) return;
     T v;
     if (interior<D>(g, p)) {
       const Strides S = make_strides(g);
@@ -271,6 +271,34 @@ __global__ void __launch_bounds__(256) k_visc_smooth_c(T* __restrict__ u, const 
       v = visc_gs_point<D, T>(u, b, ef, g, C, p, beta, hom != 0);
     }
     u[(size_t)C * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
+  }
+
+template <int D, typename T, int C>
+__global__ void k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
+                                                      const T* ef1, const T* ef2, Geom g, int col, T beta, int hom) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  const int nt = rb_count<D>(g);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    k_visc_smooth_c_at<D, T, C>(u, b, ef0, ef1, ef2, g, col, beta, hom, t);
+  }
+}
+
+// out = u - beta L u, or r = b - (u - beta L u) when b != nullptr, at cell t
+template <int D, typename T>
+__host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, const T* __restrict__ b,
+                                                     T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
+                                                     Geom g, T beta, int hom, int t) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  int p[3];
+  cell_coords<D>(g, t, p[0], p[1], p[2]);
+  const bool in = interior<D>(g, p);
+  const Strides S = make_strides(g);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    size_t o = (size_t)c * g.ncell + t;
+    T Lu = in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+    T Au = u[o] - beta * Lu;
+    out[o] = b ? b[o] - Au : Au;
   }
 }
 
@@ -297,50 +325,14 @@ __global__ void __launch_bounds__(256) k_visc_op3(const T* __restrict__ u, const
   }
 }
 
-template <int D, typename T>
-__global__ void k_visc_resid(const T* __restrict__ u, const T* __restrict__ b, T* __restrict__ r,
-                             const T* ef0, const T* ef1, const T* ef2, Geom g, T beta, int hom) {
-  const T* ef[3] = {ef0, ef1, ef2};
-  const Strides S = make_strides(g);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    int p[3];
-    cell_coords<D>(g, t, p[0], p[1], p[2]);
-    const bool in = interior<D>(g, p);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      size_t o = (size_t)c * g.ncell + t;
-      T Lu = in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
-      r[o] = b[o] - (u[o] - beta * Lu);
-    }
-  }
-}
-
-// out = u - beta L_eta u (the operator itself, for the Krylov iteration)
-template <int D, typename T>
-__global__ void k_visc_apply(const T* __restrict__ u, T* __restrict__ out, const T* ef0, const T* ef1,
-                             const T* ef2, Geom g, T beta, int hom) {
-  const T* ef[3] = {ef0, ef1, ef2};
-  const Strides S = make_strides(g);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    int p[3];
-    cell_coords<D>(g, t, p[0], p[1], p[2]);
-    const bool in = interior<D>(g, p);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      size_t o = (size_t)c * g.ncell + t;
-      T Lu = in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
-      out[o] = u[o] - beta * Lu;
-    }
-  }
-}
 
 // out = L_eta u (the stress divergence alone), grid-stride over cells
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_tensor_lu(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
-                                                  const T* ef1, const T* ef2, Geom g, int hom) {
+__host__ __device__ __forceinline__ void k_tensor_lu_at(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
+                                                  const T* ef1, const T* ef2, Geom g, int hom, int t) {
   const T* ef[3] = {ef0, ef1, ef2};
   const Strides S = make_strides(g);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+  
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
     const bool in = interior<D>(g, p);
@@ -348,6 +340,15 @@ __global__ void __launch_bounds__(256) k_tensor_lu(const T* __restrict__ u, T* _
     for (int c = 0; c < D; ++c)
       out[(size_t)c * g.ncell + t] =
           in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+  }
+
+template <int D, typename T>
+__global__ void k_tensor_lu(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
+                                                  const T* ef1, const T* ef2, Geom g, int hom) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  const Strides S = make_strides(g);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_tensor_lu_at<D, T>(u, out, ef0, ef1, ef2, g, hom, t);
   }
 }
 
@@ -400,19 +401,26 @@ __host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __r
 }
 
 template <int D, typename T>
+__host__ __device__ __forceinline__ void k_cell_smooth_at(T* __restrict__ x, const T* __restrict__ b, Geom g, int col, int t) {
+  int nt = rb_count<D>(g);
+  
+    int p[3];
+    if (!rb_cell<D>(g, t, col, p)) return;
+    x[cidx<D>(g, p[0], p[1], p[2])] = cell_gs_point<D, T>(x, b, g, p);
+  }
+
+template <int D, typename T>
 __global__ void k_cell_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g, int col) {
   int nt = rb_count<D>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-    int p[3];
-    if (!rb_cell<D>(g, t, col, p)) continue;
-    x[cidx<D>(g, p[0], p[1], p[2])] = cell_gs_point<D, T>(x, b, g, p);
+    k_cell_smooth_at<D, T>(x, b, g, col, t);
   }
 }
 
 template <int D, typename T>
-__global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
+__host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g, int t) {
   const T ih = T(1.0 / g.h);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+  
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
     T xc = x[t];
@@ -433,6 +441,13 @@ __global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T
       acc += (ghi - glo) * ih;
     }
     r[t] = b[t] - acc;
+  }
+
+template <int D, typename T>
+__global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
+  const T ih = T(1.0 / g.h);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_cell_resid_at<D, T>(x, b, r, g, t);
   }
 }
 
@@ -514,30 +529,47 @@ __host__ __device__ inline int mc_count(const Geom& g, int col) {
 }
 
 template <int D, typename T>
+__host__ __device__ __forceinline__ void k_nodal_smooth_at(T* __restrict__ x, const T* __restrict__ b, Geom g, int col, int t) {
+  int nt = mc_count<D>(g, col);
+  const T hh = T(g.h * g.h);
+  const T is0 = T(-3.0 / 8.0);  // 1 / centre weight
+  
+    int p[3];
+    if (!mc_node<D>(g, t, col, p)) return;
+    int id = nidx(g, p[0], p[1], p[2]);
+    T s = nodal_lap_point<D, T>(x, g, p, true);
+    x[id] = (hh * b[id] - s) * is0;
+  }
+
+template <int D, typename T>
 __global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g, int col) {
   int nt = mc_count<D>(g, col);
   const T hh = T(g.h * g.h);
   const T is0 = T(-3.0 / 8.0);  // 1 / centre weight
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-    int p[3];
-    if (!mc_node<D>(g, t, col, p)) continue;
-    int id = nidx(g, p[0], p[1], p[2]);
-    T s = nodal_lap_point<D, T>(x, g, p, true);
-    x[id] = (hh * b[id] - s) * is0;
+    k_nodal_smooth_at<D, T>(x, b, g, col, t);
   }
 }
 
 template <int D, typename T>
-__global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
+__host__ __device__ __forceinline__ void k_nodal_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g, int t) {
   int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
   const T ihh = T(1.0 / (g.h * g.h));
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
+  
     int p[3];
     p[0] = t % e0;
     int q = t / e0;
     p[1] = q % e1;
     p[2] = q / e1;
     r[t] = b[t] - nodal_lap_point<D, T>(x, g, p, false) * ihh;
+  }
+
+template <int D, typename T>
+__global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
+  int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
+  const T ihh = T(1.0 / (g.h * g.h));
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
+    k_nodal_resid_at<D, T>(x, b, r, g, t);
   }
 }
 
@@ -565,10 +597,9 @@ __global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom 
 // ---------------------------------------------------------------------------
 // mean of the 2^D children, averaged axis by axis (x, then y, then z)
 template <int D, typename T>
-__global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, Geom gf, Geom gc, int ncomp) {
+__host__ __device__ __forceinline__ void k_restrict_cells_at(const T* __restrict__ f, T* __restrict__ c, Geom gf, Geom gc, int ncomp, long long tt) {
   long long tot = (long long)gc.ncell * ncomp;
-  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
-       tt += (long long)gridDim.x * blockDim.x) {
+  
     int comp = (int)(tt / gc.ncell);
     int t = (int)(tt % gc.ncell);
     int I, J, K;
@@ -588,14 +619,22 @@ __global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, Geo
     }
     c[(size_t)comp * gc.ncell + t] = out;
   }
+
+template <int D, typename T>
+__global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, Geom gf, Geom gc, int ncomp) {
+  long long tot = (long long)gc.ncell * ncomp;
+  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
+       tt += (long long)gridDim.x * blockDim.x) {
+    k_restrict_cells_at<D, T>(f, c, gf, gc, ncomp, tt);
+  }
 }
 
 // coarse a-face eta: mean of the fine a-faces tiling it (pairwise, axis order)
 template <int D, typename T>
-__global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, int a, Geom gf, Geom gc) {
+__host__ __device__ __forceinline__ void k_restrict_faces_at(const T* __restrict__ ff, T* __restrict__ fc, int a, Geom gf, Geom gc, int t) {
   int ex[3] = {gc.n[0] + (a == 0), gc.n[1] + (a == 1), gc.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+  
     int P[3];
     P[0] = t % ex[0];
     int r = t / ex[0];
@@ -626,6 +665,14 @@ __global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, i
     }
     fc[t] = out;
   }
+
+template <int D, typename T>
+__global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, int a, Geom gf, Geom gc) {
+  int ex[3] = {gc.n[0] + (a == 0), gc.n[1] + (a == 1), gc.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    k_restrict_faces_at<D, T>(ff, fc, a, gf, gc, t);
+  }
 }
 
 // coarse cell value with ghost by reflection: sign -1 (Dirichlet error), +1 (Neumann)
@@ -645,11 +692,10 @@ __host__ __device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, i
 
 // x_f += P e_c, cell-centred multilinear (3/4, 1/4 per axis), axis by axis
 template <int D, typename T>
-__global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc,
-                                    int ncomp, T sign) {
+__host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc,
+                                    int ncomp, T sign, long long tt) {
   long long tot = (long long)gf.ncell * ncomp;
-  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
-       tt += (long long)gridDim.x * blockDim.x) {
+  
     int comp = (int)(tt / gf.ncell);
     int t = (int)(tt % gf.ncell);
     int i, j, k;
@@ -672,13 +718,22 @@ __global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec
     T v = D == 3 ? T(0.75) * tz[0] + T(0.25) * tz[1] : tz[0];
     xf[(size_t)comp * gf.ncell + t] += v;
   }
+
+template <int D, typename T>
+__global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc,
+                                    int ncomp, T sign) {
+  long long tot = (long long)gf.ncell * ncomp;
+  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
+       tt += (long long)gridDim.x * blockDim.x) {
+    k_prolong_cells_add_at<D, T>(xf, ec, gf, gc, ncomp, sign, tt);
+  }
 }
 
 // full weighting onto coarse nodes (even reflection), axis by axis
 template <int D, typename T>
-__global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, Geom gf, Geom gc) {
+__host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict__ rf, T* __restrict__ rc, Geom gf, Geom gc, int t) {
   int e0 = gc.n[0] + 1, e1 = gc.n[1] + 1;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gc.nnode; t += gridDim.x * blockDim.x) {
+  
     int I = t % e0;
     int q = t / e0;
     int J = q % e1;
@@ -698,13 +753,20 @@ __global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, G
     }
     rc[t] = D == 3 ? T(0.5) * zr[1] + T(0.25) * (zr[0] + zr[2]) : zr[0];
   }
+
+template <int D, typename T>
+__global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, Geom gf, Geom gc) {
+  int e0 = gc.n[0] + 1, e1 = gc.n[1] + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gc.nnode; t += gridDim.x * blockDim.x) {
+    k_restrict_nodes_at<D, T>(rf, rc, gf, gc, t);
+  }
 }
 
 // x_f += P e_c, nodal multilinear, axis by axis
 template <int D, typename T>
-__global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc) {
+__host__ __device__ __forceinline__ void k_prolong_nodes_add_at(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc, int t) {
   int e0 = gf.n[0] + 1, e1 = gf.n[1] + 1;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gf.nnode; t += gridDim.x * blockDim.x) {
+  
     int i = t % e0;
     int q = t / e0;
     int j = q % e1;
@@ -715,14 +777,14 @@ __global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec
       int kc = K + kk;
       if (D == 3 && kk == 1 && !(k & 1)) {
         tz[1] = T(0);
-        continue;
+        return;
       }
       T ty[2];
       for (int jj = 0; jj < 2; ++jj) {
         int jc = J + jj;
         if (jj == 1 && !(j & 1)) {
           ty[1] = T(0);
-          continue;
+          return;
         }
         T a0 = ec[nidx(gc, I, jc, D == 3 ? kc : 0)];
         ty[jj] = (i & 1) ? T(0.5) * (a0 + ec[nidx(gc, I + 1, jc, D == 3 ? kc : 0)]) : a0;
@@ -731,6 +793,13 @@ __global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec
     }
     T v = (D == 3 && (k & 1)) ? T(0.5) * (tz[0] + tz[1]) : tz[0];
     xf[t] += v;
+  }
+
+template <int D, typename T>
+__global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc) {
+  int e0 = gf.n[0] + 1, e1 = gf.n[1] + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gf.nnode; t += gridDim.x * blockDim.x) {
+    k_prolong_nodes_add_at<D, T>(xf, ec, gf, gc, t);
   }
 }
 
