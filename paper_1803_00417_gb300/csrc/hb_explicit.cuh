@@ -1,0 +1,551 @@
+// Device code of the explicit stages (Sec. III A-B), shared by the
+// single-cavity launches (hb_explicit.cu) and the batched ones: per-element
+// functions k_*_at and their grid-stride kernels.  Translation units that
+// include it are compiled without FMA contraction (see hb_explicit.cu).
+#pragma once
+#include <cmath>
+
+#include "hb_internal.h"
+
+namespace hb {
+
+// ---------------------------------------------------------------------------
+// Stage 1: strain rate and regularised viscosity (Eqs. 1, 21-23)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double viscosity(double g, const Rheo& r) {
+  double x = r.m * g;
+  double F;
+  if (x < 1.0e-3) {
+    // Taylor series of (1 - e^-x)/x, truncation below 1e-14 relative
+    F = r.m * (1.0 - x / 2.0 + x * x / 6.0 - x * x * x / 24.0);
+  } else {
+    F = -expm1(-x) / g;
+  }
+  if (r.reg_power) return (r.c2 * pow(g, r.n) + 0.5 * r.tau) * F;
+  return r.c2 * pow(g, r.n - 1.0) + 0.5 * r.tau * F;
+}
+
+template <int D>
+__host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, double* __restrict__ eta, Geom g, Rheo r, int t) {
+  
+    int i, j, k;
+    cell_coords<D>(g, t, i, j, k);
+    int p[3] = {i, j, k};
+    double G[3][3];
+    // (grad u)_{ab} = d u_b / d x_a by central differences
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const double* ub = u + (size_t)b * g.ncell;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        int q1[3] = {p[0], p[1], p[2]}, q0[3] = {p[0], p[1], p[2]};
+        q1[a] += 1;
+        q0[a] -= 1;
+        G[a][b] = (uget<D>(ub, g, b, q1[0], q1[1], q1[2], false) -
+                   uget<D>(ub, g, b, q0[0], q0[1], q0[2], false)) /
+                  (2.0 * g.h);
+      }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        double Dab = 0.5 * (G[a][b] + G[b][a]);
+        s += Dab * Dab;
+      }
+    double gn = sqrt(0.5 * s);
+    eta[t] = viscosity(gn, r);
+  }
+
+template <int D>
+__global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, Geom g, Rheo r) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_eta_at<D>(u, eta, g, r, t);
+  }
+}
+
+// face eta on level 0: mean of the two cells, wall faces take the interior cell
+template <int D>
+__host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict__ eta, double* __restrict__ ef, int a, Geom g, int t) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  
+    int p[3];
+    p[0] = t % ex[0];
+    int r = t / ex[0];
+    p[1] = r % ex[1];
+    p[2] = r / ex[1];
+    int L[3] = {p[0], p[1], p[2]}, R[3] = {p[0], p[1], p[2]};
+    L[a] -= 1;
+    if (L[a] < 0) L[a] = 0;
+    if (R[a] >= g.n[a]) R[a] = g.n[a] - 1;
+    ef[t] = 0.5 * (eta[cidx<D>(g, L[0], L[1], L[2])] + eta[cidx<D>(g, R[0], R[1], R[2])]);
+  }
+
+template <int D>
+__global__ void k_eta_faces(const double* __restrict__ eta, double* __restrict__ ef, int a, Geom g) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    k_eta_faces_at<D>(eta, ef, a, g, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: cell G p from nodes (L_eta u itself is evaluated by the
+// multigrid unit's operator kernel, k_tensor_lu)
+// ---------------------------------------------------------------------------
+template <int D>
+__host__ __device__ inline double grad_nodal(const double* __restrict__ p, const Geom& g, int a, int i, int j,
+                                    int k) {
+  // (p_+ - p_-)/h on each node pair along a, averaged over the other axes in order
+  int c[3] = {i, j, k};
+  double v[2][2];
+  int o1 = -1, o2 = -1;
+  for (int b = 0; b < D; ++b)
+    if (b != a) {
+      if (o1 < 0)
+        o1 = b;
+      else
+        o2 = b;
+    }
+  for (int s1 = 0; s1 < 2; ++s1)
+    for (int s2 = 0; s2 < (D == 3 ? 2 : 1); ++s2) {
+      int q[3] = {c[0], c[1], c[2]};
+      q[o1] += s1;
+      if (D == 3) q[o2] += s2;
+      int qh[3] = {q[0], q[1], q[2]};
+      qh[a] += 1;
+      v[s1][s2] = (p[nidx(g, qh[0], qh[1], qh[2])] - p[nidx(g, q[0], q[1], q[2])]) / g.h;
+    }
+  if (D == 2) return 0.5 * (v[0][0] + v[1][0]);
+  // average over o1 first, then o2
+  double w0 = 0.5 * (v[0][0] + v[1][0]);
+  double w1 = 0.5 * (v[0][1] + v[1][1]);
+  return 0.5 * (w0 + w1);
+}
+
+template <int D>
+__host__ __device__ __forceinline__ void k_grad_p_at(const double* __restrict__ p, double* __restrict__ Gp, Geom g, int t) {
+  
+    int i, j, k;
+    cell_coords<D>(g, t, i, j, k);
+#pragma unroll
+    for (int a = 0; a < D; ++a) Gp[(size_t)a * g.ncell + t] = grad_nodal<D>(p, g, a, i, j, k);
+  }
+
+template <int D>
+__global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, Geom g) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_grad_p_at<D>(p, Gp, g, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 3: Godunov edge states (Eqs. 11-14)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double sgn_min(double v, double lim) {
+  // sign(v) * min(|v|, lim) with sign(0) = 0
+  if (v == 0.0) return 0.0;
+  double m = fmin(fabs(v), lim);
+  return v > 0.0 ? m : -m;
+}
+
+// Colella's slope from the five values w[0..4] at offsets -2..2
+__host__ __device__ inline double slope5(const double* w) {
+  double dlim[3], dC[3], df[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {  // cells p-1, p, p+1
+    double dL = w[s + 1] - w[s];
+    double dR = w[s + 2] - w[s + 1];
+    dC[s] = 0.5 * (w[s + 2] - w[s]);
+    dlim[s] = (dL * dR > 0.0) ? 2.0 * fmin(fabs(dL), fabs(dR)) : 0.0;
+    df[s] = sgn_min(dC[s], dlim[s]);
+  }
+  double d4 = (4.0 / 3.0) * dC[1] - (1.0 / 6.0) * (df[2] + df[0]);
+  return sgn_min(d4, dlim[1]);
+}
+
+template <int D>
+__host__ __device__ __forceinline__ void k_slopes_at(const double* __restrict__ u, double* __restrict__ slopes, Geom g, int t) {
+  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  
+    int p[3];
+    cell_coords<D>(g, t, p[0], p[1], p[2]);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const bool inner = p[a] >= 2 && p[a] <= g.n[a] - 3;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const double* uc = u + (size_t)c * g.ncell;
+        double w[5];
+        if (inner) {
+#pragma unroll
+          for (int o = -2; o <= 2; ++o) w[o + 2] = uc[t + o * st[a]];
+        } else {
+#pragma unroll
+          for (int o = -2; o <= 2; ++o) {
+            int q[3] = {p[0], p[1], p[2]};
+            q[a] += o;
+            w[o + 2] = uget<D>(uc, g, c, q[0], q[1], q[2], false);
+          }
+        }
+        slopes[(size_t)(a * D + c) * g.ncell + t] = slope5(w);
+      }
+    }
+  }
+
+template <int D>
+__global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slopes, Geom g) {
+  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_slopes_at<D>(u, slopes, g, t);
+  }
+}
+
+__host__ __device__ inline double riemann(double uL, double uR) {
+  double s = uL + uR;
+  if (uL > 0.0 && s > 0.0) return uL;
+  if (uR < 0.0 && s < 0.0) return uR;
+  return 0.0;
+}
+
+__host__ __device__ inline double upwind(double uL, double uR, double v) {
+  if (v > 0.0) return uL;
+  if (v < 0.0) return uR;
+  return 0.5 * (uL + uR);
+}
+
+// Slope-only pre-states on the b-face between L and L+e_b (or wall values);
+// st[c] returns the upwinded state of each component, vb the normal velocity.
+template <int D>
+__host__ __device__ inline void prestate_face(const double* __restrict__ u, const double* __restrict__ slopes,
+                                     const Geom& g, double dt, int b, const int* L, double* st,
+                                     double& vb) {
+  int R[3] = {L[0], L[1], L[2]};
+  R[b] += 1;
+  double sL[3], sR[3];
+  if (L[b] < 0 || R[b] >= g.n[b]) {
+    int side = L[b] < 0 ? 0 : 1;
+#pragma unroll
+    for (int c = 0; c < D; ++c) sL[c] = sR[c] = g.wu[b][side][c];
+  } else {
+    int tl = cidx<D>(g, L[0], L[1], L[2]), tr = cidx<D>(g, R[0], R[1], R[2]);
+    double ubL = u[(size_t)b * g.ncell + tl], ubR = u[(size_t)b * g.ncell + tr];
+    double facL = 0.5 - ubL * dt / (2.0 * g.h);
+    double facR = 0.5 + ubR * dt / (2.0 * g.h);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      sL[c] = u[(size_t)c * g.ncell + tl] + facL * slopes[(size_t)(b * D + c) * g.ncell + tl];
+      sR[c] = u[(size_t)c * g.ncell + tr] - facR * slopes[(size_t)(b * D + c) * g.ncell + tr];
+    }
+  }
+  vb = riemann(sL[b], sR[b]);
+#pragma unroll
+  for (int c = 0; c < D; ++c) st[c] = (c == b) ? vb : upwind(sL[c], sR[c], vb);
+}
+
+template <int D>
+__host__ __device__ __forceinline__ void k_hats_at(const double* __restrict__ u, const double* __restrict__ slopes,
+                       double* __restrict__ hats, Geom g, double dt, int t) {
+  
+    int p[3];
+    cell_coords<D>(g, t, p[0], p[1], p[2]);
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      double stHi[3], stLo[3], vHi, vLo;
+      prestate_face<D>(u, slopes, g, dt, b, p, stHi, vHi);
+      int Lm[3] = {p[0], p[1], p[2]};
+      Lm[b] -= 1;
+      prestate_face<D>(u, slopes, g, dt, b, Lm, stLo, vLo);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        hats[(size_t)(b * D + c) * g.ncell + t] = 0.5 * (vHi + vLo) * (stHi[c] - stLo[c]) / g.h;
+    }
+  }
+
+template <int D>
+__global__ void k_hats(const double* __restrict__ u, const double* __restrict__ slopes,
+                       double* __restrict__ hats, Geom g, double dt) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_hats_at<D>(u, slopes, hats, g, dt, t);
+  }
+}
+
+// one-sided extrapolation of component c from cell q to its face along a,
+// side = -1 (left state: face above q) or +1 (right state: face below q)
+template <int D>
+__host__ __device__ inline double trace(const double* __restrict__ u, const double* __restrict__ slopes,
+                               const double* __restrict__ hats, const double* __restrict__ Gp,
+                               const double* __restrict__ Lu, const double* f, double rho, int pv,
+                               const Geom& g, double dt, int a, int c, int tq, bool left) {
+  double trans = 0.0;
+#pragma unroll
+  for (int b = 0; b < D; ++b)
+    if (b != a) trans += hats[(size_t)(b * D + c) * g.ncell + tq];
+  double F = (-Gp[(size_t)c * g.ncell + tq] + (pv ? Lu[(size_t)c * g.ncell + tq] : 0.0) + f[c]) / rho;
+  double common = -0.5 * dt * trans + 0.5 * dt * F;
+  double ua = u[(size_t)a * g.ncell + tq];
+  double s = slopes[(size_t)(a * D + c) * g.ncell + tq];
+  double uc = u[(size_t)c * g.ncell + tq];
+  if (left) {
+    double fac = 0.5 - ua * dt / (2.0 * g.h);
+    return uc + fac * s + common;
+  }
+  double fac = 0.5 + ua * dt / (2.0 * g.h);
+  return uc - fac * s + common;
+}
+
+struct Force {
+  double f[3];
+};
+
+template <int D>
+__host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ u, const double* __restrict__ slopes,
+                         const double* __restrict__ hats, const double* __restrict__ Gp,
+                         const double* __restrict__ Lu, Force fo, double rho, int pv, int a,
+                         double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
+                         Geom g, double dt, int t) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  
+    int R[3];
+    R[0] = t % ex[0];
+    int r = t / ex[0];
+    R[1] = r % ex[1];
+    R[2] = r / ex[1];
+    int L[3] = {R[0], R[1], R[2]};
+    L[a] -= 1;
+    if (L[a] < 0 || R[a] >= g.n[a]) {
+      int side = L[a] < 0 ? 0 : 1;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        uL[(size_t)c * nf + t] = g.wu[a][side][c];
+        uR[(size_t)c * nf + t] = g.wu[a][side][c];
+      }
+      uadv[t] = 0.0;
+      return;
+    }
+    int tl = cidx<D>(g, L[0], L[1], L[2]), tr = cidx<D>(g, R[0], R[1], R[2]);
+    double vl = 0, vr = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double l = trace<D>(u, slopes, hats, Gp, Lu, fo.f, rho, pv, g, dt, a, c, tl, true);
+      double rr = trace<D>(u, slopes, hats, Gp, Lu, fo.f, rho, pv, g, dt, a, c, tr, false);
+      uL[(size_t)c * nf + t] = l;
+      uR[(size_t)c * nf + t] = rr;
+      if (c == a) {
+        vl = l;
+        vr = rr;
+      }
+    }
+    uadv[t] = riemann(vl, vr);
+  }
+
+template <int D>
+__global__ void k_traces(const double* __restrict__ u, const double* __restrict__ slopes,
+                         const double* __restrict__ hats, const double* __restrict__ Gp,
+                         const double* __restrict__ Lu, Force fo, double rho, int pv, int a,
+                         double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
+                         Geom g, double dt) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    k_traces_at<D>(u, slopes, hats, Gp, Lu, fo, rho, pv, a, uL, uR, uadv, g, dt, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 4: MAC divergence and correction
+// ---------------------------------------------------------------------------
+template <int D>
+__host__ __device__ __forceinline__ void k_mac_rhs_at(const double* ua0, const double* ua1, const double* ua2,
+                          double* __restrict__ rhs, Geom g, int t) {
+  const double* ua[3] = {ua0, ua1, ua2};
+  
+    int p[3];
+    cell_coords<D>(g, t, p[0], p[1], p[2]);
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int q[3] = {p[0], p[1], p[2]};
+      double lo = ua[a][fidx(g, a, q[0], q[1], q[2])];
+      q[a] += 1;
+      double hi = ua[a][fidx(g, a, q[0], q[1], q[2])];
+      acc += (hi - lo) / g.h;
+    }
+    rhs[t] = acc;
+  }
+
+template <int D>
+__global__ void k_mac_rhs(const double* ua0, const double* ua1, const double* ua2,
+                          double* __restrict__ rhs, Geom g) {
+  const double* ua[3] = {ua0, ua1, ua2};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_mac_rhs_at<D>(ua0, ua1, ua2, rhs, g, t);
+  }
+}
+
+template <int D>
+__host__ __device__ __forceinline__ void k_mac_correct_at(const double* __restrict__ uadv, const double* __restrict__ phi,
+                              double* __restrict__ umac, int a, Geom g, int t) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  
+    int R[3];
+    R[0] = t % ex[0];
+    int r = t / ex[0];
+    R[1] = r % ex[1];
+    R[2] = r / ex[1];
+    if (R[a] == 0 || R[a] == g.n[a]) {
+      umac[t] = 0.0;
+      return;
+    }
+    int L[3] = {R[0], R[1], R[2]};
+    L[a] -= 1;
+    double gr = (phi[cidx<D>(g, R[0], R[1], R[2])] - phi[cidx<D>(g, L[0], L[1], L[2])]) / g.h;
+    umac[t] = uadv[t] - gr;
+  }
+
+template <int D>
+__global__ void k_mac_correct(const double* __restrict__ uadv, const double* __restrict__ phi,
+                              double* __restrict__ umac, int a, Geom g) {
+  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
+  int nf = ex[0] * ex[1] * ex[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
+    k_mac_correct_at<D>(uadv, phi, umac, a, g, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 5: upwinding with u^MAC, convective term, viscous right-hand side
+// ---------------------------------------------------------------------------
+template <int D>
+__host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restrict__ u, const double* uL0, const double* uL1,
+                             const double* uL2, const double* uR0, const double* uR1,
+                             const double* uR2, const double* um0, const double* um1,
+                             const double* um2, const double* __restrict__ Gp,
+                             const double* __restrict__ Lu, Force fo, double rho,
+                             double* __restrict__ rhs, Geom g, double dt, int t) {
+  const double* uL[3] = {uL0, uL1, uL2};
+  const double* uR[3] = {uR0, uR1, uR2};
+  const double* um[3] = {um0, um1, um2};
+  
+    int p[3];
+    cell_coords<D>(g, t, p[0], p[1], p[2]);
+    double A[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int nf = g.nface[a];
+      int q[3] = {p[0], p[1], p[2]};
+      int flo = fidx(g, a, q[0], q[1], q[2]);
+      q[a] += 1;
+      int fhi = fidx(g, a, q[0], q[1], q[2]);
+      double vlo = um[a][flo], vhi = um[a][fhi];
+      double vbar = 0.5 * (vhi + vlo);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        double thi = upwind(uL[a][(size_t)c * nf + fhi], uR[a][(size_t)c * nf + fhi], vhi);
+        double tlo = upwind(uL[a][(size_t)c * nf + flo], uR[a][(size_t)c * nf + flo], vlo);
+        A[c] += vbar * (thi - tlo) / g.h;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      size_t o = (size_t)c * g.ncell + t;
+      rhs[o] = u[o] - dt * A[c] + (dt / rho) * (-Gp[o] + 0.5 * Lu[o] + fo.f[c]);
+    }
+  }
+
+template <int D>
+__global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, const double* uL1,
+                             const double* uL2, const double* uR0, const double* uR1,
+                             const double* uR2, const double* um0, const double* um1,
+                             const double* um2, const double* __restrict__ Gp,
+                             const double* __restrict__ Lu, Force fo, double rho,
+                             double* __restrict__ rhs, Geom g, double dt) {
+  const double* uL[3] = {uL0, uL1, uL2};
+  const double* uR[3] = {uR0, uR1, uR2};
+  const double* um[3] = {um0, um1, um2};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_advect_rhs_at<D>(u, uL0, uL1, uL2, uR0, uR1, uR2, um0, um1, um2, Gp, Lu, fo, rho, rhs, g, dt, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 7: nodal divergence of u*/dt + G p/rho, projection update
+// ---------------------------------------------------------------------------
+template <int D>
+__host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict__ ustar, const double* __restrict__ Gp,
+                            double* __restrict__ out, Geom g, double dt, double rho, int t) {
+  int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
+  
+    int p[3];
+    p[0] = t % ex[0];
+    int r = t / ex[0];
+    p[1] = r % ex[1];
+    p[2] = r / ex[1];
+    double acc = 0.0;
+    const int ncorner = D == 3 ? 8 : 4;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+#pragma unroll
+      for (int cn = 0; cn < ncorner; ++cn) {
+        // corner bits, last axis fastest (lexicographic order)
+        int cb[3];
+        if (D == 3) {
+          cb[0] = (cn >> 2) & 1;
+          cb[1] = (cn >> 1) & 1;
+          cb[2] = cn & 1;
+        } else {
+          cb[0] = (cn >> 1) & 1;
+          cb[1] = cn & 1;
+          cb[2] = 1;
+        }
+        int q[3] = {p[0] - 1 + cb[0], p[1] - 1 + cb[1], D == 3 ? p[2] - 1 + cb[2] : 0};
+        bool in = q[0] >= 0 && q[0] < g.n[0] && q[1] >= 0 && q[1] < g.n[1] &&
+                  (D == 2 || (q[2] >= 0 && q[2] < g.n[2]));
+        if (!in) continue;
+        size_t o = (size_t)a * g.ncell + cidx<D>(g, q[0], q[1], q[2]);
+        double v = ustar[o] / dt + Gp[o] / rho;
+        acc += cb[a] ? v : -v;
+      }
+    }
+    double w = 1.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (p[a] == 0 || p[a] == g.n[a]) w *= 0.5;
+    out[t] = rho * (acc / (w * (double)(1 << (D - 1)) * g.h));
+  }
+
+template <int D>
+__global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __restrict__ Gp,
+                            double* __restrict__ out, Geom g, double dt, double rho) {
+  int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
+    k_nodal_rhs_at<D>(ustar, Gp, out, g, dt, rho, t);
+  }
+}
+
+template <int D>
+__host__ __device__ __forceinline__ void k_project_update_at(double* __restrict__ u, const double* __restrict__ Gp,
+                                 const double* __restrict__ phi, Geom g, double dt, double rho, int t) {
+  
+    int i, j, k;
+    cell_coords<D>(g, t, i, j, k);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      size_t o = (size_t)a * g.ncell + t;
+      double gphi = grad_nodal<D>(phi, g, a, i, j, k);
+      u[o] = u[o] + (dt / rho) * (Gp[o] - gphi);
+    }
+  }
+
+template <int D>
+__global__ void k_project_update(double* __restrict__ u, const double* __restrict__ Gp,
+                                 const double* __restrict__ phi, Geom g, double dt, double rho) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_project_update_at<D>(u, Gp, phi, g, dt, rho, t);
+  }
+}
+
+}  // namespace hb

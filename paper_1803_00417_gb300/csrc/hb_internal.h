@@ -192,6 +192,7 @@ int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_sol
 int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
 int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r);
 int tensor_lu(hbf_ctx* c, const double* u, double* out);  // out = L_eta u, finest level
+bool ensure_dense(hbf_ctx* c, int kind, double beta);      // dense bottom inverse ready?
 void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, long long n);  // out = x - a y
 
 // learned initial guess (hb_unet.cu): replaces p by the network's guess when

@@ -947,6 +947,22 @@ int tensor_lu(hbf_ctx* c, const double* u, double* out) {
   return cuda_check(c, cudaGetLastError(), "k_tensor_lu");
 }
 
+// exact bottom solve of problem `kind` (0 viscous, 1 MAC, 2 nodal) for a
+// context whose coarsest level is small enough; returns false otherwise
+bool ensure_dense(hbf_ctx* c, int kind, double beta) {
+  const int l = (int)c->lv.size() - 1;
+  const Level& L = c->lv[l];
+  const long long n = kind == 0 ? (long long)c->dim * L.g.ncell : (kind == 1 ? L.g.ncell : L.g.nnode);
+  if (n > kDenseMax) return false;
+  if (!c->dense[kind].valid) {
+    if (c->dim == 2)
+      build_dense<2>(c, kind, l, n, beta);
+    else
+      build_dense<3>(c, kind, l, n, beta);
+  }
+  return true;
+}
+
 }  // namespace hb
 
 extern "C" int hbf_cfl_dt_noalloc(const double* u_dev, int64_t n, double h, double cfl, double* dt_dev,

@@ -274,7 +274,7 @@ __host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, c
   }
 
 template <int D, typename T, int C>
-__global__ void k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
+__global__ void __launch_bounds__(256) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
                                                       const T* ef1, const T* ef2, Geom g, int col, T beta, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
   const int nt = rb_count<D>(g);
@@ -343,7 +343,7 @@ __host__ __device__ __forceinline__ void k_tensor_lu_at(const T* __restrict__ u,
   }
 
 template <int D, typename T>
-__global__ void k_tensor_lu(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
+__global__ void __launch_bounds__(256) k_tensor_lu(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
                                                   const T* ef1, const T* ef2, Geom g, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
   const Strides S = make_strides(g);
@@ -598,7 +598,6 @@ __global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom 
 // mean of the 2^D children, averaged axis by axis (x, then y, then z)
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_restrict_cells_at(const T* __restrict__ f, T* __restrict__ c, Geom gf, Geom gc, int ncomp, long long tt) {
-  long long tot = (long long)gc.ncell * ncomp;
   
     int comp = (int)(tt / gc.ncell);
     int t = (int)(tt % gc.ncell);
@@ -633,7 +632,6 @@ __global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, Geo
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_restrict_faces_at(const T* __restrict__ ff, T* __restrict__ fc, int a, Geom gf, Geom gc, int t) {
   int ex[3] = {gc.n[0] + (a == 0), gc.n[1] + (a == 1), gc.n[2] + (a == 2 && D == 3)};
-  int nf = ex[0] * ex[1] * ex[2];
   
     int P[3];
     P[0] = t % ex[0];
@@ -694,7 +692,6 @@ __host__ __device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, i
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc,
                                     int ncomp, T sign, long long tt) {
-  long long tot = (long long)gf.ncell * ncomp;
   
     int comp = (int)(tt / gf.ncell);
     int t = (int)(tt % gf.ncell);
@@ -777,14 +774,14 @@ __host__ __device__ __forceinline__ void k_prolong_nodes_add_at(T* __restrict__ 
       int kc = K + kk;
       if (D == 3 && kk == 1 && !(k & 1)) {
         tz[1] = T(0);
-        return;
+        continue;
       }
       T ty[2];
       for (int jj = 0; jj < 2; ++jj) {
         int jc = J + jj;
         if (jj == 1 && !(j & 1)) {
           ty[1] = T(0);
-          return;
+          continue;
         }
         T a0 = ec[nidx(gc, I, jc, D == 3 ? kc : 0)];
         ty[jj] = (i & 1) ? T(0.5) * (a0 + ec[nidx(gc, I + 1, jc, D == 3 ? kc : 0)]) : a0;
@@ -835,9 +832,9 @@ __device__ inline T cell_lap_point(const T* __restrict__ x, const Geom& g, const
 // Singular problems get the constraint row/column of weights w (1 for cells,
 // the dual-cell fraction for nodes).
 template <int D>
-__global__ void k_dense_build(int kind, double* __restrict__ X, double* __restrict__ M, int n, int ld,
-                              const double* ef0, const double* ef1, const double* ef2, Geom g, double beta) {
-  const int k = blockIdx.x;
+__device__ inline void dense_build_col(int kind, double* __restrict__ X, double* __restrict__ M, int n, int ld,
+                                       const double* ef0, const double* ef1, const double* ef2, Geom g, double beta,
+                                       int k) {
   double* e = X + (size_t)k * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) e[i] = (i == k) ? 1.0 : 0.0;
   __syncthreads();
@@ -877,9 +874,16 @@ __global__ void k_dense_build(int kind, double* __restrict__ X, double* __restri
   }
 }
 
+template <int D>
+__global__ void k_dense_build(int kind, double* __restrict__ X, double* __restrict__ M, int n, int ld,
+                              const double* ef0, const double* ef1, const double* ef2, Geom g, double beta) {
+  dense_build_col<D>(kind, X, M, n, ld, ef0, ef1, ef2, g, beta, blockIdx.x);
+}
+
 // Gauss-Jordan with partial pivoting on [M | I] (m x 2m, A), one block;
 // writes the inverse to Minv (m x m).  Returns with Minv = 0 if singular.
-__global__ void k_gauss_jordan(const double* __restrict__ M, int m, double* __restrict__ A, double* __restrict__ Minv) {
+__device__ inline void gauss_jordan_block(const double* __restrict__ M, int m, double* __restrict__ A,
+                                          double* __restrict__ Minv) {
   __shared__ double fcol[kDenseMax + 1];
   __shared__ double sv[256];
   __shared__ int si[256];
@@ -937,9 +941,13 @@ __global__ void k_gauss_jordan(const double* __restrict__ M, int m, double* __re
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) Minv[t] = A[(size_t)(t / m) * w2 + m + t % m];
 }
 
+static __global__ void k_gauss_jordan(const double* __restrict__ M, int m, double* __restrict__ A, double* __restrict__ Minv) {
+  gauss_jordan_block(M, m, A, Minv);
+}
+
 // x[i] = sum_j Minv[i][j] b[j] over the n unknowns (the bordered row/column,
 // when present, multiplies a zero constraint value)
-__global__ void k_dense_apply(const double* __restrict__ Minv, int m, const double* __restrict__ b, int n,
+static __global__ void k_dense_apply(const double* __restrict__ Minv, int m, const double* __restrict__ b, int n,
                               double* __restrict__ x) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double acc = 0.0;
