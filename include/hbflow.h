@@ -255,6 +255,56 @@ int hbf_sync(hbf_ctx* ctx);
 const char* hbf_last_error(const hbf_ctx* ctx);
 void hbf_destroy(hbf_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batched sweep: ncav independent cavities (sizes, rheology and time steps of
+ * their own) each advanced by the step of hbf_step (Sec. III A) in one call.
+ * The paper runs one problem at a time; batching is a service of this
+ * library for parameter sweeps.  Every stage is one persistent kernel launch
+ * over a work list of tiles (cavity, element range) spanning all cavities;
+ * the multigrid levels of all cavities are smoothed together; each cavity
+ * keeps its own solver state and tolerance and drops out of the launches once
+ * it has converged.  Fixed launch sequences (the explicit stages, V-cycles)
+ * are recorded once as CUDA graphs and replayed.  Per cavity the arithmetic
+ * is the single-context step's; only the summation order of norms and dot
+ * products differs.
+ *
+ * Each cavity must coarsen to an exact bottom solve: its coarsest level
+ * (sizes halved while even and >= 4) has at most 128 unknowns in each of the
+ * three solves, e.g. every size a power of two, or 3 * 2^k.  No learned
+ * initial guess is used in the batch.
+ * ------------------------------------------------------------------------- */
+typedef struct hbf_batch hbf_batch;
+
+/* dim 2 or 3; n: ncav x 3 cell counts (the third ignored in 2D); h: ncav cell
+ * sizes; wall_u: ncav x 18 wall velocities laid out as for hbf_init_grid, or
+ * NULL for resting walls; precision HBF_FP64 or HBF_MIXED (all cavities);
+ * stream: a cudaStream_t, or NULL to let the batch create its own (graphs
+ * need a stream other than the legacy default one).  Host arrays. */
+int hbf_batch_create(hbf_batch** out, int dim, int ncav, const int64_t* n, const double* h, const double* wall_u,
+                     int precision, void* stream);
+void hbf_batch_destroy(hbf_batch* b);
+/* Borrow cavity i's context for hbf_set_rheology / _density / _body_force /
+ * _solver / _predictor_viscous and hbf_set_field / hbf_get_field.  The batch
+ * owns it: do not destroy it.  Settings are read at the next hbf_batch_step. */
+int hbf_batch_cavity(hbf_batch* b, int i, hbf_ctx** ctx);
+/* per-cavity time steps (ncav positive values, host) */
+int hbf_batch_set_dt(hbf_batch* b, const double* dt);
+/* One step of every cavity.  stats: NULL or ncav entries.  Returns HBF_OK,
+ * HBF_ERR_NOT_CONVERGED when some solve stopped at its cycle cap (the step
+ * still completes), or an error.  All cavities share the nu1/nu2 counts. */
+int hbf_batch_step(hbf_batch* b, hbf_step_stats* stats);
+/* Work-list tiling: elements per tile (>= 32) and the persistent grid size
+ * (152 x blocks_per_sm blocks at most per launch). */
+int hbf_batch_set_tiling(hbf_batch* b, int tile, int blocks_per_sm);
+int hbf_batch_get_tiling(const hbf_batch* b, int* tile, int* blocks_per_sm, int64_t* tiles_level0);
+/* Time a representative launch sequence (explicit stages and one viscous
+ * V-cycle of every cavity; no cavity state changes) for each tiling
+ * candidate, reps times each, and keep the fastest.  Outputs may be NULL. */
+int hbf_batch_autotune(hbf_batch* b, int reps, int* best_tile, int* best_blocks_per_sm, double* best_ms);
+int64_t hbf_batch_launch_count(const hbf_batch* b);
+int hbf_batch_sync(hbf_batch* b);
+const char* hbf_batch_last_error(const hbf_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

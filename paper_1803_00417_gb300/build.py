@@ -21,6 +21,8 @@ UNITS = {
     "hb_explicit.cu": ["-fmad=false"],
     "hb_mg.cu": [],
     "hb_unet.cu": [],
+    "hb_batch_explicit.cu": ["-fmad=false"],
+    "hb_batch.cu": [],
 }
 
 

@@ -1,0 +1,116 @@
+// Batched execution over many independent cavities: one persistent launch
+// per stage walks a work list of tiles (cavity, element range) with the
+// cavity's own arguments, so cavities of different sizes share each launch.
+#pragma once
+#include "hb_internal.h"
+
+namespace hb {
+namespace batch {
+
+struct Tile {
+  int cav;
+  int begin;
+  int end;
+};
+
+// Persistent grid-stride over tiles; a tile whose cavity is masked off is
+// skipped (mask may be null).  Op::apply(arg, element, extra) does the work.
+template <class Op>
+__global__ void __launch_bounds__(256) k_batch(const typename Op::Arg* __restrict__ args,
+                                               const Tile* __restrict__ tiles, int ntiles,
+                                               const int* __restrict__ mask, int extra) {
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const Tile T = tiles[ti];
+    if (mask && !mask[T.cav]) continue;
+    const typename Op::Arg& a = args[T.cav];
+    for (int t = T.begin + (int)threadIdx.x; t < T.end; t += (int)blockDim.x) Op::apply(a, t, extra);
+  }
+}
+
+// face spaces: t runs over the faces of every axis, axis-major; returns the
+// axis and leaves t as the index within that axis
+__device__ inline int face_axis(const Geom& g, int& t) {
+  if (t < g.nface[0]) return 0;
+  t -= g.nface[0];
+  if (t < g.nface[1]) return 1;
+  t -= g.nface[1];
+  return 2;
+}
+
+// Per-tile partial reductions (mode 0: max |x| with non-finite -> +inf,
+// mode 1: sum x, mode 2: sum x*y, mode 3: sum w_node x for nodal arrays);
+// a second kernel combines each cavity's contiguous range of tiles in a fixed
+// order, so results do not depend on scheduling.  Sums run in FP64 for either
+// element type.
+template <typename T>
+struct RedArg {
+  const T* x;
+  const T* y;
+  Geom g;
+  int dim;
+};
+
+__host__ __device__ inline double node_weight(const Geom& g, int dim, int t) {
+  const int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
+  const int i = t % e0, j = (t / e0) % e1, k = t / (e0 * e1);
+  double w = 1.0;
+  if (i == 0 || i == g.n[0]) w *= 0.5;
+  if (j == 0 || j == g.n[1]) w *= 0.5;
+  if (dim == 3 && (k == 0 || k == g.n[2])) w *= 0.5;
+  return w;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_batch_reduce(const RedArg<T>* __restrict__ args,
+                                                      const Tile* __restrict__ tiles, int ntiles,
+                                                      const int* __restrict__ mask, int mode,
+                                                      double* __restrict__ part) {
+  __shared__ double sh[8];
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const Tile T0 = tiles[ti];
+    double acc = 0.0;
+    if (!mask || mask[T0.cav]) {
+      const RedArg<T>& a = args[T0.cav];
+      for (int t = T0.begin + (int)threadIdx.x; t < T0.end; t += (int)blockDim.x) {
+        const double v = (double)a.x[t];
+        if (mode == 0) {
+          double m = fabs(v);
+          if (!isfinite(m)) m = INFINITY;
+          acc = fmax(acc, m);
+        } else if (mode == 1) {
+          acc += v;
+        } else if (mode == 2) {
+          acc += v * (double)a.y[t];
+        } else {
+          acc += node_weight(a.g, a.dim, t) * v;
+        }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_xor_sync(0xffffffffu, acc, off);
+      acc = mode == 0 ? fmax(acc, o) : acc + o;
+    }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = mode == 0 ? fmax(s, sh[w]) : s + sh[w];
+      part[ti] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[c] = (combination of the partials of cavity c's tiles
+// [first[c], first[c+1])) * (scale ? scale[c] : 1)
+static __global__ void k_batch_combine(const double* __restrict__ part, const int* __restrict__ first, int ncav, int mode,
+                                const double* __restrict__ scale, double* __restrict__ out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncav; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = first[c]; q < first[c + 1]; ++q) s = mode == 0 ? fmax(s, part[q]) : s + part[q];
+    out[c] = scale ? s * scale[c] : s;
+  }
+}
+
+}  // namespace batch
+}  // namespace hb

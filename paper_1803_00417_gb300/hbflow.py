@@ -91,6 +91,21 @@ SIGNATURES = {
     "hbf_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hbf_destroy": (None, [ctypes.c_void_p]),
+    "hbf_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]),
+    "hbf_batch_destroy": (None, [ctypes.c_void_p]),
+    "hbf_batch_cavity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "hbf_batch_set_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "hbf_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_batch_set_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hbf_batch_get_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
+    "hbf_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "hbf_batch_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "hbf_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "hbf_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
 
@@ -163,12 +178,28 @@ class HBFlow:
         if st != HBF_OK:
             raise HBFlowError(st, "hbf_init_grid failed")
         self.ctx = ctx
+        self._owned = True
         self.ncell = int(np.prod(self.n))
         self.node_shape = tuple(v + 1 for v in self.n)
 
+    @classmethod
+    def _borrow(cls, lib, ctx, n, h):
+        """A view of a context owned by someone else (a batch's cavity)."""
+        self = cls.__new__(cls)
+        self.lib = lib
+        self.n = tuple(int(v) for v in n)
+        self.d = len(self.n)
+        self.h = float(h)
+        self.ctx = ctx
+        self._owned = False
+        self.ncell = int(np.prod(self.n))
+        self.node_shape = tuple(v + 1 for v in self.n)
+        return self
+
     def close(self):
         if getattr(self, "ctx", None):
-            self.lib.hbf_destroy(self.ctx)
+            if getattr(self, "_owned", True):
+                self.lib.hbf_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):
@@ -371,3 +402,90 @@ def set_guess_model(sim, net):
     """Use ``net`` (a UNet, or None) for the nodal projection's initial guess."""
     st = sim.lib.hbf_set_guess_model(sim.ctx, net.net if net is not None else None)
     sim._check(st)
+
+
+class Batch:
+    """Many independent cavities advanced together (``hbf_batch_*``): ``ns`` is a
+    list of cell counts (all of one dimension), ``hs`` their cell sizes,
+    ``wall_us`` their wall velocities (as for :class:`HBFlow`, or None).  Each
+    cavity is configured through :meth:`cavity`, which returns a borrowed
+    :class:`HBFlow` view."""
+
+    def __init__(self, ns, hs, wall_us=None, precision=FP64, stream=None):
+        self.lib = load()
+        self.ns = [tuple(int(v) for v in n) for n in ns]
+        self.d = len(self.ns[0])
+        assert all(len(n) == self.d for n in self.ns)
+        self.hs = [float(h) for h in hs]
+        k = len(self.ns)
+        nn = (ctypes.c_int64 * (3 * k))(*[v for n in self.ns for v in (list(n) + [1] * (3 - self.d))])
+        hh = (ctypes.c_double * k)(*self.hs)
+        wu = np.zeros((k, 3, 2, 3))
+        if wall_us is not None:
+            for i, w in enumerate(wall_us):
+                if w is not None:
+                    wu[i, :self.d, :, :self.d] = np.asarray(w, dtype=np.float64).reshape(self.d, 2, self.d)
+        wuc = (ctypes.c_double * (18 * k))(*wu.ravel())
+        b = ctypes.c_void_p()
+        st = self.lib.hbf_batch_create(ctypes.byref(b), self.d, k, nn, hh, wuc, int(precision),
+                                       ctypes.c_void_p(stream) if stream is not None else None)
+        if st != HBF_OK:
+            raise HBFlowError(st, "hbf_batch_create failed")
+        self.b = b
+        self.ncav = k
+        self._views = []
+        for i in range(k):
+            c = ctypes.c_void_p()
+            self._check(self.lib.hbf_batch_cavity(self.b, i, ctypes.byref(c)))
+            self._views.append(HBFlow._borrow(self.lib, c, self.ns[i], self.hs[i]))
+
+    def close(self):
+        if getattr(self, "b", None):
+            for v in self._views:
+                v.ctx = None
+            self.lib.hbf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow_nc=False):
+        if st == HBF_OK or (allow_nc and st == HBF_ERR_NOT_CONVERGED):
+            return st
+        raise HBFlowError(st, self.lib.hbf_batch_last_error(self.b).decode())
+
+    def cavity(self, i):
+        return self._views[i]
+
+    def set_dt(self, dts):
+        arr = (ctypes.c_double * self.ncav)(*[float(x) for x in dts])
+        self._check(self.lib.hbf_batch_set_dt(self.b, arr))
+
+    def step(self):
+        """One step of every cavity; returns the per-cavity solver statistics."""
+        stats = (StepStats * self.ncav)()
+        self._check(self.lib.hbf_batch_step(self.b, ctypes.cast(stats, ctypes.c_void_p)), allow_nc=True)
+        return [s.as_dict() for s in stats]
+
+    def set_tiling(self, tile, blocks_per_sm):
+        self._check(self.lib.hbf_batch_set_tiling(self.b, int(tile), int(blocks_per_sm)))
+
+    def tiling(self):
+        t, b, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        self._check(self.lib.hbf_batch_get_tiling(self.b, ctypes.byref(t), ctypes.byref(b), ctypes.byref(n)))
+        return dict(tile=t.value, blocks_per_sm=b.value, tiles_level0=n.value)
+
+    def autotune(self, reps=3):
+        t, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.hbf_batch_autotune(self.b, int(reps), ctypes.byref(t), ctypes.byref(b),
+                                                ctypes.byref(ms)))
+        return dict(tile=t.value, blocks_per_sm=b.value, probe_ms=ms.value)
+
+    def launch_count(self):
+        return int(self.lib.hbf_batch_launch_count(self.b))
+
+    def sync(self):
+        self._check(self.lib.hbf_batch_sync(self.b))
