@@ -50,6 +50,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep measurement")
+    ap.add_argument("--batch-only", action="store_true", help="measure only the batched sweep")
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--batch-warmup", type=int, default=3)
+    ap.add_argument("--batch-ncav", type=int, default=64)
+    ap.add_argument("--no-batch-sequential", action="store_true",
+                    help="skip timing the same cavities one context at a time")
     ap.add_argument("--breakdown", action="store_true",
                     help="also time bottom solves, transfers, reductions, vector updates and coarse levels")
     ap.add_argument("--profiler-range", action="store_true",
@@ -172,6 +179,96 @@ def visc_smoother_bytes(d, ncell, elem):
     return elem * ncell * (0.5 + (d - 1) + 0.5 + d + 0.5)
 
 
+def run_batch_sweep(args, clocks=None):
+    """64 seeded 2D cavities (sizes 128..512, random Bi, n, Re) advanced together
+    by the batched step in mixed precision, after the tiling autotuner; then the
+    same cavities advanced one context at a time for comparison."""
+    import torch
+
+    from paper_1803_00417_gb300.hbflow import MIXED, Batch, HBFlow
+    from paper_1803_00417_gb300.inputs import batch_sweep
+
+    cfgs = batch_sweep(ncav=args.batch_ncav, seed=0)
+    cells = int(sum(np.prod(c["n"]) for c in cfgs))
+    B = Batch([c["n"] for c in cfgs], [c["h"] for c in cfgs], [c["wall_u"] for c in cfgs], precision=MIXED)
+    for i, c in enumerate(cfgs):
+        v = B.cavity(i)
+        v.set_rheology(c["K"], c["nexp"], c["tau_y"], c["m"])
+        v.set_solver(rtol=1e-10, max_cycles=200)
+        v.set_field("U", np.zeros(2 * int(np.prod(c["n"]))))
+        v.set_field("P", np.zeros(int(np.prod([s + 1 for s in c["n"]]))))
+    B.set_dt([c["dt"] for c in cfgs])
+    t0 = time.perf_counter()
+    tuned = B.autotune(reps=3)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.batch_warmup):
+        B.step()
+    B.sync()
+    n0 = B.launch_count()
+    cyc = {"mac": 0, "visc": 0, "nodal": 0}
+    conv = 0
+    if clocks is not None:
+        clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.batch_steps):
+        st = B.step()
+        for s in st:
+            for k in cyc:
+                cyc[k] += s[k]["cycles"]
+            conv += int(all(s[k]["converged"] for k in cyc))
+    B.sync()
+    secs = time.perf_counter() - t0
+    clk = clocks.stop() if clocks is not None else None
+    launches = B.launch_count() - n0
+    tiling = B.tiling()
+    B.profile(True)
+    for _ in range(2):
+        B.step()
+    phases = B.profile_read()
+    B.profile(False)
+    out = {"value": cells * args.batch_steps / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / args.batch_steps,
+           "steps": args.batch_steps, "warmup": args.batch_warmup, "precision": "mixed", "rtol": 1e-10,
+           "workload": f"{len(cfgs)} 2D lid-driven cavities, sizes {{128,256,384,512}}^2 (seed 0), Bi U[0,50], "
+                       f"n U[0.3,1.5], Re log-U[1,1000], m=1e4, dt=0.5h each, from rest",
+           "cells": cells, "tiling": tiling, "autotune": dict(tuned, seconds=tune_s),
+           "launches_per_step": launches / args.batch_steps,
+           "converged_solves": f"{conv}/{len(cfgs) * args.batch_steps}",
+           "cycles_per_cavity_step": {k: v / (len(cfgs) * args.batch_steps) for k, v in cyc.items()},
+           "timer": "host wall clock around the steps (each step synchronises on its residual norms)",
+           "phases_2_steps": phases,
+           "clocks": clk}
+    B.close()
+    if not args.no_batch_sequential:
+        sims = []
+        for c in cfgs:
+            s_ = HBFlow(c["n"], c["h"], c["wall_u"], precision=MIXED)
+            s_.set_rheology(c["K"], c["nexp"], c["tau_y"], c["m"])
+            s_.set_solver(rtol=1e-10, max_cycles=200)
+            s_.set_field("U", np.zeros(2 * int(np.prod(c["n"]))))
+            s_.set_field("P", np.zeros(int(np.prod([v + 1 for v in c["n"]]))))
+            sims.append(s_)
+        for _ in range(args.batch_warmup):
+            for s_, c in zip(sims, cfgs):
+                s_.step(c["dt"])
+        torch.cuda.synchronize()
+        n0 = sum(s_.launch_count() for s_ in sims)
+        t0 = time.perf_counter()
+        for _ in range(args.batch_steps):
+            for s_, c in zip(sims, cfgs):
+                s_.step(c["dt"])
+        torch.cuda.synchronize()
+        secs1 = time.perf_counter() - t0
+        nl = sum(s_.launch_count() for s_ in sims) - n0
+        for s_ in sims:
+            s_.close()
+        seq = cells * args.batch_steps / secs1
+        out["sequential_contexts"] = {"value": seq, "unit": UNIT, "ms_per_step": 1e3 * secs1 / args.batch_steps,
+                                      "launches_per_step": nl / args.batch_steps}
+        out["speedup_vs_sequential"] = out["value"] / seq
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -192,6 +289,14 @@ def run_ours(args):
         build.build()
     if dist is not None:
         dist.barrier()
+
+    if args.batch_only:
+        if rank == 0:
+            res = run_batch_sweep(args, Clocks(local))
+            print(json.dumps({"batch_sweep": res}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     over = {"n": (args.n,) * 3} if args.n else {}
     cfg = cavity(args.workload, **over)
@@ -366,6 +471,10 @@ def run_ours(args):
         cpu = {"value": val, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
                "sample": f"2 steps from rest of the same cavity at {nsample}^{d} cells ({secs:.1f} s)"}
 
+    batch = None
+    if not args.no_batch:
+        batch = run_batch_sweep(args, clocks)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == FP64 else ("f64+f32+bf16" if learned else "f64+f32"), "data": "synthetic",
@@ -377,6 +486,7 @@ def run_ours(args):
                        "converged": bool(converged)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "fp64_method": fp64, "learned_guess": learned, "mixed_without_learned": mixed_only,
+            "batch_sweep": batch,
             "clocks": clk,
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0}}
     print(json.dumps(line), flush=True)

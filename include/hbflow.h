@@ -301,6 +301,15 @@ int hbf_batch_get_tiling(const hbf_batch* b, int* tile, int* blocks_per_sm, int6
  * V-cycle of every cavity; no cavity state changes) for each tiling
  * candidate, reps times each, and keep the fastest.  Outputs may be NULL. */
 int hbf_batch_autotune(hbf_batch* b, int reps, int* best_tile, int* best_blocks_per_sm, double* best_ms);
+/* Phase timing of the following steps (on != 0 starts and resets it, 0
+ * stops it): CUDA events between the stages, so each step then ends with a
+ * synchronisation.  phase_ms[7]: explicit predictor stages, MAC solve, MAC
+ * correction and advective rhs, viscous solve, nodal rhs, nodal solve,
+ * projection update, summed over the timed steps.  trips[3]: batched
+ * iterations of the MAC, viscous (inner Krylov) and nodal loops, counted
+ * whether timing is on or not since the last hbf_batch_profile call. */
+int hbf_batch_profile(hbf_batch* b, int on);
+int hbf_batch_profile_read(const hbf_batch* b, double phase_ms[7], int64_t trips[3], int64_t* steps);
 int64_t hbf_batch_launch_count(const hbf_batch* b);
 int hbf_batch_sync(hbf_batch* b);
 const char* hbf_batch_last_error(const hbf_batch* b);

@@ -52,6 +52,7 @@ static Geom make_geom(int dim, const int n[3], double h) {
   g.nface[0] = (g.n[0] + 1) * g.n[1] * g.n[2];
   g.nface[1] = g.n[0] * (g.n[1] + 1) * g.n[2];
   g.nface[2] = dim == 3 ? g.n[0] * g.n[1] * (g.n[2] + 1) : 0;
+  geom_finish(g);
   return g;
 }
 

@@ -418,12 +418,13 @@ static void* make_table(hbf_batch* B, F f) {
 template <typename T>
 static void reduce(hbf_batch* B, const void* tab, const List& L, int mode, int slot, const int* mask,
                    const double* scale = nullptr) {
+  const int wpb = kThreads / 32;  // warps (tiles in flight) per block
   int grid = 152 * B->blocks_per_sm;
-  if (grid > L.n) grid = L.n;
+  if (grid > (L.n + wpb - 1) / wpb) grid = (L.n + wpb - 1) / wpb;
   if (grid < 1) grid = 1;
   k_batch_reduce<T><<<grid, kThreads, 0, B->stream>>>((const RedArg<T>*)tab, L.d, L.n, mask, mode, B->part);
-  k_batch_combine<<<(B->ncav + 127) / 128, 128, 0, B->stream>>>(B->part, L.dfirst, B->ncav, mode, scale,
-                                                                B->red + (size_t)slot * B->ncav);
+  k_batch_combine<<<(B->ncav + wpb - 1) / wpb, kThreads, 0, B->stream>>>(B->part, L.dfirst, B->ncav, mode, scale,
+                                                                         B->red + (size_t)slot * B->ncav);
   B->nlaunch += 2;
 }
 
@@ -976,6 +977,7 @@ struct SolversT : Solvers {
       act[c] = rn[c] > tol[c] && cyc[c] < B->cav[c]->cfg.max_cycles && std::isfinite(rn[c]);
     }
     while (any(act)) {
+      ++B->trips[w == 0 ? 0 : 2];
       set_mask(B, act);
       if (kMixed) {
         run<OpToF32>(B, G.tof, L0, act_d);
@@ -1044,7 +1046,7 @@ struct SolversT : Solvers {
     reduce<double>(B, v_redr, Lv, 0, 1, all);
     int st = fetch(B, 2);
     if (st) return st;
-    std::vector<double> bnorm(n), rn(n), r0(n), tol(n), itol(n), rho(n), alpha(n), omega(n), rho1(n);
+    std::vector<double> bnorm(n), rn(n), r0(n), tol(n), itol(n), rho(n), alpha(n), omega(n), rho1(n), rho1n(n);
     std::vector<int> it(n, 0), k(n, 0);
     std::vector<char> outer(n, 0), inner(n, 0);
     auto cap = [&](int c) { return B->cav[c]->cfg.max_cycles; };
@@ -1064,12 +1066,16 @@ struct SolversT : Solvers {
         run<OpZero<T>>(B, k_zero_v, Lv, act_d);
         run<OpZero<T>>(B, k_zero_p, Lv, act_d);
         reduce<T>(B, k_red_r0, Lv, 0, 0, act_d);
-        if ((st = fetch(B, 1))) return st;
       } else {
         run<OpCopy<T>>(B, k_copy_rh, Lv, act_d);
         run<OpZero<T>>(B, k_zero_v, Lv, act_d);
         run<OpZero<T>>(B, k_zero_p, Lv, act_d);
       }
+      // rho1 = (rh, r) of the first inner iteration (outer cavities are exactly
+      // the ones entering it); later ones arrive with the residual norm of the
+      // previous iteration (same r, one fetch)
+      reduce<T>(B, k_dot_rh_r, Lv, 2, 1, act_d);
+      if ((st = fetch(B, 2))) return st;
       for (int c = 0; c < n; ++c) {
         if (!outer[c]) {
           inner[c] = 0;
@@ -1079,14 +1085,13 @@ struct SolversT : Solvers {
         rho[c] = alpha[c] = omega[c] = 1.0;
         k[c] = 0;
         inner[c] = it[c] < cap(c);
+        rho1n[c] = hr(B, 1, c);
       }
       while (any(inner)) {
-        set_mask(B, inner);
-        reduce<T>(B, k_dot_rh_r, Lv, 2, 0, act_d);
-        if ((st = fetch(B, 1))) return st;
+        ++B->trips[1];
         for (int c = 0; c < n; ++c)
           if (inner[c]) {
-            rho1[c] = hr(B, 0, c);
+            rho1[c] = rho1n[c];
             if (rho1[c] == 0.0 || !std::isfinite(rho1[c])) {
               inner[c] = 0;
               continue;
@@ -1133,13 +1138,15 @@ struct SolversT : Solvers {
         run<OpBicgX<T>>(B, k_bicg_x, Lv, act_d);
         run<OpAxmy<T>>(B, k_axmy_r, Lv, act_d, 3);
         reduce<T>(B, k_red_r, Lv, 0, 0, act_d);
-        if ((st = fetch(B, 1))) return st;
+        reduce<T>(B, k_dot_rh_r, Lv, 2, 1, act_d);
+        if ((st = fetch(B, 2))) return st;
         for (int c = 0; c < n; ++c)
           if (inner[c]) {
             rho[c] = rho1[c];
             ++it[c];
             ++k[c];
             const double rr = hr(B, 0, c);
+            rho1n[c] = hr(B, 1, c);
             const bool stop = rr <= itol[c] || omega[c] == 0.0 || !std::isfinite(rr);
             inner[c] = !stop && it[c] < cap(c) && (!kMixed || k[c] < kInnerMax);
           }
@@ -1170,6 +1177,10 @@ struct SolversT : Solvers {
       }
       return s != HBF_OK;
     };
+    auto mark = [&](int q) {
+      if (B->prof) cudaEventRecord(B->pev[q], B->stream);
+    };
+    mark(0);
     st = replay(B, g_pre, [&] {
       explicit_stage(B, B->expl, 0);
       run<OpTensorLu<D>>(B, tlu, B->H[0][kCells], all);
@@ -1178,20 +1189,36 @@ struct SolversT : Solvers {
       prep_visc(B);
     });
     if (st) return st;
+    mark(1);
     if (keep(st = mg_solve(B, 0, smac.data()))) return st;
+    mark(2);
     st = replay(B, g_post, [&] {
       explicit_stage(B, B->expl, 2);
       run<OpCopy<double>>(B, cp_in, B->H[0][kCellsD], all);
     });
     if (st) return st;
+    mark(3);
     if (keep(st = visc_solve(B, svisc.data()))) return st;
+    mark(4);
     if ((st = replay(B, g_nrhs, [&] { explicit_stage(B, B->expl, 3); }))) return st;
+    mark(5);
     if (keep(st = mg_solve(B, 1, snod.data()))) return st;
+    mark(6);
     st = replay(B, g_upd, [&] {
       explicit_stage(B, B->expl, 4);
       run<OpCopy<double>>(B, cp_out, B->H[0][kCellsD], all);
     });
     if (st) return st;
+    mark(7);
+    if (B->prof) {
+      if ((st = bcheck(B, cudaEventSynchronize(B->pev[7]), "phase timing"))) return st;
+      for (int q = 0; q < 7; ++q) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, B->pev[q], B->pev[q + 1]);
+        B->phase_ms[q] += ms;
+      }
+      ++B->prof_steps;
+    }
     if (stats)
       for (int c = 0; c < n; ++c) {
         stats[c].mac = smac[c];
@@ -1411,6 +1438,8 @@ void hbf_batch_destroy(hbf_batch* B) {
   if (B->h_act) cudaFreeHost(B->h_act);
   if (B->hred) cudaFreeHost(B->hred);
   if (B->hscal) cudaFreeHost(B->hscal);
+  for (int q = 0; q < 8; ++q)
+    if (B->pev[q]) cudaEventDestroy(B->pev[q]);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
   delete B;
 }
@@ -1492,6 +1521,30 @@ int hbf_batch_autotune(hbf_batch* B, int reps, int* best_tile, int* best_bps, do
   if (best_tile) *best_tile = bt;
   if (best_bps) *best_bps = bb;
   if (best_ms) *best_ms = best;
+  return HBF_OK;
+}
+
+int hbf_batch_profile(hbf_batch* B, int on) {
+  if (!B) return HBF_ERR_ARG;
+  int st = bcheck(B, cudaStreamSynchronize(B->stream), "profile");
+  if (st) return st;
+  if (on && !B->pev[0])
+    for (int q = 0; q < 8; ++q)
+      if ((st = bcheck(B, cudaEventCreate(&B->pev[q]), "profile events"))) return st;
+  B->prof = on != 0;
+  for (int q = 0; q < 7; ++q) B->phase_ms[q] = 0.0;
+  for (int q = 0; q < 3; ++q) B->trips[q] = 0;
+  B->prof_steps = 0;
+  return HBF_OK;
+}
+
+int hbf_batch_profile_read(const hbf_batch* B, double phase_ms[7], int64_t trips[3], int64_t* steps) {
+  if (!B) return HBF_ERR_ARG;
+  if (phase_ms)
+    for (int q = 0; q < 7; ++q) phase_ms[q] = B->phase_ms[q];
+  if (trips)
+    for (int q = 0; q < 3; ++q) trips[q] = B->trips[q];
+  if (steps) *steps = B->prof_steps;
   return HBF_OK;
 }
 

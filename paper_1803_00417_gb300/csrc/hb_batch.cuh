@@ -51,8 +51,8 @@ struct RedArg {
 };
 
 __host__ __device__ inline double node_weight(const Geom& g, int dim, int t) {
-  const int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
-  const int i = t % e0, j = (t / e0) % e1, k = t / (e0 * e1);
+  int i, j, k;
+  node_coords(g, t, i, j, k);
   double w = 1.0;
   if (i == 0 || i == g.n[0]) w *= 0.5;
   if (j == 0 || j == g.n[1]) w *= 0.5;
@@ -60,55 +60,59 @@ __host__ __device__ inline double node_weight(const Geom& g, int dim, int t) {
   return w;
 }
 
+// One warp per tile: lanes stride over the tile's elements, then a fixed
+// xor-shuffle tree; no block barriers, so short tiles stay cheap.
 template <typename T>
 __global__ void __launch_bounds__(256) k_batch_reduce(const RedArg<T>* __restrict__ args,
                                                       const Tile* __restrict__ tiles, int ntiles,
                                                       const int* __restrict__ mask, int mode,
                                                       double* __restrict__ part) {
-  __shared__ double sh[8];
-  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int ti = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); ti < ntiles; ti += nwarps) {
     const Tile T0 = tiles[ti];
     double acc = 0.0;
     if (!mask || mask[T0.cav]) {
-      const RedArg<T>& a = args[T0.cav];
-      for (int t = T0.begin + (int)threadIdx.x; t < T0.end; t += (int)blockDim.x) {
-        const double v = (double)a.x[t];
-        if (mode == 0) {
-          double m = fabs(v);
+      const RedArg<T> a = args[T0.cav];
+      if (mode == 0) {
+        for (int t = T0.begin + lane; t < T0.end; t += 32) {
+          double m = fabs((double)a.x[t]);
           if (!isfinite(m)) m = INFINITY;
           acc = fmax(acc, m);
-        } else if (mode == 1) {
-          acc += v;
-        } else if (mode == 2) {
-          acc += v * (double)a.y[t];
-        } else {
-          acc += node_weight(a.g, a.dim, t) * v;
         }
+      } else if (mode == 1) {
+        for (int t = T0.begin + lane; t < T0.end; t += 32) acc += (double)a.x[t];
+      } else if (mode == 2) {
+        for (int t = T0.begin + lane; t < T0.end; t += 32) acc += (double)a.x[t] * (double)a.y[t];
+      } else {
+        for (int t = T0.begin + lane; t < T0.end; t += 32) acc += node_weight(a.g, a.dim, t) * (double)a.x[t];
       }
     }
     for (int off = 16; off > 0; off >>= 1) {
       const double o = __shfl_xor_sync(0xffffffffu, acc, off);
       acc = mode == 0 ? fmax(acc, o) : acc + o;
     }
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = mode == 0 ? fmax(s, sh[w]) : s + sh[w];
-      part[ti] = s;
-    }
-    __syncthreads();
+    if (lane == 0) part[ti] = acc;
   }
 }
 
 // out[c] = (combination of the partials of cavity c's tiles
-// [first[c], first[c+1])) * (scale ? scale[c] : 1)
-static __global__ void k_batch_combine(const double* __restrict__ part, const int* __restrict__ first, int ncav, int mode,
-                                const double* __restrict__ scale, double* __restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncav; c += gridDim.x * blockDim.x) {
+// [first[c], first[c+1])) * (scale ? scale[c] : 1); one warp per cavity,
+// fixed order
+static __global__ void __launch_bounds__(256) k_batch_combine(const double* __restrict__ part,
+                                                              const int* __restrict__ first, int ncav, int mode,
+                                                              const double* __restrict__ scale,
+                                                              double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < ncav; c += nwarps) {
     double s = 0.0;
-    for (int q = first[c]; q < first[c + 1]; ++q) s = mode == 0 ? fmax(s, part[q]) : s + part[q];
-    out[c] = scale ? s * scale[c] : s;
+    for (int q = first[c] + lane; q < first[c + 1]; q += 32) s = mode == 0 ? fmax(s, part[q]) : s + part[q];
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_xor_sync(0xffffffffu, s, off);
+      s = mode == 0 ? fmax(s, o) : s + o;
+    }
+    if (lane == 0) out[c] = scale ? s * scale[c] : s;
   }
 }
 

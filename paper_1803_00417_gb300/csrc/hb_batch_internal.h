@@ -73,6 +73,12 @@ struct hbf_batch {
   bool prepared = false;
   std::vector<hb::batch::Sig> sig;
   long long nlaunch = 0;
+  // phase timing (hbf_batch_profile): events between the stages of a step
+  bool prof = false;
+  cudaEvent_t pev[8] = {};
+  double phase_ms[7] = {};
+  long long prof_steps = 0;
+  long long trips[3] = {};     // batched iterations of the MAC, viscous and nodal loops
   std::string err;
 };
 

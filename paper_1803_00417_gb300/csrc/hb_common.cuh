@@ -22,7 +22,76 @@ struct Geom {
   int ncell;
   int nnode;
   int nface[3];
+  // derived on the host by geom_finish(): the constants 1/h, 1/h^2, 0.25/h,
+  // h^2 (and their FP32 roundings), and exact division multipliers for the
+  // index decompositions (see divm)
+  double ih, ihh, q4, hh;
+  float fih, fihh, fq4, fhh;
+  unsigned long long m_n0, m_n1, m_e0, m_e1, m_rb, m_mc0[2], m_mc1[2];
 };
+
+// Multiplier M for the exact quotient t / d = floor(t * M / 2^64) of any
+// 0 <= t < 2^32 by a fixed 1 <= d < 2^32: M = ceil(2^64 / d), with the error
+// t * (M d - 2^64) / (d 2^64) < 1/d never reaching the next integer.  d = 1
+// gives M = 0 (wrapped), handled by divm.
+__host__ __device__ inline unsigned long long div_magic(unsigned d) {
+  return d <= 1 ? 0ull : (~0ull) / d + 1ull;
+}
+
+__host__ __device__ __forceinline__ int divm(int t, int d, unsigned long long M) {
+#ifdef __CUDA_ARCH__
+  return M ? (int)__umul64hi((unsigned long long)(unsigned)t, M) : t;
+#else
+  (void)M;
+  return t / d;
+#endif
+}
+
+__host__ __device__ inline void geom_finish(Geom& g) {
+  g.ih = 1.0 / g.h;
+  g.ihh = 1.0 / (g.h * g.h);
+  g.q4 = 0.25 / g.h;
+  g.hh = g.h * g.h;
+  g.fih = (float)g.ih;
+  g.fihh = (float)g.ihh;
+  g.fq4 = (float)g.q4;
+  g.fhh = (float)g.hh;
+  g.m_n0 = div_magic((unsigned)g.n[0]);
+  g.m_n1 = div_magic((unsigned)g.n[1]);
+  g.m_e0 = div_magic((unsigned)(g.n[0] + 1));
+  g.m_e1 = div_magic((unsigned)(g.n[1] + 1));
+  g.m_rb = div_magic((unsigned)((g.n[0] + 1) / 2));
+  for (int b = 0; b < 2; ++b) {
+    g.m_mc0[b] = div_magic((unsigned)((g.n[0] + 1 - b + 1) / 2));
+    g.m_mc1[b] = div_magic((unsigned)((g.n[1] + 1 - b + 1) / 2));
+  }
+}
+
+// the derived constants in arithmetic T
+template <typename T>
+__host__ __device__ inline T g_ih(const Geom& g);
+template <>
+__host__ __device__ inline double g_ih<double>(const Geom& g) { return g.ih; }
+template <>
+__host__ __device__ inline float g_ih<float>(const Geom& g) { return g.fih; }
+template <typename T>
+__host__ __device__ inline T g_ihh(const Geom& g);
+template <>
+__host__ __device__ inline double g_ihh<double>(const Geom& g) { return g.ihh; }
+template <>
+__host__ __device__ inline float g_ihh<float>(const Geom& g) { return g.fihh; }
+template <typename T>
+__host__ __device__ inline T g_q4(const Geom& g);
+template <>
+__host__ __device__ inline double g_q4<double>(const Geom& g) { return g.q4; }
+template <>
+__host__ __device__ inline float g_q4<float>(const Geom& g) { return g.fq4; }
+template <typename T>
+__host__ __device__ inline T g_hh(const Geom& g);
+template <>
+__host__ __device__ inline double g_hh<double>(const Geom& g) { return g.hh; }
+template <>
+__host__ __device__ inline float g_hh<float>(const Geom& g) { return g.fhh; }
 
 struct Rheo {
   double c2;     // 2^(n-1) K
@@ -49,15 +118,33 @@ __host__ __device__ inline int fidx(const Geom& g, int a, int i, int j, int k) {
 
 template <int D>
 __host__ __device__ inline void cell_coords(const Geom& g, int t, int& i, int& j, int& k) {
-  i = t % g.n[0];
-  int r = t / g.n[0];
+  const int r = divm(t, g.n[0], g.m_n0);
+  i = t - r * g.n[0];
   if (D == 3) {
-    j = r % g.n[1];
-    k = r / g.n[1];
+    k = divm(r, g.n[1], g.m_n1);
+    j = r - k * g.n[1];
   } else {
     j = r;
     k = 0;
   }
+}
+
+// node t -> (i, j, k) on the (n0+1) x (n1+1) x (n2+1) node grid
+__host__ __device__ inline void node_coords(const Geom& g, int t, int& i, int& j, int& k) {
+  const int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
+  const int r = divm(t, e0, g.m_e0);
+  i = t - r * e0;
+  k = divm(r, e1, g.m_e1);
+  j = r - k * e1;
+}
+
+// a-face t -> (i, j, k) on the face grid (one more point along a)
+__host__ __device__ inline void face_coords(const Geom& g, int a, int t, int& i, int& j, int& k) {
+  const int ex = g.n[0] + (a == 0), ey = g.n[1] + (a == 1);
+  const int r = divm(t, ex, a == 0 ? g.m_e0 : g.m_n0);
+  i = t - r * ex;
+  k = divm(r, ey, a == 1 ? g.m_e1 : g.m_n1);
+  j = r - k * ey;
 }
 
 // Velocity component c at cell (i,j,k) where at most one axis is out of range
@@ -120,6 +207,7 @@ __host__ __device__ inline Geom coarse_of(const Geom& f) {
   c.nface[0] = (c.n[0] + 1) * c.n[1] * c.n[2];
   c.nface[1] = c.n[0] * (c.n[1] + 1) * c.n[2];
   c.nface[2] = D == 3 ? c.n[0] * c.n[1] * (c.n[2] + 1) : 0;
+  geom_finish(c);
   return c;
 }
 

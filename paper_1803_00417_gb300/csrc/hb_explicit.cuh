@@ -71,10 +71,7 @@ __host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   
     int p[3];
-    p[0] = t % ex[0];
-    int r = t / ex[0];
-    p[1] = r % ex[1];
-    p[2] = r / ex[1];
+    face_coords(g, a, t, p[0], p[1], p[2]);
     int L[3] = {p[0], p[1], p[2]}, R[3] = {p[0], p[1], p[2]};
     L[a] -= 1;
     if (L[a] < 0) L[a] = 0;
@@ -310,10 +307,7 @@ __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ 
   int nf = ex[0] * ex[1] * ex[2];
   
     int R[3];
-    R[0] = t % ex[0];
-    int r = t / ex[0];
-    R[1] = r % ex[1];
-    R[2] = r / ex[1];
+    face_coords(g, a, t, R[0], R[1], R[2]);
     int L[3] = {R[0], R[1], R[2]};
     L[a] -= 1;
     if (L[a] < 0 || R[a] >= g.n[a]) {
@@ -392,10 +386,7 @@ __host__ __device__ __forceinline__ void k_mac_correct_at(const double* __restri
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   
     int R[3];
-    R[0] = t % ex[0];
-    int r = t / ex[0];
-    R[1] = r % ex[1];
-    R[2] = r / ex[1];
+    face_coords(g, a, t, R[0], R[1], R[2]);
     if (R[a] == 0 || R[a] == g.n[a]) {
       umac[t] = 0.0;
       return;
@@ -480,10 +471,7 @@ __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict
   int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
   
     int p[3];
-    p[0] = t % ex[0];
-    int r = t / ex[0];
-    p[1] = r % ex[1];
-    p[2] = r / ex[1];
+    node_coords(g, t, p[0], p[1], p[2]);
     double acc = 0.0;
     const int ncorner = D == 3 ? 8 : 4;
 #pragma unroll

@@ -30,7 +30,7 @@ __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom&
   p1[a] += 1;
   p0[a] += 1;
   T dR = uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom);
-  return (dL + dR) * T(0.25 / g.h);
+  return (dL + dR) * g_q4<T>(g);
 }
 
 template <int D, typename T>
@@ -38,7 +38,7 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const T* c
                                     const int* p, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
   T acc = T(0);
-  const T ih = T(1.0 / g.h);
+  const T ih = g_ih<T>(g);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T flux[2];
@@ -65,8 +65,8 @@ template <int D, typename T>
 __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
                                   const Geom& g, int c, const int* p, T beta, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
-  const T ih = T(1.0 / g.h);
-  const T ihh = T(1.0 / (g.h * g.h));
+  const T ih = g_ih<T>(g);
+  const T ihh = g_ihh<T>(g);
   T offd = T(0), diag = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -144,9 +144,9 @@ __host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, 
                                               const Geom& g, const Strides& S, int c, const int* p, T beta) {
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
-  const T ih = T(1.0 / g.h);
-  const T ihh = T(1.0 / (g.h * g.h));
-  const T q = T(0.25 / g.h);
+  const T ih = g_ih<T>(g);
+  const T ihh = g_ihh<T>(g);
+  const T q = g_q4<T>(g);
   int fid[3];
 #pragma unroll
   for (int a = 0; a < D; ++a) fid[a] = fidx(g, a, p[0], p[1], p[2]);
@@ -183,8 +183,8 @@ __host__ __device__ __forceinline__ T tensor_interior(const T* __restrict__ u, c
                                              const Strides& S, int c, const int* p) {
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
-  const T ih = T(1.0 / g.h);
-  const T q = T(0.25 / g.h);
+  const T ih = g_ih<T>(g);
+  const T q = g_q4<T>(g);
   T acc = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -214,13 +214,13 @@ __host__ __device__ __forceinline__ T tensor_interior(const T* __restrict__ u, c
 // thread t -> cell of red-black colour col (x index stride 2)
 template <int D>
 __host__ __device__ inline bool rb_cell(const Geom& g, int t, int col, int* p) {
-  int nxh = (g.n[0] + 1) / 2;
-  int ih = t % nxh;
-  int r = t / nxh;
+  const int nxh = (g.n[0] + 1) / 2;
+  const int r = divm(t, nxh, g.m_rb);
+  const int ih = t - r * nxh;
   int j, k;
   if (D == 3) {
-    j = r % g.n[1];
-    k = r / g.n[1];
+    k = divm(r, g.n[1], g.m_n1);
+    j = r - k * g.n[1];
   } else {
     j = r;
     k = 0;
@@ -396,7 +396,7 @@ __host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __r
     }
     s += lo + hi;
   }
-  T hh = T(g.h * g.h);
+  T hh = g_hh<T>(g);
   return (s - hh * b[cidx<D>(g, p[0], p[1], p[2])]) / T(cnt);
 }
 
@@ -419,7 +419,7 @@ __global__ void k_cell_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g
 
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g, int t) {
-  const T ih = T(1.0 / g.h);
+  const T ih = g_ih<T>(g);
   
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
@@ -445,7 +445,7 @@ __host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x
 
 template <int D, typename T>
 __global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
-  const T ih = T(1.0 / g.h);
+  const T ih = g_ih<T>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_cell_resid_at<D, T>(x, b, r, g, t);
   }
@@ -510,10 +510,11 @@ __host__ __device__ inline bool mc_node(const Geom& g, int t, int col, int* p) {
     int bit = (a < D) ? ((col >> a) & 1) : 0;
     cnt[a] = (a < D) ? (e[a] - bit + 1) / 2 : 1;
   }
-  int i0 = t % cnt[0];
-  int r = t / cnt[0];
-  int i1 = r % cnt[1];
-  int i2 = r / cnt[1];
+  const int b0 = col & 1, b1 = (col >> 1) & 1;
+  const int r = divm(t, cnt[0], g.m_mc0[b0]);
+  const int i0 = t - r * cnt[0];
+  const int i2 = divm(r, cnt[1], g.m_mc1[b1]);
+  const int i1 = r - i2 * cnt[1];
   p[0] = 2 * i0 + (col & 1);
   p[1] = 2 * i1 + ((col >> 1) & 1);
   p[2] = D == 3 ? 2 * i2 + ((col >> 2) & 1) : 0;
@@ -531,7 +532,7 @@ __host__ __device__ inline int mc_count(const Geom& g, int col) {
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_nodal_smooth_at(T* __restrict__ x, const T* __restrict__ b, Geom g, int col, int t) {
   int nt = mc_count<D>(g, col);
-  const T hh = T(g.h * g.h);
+  const T hh = g_hh<T>(g);
   const T is0 = T(-3.0 / 8.0);  // 1 / centre weight
   
     int p[3];
@@ -544,7 +545,7 @@ __host__ __device__ __forceinline__ void k_nodal_smooth_at(T* __restrict__ x, co
 template <int D, typename T>
 __global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g, int col) {
   int nt = mc_count<D>(g, col);
-  const T hh = T(g.h * g.h);
+  const T hh = g_hh<T>(g);
   const T is0 = T(-3.0 / 8.0);  // 1 / centre weight
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     k_nodal_smooth_at<D, T>(x, b, g, col, t);
@@ -554,20 +555,17 @@ __global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, Geom 
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_nodal_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g, int t) {
   int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
-  const T ihh = T(1.0 / (g.h * g.h));
+  const T ihh = g_ihh<T>(g);
   
     int p[3];
-    p[0] = t % e0;
-    int q = t / e0;
-    p[1] = q % e1;
-    p[2] = q / e1;
+    node_coords(g, t, p[0], p[1], p[2]);
     r[t] = b[t] - nodal_lap_point<D, T>(x, g, p, false) * ihh;
   }
 
 template <int D, typename T>
 __global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
   int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
-  const T ihh = T(1.0 / (g.h * g.h));
+  const T ihh = g_ihh<T>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
     k_nodal_resid_at<D, T>(x, b, r, g, t);
   }
@@ -575,7 +573,7 @@ __global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, 
 
 template <int D, typename T>
 __global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom g, int nsweep) {
-  const T hh = T(g.h * g.h);
+  const T hh = g_hh<T>(g);
   const T is0 = T(-3.0 / 8.0);
   const int ncol = 1 << D;
   for (int sw = 0; sw < nsweep; ++sw)
@@ -599,8 +597,12 @@ __global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom 
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_restrict_cells_at(const T* __restrict__ f, T* __restrict__ c, Geom gf, Geom gc, int ncomp, long long tt) {
   
-    int comp = (int)(tt / gc.ncell);
-    int t = (int)(tt % gc.ncell);
+    int comp = 0;
+    int t = (int)tt;
+    while (t >= gc.ncell) {
+      t -= gc.ncell;
+      ++comp;
+    }
     int I, J, K;
     cell_coords<D>(gc, t, I, J, K);
     const T* fc = f + (size_t)comp * gf.ncell;
@@ -634,10 +636,7 @@ __host__ __device__ __forceinline__ void k_restrict_faces_at(const T* __restrict
   int ex[3] = {gc.n[0] + (a == 0), gc.n[1] + (a == 1), gc.n[2] + (a == 2 && D == 3)};
   
     int P[3];
-    P[0] = t % ex[0];
-    int r = t / ex[0];
-    P[1] = r % ex[1];
-    P[2] = r / ex[1];
+    face_coords(gc, a, t, P[0], P[1], P[2]);
     // the two tangential axes in increasing order
     int o1 = -1, o2 = -1;
     for (int b = 0; b < D; ++b)
@@ -693,8 +692,12 @@ template <int D, typename T>
 __host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc,
                                     int ncomp, T sign, long long tt) {
   
-    int comp = (int)(tt / gf.ncell);
-    int t = (int)(tt % gf.ncell);
+    int comp = 0;
+    int t = (int)tt;
+    while (t >= gf.ncell) {
+      t -= gf.ncell;
+      ++comp;
+    }
     int i, j, k;
     cell_coords<D>(gf, t, i, j, k);
     const T* e = ec + (size_t)comp * gc.ncell;
@@ -731,10 +734,8 @@ template <int D, typename T>
 __host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict__ rf, T* __restrict__ rc, Geom gf, Geom gc, int t) {
   int e0 = gc.n[0] + 1, e1 = gc.n[1] + 1;
   
-    int I = t % e0;
-    int q = t / e0;
-    int J = q % e1;
-    int K = q / e1;
+    int I, J, K;
+    node_coords(gc, t, I, J, K);
     T zr[3];
     for (int kk = 0; kk < (D == 3 ? 3 : 1); ++kk) {
       int k = D == 3 ? 2 * K + kk - 1 : 0;
@@ -764,10 +765,8 @@ template <int D, typename T>
 __host__ __device__ __forceinline__ void k_prolong_nodes_add_at(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc, int t) {
   int e0 = gf.n[0] + 1, e1 = gf.n[1] + 1;
   
-    int i = t % e0;
-    int q = t / e0;
-    int j = q % e1;
-    int k = q / e1;
+    int i, j, k;
+    node_coords(gf, t, i, j, k);
     int I = i >> 1, J = j >> 1, K = k >> 1;
     T tz[2];
     for (int kk = 0; kk < (D == 3 ? 2 : 1); ++kk) {
@@ -806,7 +805,7 @@ __global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec
 // cell Laplacian of x at p (Neumann walls), as k_cell_resid
 template <int D, typename T>
 __device__ inline T cell_lap_point(const T* __restrict__ x, const Geom& g, const int* p) {
-  const T ih = T(1.0 / g.h);
+  const T ih = g_ih<T>(g);
   const T xc = x[cidx<D>(g, p[0], p[1], p[2])];
   T acc = T(0);
 #pragma unroll

@@ -103,6 +103,9 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
     "hbf_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "hbf_batch_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hbf_batch_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "hbf_batch_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "hbf_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -483,6 +486,21 @@ class Batch:
         self._check(self.lib.hbf_batch_autotune(self.b, int(reps), ctypes.byref(t), ctypes.byref(b),
                                                 ctypes.byref(ms)))
         return dict(tile=t.value, blocks_per_sm=b.value, probe_ms=ms.value)
+
+    PHASES = ("explicit_pre", "mac_solve", "explicit_post", "viscous_solve", "nodal_rhs", "nodal_solve",
+              "update")
+
+    def profile(self, on=True):
+        """Start (and reset) or stop phase timing of the following steps."""
+        self._check(self.lib.hbf_batch_profile(self.b, int(bool(on))))
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 7)()
+        trips = (ctypes.c_int64 * 3)()
+        steps = ctypes.c_int64()
+        self._check(self.lib.hbf_batch_profile_read(self.b, ms, trips, ctypes.byref(steps)))
+        return dict(steps=steps.value, phase_ms=dict(zip(self.PHASES, list(ms))),
+                    loop_trips=dict(zip(("mac", "visc", "nodal"), list(trips))))
 
     def launch_count(self):
         return int(self.lib.hbf_batch_launch_count(self.b))

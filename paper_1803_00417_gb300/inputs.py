@@ -100,3 +100,22 @@ def random_state(n, seed, amp=1.0, pamp=1.0):
     u = [amp * c / s for c in u]
     p = pamp * smooth_field(tuple(v + 1 for v in n), int(seeds[3]), kmax=4, centred=False)
     return u, p
+
+
+def batch_sweep(ncav=64, seed=0, sizes=(128, 256, 384, 512), bi=(0.0, 50.0), nexp=(0.3, 1.5), re=(1.0, 1000.0),
+                pa=1e4):
+    """A seeded parameter sweep of 2D lid-driven cavities: sizes drawn from
+    ``sizes`` (square, cells per side), Bi uniform in ``bi``, n uniform in
+    ``nexp``, Re log-uniform in ``re``, fixed m = ``pa``.  Returns a list of
+    :func:`cavity` dicts (each with its own dt = 0.5 h)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(ncav):
+        s = int(rng.choice(sizes))
+        b = float(rng.uniform(*bi))
+        ne = float(rng.uniform(*nexp))
+        r = float(np.exp(rng.uniform(np.log(re[0]), np.log(re[1]))))
+        c = cavity((s, s), Re=r, Bi=b, Pa=pa, nexp=ne)
+        c.update(Re=r, Bi=b)
+        out.append(c)
+    return out

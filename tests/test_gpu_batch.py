@@ -188,3 +188,44 @@ def test_batch_rejects_cavity_without_exact_bottom():
     with pytest.raises(HBFlowError, match="exact"):
         B.step()
     B.close()
+
+
+def test_batch_sweep_full_size_sample():
+    """The 64-cavity sweep the bench times (mixed precision): after one batched
+    step, one cavity of each size matches a separate context stepped from the
+    same state, and every solve of every cavity reached its tolerance."""
+    from paper_1803_00417_gb300.hbflow import MIXED, Batch, HBFlow
+    from paper_1803_00417_gb300.inputs import batch_sweep
+
+    cfgs = batch_sweep(ncav=64, seed=0)
+    B = Batch([c["n"] for c in cfgs], [c["h"] for c in cfgs], [c["wall_u"] for c in cfgs], precision=MIXED)
+    states = []
+    for i, c in enumerate(cfgs):
+        v = B.cavity(i)
+        v.set_rheology(c["K"], c["nexp"], c["tau_y"], c["m"])
+        u, p = random_state(c["n"], seed=1000 + i, amp=0.5)
+        v.set_velocity(u)
+        v.set_pressure(p)
+        states.append((u, p))
+    B.set_dt([c["dt"] for c in cfgs])
+    B.autotune(reps=1)
+    st = B.step()
+    for i in range(len(cfgs)):
+        for key in ("mac", "visc", "nodal"):
+            assert st[i][key]["converged"], (i, key, st[i][key])
+    picked = {}
+    for i, c in enumerate(cfgs):
+        picked.setdefault(c["n"][0], i)
+    assert len(picked) == 4
+    for size, i in sorted(picked.items()):
+        c = cfgs[i]
+        s = HBFlow(c["n"], c["h"], c["wall_u"], precision=MIXED)
+        s.set_rheology(c["K"], c["nexp"], c["tau_y"], c["m"])
+        s.set_velocity(states[i][0])
+        s.set_pressure(states[i][1])
+        s.step(c["dt"])
+        eu = rel(B.cavity(i).get_field("U"), s.get_field("U"))
+        ep = rel(B.cavity(i).get_field("P"), s.get_field("P"))
+        s.close()
+        assert eu < 1e-6 and ep < 1e-6, (size, i, eu, ep)
+    B.close()
