@@ -74,16 +74,22 @@ __global__ void __launch_bounds__(256) k_batch_reduce(const RedArg<T>* __restric
     double acc = 0.0;
     if (!mask || mask[T0.cav]) {
       const RedArg<T> a = args[T0.cav];
+      // max and dot accumulate in T over the lane's share of the tile (at
+      // most tile/32 elements), then in FP64 across lanes and tiles
       if (mode == 0) {
+        T m = T(0);
         for (int t = T0.begin + lane; t < T0.end; t += 32) {
-          double m = fabs((double)a.x[t]);
-          if (!isfinite(m)) m = INFINITY;
-          acc = fmax(acc, m);
+          T v = a.x[t] < T(0) ? -a.x[t] : a.x[t];
+          if (!isfinite(v)) v = T(INFINITY);
+          m = v > m ? v : m;
         }
+        acc = (double)m;
       } else if (mode == 1) {
         for (int t = T0.begin + lane; t < T0.end; t += 32) acc += (double)a.x[t];
       } else if (mode == 2) {
-        for (int t = T0.begin + lane; t < T0.end; t += 32) acc += (double)a.x[t] * (double)a.y[t];
+        T d = T(0);
+        for (int t = T0.begin + lane; t < T0.end; t += 32) d += a.x[t] * a.y[t];
+        acc = (double)d;
       } else {
         for (int t = T0.begin + lane; t < T0.end; t += 32) acc += node_weight(a.g, a.dim, t) * (double)a.x[t];
       }

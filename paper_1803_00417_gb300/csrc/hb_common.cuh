@@ -27,6 +27,7 @@ struct Geom {
   // index decompositions (see divm)
   double ih, ihh, q4, hh;
   float fih, fihh, fq4, fhh;
+  float fwu[3][2][3];  // FP32 wall velocities
   unsigned long long m_n0, m_n1, m_e0, m_e1, m_rb, m_mc0[2], m_mc1[2];
 };
 
@@ -56,6 +57,9 @@ __host__ __device__ inline void geom_finish(Geom& g) {
   g.fihh = (float)g.ihh;
   g.fq4 = (float)g.q4;
   g.fhh = (float)g.hh;
+  for (int a = 0; a < 3; ++a)
+    for (int sd = 0; sd < 2; ++sd)
+      for (int q = 0; q < 3; ++q) g.fwu[a][sd][q] = (float)g.wu[a][sd][q];
   g.m_n0 = div_magic((unsigned)g.n[0]);
   g.m_n1 = div_magic((unsigned)g.n[1]);
   g.m_e0 = div_magic((unsigned)(g.n[0] + 1));
@@ -68,6 +72,13 @@ __host__ __device__ inline void geom_finish(Geom& g) {
 }
 
 // the derived constants in arithmetic T
+template <typename T>
+__host__ __device__ inline T g_wu(const Geom& g, int a, int s, int c);
+template <>
+__host__ __device__ inline double g_wu<double>(const Geom& g, int a, int s, int c) { return g.wu[a][s][c]; }
+template <>
+__host__ __device__ inline float g_wu<float>(const Geom& g, int a, int s, int c) { return g.fwu[a][s][c]; }
+
 template <typename T>
 __host__ __device__ inline T g_ih(const Geom& g);
 template <>
@@ -170,7 +181,7 @@ __host__ __device__ inline T uget(const T* __restrict__ uc, const Geom& g, int c
   }
   T v = uc[cidx<D>(g, i, j, k)];
   if (ax < 0) return v;
-  T ub = hom ? T(0) : T(g.wu[ax][side][c]);
+  T ub = hom ? T(0) : g_wu<T>(g, ax, side, c);
   return T(2) * ub - v;
 }
 

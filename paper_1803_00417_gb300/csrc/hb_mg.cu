@@ -276,13 +276,26 @@ __global__ void k_bicg_x(T* __restrict__ x, const T* __restrict__ ph, const T* _
     x[t] = x[t] + alpha * ph[t] + omega * sh[t];
 }
 
-// sum of a*b over float arrays, accumulated in FP64
+// sum of a*b over float arrays: FP32 products summed in FP32 over runs of
+// kDotRun elements per thread, the runs summed in FP64 (GB300's FP64 rate is a
+// small fraction of its FP32 rate, so a per-element FP64 product is the
+// bottleneck of this reduction)
+constexpr int kDotRun = 64;
 __global__ void k_dot_partial_f(const float* __restrict__ a, const float* __restrict__ b, long long n,
                                 double* __restrict__ part) {
   double acc = 0.0;
+  float run = 0.f;
+  int k = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    acc += (double)a[t] * (double)b[t];
+       t += (long long)gridDim.x * blockDim.x) {
+    run = fmaf(a[t], b[t], run);
+    if (++k == kDotRun) {
+      acc += (double)run;
+      run = 0.f;
+      k = 0;
+    }
+  }
+  acc += (double)run;
   __shared__ double sh[kThreads / 32];
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -296,13 +309,14 @@ __global__ void k_dot_partial_f(const float* __restrict__ a, const float* __rest
 
 // max |x| over a float array (non-finite -> +inf)
 __global__ void k_maxabs_partial_f(const float* __restrict__ x, long long n, double* __restrict__ part) {
-  double acc = 0.0;
+  float m = 0.f;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    double a = fabs((double)x[t]);
+    float a = fabsf(x[t]);
     if (!isfinite(a)) a = INFINITY;
-    acc = fmax(acc, a);
+    m = fmaxf(m, a);
   }
+  double acc = (double)m;
   __shared__ double sh[kThreads / 32];
   for (int off = 16; off > 0; off >>= 1) acc = fmax(acc, __shfl_xor_sync(0xffffffffu, acc, off));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;

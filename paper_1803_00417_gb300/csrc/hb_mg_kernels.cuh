@@ -84,7 +84,7 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
       T wf = kappa * ef[a][fidx(g, a, fq[0], fq[1], fq[2])] * ihh;
       bool wall = (s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1);
       if (wall) {
-        T ub = hom ? T(0) : T(g.wu[a][s][c]);
+        T ub = hom ? T(0) : g_wu<T>(g, a, s, c);
         offd += T(2) * wf * ub;
         diag += T(2) * wf;
       } else {
@@ -274,7 +274,7 @@ __host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, c
   }
 
 template <int D, typename T, int C>
-__global__ void __launch_bounds__(256) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
+__global__ void __launch_bounds__(256, 8) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
                                                       const T* ef1, const T* ef2, Geom g, int col, T beta, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
   const int nt = rb_count<D>(g);
