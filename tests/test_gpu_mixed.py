@@ -37,6 +37,9 @@ def rel_l2(a, b):
     ((48, 32), 32, dict(Re=1000.0, Bi=5.0, Pa=1e5, nexp=0.5)),
     ((16, 16, 16), 33, dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)),
     ((24, 20, 12), 34, dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)),
+    # wide enough for the shared-memory staged smoother on two levels, with
+    # ragged x tiles and a ragged z chunk
+    ((64, 32, 40), 35, dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)),
 ])
 def test_mixed_step_matches_fp64_oracle(n, seed, over):
     from paper_1803_00417_gb300.hbflow import MIXED, HBFlow
