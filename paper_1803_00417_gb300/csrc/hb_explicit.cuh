@@ -26,12 +26,13 @@ __host__ __device__ inline double viscosity(double g, const Rheo& r) {
 }
 
 template <int D>
-__host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, double* __restrict__ eta, Geom g, Rheo r, int t) {
+__host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, double* __restrict__ eta, const Geom& g, Rheo r, int t) {
   
     int i, j, k;
     cell_coords<D>(g, t, i, j, k);
     int p[3] = {i, j, k};
     double G[3][3];
+    const double i2h = 0.5 * g.ih;  // 1/(2h), rounded once on the host
     // (grad u)_{ab} = d u_b / d x_a by central differences
 #pragma unroll
     for (int b = 0; b < D; ++b) {
@@ -42,8 +43,8 @@ __host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, 
         q1[a] += 1;
         q0[a] -= 1;
         G[a][b] = (uget<D>(ub, g, b, q1[0], q1[1], q1[2], false) -
-                   uget<D>(ub, g, b, q0[0], q0[1], q0[2], false)) /
-                  (2.0 * g.h);
+                   uget<D>(ub, g, b, q0[0], q0[1], q0[2], false)) *
+                  i2h;
       }
     }
     double s = 0.0;
@@ -59,7 +60,7 @@ __host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, 
   }
 
 template <int D>
-__global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, Geom g, Rheo r) {
+__global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, const __grid_constant__ Geom g, Rheo r) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_eta_at<D>(u, eta, g, r, t);
   }
@@ -67,7 +68,7 @@ __global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, Ge
 
 // face eta on level 0: mean of the two cells, wall faces take the interior cell
 template <int D>
-__host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict__ eta, double* __restrict__ ef, int a, Geom g, int t) {
+__host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict__ eta, double* __restrict__ ef, int a, const Geom& g, int t) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   
     int p[3];
@@ -80,7 +81,7 @@ __host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict
   }
 
 template <int D>
-__global__ void k_eta_faces(const double* __restrict__ eta, double* __restrict__ ef, int a, Geom g) {
+__global__ void k_eta_faces(const double* __restrict__ eta, double* __restrict__ ef, int a, const __grid_constant__ Geom g) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
@@ -123,7 +124,7 @@ __host__ __device__ inline double grad_nodal(const double* __restrict__ p, const
 }
 
 template <int D>
-__host__ __device__ __forceinline__ void k_grad_p_at(const double* __restrict__ p, double* __restrict__ Gp, Geom g, int t) {
+__host__ __device__ __forceinline__ void k_grad_p_at(const double* __restrict__ p, double* __restrict__ Gp, const Geom& g, int t) {
   
     int i, j, k;
     cell_coords<D>(g, t, i, j, k);
@@ -132,7 +133,7 @@ __host__ __device__ __forceinline__ void k_grad_p_at(const double* __restrict__ 
   }
 
 template <int D>
-__global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, Geom g) {
+__global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, const __grid_constant__ Geom g) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_grad_p_at<D>(p, Gp, g, t);
   }
@@ -164,7 +165,7 @@ __host__ __device__ inline double slope5(const double* w) {
 }
 
 template <int D>
-__host__ __device__ __forceinline__ void k_slopes_at(const double* __restrict__ u, double* __restrict__ slopes, Geom g, int t) {
+__host__ __device__ __forceinline__ void k_slopes_at(const double* __restrict__ u, double* __restrict__ slopes, const Geom& g, int t) {
   const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
   
     int p[3];
@@ -193,7 +194,7 @@ __host__ __device__ __forceinline__ void k_slopes_at(const double* __restrict__ 
   }
 
 template <int D>
-__global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slopes, Geom g) {
+__global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slopes, const __grid_constant__ Geom g) {
   const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_slopes_at<D>(u, slopes, g, t);
@@ -244,7 +245,7 @@ __host__ __device__ inline void prestate_face(const double* __restrict__ u, cons
 
 template <int D>
 __host__ __device__ __forceinline__ void k_hats_at(const double* __restrict__ u, const double* __restrict__ slopes,
-                       double* __restrict__ hats, Geom g, double dt, int t) {
+                       double* __restrict__ hats, const Geom& g, double dt, int t) {
   
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
@@ -263,7 +264,7 @@ __host__ __device__ __forceinline__ void k_hats_at(const double* __restrict__ u,
 
 template <int D>
 __global__ void k_hats(const double* __restrict__ u, const double* __restrict__ slopes,
-                       double* __restrict__ hats, Geom g, double dt) {
+                       double* __restrict__ hats, const __grid_constant__ Geom g, double dt) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_hats_at<D>(u, slopes, hats, g, dt, t);
   }
@@ -302,7 +303,7 @@ __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ 
                          const double* __restrict__ hats, const double* __restrict__ Gp,
                          const double* __restrict__ Lu, Force fo, double rho, int pv, int a,
                          double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
-                         Geom g, double dt, int t) {
+                         const Geom& g, double dt, int t) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
   
@@ -341,7 +342,7 @@ __global__ void k_traces(const double* __restrict__ u, const double* __restrict_
                          const double* __restrict__ hats, const double* __restrict__ Gp,
                          const double* __restrict__ Lu, Force fo, double rho, int pv, int a,
                          double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
-                         Geom g, double dt) {
+                         const __grid_constant__ Geom g, double dt) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
@@ -354,7 +355,7 @@ __global__ void k_traces(const double* __restrict__ u, const double* __restrict_
 // ---------------------------------------------------------------------------
 template <int D>
 __host__ __device__ __forceinline__ void k_mac_rhs_at(const double* ua0, const double* ua1, const double* ua2,
-                          double* __restrict__ rhs, Geom g, int t) {
+                          double* __restrict__ rhs, const Geom& g, int t) {
   const double* ua[3] = {ua0, ua1, ua2};
   
     int p[3];
@@ -373,7 +374,7 @@ __host__ __device__ __forceinline__ void k_mac_rhs_at(const double* ua0, const d
 
 template <int D>
 __global__ void k_mac_rhs(const double* ua0, const double* ua1, const double* ua2,
-                          double* __restrict__ rhs, Geom g) {
+                          double* __restrict__ rhs, const __grid_constant__ Geom g) {
   const double* ua[3] = {ua0, ua1, ua2};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_mac_rhs_at<D>(ua0, ua1, ua2, rhs, g, t);
@@ -382,7 +383,7 @@ __global__ void k_mac_rhs(const double* ua0, const double* ua1, const double* ua
 
 template <int D>
 __host__ __device__ __forceinline__ void k_mac_correct_at(const double* __restrict__ uadv, const double* __restrict__ phi,
-                              double* __restrict__ umac, int a, Geom g, int t) {
+                              double* __restrict__ umac, int a, const Geom& g, int t) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   
     int R[3];
@@ -399,7 +400,7 @@ __host__ __device__ __forceinline__ void k_mac_correct_at(const double* __restri
 
 template <int D>
 __global__ void k_mac_correct(const double* __restrict__ uadv, const double* __restrict__ phi,
-                              double* __restrict__ umac, int a, Geom g) {
+                              double* __restrict__ umac, int a, const __grid_constant__ Geom g) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
@@ -416,7 +417,7 @@ __host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restric
                              const double* uR2, const double* um0, const double* um1,
                              const double* um2, const double* __restrict__ Gp,
                              const double* __restrict__ Lu, Force fo, double rho,
-                             double* __restrict__ rhs, Geom g, double dt, int t) {
+                             double* __restrict__ rhs, const Geom& g, double dt, int t) {
   const double* uL[3] = {uL0, uL1, uL2};
   const double* uR[3] = {uR0, uR1, uR2};
   const double* um[3] = {um0, um1, um2};
@@ -453,7 +454,7 @@ __global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, co
                              const double* uR2, const double* um0, const double* um1,
                              const double* um2, const double* __restrict__ Gp,
                              const double* __restrict__ Lu, Force fo, double rho,
-                             double* __restrict__ rhs, Geom g, double dt) {
+                             double* __restrict__ rhs, const __grid_constant__ Geom g, double dt) {
   const double* uL[3] = {uL0, uL1, uL2};
   const double* uR[3] = {uR0, uR1, uR2};
   const double* um[3] = {um0, um1, um2};
@@ -467,7 +468,7 @@ __global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, co
 // ---------------------------------------------------------------------------
 template <int D>
 __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict__ ustar, const double* __restrict__ Gp,
-                            double* __restrict__ out, Geom g, double dt, double rho, int t) {
+                            double* __restrict__ out, const Geom& g, double dt, double rho, int t) {
   int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
   
     int p[3];
@@ -507,7 +508,7 @@ __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict
 
 template <int D>
 __global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __restrict__ Gp,
-                            double* __restrict__ out, Geom g, double dt, double rho) {
+                            double* __restrict__ out, const __grid_constant__ Geom g, double dt, double rho) {
   int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
     k_nodal_rhs_at<D>(ustar, Gp, out, g, dt, rho, t);
@@ -516,7 +517,7 @@ __global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __re
 
 template <int D>
 __host__ __device__ __forceinline__ void k_project_update_at(double* __restrict__ u, const double* __restrict__ Gp,
-                                 const double* __restrict__ phi, Geom g, double dt, double rho, int t) {
+                                 const double* __restrict__ phi, const Geom& g, double dt, double rho, int t) {
   
     int i, j, k;
     cell_coords<D>(g, t, i, j, k);
@@ -530,7 +531,7 @@ __host__ __device__ __forceinline__ void k_project_update_at(double* __restrict_
 
 template <int D>
 __global__ void k_project_update(double* __restrict__ u, const double* __restrict__ Gp,
-                                 const double* __restrict__ phi, Geom g, double dt, double rho) {
+                                 const double* __restrict__ phi, const __grid_constant__ Geom g, double dt, double rho) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_project_update_at<D>(u, Gp, phi, g, dt, rho, t);
   }

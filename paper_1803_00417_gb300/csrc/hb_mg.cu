@@ -22,7 +22,7 @@ namespace hb {
 // ---------------------------------------------------------------------------
 template <int MODE>  // 0: max |x| (non-finite -> +inf), 1: sum x, 2: weighted nodal sum
 __global__ void k_reduce_partial(const double* __restrict__ x, long long n, double* __restrict__ part,
-                                 Geom g, int dim) {
+                                 const __grid_constant__ Geom g, int dim) {
   double acc = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {

@@ -239,7 +239,7 @@ __host__ __device__ inline int rb_count(const Geom& g) {
 
 template <int D, typename T>
 __global__ void k_visc_smooth(T* __restrict__ u, const T* __restrict__ b, const T* ef0, const T* ef1,
-                              const T* ef2, Geom g, int c, int col, T beta, int hom) {
+                              const T* ef2, const __grid_constant__ Geom g, int c, int col, T beta, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
   const Strides S = make_strides(g);
   int nt = rb_count<D>(g);
@@ -257,7 +257,7 @@ __global__ void k_visc_smooth(T* __restrict__ u, const T* __restrict__ b, const 
 // launch of about 24 blocks per SM measured faster than one thread per cell.)
 template <int D, typename T, int C>
 __host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
-                                                      const T* ef1, const T* ef2, Geom g, int col, T beta, int hom, int t) {
+                                                      const T* ef1, const T* ef2, const Geom& g, int col, T beta, int hom, int t) {
   const T* ef[3] = {ef0, ef1, ef2};
   const int nt = rb_count<D>(g);
   
@@ -275,7 +275,7 @@ __host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, c
 
 template <int D, typename T, int C>
 __global__ void __launch_bounds__(256, 8) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
-                                                      const T* ef1, const T* ef2, Geom g, int col, T beta, int hom) {
+                                                      const T* ef1, const T* ef2, const __grid_constant__ Geom g, int col, T beta, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
   const int nt = rb_count<D>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256, 8) k_visc_smooth_c(T* __restrict__ u, con
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, const T* __restrict__ b,
                                                      T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
-                                                     Geom g, T beta, int hom, int t) {
+                                                     const Geom& g, T beta, int hom, int t) {
   const T* ef[3] = {ef0, ef1, ef2};
   int p[3];
   cell_coords<D>(g, t, p[0], p[1], p[2]);
@@ -306,7 +306,7 @@ __host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, c
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_visc_op3(const T* __restrict__ u, const T* __restrict__ b,
                                                  T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
-                                                 Geom g, T beta, int hom) {
+                                                 const __grid_constant__ Geom g, T beta, int hom) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) k_visc_op3(const T* __restrict__ u, const
 // out = L_eta u (the stress divergence alone), grid-stride over cells
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_tensor_lu_at(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
-                                                  const T* ef1, const T* ef2, Geom g, int hom, int t) {
+                                                  const T* ef1, const T* ef2, const Geom& g, int hom, int t) {
   const T* ef[3] = {ef0, ef1, ef2};
   const Strides S = make_strides(g);
   
@@ -344,7 +344,7 @@ __host__ __device__ __forceinline__ void k_tensor_lu_at(const T* __restrict__ u,
 
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_tensor_lu(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
-                                                  const T* ef1, const T* ef2, Geom g, int hom) {
+                                                  const T* ef1, const T* ef2, const __grid_constant__ Geom g, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
   const Strides S = make_strides(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(256) k_tensor_lu(const T* __restrict__ u, T* _
 // coarsest level: all sweeps in one block
 template <int D, typename T>
 __global__ void k_visc_bottom(T* __restrict__ u, const T* __restrict__ b, const T* ef0, const T* ef1,
-                              const T* ef2, Geom g, T beta, int nsweep, int hom) {
+                              const T* ef2, const __grid_constant__ Geom g, T beta, int nsweep, int hom) {
   const T* ef[3] = {ef0, ef1, ef2};
   int nt = rb_count<D>(g);
   for (int sw = 0; sw < nsweep; ++sw)
@@ -401,7 +401,7 @@ __host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __r
 }
 
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_cell_smooth_at(T* __restrict__ x, const T* __restrict__ b, Geom g, int col, int t) {
+__host__ __device__ __forceinline__ void k_cell_smooth_at(T* __restrict__ x, const T* __restrict__ b, const Geom& g, int col, int t) {
   int nt = rb_count<D>(g);
   
     int p[3];
@@ -410,7 +410,7 @@ __host__ __device__ __forceinline__ void k_cell_smooth_at(T* __restrict__ x, con
   }
 
 template <int D, typename T>
-__global__ void k_cell_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g, int col) {
+__global__ void k_cell_smooth(T* __restrict__ x, const T* __restrict__ b, const __grid_constant__ Geom g, int col) {
   int nt = rb_count<D>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     k_cell_smooth_at<D, T>(x, b, g, col, t);
@@ -418,7 +418,7 @@ __global__ void k_cell_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g
 }
 
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g, int t) {
+__host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const Geom& g, int t) {
   const T ih = g_ih<T>(g);
   
     int p[3];
@@ -444,7 +444,7 @@ __host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x
   }
 
 template <int D, typename T>
-__global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
+__global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const __grid_constant__ Geom g) {
   const T ih = g_ih<T>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_cell_resid_at<D, T>(x, b, r, g, t);
@@ -452,7 +452,7 @@ __global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T
 }
 
 template <int D, typename T>
-__global__ void k_cell_bottom(T* __restrict__ x, const T* __restrict__ b, Geom g, int nsweep) {
+__global__ void k_cell_bottom(T* __restrict__ x, const T* __restrict__ b, const __grid_constant__ Geom g, int nsweep) {
   int nt = rb_count<D>(g);
   for (int sw = 0; sw < nsweep; ++sw)
     for (int col = 0; col < 2; ++col) {
@@ -530,7 +530,7 @@ __host__ __device__ inline int mc_count(const Geom& g, int col) {
 }
 
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_nodal_smooth_at(T* __restrict__ x, const T* __restrict__ b, Geom g, int col, int t) {
+__host__ __device__ __forceinline__ void k_nodal_smooth_at(T* __restrict__ x, const T* __restrict__ b, const Geom& g, int col, int t) {
   int nt = mc_count<D>(g, col);
   const T hh = g_hh<T>(g);
   const T is0 = T(-3.0 / 8.0);  // 1 / centre weight
@@ -543,7 +543,7 @@ __host__ __device__ __forceinline__ void k_nodal_smooth_at(T* __restrict__ x, co
   }
 
 template <int D, typename T>
-__global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, Geom g, int col) {
+__global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, const __grid_constant__ Geom g, int col) {
   int nt = mc_count<D>(g, col);
   const T hh = g_hh<T>(g);
   const T is0 = T(-3.0 / 8.0);  // 1 / centre weight
@@ -553,7 +553,7 @@ __global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, Geom 
 }
 
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_nodal_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g, int t) {
+__host__ __device__ __forceinline__ void k_nodal_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const Geom& g, int t) {
   int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
   const T ihh = g_ihh<T>(g);
   
@@ -563,7 +563,7 @@ __host__ __device__ __forceinline__ void k_nodal_resid_at(const T* __restrict__ 
   }
 
 template <int D, typename T>
-__global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, Geom g) {
+__global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const __grid_constant__ Geom g) {
   int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
   const T ihh = g_ihh<T>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
@@ -572,7 +572,7 @@ __global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, 
 }
 
 template <int D, typename T>
-__global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom g, int nsweep) {
+__global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, const __grid_constant__ Geom g, int nsweep) {
   const T hh = g_hh<T>(g);
   const T is0 = T(-3.0 / 8.0);
   const int ncol = 1 << D;
@@ -595,7 +595,7 @@ __global__ void k_nodal_bottom(T* __restrict__ x, const T* __restrict__ b, Geom 
 // ---------------------------------------------------------------------------
 // mean of the 2^D children, averaged axis by axis (x, then y, then z)
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_restrict_cells_at(const T* __restrict__ f, T* __restrict__ c, Geom gf, Geom gc, int ncomp, long long tt) {
+__host__ __device__ __forceinline__ void k_restrict_cells_at(const T* __restrict__ f, T* __restrict__ c, const Geom& gf, const Geom& gc, int ncomp, long long tt) {
   
     int comp = 0;
     int t = (int)tt;
@@ -622,7 +622,7 @@ __host__ __device__ __forceinline__ void k_restrict_cells_at(const T* __restrict
   }
 
 template <int D, typename T>
-__global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, Geom gf, Geom gc, int ncomp) {
+__global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc, int ncomp) {
   long long tot = (long long)gc.ncell * ncomp;
   for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
        tt += (long long)gridDim.x * blockDim.x) {
@@ -632,7 +632,7 @@ __global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, Geo
 
 // coarse a-face eta: mean of the fine a-faces tiling it (pairwise, axis order)
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_restrict_faces_at(const T* __restrict__ ff, T* __restrict__ fc, int a, Geom gf, Geom gc, int t) {
+__host__ __device__ __forceinline__ void k_restrict_faces_at(const T* __restrict__ ff, T* __restrict__ fc, int a, const Geom& gf, const Geom& gc, int t) {
   int ex[3] = {gc.n[0] + (a == 0), gc.n[1] + (a == 1), gc.n[2] + (a == 2 && D == 3)};
   
     int P[3];
@@ -664,7 +664,7 @@ __host__ __device__ __forceinline__ void k_restrict_faces_at(const T* __restrict
   }
 
 template <int D, typename T>
-__global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, int a, Geom gf, Geom gc) {
+__global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, int a, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc) {
   int ex[3] = {gc.n[0] + (a == 0), gc.n[1] + (a == 1), gc.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
@@ -689,7 +689,7 @@ __host__ __device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, i
 
 // x_f += P e_c, cell-centred multilinear (3/4, 1/4 per axis), axis by axis
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc,
+__host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ xf, const T* __restrict__ ec, const Geom& gf, const Geom& gc,
                                     int ncomp, T sign, long long tt) {
   
     int comp = 0;
@@ -720,7 +720,7 @@ __host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ 
   }
 
 template <int D, typename T>
-__global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc,
+__global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
                                     int ncomp, T sign) {
   long long tot = (long long)gf.ncell * ncomp;
   for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
@@ -731,7 +731,7 @@ __global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec
 
 // full weighting onto coarse nodes (even reflection), axis by axis
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict__ rf, T* __restrict__ rc, Geom gf, Geom gc, int t) {
+__host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict__ rf, T* __restrict__ rc, const Geom& gf, const Geom& gc, int t) {
   int e0 = gc.n[0] + 1, e1 = gc.n[1] + 1;
   
     int I, J, K;
@@ -753,7 +753,7 @@ __host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict
   }
 
 template <int D, typename T>
-__global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, Geom gf, Geom gc) {
+__global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc) {
   int e0 = gc.n[0] + 1, e1 = gc.n[1] + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gc.nnode; t += gridDim.x * blockDim.x) {
     k_restrict_nodes_at<D, T>(rf, rc, gf, gc, t);
@@ -762,7 +762,7 @@ __global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, G
 
 // x_f += P e_c, nodal multilinear, axis by axis
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_prolong_nodes_add_at(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc, int t) {
+__host__ __device__ __forceinline__ void k_prolong_nodes_add_at(T* __restrict__ xf, const T* __restrict__ ec, const Geom& gf, const Geom& gc, int t) {
   int e0 = gf.n[0] + 1, e1 = gf.n[1] + 1;
   
     int i, j, k;
@@ -792,7 +792,7 @@ __host__ __device__ __forceinline__ void k_prolong_nodes_add_at(T* __restrict__ 
   }
 
 template <int D, typename T>
-__global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec, Geom gf, Geom gc) {
+__global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc) {
   int e0 = gf.n[0] + 1, e1 = gf.n[1] + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gf.nnode; t += gridDim.x * blockDim.x) {
     k_prolong_nodes_add_at<D, T>(xf, ec, gf, gc, t);
@@ -832,7 +832,7 @@ __device__ inline T cell_lap_point(const T* __restrict__ x, const Geom& g, const
 // the dual-cell fraction for nodes).
 template <int D>
 __device__ inline void dense_build_col(int kind, double* __restrict__ X, double* __restrict__ M, int n, int ld,
-                                       const double* ef0, const double* ef1, const double* ef2, Geom g, double beta,
+                                       const double* ef0, const double* ef1, const double* ef2, const Geom& g, double beta,
                                        int k) {
   double* e = X + (size_t)k * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) e[i] = (i == k) ? 1.0 : 0.0;
@@ -875,7 +875,7 @@ __device__ inline void dense_build_col(int kind, double* __restrict__ X, double*
 
 template <int D>
 __global__ void k_dense_build(int kind, double* __restrict__ X, double* __restrict__ M, int n, int ld,
-                              const double* ef0, const double* ef1, const double* ef2, Geom g, double beta) {
+                              const double* ef0, const double* ef1, const double* ef2, const __grid_constant__ Geom g, double beta) {
   dense_build_col<D>(kind, X, M, n, ld, ef0, ef1, ef2, g, beta, blockIdx.x);
 }
 
