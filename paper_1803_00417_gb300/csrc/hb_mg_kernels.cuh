@@ -283,7 +283,33 @@ __global__ void __launch_bounds__(256, 8) k_visc_smooth_c(T* __restrict__ u, con
   }
 }
 
-// out = u - beta L u, or r = b - (u - beta L u) when b != nullptr, at cell t
+// out = u - beta L u, or r = b - (u - beta L u) when b != nullptr, for every
+// component of cell p (flat index t).  Interior cells and wall cells are two
+// separate branches (warps are almost always uniform).
+template <int D, typename T>
+__host__ __device__ __forceinline__ void visc_op_cell(const T* __restrict__ u, const T* __restrict__ b,
+                                                     T* __restrict__ out, const T* const* ef, const Geom& g, T beta,
+                                                     int hom, const int* p, int t) {
+  if (interior<D>(g, p)) {
+    const Strides S = make_strides(g);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const size_t o = (size_t)c * g.ncell + t;
+      const T Lu = tensor_interior<D, T>(u, ef, g, S, c, p);
+      const T Au = u[o] - beta * Lu;
+      out[o] = b ? b[o] - Au : Au;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const size_t o = (size_t)c * g.ncell + t;
+      const T Lu = mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+      const T Au = u[o] - beta * Lu;
+      out[o] = b ? b[o] - Au : Au;
+    }
+  }
+}
+
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, const T* __restrict__ b,
                                                      T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
@@ -291,15 +317,7 @@ __host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, c
   const T* ef[3] = {ef0, ef1, ef2};
   int p[3];
   cell_coords<D>(g, t, p[0], p[1], p[2]);
-  const bool in = interior<D>(g, p);
-  const Strides S = make_strides(g);
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    size_t o = (size_t)c * g.ncell + t;
-    T Lu = in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
-    T Au = u[o] - beta * Lu;
-    out[o] = b ? b[o] - Au : Au;
-  }
+  visc_op_cell<D, T>(u, b, out, ef, g, beta, hom, p, t);
 }
 
 // out = u - beta L u, or r = b - (u - beta L u) when b != nullptr; 3D grid over cells
@@ -311,36 +329,28 @@ __global__ void __launch_bounds__(256) k_visc_op3(const T* __restrict__ u, const
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= g.n[0] || j >= g.n[1]) return;
-  int p[3] = {i, j, k};
+  const int p[3] = {i, j, k};
   const T* ef[3] = {ef0, ef1, ef2};
-  const int t = cidx<D>(g, i, j, k);
-  const bool in = interior<D>(g, p);
-  const Strides S = make_strides(g);
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    size_t o = (size_t)c * g.ncell + t;
-    T Lu = in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
-    T Au = u[o] - beta * Lu;
-    out[o] = b ? b[o] - Au : Au;
-  }
+  visc_op_cell<D, T>(u, b, out, ef, g, beta, hom, p, cidx<D>(g, i, j, k));
 }
 
-
-// out = L_eta u (the stress divergence alone), grid-stride over cells
+// out = L_eta u (the stress divergence alone) at cell t; interior and wall
+// cells in separate branches as in visc_op_cell
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_tensor_lu_at(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
-                                                  const T* ef1, const T* ef2, const Geom& g, int hom, int t) {
+                                                        const T* ef1, const T* ef2, const Geom& g, int hom, int t) {
   const T* ef[3] = {ef0, ef1, ef2};
-  const Strides S = make_strides(g);
-  
-    int p[3];
-    cell_coords<D>(g, t, p[0], p[1], p[2]);
-    const bool in = interior<D>(g, p);
+  int p[3];
+  cell_coords<D>(g, t, p[0], p[1], p[2]);
+  if (interior<D>(g, p)) {
+    const Strides S = make_strides(g);
 #pragma unroll
-    for (int c = 0; c < D; ++c)
-      out[(size_t)c * g.ncell + t] =
-          in ? tensor_interior<D, T>(u, ef, g, S, c, p) : mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+    for (int c = 0; c < D; ++c) out[(size_t)c * g.ncell + t] = tensor_interior<D, T>(u, ef, g, S, c, p);
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c) out[(size_t)c * g.ncell + t] = mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
   }
+}
 
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_tensor_lu(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
