@@ -39,10 +39,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-learned", action="store_true", help="time the mixed method without the learned guess")
-    ap.add_argument("--learn-n", type=int, default=64, help="cells per axis of the training cavities")
+    ap.add_argument("--learn-n", type=int, default=128, help="cells per axis of the training cavities")
     ap.add_argument("--learn-seeds", type=int, default=6)
     ap.add_argument("--learn-steps", type=int, default=10)
     ap.add_argument("--learn-epochs", type=int, default=15)
+    ap.add_argument("--learn-level", type=int, default=2,
+                    help="multigrid level whose nodes the network sees (0 = finest)")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 method on the same workload")
     ap.add_argument("--workload", default="cavity256_3d_hb")
@@ -310,29 +312,33 @@ def run_ours(args):
         # offline part of the learned guess: solver-generated pairs on small
         # cavities of the same family, trained by the library's kernels
         from paper_1803_00417_gb300.hbflow import UNet
-        from paper_1803_00417_gb300.learned import box_mask, generate_pairs, net_box, train
+        from paper_1803_00417_gb300.learned import box_mask, coarse_cells, generate_pairs, net_box, train
 
         t0 = time.perf_counter()
+        lv = args.learn_level
         ln = (args.learn_n,) * d
-        xs, ys, _ = generate_pairs(ln, seeds=range(args.learn_seeds), steps=args.learn_steps, precision=MIXED)
-        lbox = net_box(ln)
+        xs, ys, _ = generate_pairs(ln, seeds=range(args.learn_seeds), steps=args.learn_steps, precision=MIXED,
+                                   level=lv)
+        lbox = net_box(coarse_cells(ln, lv))
         tnet = UNet(lbox, train=True, seed=0)
-        hist = train(tnet, xs, ys, box_mask(ln, lbox), epochs=args.learn_epochs, lr=1e-3, batch=4)
+        hist = train(tnet, xs, ys, box_mask(coarse_cells(ln, lv), lbox), epochs=args.learn_epochs, lr=1e-3,
+                     batch=4)
         params = tnet.get_params()
         tnet.close()
-        model = UNet(net_box(cfg["n"]), train=False)
+        model = UNet(net_box(coarse_cells(cfg["n"], lv)), train=False)
         model.set_params(params)
         learned = {"train_cavities": f"{args.learn_seeds} x {args.learn_n}^{d}, random Bi/n/Re",
-                   "train_pairs": int(len(xs)),
+                   "train_pairs": int(len(xs)), "level": lv,
                    "epochs": args.learn_epochs, "loss_first": hist[0], "loss_last": hist[-1],
-                   "offline_seconds": time.perf_counter() - t0, "box": list(net_box(cfg["n"]))}
+                   "offline_seconds": time.perf_counter() - t0,
+                   "box": list(net_box(coarse_cells(cfg["n"], lv)))}
     sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=prec)
     sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
     sim.set_solver(rtol=1e-10, max_cycles=200)
     if model is not None:
         from paper_1803_00417_gb300.hbflow import set_guess_model
 
-        set_guess_model(sim, model)
+        set_guess_model(sim, model, args.learn_level)
     zeros_u = np.zeros(d * ncell)
     zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
     sim.set_field("U", zeros_u)

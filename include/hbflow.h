@@ -250,6 +250,14 @@ int hbf_unet_adam(hbf_unet* net, double lr, double beta1, double beta2, double e
  * smaller than |r0|_inf, otherwise the solve starts from p.  The network's
  * box must hold the (n+1)^d nodes: each of its sizes >= n[a] + 1. */
 int hbf_set_guess_model(hbf_ctx* ctx, hbf_unet* net);
+/* The same with the network on the nodes of multigrid level `level` (0 = the
+ * finest grid; each level halves the cells per axis): the warm-start residual
+ * is restricted to that level by nodal full weighting, the network's output
+ * is interpolated back to the finest nodes, and the step and acceptance rule
+ * are as above.  A coarse level makes the network 2^(d*level) times cheaper;
+ * the correction it has to predict is the smooth part.  The box must hold
+ * that level's nodes.  HBF_ERR_ARG if the level does not exist. */
+int hbf_set_guess_model_level(hbf_ctx* ctx, hbf_unet* net, int level);
 
 int hbf_sync(hbf_ctx* ctx);
 const char* hbf_last_error(const hbf_ctx* ctx);

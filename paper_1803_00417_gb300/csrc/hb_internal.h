@@ -119,6 +119,7 @@ struct hbf_ctx {
   double* nres0 = nullptr;    // nnode: warm-start residual of the last nodal solve
   // learned initial guess (optional)
   hbf_unet* guess = nullptr;
+  int guess_level = 0;        // multigrid level whose nodes the network sees
   double* ntry = nullptr;     // nnode: network correction on the nodes
   double* nzero = nullptr;    // nnode zeros
   float* net_x = nullptr;     // network input, one value per network point
@@ -191,6 +192,9 @@ int solve_mac(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
 int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s);
 int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s);
 int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r);
+// FP64 nodal full weighting from level l to l+1, and coarse += P fine correction
+void nodal_restrict(hbf_ctx* c, int l, const double* fine, double* coarse);
+void nodal_prolong_add(hbf_ctx* c, int l, double* fine, const double* coarse);
 int tensor_lu(hbf_ctx* c, const double* u, double* out);  // out = L_eta u, finest level
 bool ensure_dense(hbf_ctx* c, int kind, double beta);      // dense bottom inverse ready?
 void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, long long n);  // out = x - a y

@@ -946,6 +946,22 @@ int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r) {
   return cuda_check(c, cudaGetLastError(), "nodal residual");
 }
 
+void nodal_restrict(hbf_ctx* c, int l, const double* fine, double* coarse) {
+  const Level &F = c->lv[l], &C = c->lv[l + 1];
+  if (c->dim == 2)
+    launch(c, kSlotTransfer, k_restrict_nodes<2, double>, grid_for(C.g.nnode), kThreads, fine, coarse, F.g, C.g);
+  else
+    launch(c, kSlotTransfer, k_restrict_nodes<3, double>, grid_for(C.g.nnode), kThreads, fine, coarse, F.g, C.g);
+}
+
+void nodal_prolong_add(hbf_ctx* c, int l, double* fine, const double* coarse) {
+  const Level &F = c->lv[l], &C = c->lv[l + 1];
+  if (c->dim == 2)
+    launch(c, kSlotTransfer, k_prolong_nodes_add<2, double>, grid_for(F.g.nnode), kThreads, fine, coarse, F.g, C.g);
+  else
+    launch(c, kSlotTransfer, k_prolong_nodes_add<3, double>, grid_for(F.g.nnode), kThreads, fine, coarse, F.g, C.g);
+}
+
 void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, long long n) {
   launch(c, kSlotVector, k_axmy<double>, grid_for(n), kThreads, out, x, a, y, n);
 }

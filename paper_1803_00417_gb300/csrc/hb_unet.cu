@@ -497,14 +497,32 @@ int apply_guess(hbf_ctx* c, const double* b, double* p, int* used) {
   const double n0 = reduce_max_abs(c, c->nres0, nn, &st);
   if (st) return st;
   if (!(n0 > 0.0) || !std::isfinite(n0)) return HBF_OK;
-  const int e0 = c->g.n[0] + 1, e1 = c->g.n[1] + 1, e2 = c->dim == 3 ? c->g.n[2] + 1 : 1;
+  // the network sees the warm-start residual on the nodes of level L
+  // (full weighting down from the finest level) and its output is
+  // interpolated back up, level by level
+  const int L = c->guess_level;
+  const double* src = c->nres0;
+  for (int l = 0; l < L; ++l) {
+    nodal_restrict(c, l, src, c->lv[l + 1].nb);
+    src = c->lv[l + 1].nb;
+  }
+  const Geom& gL = c->lv[L].g;
+  const int e0 = gL.n[0] + 1, e1 = gL.n[1] + 1, e2 = c->dim == 3 ? gL.n[2] + 1 : 1;
   cudaStream_t saved = N->stream;
   N->stream = c->stream;
-  k_nodes_to_net<<<grid(N->P[0]), kThreads, 0, c->stream>>>(c->nres0, 1.0 / n0, e0, e1, e2, N->box[0], c->net_x);
+  k_nodes_to_net<<<grid(N->P[0]), kThreads, 0, c->stream>>>(src, 1.0 / n0, e0, e1, e2, N->box[0], c->net_x);
   forward(N, c->net_x);
   N->stream = saved;
-  k_net_to_nodes<<<grid(nn), kThreads, 0, c->stream>>>(N->y, e0, e1, e2, N->box[0], c->ntry);
+  double* outL = L == 0 ? c->ntry : c->lv[L].nx;
+  k_net_to_nodes<<<grid((long long)gL.nnode), kThreads, 0, c->stream>>>(N->y, e0, e1, e2, N->box[0], outL);
   c->nlaunch += N->nlaunch_fwd + 2;
+  for (int l = L - 1; l >= 0; --l) {
+    double* fine = l == 0 ? c->ntry : c->lv[l].nx;
+    if ((st = cuda_check(c, cudaMemsetAsync(fine, 0, (size_t)c->lv[l].g.nnode * sizeof(double), c->stream),
+                         "learned guess")))
+      return st;
+    nodal_prolong_add(c, l, fine, c->lv[l + 1].nx);
+  }
   if ((st = cuda_check(c, cudaGetLastError(), "learned guess"))) return st;
   // w = -L delta, alpha = -(r0, w)/(w, w), candidate residual r0 + alpha w
   double* w = c->lv[0].nr;
@@ -732,12 +750,17 @@ int hbf_unet_adam(hbf_unet* N, double lr, double b1, double b2, double eps) {
   return check(N, "unet adam");
 }
 
-int hbf_set_guess_model(hbf_ctx* c, hbf_unet* N) {
+int hbf_set_guess_model(hbf_ctx* c, hbf_unet* N) { return hbf_set_guess_model_level(c, N, 0); }
+
+int hbf_set_guess_model_level(hbf_ctx* c, hbf_unet* N, int level) {
   if (!c) return HBF_ERR_ARG;
   hb::release_guess(c);
   if (!N) return HBF_OK;
   if (N->d != c->dim) return hb::fail(c, HBF_ERR_ARG, "guess model dimension differs from the grid's");
-  const int e[3] = {c->g.n[0] + 1, c->g.n[1] + 1, c->dim == 3 ? c->g.n[2] + 1 : 1};
+  if (level < 0 || level >= (int)c->lv.size())
+    return hb::fail(c, HBF_ERR_ARG, "guess level outside the multigrid hierarchy");
+  const hb::Geom& gL = c->lv[level].g;
+  const int e[3] = {gL.n[0] + 1, gL.n[1] + 1, c->dim == 3 ? gL.n[2] + 1 : 1};
   const int b[3] = {N->box[0].X, N->box[0].Y, N->box[0].Z};
   for (int a = 0; a < c->dim; ++a)
     if (b[a] < e[a]) return hb::fail(c, HBF_ERR_ARG, "guess model box is smaller than the node grid");
@@ -749,6 +772,7 @@ int hbf_set_guess_model(hbf_ctx* c, hbf_unet* N) {
     return hb::fail(c, HBF_ERR_OOM, "guess buffers");
   }
   c->guess = N;
+  c->guess_level = level;
   return HBF_OK;
 }
 

@@ -88,6 +88,7 @@ SIGNATURES = {
     "hbf_unet_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double]),
     "hbf_set_guess_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_set_guess_model_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "hbf_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hbf_destroy": (None, [ctypes.c_void_p]),
@@ -401,9 +402,10 @@ class UNet:
         self._check(self.lib.hbf_unet_adam(self.net, lr, beta1, beta2, eps))
 
 
-def set_guess_model(sim, net):
-    """Use ``net`` (a UNet, or None) for the nodal projection's initial guess."""
-    st = sim.lib.hbf_set_guess_model(sim.ctx, net.net if net is not None else None)
+def set_guess_model(sim, net, level=0):
+    """Use ``net`` (a UNet, or None) for the nodal projection's initial guess,
+    evaluated on the nodes of multigrid level ``level`` (0 = finest)."""
+    st = sim.lib.hbf_set_guess_model_level(sim.ctx, net.net if net is not None else None, int(level))
     sim._check(st)
 
 

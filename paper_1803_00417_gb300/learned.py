@@ -28,6 +28,31 @@ def nodes_to_box(a_nodes, n, box):
     return out.ravel()
 
 
+def coarse_cells(n, level):
+    """Cells per axis of multigrid level ``level`` (halved per level)."""
+    return tuple(v >> level for v in n)
+
+
+def restrict_nodes(a_nodes, n):
+    """Nodal full weighting onto the next coarser level (as the multigrid's
+    nodal restriction): along x, then y, then z, coarse node I takes
+    1/2 of fine node 2I and 1/4 of each of 2I - 1, 2I + 1, with the fine nodes
+    beyond a wall mirrored back inside.  Flat x-fastest arrays; returns the
+    coarse array and its cell counts."""
+    d = len(n)
+    shp = tuple(v + 1 for v in n)
+    arr = np.asarray(a_nodes, dtype=np.float64).reshape(shp[::-1])
+    for a in range(d):
+        ax = d - 1 - a  # numpy axis of spatial axis a (x fastest = last)
+        m = n[a]
+        lo = np.abs(np.arange(0, m + 1, 2) - 1)
+        hi = np.arange(0, m + 1, 2) + 1
+        hi = np.where(hi > m, 2 * m - hi, hi)
+        cen = np.take(arr, np.arange(0, m + 1, 2), axis=ax)
+        arr = 0.5 * cen + 0.25 * (np.take(arr, lo, axis=ax) + np.take(arr, hi, axis=ax))
+    return arr.ravel(), coarse_cells(n, 1)
+
+
 def box_mask(n, box):
     return nodes_to_box(np.ones(int(np.prod([v + 1 for v in n]))), n, box)
 
@@ -38,12 +63,14 @@ def sample_params(rng, bi_max=20.0):
     return dict(Re=10.0 ** rng.uniform(0, 3), nexp=rng.uniform(0.5, 1.5), Bi=rng.uniform(0, bi_max), Pa=1e4)
 
 
-def generate_pairs(n, seeds, steps, skip=1, precision=0, stream=None):
+def generate_pairs(n, seeds, steps, skip=1, precision=0, stream=None, level=0):
     """Run cavities from rest with seeded random rheology and collect the
-    nodal-solve pairs of every ``skip``-th step after the first."""
+    nodal-solve pairs of every ``skip``-th step after the first, restricted to
+    multigrid level ``level`` (the level the network will run on)."""
     import torch
 
-    box = net_box(n)
+    nL = coarse_cells(n, level)
+    box = net_box(nL)
     xs, ys, info = [], [], []
     for seed in seeds:
         rng = np.random.default_rng(seed)
@@ -62,10 +89,14 @@ def generate_pairs(n, seeds, steps, skip=1, precision=0, stream=None):
                 p_new = sim.get_field("P")
                 nrm = float(np.max(np.abs(r0)))
                 dphi = p_new - p_old
-                dn = float(np.max(np.abs(dphi)))
+                rc, dc, nc = r0, dphi, tuple(n)
+                for _ in range(level):
+                    rc, _n = restrict_nodes(rc, nc)
+                    dc, nc = restrict_nodes(dc, nc)
+                dn = float(np.max(np.abs(dc)))
                 if nrm > 0 and dn > 0:
-                    xs.append(nodes_to_box(r0 / nrm, n, box))
-                    ys.append(nodes_to_box(dphi / dn, n, box))
+                    xs.append(nodes_to_box(rc / nrm, nc, box))
+                    ys.append(nodes_to_box(dc / dn, nc, box))
                     info.append(dict(seed=seed, step=s, cycles=st["nodal"]["cycles"]))
         sim.close()
     return np.array(xs), np.array(ys), info

@@ -66,3 +66,52 @@ def test_learned_guess_gain_2d():
           f"(guess accepted at {used}/{total} steps)")
     assert used >= total // 2
     assert with_ <= without + max(2, without // 20)
+
+
+def test_learned_guess_on_a_coarse_level_2d():
+    """The network on the nodes of multigrid level 1 (trained on pairs
+    restricted the same way): the guess is restricted in, interpolated out,
+    and the solves still reach the same tolerance and agree with the plain
+    method; a level outside the hierarchy is rejected."""
+    from paper_1803_00417_gb300.hbflow import MIXED, HBFlow, HBFlowError, UNet, set_guess_model
+    from paper_1803_00417_gb300.inputs import cavity
+    from paper_1803_00417_gb300.learned import (box_mask, coarse_cells, generate_pairs, net_box, sample_params,
+                                                train)
+
+    n = (48, 48)
+    nc = coarse_cells(n, 1)
+    xs, ys, _ = generate_pairs(n, seeds=range(6), steps=12, precision=MIXED, level=1)
+    box = net_box(nc)
+    assert xs.shape[1] == int(np.prod(box))
+    net = UNet(box, train=True, seed=0)
+    hist = train(net, xs, ys, box_mask(nc, box), epochs=12, lr=1e-3, batch=4)
+    assert hist[-1] < 0.5 * hist[0]
+    model = UNet(box, train=False)
+    model.set_params(net.get_params())
+    without = with_ = used = total = 0
+    cfg = cavity(n, **sample_params(np.random.default_rng(1000)))
+    a = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=MIXED)
+    b = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=MIXED)
+    for s in (a, b):
+        s.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+        s.set_field("U", np.zeros(2 * 48 * 48))
+        s.set_field("P", np.zeros(49 * 49))
+    with pytest.raises(HBFlowError):
+        set_guess_model(b, model, 40)
+    set_guess_model(b, model, 1)
+    for k in range(12):
+        b.set_field("U", a.get_field("U").copy())
+        b.set_field("P", a.get_field("P").copy())
+        sa, sb = a.step(cfg["dt"]), b.step(cfg["dt"])
+        assert sa["nodal"]["converged"] and sb["nodal"]["converged"]
+        ua, ub = a.get_field("U"), b.get_field("U")
+        assert np.linalg.norm(ua - ub) <= 1e-8 * max(np.linalg.norm(ua), 1e-30)
+        if k >= 1:
+            without += sa["nodal"]["cycles"]
+            with_ += sb["nodal"]["cycles"]
+            used += int(sb["nodal"]["guess"])
+            total += 1
+    a.close()
+    b.close()
+    print(f"level-1 guess: nodal V-cycles without / with: {without} / {with_} (accepted {used}/{total})")
+    assert with_ <= without + max(2, without // 20)
