@@ -305,6 +305,12 @@ int hbf_batch_step(hbf_batch* b, hbf_step_stats* stats);
  * (152 x blocks_per_sm blocks at most per launch). */
 int hbf_batch_set_tiling(hbf_batch* b, int tile, int blocks_per_sm);
 int hbf_batch_get_tiling(const hbf_batch* b, int* tile, int* blocks_per_sm, int64_t* tiles_level0);
+/* Multigrid levels on which every cavity has at most max_cells cells (and
+ * all coarser levels) run as one launch per V-cycle, one thread block per
+ * cavity, with block barriers between colour sweeps; the arithmetic and its
+ * order are those of the level-by-level launches.  0 disables it; default
+ * 4096. */
+int hbf_batch_set_tail(hbf_batch* b, int max_cells);
 /* Time a representative launch sequence (explicit stages and one viscous
  * V-cycle of every cavity; no cavity state changes) for each tiling
  * candidate, reps times each, and keep the fastest.  Outputs may be NULL. */

@@ -254,6 +254,7 @@ struct BottomArg {
   T* b;
   Geom g;
   int kind;   // 0 viscous, 1 MAC, 2 nodal
+  int level;  // the cavity's coarsest level
 };
 
 // weighted mean of v over the unknowns of a singular problem, one thread,
@@ -266,12 +267,9 @@ __device__ inline double bottom_mean(const double* v, int n, int kind, const Geo
   return s * (1.0 / wsum);
 }
 
+// exact solve of one cavity's coarsest level by the whole block
 template <int D, typename T>
-__global__ void __launch_bounds__(128) k_batch_bottom(const BottomArg<T>* __restrict__ args, int ncav,
-                                                      const int* __restrict__ mask) {
-  const int c = blockIdx.x;
-  if (c >= ncav || (mask && !mask[c])) return;
-  const BottomArg<T> a = args[c];
+__device__ void bottom_block(const BottomArg<T>& a) {
   __shared__ double sb[kDenseMax + 1];
   __shared__ double sx[kDenseMax + 1];
   __shared__ double mean;
@@ -296,6 +294,19 @@ __global__ void __launch_bounds__(128) k_batch_bottom(const BottomArg<T>* __rest
     __syncthreads();
   }
   for (int i = threadIdx.x; i < a.n; i += blockDim.x) a.x[i] = (T)sx[i];
+  __syncthreads();
+}
+
+// the bottom solves of the cavities whose coarsest level is below `below`
+// (the others are solved inside the fused tail of the V-cycle)
+template <int D, typename T>
+__global__ void __launch_bounds__(128) k_batch_bottom(const BottomArg<T>* __restrict__ args, int ncav,
+                                                      const int* __restrict__ mask, int below) {
+  const int c = blockIdx.x;
+  if (c >= ncav || (mask && !mask[c])) return;
+  const BottomArg<T>& a = args[c];
+  if (a.level >= below) return;
+  bottom_block<D, T>(a);
 }
 
 // dense bottom operator of the viscous problem (it changes with eta and dt
@@ -539,8 +550,17 @@ struct LvView<float> {
 // ---------------------------------------------------------------------------
 enum Kind { kVisc = 0, kMac = 1, kNodal = 2 };
 
+// the argument tables of an instance, by level, for the fused tail kernel
+struct TailTabs {
+  const void* lv[kMaxLev];
+  const void* re[kMaxLev];
+  const void* pr[kMaxLev];
+  const void* bot;
+};
+
 struct Inst {
   int kind = 0;
+  TailTabs tail = {};
   void* lv[kMaxLev] = {};  // smoother / residual arguments of level l
   void* re[kMaxLev] = {};  // restriction l -> l+1
   void* pr[kMaxLev] = {};  // prolongation l+1 -> l
@@ -632,8 +652,108 @@ static void build_inst(hbf_batch* B, Inst& I, int kind, bool hom0, T* (*x0)(hbf_
     a.b = Bv(c, l);
     a.g = g;
     a.kind = kind;
+    a.level = l;
     return a;
   });
+  for (int l = 0; l < kMaxLev; ++l) {
+    I.tail.lv[l] = I.lv[l];
+    I.tail.re[l] = I.re[l];
+    I.tail.pr[l] = I.pr[l];
+  }
+  I.tail.bot = I.bot;
+}
+
+// ---------------------------------------------------------------------------
+// fused tail of the V-cycle: one block per cavity runs every level from lf
+// down to the cavity's coarsest and back, with block barriers between the
+// colour sweeps instead of kernel boundaries.  Same operations in the same
+// order as the level-by-level launches; the small levels of all cavities then
+// cost one launch per V-cycle instead of about twenty per level.
+// ---------------------------------------------------------------------------
+template <int D, typename T, int C>
+__device__ __forceinline__ void tail_visc_colours(const ViscArg<T>& a) {
+  const int nt = rb_count<D>(a.g);
+  for (int col = 0; col < 2; ++col) {
+    for (int t = threadIdx.x; t < nt; t += blockDim.x)
+      k_visc_smooth_c_at<D, T, C>(a.x, a.b, a.ef[0], a.ef[1], a.ef[2], a.g, col, a.beta, a.hom, t);
+    __syncthreads();
+  }
+}
+
+template <int D, typename T, int KIND>
+__device__ __forceinline__ void tail_smooth(const TailTabs& tb, int l, int c) {
+  if (KIND == kVisc) {
+    const ViscArg<T>& a = ((const ViscArg<T>*)tb.lv[l])[c];
+    tail_visc_colours<D, T, 0>(a);
+    tail_visc_colours<D, T, 1>(a);
+    if (D == 3) tail_visc_colours<D, T, (D == 3 ? 2 : 0)>(a);
+  } else if (KIND == kMac) {
+    const PoisArg<T>& a = ((const PoisArg<T>*)tb.lv[l])[c];
+    const int nt = rb_count<D>(a.g);
+    for (int col = 0; col < 2; ++col) {
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) k_cell_smooth_at<D, T>(a.x, a.b, a.g, col, t);
+      __syncthreads();
+    }
+  } else {
+    const PoisArg<T>& a = ((const PoisArg<T>*)tb.lv[l])[c];
+    for (int col = 0; col < (1 << D); ++col) {
+      const int nt = mc_count<D>(a.g, col);
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) k_nodal_smooth_at<D, T>(a.x, a.b, a.g, col, t);
+      __syncthreads();
+    }
+  }
+}
+
+template <int D, typename T, int KIND>
+__global__ void __launch_bounds__(256) k_batch_vcycle_tail(TailTabs tb, int lf, int ncav,
+                                                           const int* __restrict__ mask, int nu1, int nu2) {
+  const int c = blockIdx.x;
+  if (c >= ncav || (mask && !mask[c])) return;
+  const BottomArg<T>& bot = ((const BottomArg<T>*)tb.bot)[c];
+  const int L = bot.level;
+  if (L < lf) return;
+  for (int l = lf; l < L; ++l) {
+    for (int s = 0; s < nu1; ++s) tail_smooth<D, T, KIND>(tb, l, c);
+    if (KIND == kVisc) {
+      const ViscArg<T>& a = ((const ViscArg<T>*)tb.lv[l])[c];
+      for (int t = threadIdx.x; t < a.g.ncell; t += blockDim.x)
+        k_visc_op_at<D, T>(a.x, a.b, a.out, a.ef[0], a.ef[1], a.ef[2], a.g, a.beta, a.hom, t);
+    } else {
+      const PoisArg<T>& a = ((const PoisArg<T>*)tb.lv[l])[c];
+      if (KIND == kMac)
+        for (int t = threadIdx.x; t < a.g.ncell; t += blockDim.x) k_cell_resid_at<D, T>(a.x, a.b, a.r, a.g, t);
+      else
+        for (int t = threadIdx.x; t < a.g.nnode; t += blockDim.x) k_nodal_resid_at<D, T>(a.x, a.b, a.r, a.g, t);
+    }
+    __syncthreads();
+    const XferArg<T>& r = ((const XferArg<T>*)tb.re[l])[c];
+    if (KIND == kNodal) {
+      for (int t = threadIdx.x; t < r.gc.nnode; t += blockDim.x) {
+        k_restrict_nodes_at<D, T>(r.src, r.dst, r.gf, r.gc, t);
+        r.zero[t] = T(0);
+      }
+    } else {
+      const int n = r.ncomp * r.gc.ncell;
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        k_restrict_cells_at<D, T>(r.src, r.dst, r.gf, r.gc, r.ncomp, t);
+        r.zero[t] = T(0);
+      }
+    }
+    __syncthreads();
+  }
+  bottom_block<D, T>(bot);
+  for (int l = L - 1; l >= lf; --l) {
+    const XferArg<T>& q = ((const XferArg<T>*)tb.pr[l])[c];
+    if (KIND == kNodal) {
+      for (int t = threadIdx.x; t < q.gf.nnode; t += blockDim.x) k_prolong_nodes_add_at<D, T>(q.dst, q.src, q.gf, q.gc, t);
+    } else {
+      const int n = q.ncomp * q.gf.ncell;
+      for (int t = threadIdx.x; t < n; t += blockDim.x)
+        k_prolong_cells_add_at<D, T>(q.dst, q.src, q.gf, q.gc, q.ncomp, T(q.sign), t);
+    }
+    __syncthreads();
+    for (int s = 0; s < nu2; ++s) tail_smooth<D, T, KIND>(tb, l, c);
+  }
 }
 
 template <int D, typename T>
@@ -656,8 +776,9 @@ static void smooth(hbf_batch* B, Inst& I, int l, const int* mask) {
 template <int D, typename T>
 static void vcycle(hbf_batch* B, Inst& I, const int* mask) {
   const SolverCfg& cfg = B->cav[0]->cfg;
-  int top = 0;  // levels 0 .. top-1 descend
-  while (top < B->maxlev - 1 && B->A[top][kCells].n > 0) ++top;
+  const int lf = B->tail_level;  // levels >= lf run in the fused tail kernel
+  int top = 0;  // levels 0 .. top-1 descend level by level
+  while (top < B->maxlev - 1 && top < lf && B->A[top][kCells].n > 0) ++top;
   for (int l = 0; l < top; ++l) {
     for (int s = 0; s < cfg.nu1; ++s) smooth<D, T>(B, I, l, mask);
     if (I.kind == kVisc) {
@@ -671,8 +792,18 @@ static void vcycle(hbf_batch* B, Inst& I, const int* mask) {
       run<OpRestrictNodes<D, T>>(B, I.re[l], B->H[l + 1][kNodes], mask);
     }
   }
-  k_batch_bottom<D, T><<<B->ncav, 128, 0, B->stream>>>((const BottomArg<T>*)I.bot, B->ncav, mask);
+  k_batch_bottom<D, T><<<B->ncav, 128, 0, B->stream>>>((const BottomArg<T>*)I.bot, B->ncav, mask, lf);
   ++B->nlaunch;
+  if (lf < B->maxlev) {
+    if (I.kind == kVisc)
+      k_batch_vcycle_tail<D, T, kVisc><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1, cfg.nu2);
+    else if (I.kind == kMac)
+      k_batch_vcycle_tail<D, T, kMac><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1, cfg.nu2);
+    else
+      k_batch_vcycle_tail<D, T, kNodal><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1,
+                                                                         cfg.nu2);
+    ++B->nlaunch;
+  }
   for (int l = top - 1; l >= 0; --l) {
     if (I.kind == kVisc)
       run<OpProlongCells<D, T>>(B, I.pr[l], B->A[l][kCellsD], mask);
@@ -1322,6 +1453,17 @@ int prepare(hbf_batch* B) {
     ensure_dense(x, 1, 0.0);
     ensure_dense(x, 2, 0.0);
   }
+  B->tail_level = B->maxlev;
+  if (B->tail_cells > 0)
+    for (int l = 0; l < B->maxlev; ++l) {
+      bool small = true;
+      for (int c = 0; c < B->ncav && small; ++c)
+        if (l < B->nlev[c]) small = B->cav[c]->lv[l].g.ncell <= B->tail_cells;
+      if (small) {
+        B->tail_level = l;
+        break;
+      }
+    }
   int st = B->dim == 2 ? build_lists<2>(B) : build_lists<3>(B);
   if (st) return st;
   void* part = nullptr;
@@ -1464,6 +1606,15 @@ int hbf_batch_set_tiling(hbf_batch* B, int tile, int blocks_per_sm) {
     release_prepared(B);
     B->tile = tile;
     B->blocks_per_sm = blocks_per_sm;
+  }
+  return HBF_OK;
+}
+
+int hbf_batch_set_tail(hbf_batch* B, int max_cells) {
+  if (!B || max_cells < 0) return HBF_ERR_ARG;
+  if (max_cells != B->tail_cells) {
+    release_prepared(B);
+    B->tail_cells = max_cells;
   }
   return HBF_OK;
 }

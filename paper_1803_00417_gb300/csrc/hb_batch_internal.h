@@ -50,6 +50,8 @@ struct hbf_batch {
   int maxlev = 0;
   int tile = 2048;          // elements per tile
   int blocks_per_sm = 8;    // persistent grid = 152 * blocks_per_sm blocks at most
+  int tail_cells = 4096;    // levels whose every cavity has at most this many cells run fused
+  int tail_level = 0;       // first such level (maxlev: none), set by prepare
   // H[l]: cavities that have level l; A[l]: cavities for which level l is
   // not the coarsest (they smooth, restrict and prolong there)
   hb::batch::List H[hb::batch::kMaxLev][hb::batch::kSpaces];

@@ -100,6 +100,7 @@ SIGNATURES = {
     "hbf_batch_set_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "hbf_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hbf_batch_set_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hbf_batch_set_tail": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_batch_get_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]),
     "hbf_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -477,6 +478,10 @@ class Batch:
 
     def set_tiling(self, tile, blocks_per_sm):
         self._check(self.lib.hbf_batch_set_tiling(self.b, int(tile), int(blocks_per_sm)))
+
+    def set_tail(self, max_cells):
+        """Fuse the levels with at most ``max_cells`` cells per cavity (0: off)."""
+        self._check(self.lib.hbf_batch_set_tail(self.b, int(max_cells)))
 
     def tiling(self):
         t, b, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
