@@ -172,6 +172,9 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
+SMOOTHER_DRAM_BYTES_PER_CELL = (201.2e6 + 18.8e6) / 192 ** 3
+
+
 def visc_smoother_bytes(d, ncell, elem):
     """Algorithmic bytes of one finest-level launch of the viscous smoother
     (one component, one colour): reads the other colour of u_c (ncell/2), the
@@ -465,8 +468,13 @@ def run_ours(args):
         per_launch_s = sm_ms / sm_n / 1e3
         algo = visc_smoother_bytes(d, ncell, elem)
         ach = algo / per_launch_s / 1e9
+        # DRAM bytes per cell of this kernel from one full ncu capture at 192^3
+        # (profiles/k_visc_smooth_cavity192.md), scaled to this grid; valid
+        # for the FP32 kernel version recorded there
+        traffic = SMOOTHER_DRAM_BYTES_PER_CELL * ncell if prec == MIXED else None
         roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                    "traffic": None, "kernel": "k_visc_smooth (finest level)",
+                    "traffic": traffic, "traffic_source": "ncu at 192^3, 31.1 B/cell, scaled by cells"
+                    if traffic else None, "kernel": "k_visc_smooth (finest level)",
                     "launches": sm_n, "avg_launch_us": per_launch_s * 1e6,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
