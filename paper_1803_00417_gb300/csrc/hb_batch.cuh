@@ -7,6 +7,8 @@
 namespace hb {
 namespace batch {
 
+constexpr int kMaxLev = 16;  // multigrid levels a batch or a fused tail handles
+
 struct Tile {
   int cav;
   int begin;

@@ -9,7 +9,6 @@
 namespace hb {
 namespace batch {
 
-constexpr int kMaxLev = 16;
 
 // a work list: tiles over one element space, cavity-major, with each
 // cavity's first tile index (first[ncav] = total)

@@ -9,11 +9,13 @@
 // the right-hand side and pin the mean of the iterate after each cycle and the
 // bottom solve.
 #include <cmath>
+#include <cstring>
 #include <cstdio>
 #include <type_traits>
 
 #include "hb_internal.h"
 #include "hb_mg_kernels.cuh"
+#include "hb_vcycle_tail.cuh"
 
 namespace hb {
 
@@ -410,6 +412,9 @@ struct Problem {
   virtual int sub_mean(int l, double* v) { (void)l; (void)v; return 0; }
   virtual int kind() const = 0;         // 0 viscous, 1 MAC, 2 nodal
   virtual double dense_beta() const { return 0.0; }
+  // levels l..coarsest in one fused launch (hb_vcycle_tail.cuh); false when
+  // l is not the context's tail level
+  virtual bool tail(int l) { (void)l; return false; }
 };
 
 // dense inverse of the bottom operator of problem kind `kind` at level l
@@ -449,6 +454,114 @@ static void bottom_fp64(Problem<T>& P, int l, double* xd, double* bd, void (*run
     launch(c, kSlotTransfer, k_convert<T, double>, grid_for(n), kThreads, P.x(l), (const double*)xd, n);
 }
 
+// ---------------------------------------------------------------------------
+// fused tail of the V-cycle (k_vcycle_tail): from the first level with at
+// most kTailCells cells down to the exact bottom solve and back in one launch
+// of one block, instead of about twenty launches per level
+// ---------------------------------------------------------------------------
+constexpr int kTailCells = 512;
+
+static int tail_level(hbf_ctx* c) {
+  if (c->tail_lf >= 0) return c->tail_lf;
+  const int nl = (int)c->lv.size();
+  const Geom& gb = c->lv[nl - 1].g;
+  const bool dense = (long long)c->dim * gb.ncell <= kDenseMax && gb.nnode <= kDenseMax;
+  int lf = nl;
+  if (dense)
+    for (int l = 1; l < nl; ++l)
+      if (c->lv[l].g.ncell <= kTailCells) {
+        lf = l;
+        break;
+      }
+  c->tail_lf = lf;
+  return lf;
+}
+
+template <typename T, typename A>
+struct TailBlock {
+  A lv[batch::kMaxLev];
+  batch::XferArg<T> re[batch::kMaxLev];
+  batch::XferArg<T> pr[batch::kMaxLev];
+  batch::BottomArg<T> bot;
+};
+
+template <int D, typename T, int KIND>
+static bool run_tail(hbf_ctx* c, int l, double beta) {
+  using namespace batch;
+  const int lf = tail_level(c);
+  const int nl = (int)c->lv.size(), L = nl - 1;
+  if (l != lf || lf >= nl || nl > kMaxLev) return false;
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  using A = typename std::conditional<KIND == kVisc, ViscArg<T>, PoisArg<T>>::type;
+  using TB = TailBlock<T, A>;
+  std::vector<unsigned char>& host = c->tail_host[KIND][pi];
+  void*& dev = c->tail_dev[KIND][pi];
+  const bool fresh = host.empty();
+  if (fresh) {
+    void* d = nullptr;
+    if (cudaMalloc(&d, sizeof(TB)) != cudaSuccess) return false;  // fall back to level-by-level
+    c->allocs.push_back(d);
+    dev = d;
+    host.assign(sizeof(TB), 0);
+  }
+  if (fresh || (KIND == kVisc && c->tail_beta[pi] != beta)) {
+    TB* h = (TB*)host.data();
+    auto X = [&](Level& Lv) -> T* { return KIND == kVisc ? View<T>::vx(Lv) : KIND == kMac ? View<T>::cx(Lv) : View<T>::nx(Lv); };
+    auto Bv = [&](Level& Lv) -> T* { return KIND == kVisc ? View<T>::vb(Lv) : KIND == kMac ? View<T>::cb(Lv) : View<T>::nb(Lv); };
+    auto R = [&](Level& Lv) -> T* { return KIND == kVisc ? View<T>::vr(Lv) : KIND == kMac ? View<T>::cr(Lv) : View<T>::nr(Lv); };
+    const int ncomp = KIND == kVisc ? D : 1, sign = KIND == kVisc ? -1 : 1;
+    for (int q = lf; q <= L; ++q) {
+      Level& Lv = c->lv[q];
+      A a;
+      std::memset(&a, 0, sizeof a);
+      a.x = X(Lv);
+      a.b = Bv(Lv);
+      a.g = Lv.g;
+      if constexpr (KIND == kVisc) {
+        a.out = R(Lv);
+        for (int d = 0; d < D; ++d) a.ef[d] = View<T>::ef(Lv, d);
+        a.beta = (T)beta;
+        a.hom = 1;
+      } else {
+        a.r = R(Lv);
+      }
+      h->lv[q] = a;
+      if (q < L) {
+        Level& Cv = c->lv[q + 1];
+        h->re[q] = XferArg<T>{R(Lv), Bv(Cv), X(Cv), Lv.g, Cv.g, ncomp, sign};
+        h->pr[q] = XferArg<T>{X(Cv), X(Lv), nullptr, Lv.g, Cv.g, ncomp, sign};
+      }
+    }
+    BottomArg<T> bt;
+    std::memset(&bt, 0, sizeof bt);
+    const Geom& gb = c->lv[L].g;
+    bt.n = KIND == kVisc ? D * gb.ncell : KIND == kMac ? gb.ncell : gb.nnode;
+    bt.m = KIND == kVisc ? bt.n : bt.n + 1;
+    bt.Minv = c->dense[KIND].Minv;
+    bt.x = X(c->lv[L]);
+    bt.b = Bv(c->lv[L]);
+    bt.g = gb;
+    bt.kind = KIND;
+    bt.level = L;
+    h->bot = bt;
+    // pageable source: the call returns once the bytes are staged
+    if (cudaMemcpyAsync(dev, h, sizeof(TB), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return false;
+    if (KIND == kVisc) c->tail_beta[pi] = beta;
+  }
+  ensure_dense(c, KIND, beta);  // the viscous inverse changes with eta and dt
+  TB* d = (TB*)dev;
+  TailTabs tb;
+  for (int q = 0; q < kMaxLev; ++q) {
+    tb.lv[q] = &d->lv[q];
+    tb.re[q] = &d->re[q];
+    tb.pr[q] = &d->pr[q];
+  }
+  tb.bot = &d->bot;
+  launch(c, kSlotCoarse, k_vcycle_tail<D, T, KIND>, 1, kThreads, tb, lf, 1, (const int*)nullptr, c->cfg.nu1,
+         c->cfg.nu2);
+  return true;
+}
+
 template <int D, typename T>
 struct ViscProblem : Problem<T> {
   using Problem<T>::c;
@@ -457,6 +570,7 @@ struct ViscProblem : Problem<T> {
   ViscProblem(hbf_ctx* ctx, T* x_in, double bt, bool h0) : Problem<T>(ctx, false, h0), x0(x_in), beta(bt) {}
   int kind() const override { return 0; }
   double dense_beta() const override { return beta; }
+  bool tail(int l) override { return run_tail<D, T, batch::kVisc>(c, l, beta); }
   T* x(int l) override { return l == 0 ? x0 : View<T>::vx(c->lv[l]); }
   T* b(int l) override { return View<T>::vb(c->lv[l]); }
   T* r(int l) override { return View<T>::vr(c->lv[l]); }
@@ -518,6 +632,7 @@ struct MacProblem : Problem<T> {
   T* x0;
   MacProblem(hbf_ctx* ctx, T* x_in) : Problem<T>(ctx, true, true), x0(x_in) {}
   int kind() const override { return 1; }
+  bool tail(int l) override { return run_tail<D, T, batch::kMac>(c, l, 0.0); }
   T* x(int l) override { return l == 0 ? x0 : View<T>::cx(c->lv[l]); }
   T* b(int l) override { return View<T>::cb(c->lv[l]); }
   T* r(int l) override { return View<T>::cr(c->lv[l]); }
@@ -569,6 +684,7 @@ struct NodalProblem : Problem<T> {
   T* x0;
   NodalProblem(hbf_ctx* ctx, T* x_in) : Problem<T>(ctx, true, true), x0(x_in) {}
   int kind() const override { return 2; }
+  bool tail(int l) override { return run_tail<D, T, batch::kNodal>(c, l, 0.0); }
   T* x(int l) override { return l == 0 ? x0 : View<T>::nx(c->lv[l]); }
   T* b(int l) override { return View<T>::nb(c->lv[l]); }
   T* r(int l) override { return View<T>::nr(c->lv[l]); }
@@ -619,6 +735,7 @@ struct NodalProblem : Problem<T> {
 
 template <typename T>
 static void vcycle(Problem<T>& P, int l, const SolverCfg& cfg) {
+  if (P.tail(l)) return;
   if (l == P.nlev - 1) {
     P.bottom(l);
     return;
