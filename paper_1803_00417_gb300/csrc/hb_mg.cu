@@ -836,7 +836,7 @@ static void build_eta_levels(hbf_ctx* c) {
 // around an FP32 BiCGStab on A e = r, itself preconditioned by FP32 V-cycles,
 // run until its residual drops by kInnerRtol (or kInnerMax iterations).
 // cycles = total inner iterations.
-constexpr double kInnerRtol = 1e-4;
+constexpr double kInnerRtol = 1e-3;
 constexpr int kInnerMax = 40;
 
 template <int D>
