@@ -31,6 +31,25 @@ METRIC = "cell-steps/s at 256³ 3D HB cavity, mixed+learned vs plain FP64, same 
 UNIT = "cell-steps/s"
 
 
+# ---------------------------------------------------------------------------
+# replicas: the slowest rank's time and the whole-job rate
+# ---------------------------------------------------------------------------
+def max_over_ranks(x, dist, device):
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,16 +402,13 @@ def run_ours(args):
         nl = sim_.launch_count() - n0
         prof_ = {k: sim_.profile_read(k) for k in sim_.PROFILE_SLOTS}
         sim_.profile_enable(0)
-        if dist is not None:
-            t = torch.tensor([ms_], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_ = float(t.item())
+        ms_ = max_over_ranks(ms_, dist, "cuda")
         timed.guess_used = used
         return ms_, cyc, conv, nl, prof_, clk_
 
     clocks = Clocks(local)
     ms, cycles, converged, launches, prof, clk = timed(sim, 2 if args.breakdown else 1, clocks, args.profiler_range)
-    value = world * ncell * args.steps / (ms / 1e3)
+    value = job_rate(world, ncell * args.steps, ms / 1e3)
     if learned is not None:
         learned["guess_accepted_steps"] = f"{timed.guess_used}/{args.steps}"
 
@@ -415,11 +431,8 @@ def run_ours(args):
             sim.get_field("P", hp)
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([secs], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            secs = float(t.item())
-        e2e = {"value": world * ncell * args.e2e_steps / secs, "unit": UNIT,
+        secs = max_over_ranks(secs, dist, "cuda")
+        e2e = {"value": job_rate(world, ncell * args.e2e_steps, secs), "unit": UNIT,
                "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
 
     mixed_only = None
