@@ -237,21 +237,6 @@ __host__ __device__ inline int rb_count(const Geom& g) {
   return ((g.n[0] + 1) / 2) * g.n[1] * (D == 3 ? g.n[2] : 1);
 }
 
-template <int D, typename T>
-__global__ void k_visc_smooth(T* __restrict__ u, const T* __restrict__ b, const T* ef0, const T* ef1,
-                              const T* ef2, const __grid_constant__ Geom g, int c, int col, T beta, int hom) {
-  const T* ef[3] = {ef0, ef1, ef2};
-  const Strides S = make_strides(g);
-  int nt = rb_count<D>(g);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-    int p[3];
-    if (!rb_cell<D>(g, t, col, p)) continue;
-    T v = interior<D>(g, p) ? visc_gs_interior<D, T>(u, b, ef, g, S, c, p, beta)
-                            : visc_gs_point<D, T>(u, b, ef, g, c, p, beta, hom != 0);
-    u[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
-  }
-}
-
 // Grid-stride over the cells of one colour; the component is a template
 // parameter so every a == C decision folds at compile time.  (A grid-stride
 // launch of about 24 blocks per SM measured faster than one thread per cell.)
