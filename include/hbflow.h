@@ -233,6 +233,15 @@ int64_t hbf_unet_param_count(const hbf_unet* net);
 int hbf_unet_get_params(hbf_unet* net, float* dst);
 int hbf_unet_set_params(hbf_unet* net, const float* src);
 int hbf_unet_get_grads(hbf_unet* net, float* dst);
+/* Tensor-core path of the 3^d convolutions (forward and input-gradient):
+ * 0 = warp-level mma.sync (default), 1 = tcgen05.mma with TMEM accumulators
+ * (128 points x Cout per CTA, operands staged in shared memory, completion
+ * on an mbarrier with a bounded wait).  Both accumulate in FP32.  The weight
+ * gradient always uses mma.sync. */
+int hbf_unet_set_tensor_path(hbf_unet* net, int path);
+/* Synchronises; HBF_ERR_TIMEOUT (and clears it) if a tcgen05 convolution
+ * gave up waiting for the tensor cores since the last call, else HBF_OK. */
+int hbf_unet_tensor_status(hbf_unet* net);
 /* y = net(x); y_dev may be NULL (the output stays inside the network) */
 int hbf_unet_forward(hbf_unet* net, const float* x_dev, float* y_dev);
 /* masked mean squared error of the last forward output against t; writes the

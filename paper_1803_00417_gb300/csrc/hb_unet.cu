@@ -16,6 +16,7 @@
 
 #include "hb_internal.h"
 #include "hb_unet_kernels.cuh"
+#include "hb_unet_tc.cuh"
 
 using hb::nn::bf16;
 using hb::nn::Box;
@@ -281,6 +282,8 @@ struct hbf_unet {
   double* hpart = nullptr;
   long long step = 0;
   long long nlaunch_fwd = 0;  // kernel launches of one forward pass
+  int tensor_path = 0;        // 0: mma.sync convolutions, 1: tcgen05 (TMEM accumulators)
+  int* tc_err = nullptr;      // device flag: a tcgen05 wait gave up
   std::vector<void*> allocs;
   std::string err;
 };
@@ -307,6 +310,18 @@ int taps(int d) { return d == 3 ? 27 : 9; }
 
 void conv(hbf_unet* N, int lev, const bf16* in, int cin, const bf16* W, const float* b, int cout, bf16* out,
           int ostride, int ooff, int relu) {
+  if (N->tensor_path == 1 && cin % 16 == 0 && cout % 16 == 0 && cout >= 16 && cout <= 256 && N->tc_err) {
+    const int blocks = (int)((N->P[lev] + kTcM - 1) / kTcM);
+    const int smem = tc_smem_bytes(cin, cout);
+    const Box bx = N->box[lev];
+    if (N->d == 3)
+      k_conv_fwd_tc<3><<<blocks, kTcM, smem, N->stream>>>(in, cin, W, b, cout, out, ostride, ooff, relu, bx,
+                                                          tc_cols(cout), N->tc_err);
+    else
+      k_conv_fwd_tc<2><<<blocks, kTcM, smem, N->stream>>>(in, cin, W, b, cout, out, ostride, ooff, relu, bx,
+                                                          tc_cols(cout), N->tc_err);
+    return;
+  }
   const int NT = cout / 8;
   const int NTB = NT <= 8 ? NT : (NT % 8 == 0 ? 8 : (NT % 6 == 0 ? 6 : 4));
   dim3 g((unsigned)((N->P[lev] + 63) / 64), (unsigned)(NT / NTB), 1);
@@ -609,6 +624,7 @@ int hbf_unet_create(hbf_unet** out, int dim, const int64_t n[3], int train, uint
       goto fail;
     }
   }
+  NA(N->tc_err, 1);
   NA(N->x16, N->P[0] * 16);
   for (int l = 0; l < 3; ++l) {
     NA(N->e[l][0], N->P[l] * kCh[l]);
@@ -696,6 +712,35 @@ static int copy_params(hbf_unet* N, float* host_or_dev, int which, bool in) {
 int hbf_unet_get_params(hbf_unet* N, float* dst) { return copy_params(N, dst, 0, false); }
 int hbf_unet_set_params(hbf_unet* N, const float* src) { return copy_params(N, const_cast<float*>(src), 0, true); }
 int hbf_unet_get_grads(hbf_unet* N, float* dst) { return copy_params(N, dst, 1, false); }
+
+int hbf_unet_set_tensor_path(hbf_unet* N, int path) {
+  if (!N || (path != 0 && path != 1)) return HBF_ERR_ARG;
+  if (path == 1) {
+    // the largest tile: 128 points plus 256 output channels, of 256 input channels
+    const int bytes = tc_smem_bytes(256, 256);
+    if (cudaFuncSetAttribute(k_conv_fwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+      N->err = "tcgen05 convolution: shared-memory attribute";
+      return HBF_ERR_CUDA;
+    }
+  }
+  N->tensor_path = path;
+  return HBF_OK;
+}
+
+int hbf_unet_tensor_status(hbf_unet* N) {
+  if (!N) return HBF_ERR_ARG;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, N->tc_err, sizeof(int), cudaMemcpyDeviceToHost, N->stream) != cudaSuccess ||
+      cudaStreamSynchronize(N->stream) != cudaSuccess)
+    return HBF_ERR_CUDA;
+  if (h) {
+    cudaMemsetAsync(N->tc_err, 0, sizeof(int), N->stream);
+    N->err = "a tcgen05 convolution gave up waiting for the tensor cores";
+    return HBF_ERR_TIMEOUT;
+  }
+  return HBF_OK;
+}
 
 int hbf_unet_forward(hbf_unet* N, const float* x_dev, float* y_dev) {
   if (!N || !x_dev) return HBF_ERR_ARG;

@@ -80,6 +80,8 @@ SIGNATURES = {
     "hbf_unet_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hbf_unet_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hbf_unet_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_unet_set_tensor_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hbf_unet_tensor_status": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_unet_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "hbf_unet_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.POINTER(ctypes.c_double)]),
@@ -384,6 +386,13 @@ class UNet:
         out = np.empty(self.param_count(), dtype=np.float32)
         self._check(self.lib.hbf_unet_get_grads(self.net, ctypes.c_void_p(out.ctypes.data)))
         return out
+
+    def set_tensor_path(self, path):
+        """0: mma.sync convolutions, 1: tcgen05 (TMEM accumulators)."""
+        self._check(self.lib.hbf_unet_set_tensor_path(self.net, int(path)))
+
+    def tensor_status(self):
+        self._check(self.lib.hbf_unet_tensor_status(self.net))
 
     def forward(self, x_dev, y_dev=None):
         self._check(self.lib.hbf_unet_forward(self.net, _ptr(x_dev), _ptr(y_dev) if y_dev is not None else None))

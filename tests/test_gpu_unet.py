@@ -138,3 +138,34 @@ def test_training_reduces_loss():
     hist = train(net, np.array(xs), np.array(ys), np.ones(256, dtype=np.float32), epochs=25, lr=2e-3, batch=2)
     assert hist[-1] < 0.5 * hist[0], hist
     net.close()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_tcgen05_path_matches(d):
+    """The tcgen05 convolutions (TMEM accumulators) give the forward pass and
+    the gradients of the mma.sync path and of the CPU reference network."""
+    from paper_1803_00417_gb300.hbflow import UNet
+
+    n, params, x, t = make_case(d, 21 + d)
+    xd = torch.tensor(spatial_to_flat(x).astype(np.float32), device="cuda")
+    td = torch.tensor(spatial_to_flat(t).astype(np.float32), device="cuda")
+    md = torch.ones_like(xd)
+    outs, grads = [], []
+    for path in (0, 1):
+        net = UNet(n, train=True)
+        net.set_tensor_path(path)
+        net.set_params(to_gpu_params(params))
+        yd = torch.empty_like(xd)
+        gy = torch.empty_like(xd)
+        net.zero_grads()
+        net.forward(xd, yd)
+        net.loss(td, md, gy)
+        net.backward(gy)
+        net.tensor_status()
+        outs.append(yd.cpu().numpy())
+        grads.append(net.get_grads())
+        net.close()
+    y_ref = U.forward(params, U.bf16(x)[..., None])[..., 0]
+    assert rel(outs[1], spatial_to_flat(y_ref)) < 2e-2
+    assert rel(outs[1], outs[0]) < 1e-2
+    assert rel(grads[1], grads[0]) < 3e-2
