@@ -234,7 +234,7 @@ int hbf_unet_get_params(hbf_unet* net, float* dst);
 int hbf_unet_set_params(hbf_unet* net, const float* src);
 int hbf_unet_get_grads(hbf_unet* net, float* dst);
 /* Tensor-core path of the 3^d convolutions (forward and input-gradient):
- * 0 = warp-level mma.sync (default), 1 = tcgen05.mma with TMEM accumulators
+ * 0 = warp-level mma.sync, 1 = tcgen05.mma with TMEM accumulators (default)
  * (128 points x Cout per CTA, operands staged in shared memory, completion
  * on an mbarrier with a bounded wait).  Both accumulate in FP32.  The weight
  * gradient always uses mma.sync. */

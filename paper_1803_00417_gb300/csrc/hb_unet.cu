@@ -662,6 +662,8 @@ int hbf_unet_create(hbf_unet** out, int dim, const int64_t n[3], int train, uint
     st = HBF_ERR_CUDA;
     goto fail;
   }
+  // tcgen05 convolutions by default (mma.sync if their launch attribute fails)
+  if (hbf_unet_set_tensor_path(N, 1) != HBF_OK) N->tensor_path = 0;
   *out = N;
   return HBF_OK;
 fail:
@@ -720,6 +722,7 @@ int hbf_unet_set_tensor_path(hbf_unet* N, int path) {
     const int bytes = tc_smem_bytes(256, 256);
     if (cudaFuncSetAttribute(k_conv_fwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
         cudaFuncSetAttribute(k_conv_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+      cudaGetLastError();
       N->err = "tcgen05 convolution: shared-memory attribute";
       return HBF_ERR_CUDA;
     }
@@ -727,6 +730,7 @@ int hbf_unet_set_tensor_path(hbf_unet* N, int path) {
   N->tensor_path = path;
   return HBF_OK;
 }
+
 
 int hbf_unet_tensor_status(hbf_unet* N) {
   if (!N) return HBF_ERR_ARG;
