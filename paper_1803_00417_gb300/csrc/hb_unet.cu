@@ -311,9 +311,21 @@ int taps(int d) { return d == 3 ? 27 : 9; }
 void conv(hbf_unet* N, int lev, const bf16* in, int cin, const bf16* W, const float* b, int cout, bf16* out,
           int ostride, int ooff, int relu) {
   if (N->tensor_path == 1 && cin % 16 == 0 && cout % 16 == 0 && cout >= 16 && cout <= 256 && N->tc_err) {
+    const Box bx = N->box[lev];
+    const int hsmem = tc_halo_smem_bytes(N->d, cin, cout);
+    if (bx.X % 8 == 0 && hsmem <= kTcHaloMaxSmem) {
+      // every tap in shared memory: one MMA stream per CTA of 8 x 16 points
+      const int blocks = (bx.X / 8) * ((bx.Y + 15) / 16) * bx.Z;
+      if (N->d == 3)
+        k_conv_fwd_tc_halo<3><<<blocks, kTcM, hsmem, N->stream>>>(in, cin, W, b, cout, out, ostride, ooff, relu,
+                                                                  bx, tc_cols(cout), N->tc_err);
+      else
+        k_conv_fwd_tc_halo<2><<<blocks, kTcM, hsmem, N->stream>>>(in, cin, W, b, cout, out, ostride, ooff, relu,
+                                                                  bx, tc_cols(cout), N->tc_err);
+      return;
+    }
     const int blocks = (int)((N->P[lev] + kTcM - 1) / kTcM);
     const int smem = tc_smem_bytes(cin, cout);
-    const Box bx = N->box[lev];
     if (N->d == 3)
       k_conv_fwd_tc<3><<<blocks, kTcM, smem, N->stream>>>(in, cin, W, b, cout, out, ostride, ooff, relu, bx,
                                                           tc_cols(cout), N->tc_err);
@@ -721,7 +733,11 @@ int hbf_unet_set_tensor_path(hbf_unet* N, int path) {
     // the largest tile: 128 points plus 256 output channels, of 256 input channels
     const int bytes = tc_smem_bytes(256, 256);
     if (cudaFuncSetAttribute(k_conv_fwd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
-        cudaFuncSetAttribute(k_conv_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+        cudaFuncSetAttribute(k_conv_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_fwd_tc_halo<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcHaloMaxSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_fwd_tc_halo<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcHaloMaxSmem) !=
+            cudaSuccess) {
       cudaGetLastError();
       N->err = "tcgen05 convolution: shared-memory attribute";
       return HBF_ERR_CUDA;
