@@ -58,9 +58,9 @@ struct OpHats {
     const double* slopes;
     double* hats;
     Geom g;
-    double dt;
+    StepC k;
   };
-  static __device__ void apply(const Arg& a, int t, int) { k_hats_at<D>(a.u, a.slopes, a.hats, a.g, a.dt, t); }
+  static __device__ void apply(const Arg& a, int t, int) { k_hats_at<D>(a.u, a.slopes, a.hats, a.g, a.k, t); }
 };
 
 template <int D>
@@ -68,16 +68,14 @@ struct OpTraces {
   struct Arg {
     const double *u, *slopes, *hats, *Gp, *Lu;
     Force fo;
-    double rho;
     int pv;
     double *uL[3], *uR[3], *uadv[3];
     Geom g;
-    double dt;
+    StepC k;
   };
   static __device__ void apply(const Arg& a, int t, int) {
     const int ax = face_axis(a.g, t);
-    k_traces_at<D>(a.u, a.slopes, a.hats, a.Gp, a.Lu, a.fo, a.rho, a.pv, ax, a.uL[ax], a.uR[ax], a.uadv[ax], a.g,
-                   a.dt, t);
+    k_traces_at<D>(a.u, a.slopes, a.hats, a.Gp, a.Lu, a.fo, a.pv, ax, a.uL[ax], a.uR[ax], a.uadv[ax], a.g, a.k, t);
   }
 };
 
@@ -112,14 +110,13 @@ struct OpAdvectRhs {
     const double *uL[3], *uR[3], *um[3];
     const double *Gp, *Lu;
     Force fo;
-    double rho;
     double* rhs;
     Geom g;
-    double dt;
+    StepC k;
   };
   static __device__ void apply(const Arg& a, int t, int) {
     k_advect_rhs_at<D>(a.u, a.uL[0], a.uL[1], a.uL[2], a.uR[0], a.uR[1], a.uR[2], a.um[0], a.um[1], a.um[2], a.Gp,
-                       a.Lu, a.fo, a.rho, a.rhs, a.g, a.dt, t);
+                       a.Lu, a.fo, a.rhs, a.g, a.k, t);
   }
 };
 
@@ -129,9 +126,9 @@ struct OpNodalRhs {
     const double *ustar, *Gp;
     double* out;
     Geom g;
-    double dt, rho;
+    StepC k;
   };
-  static __device__ void apply(const Arg& a, int t, int) { k_nodal_rhs_at<D>(a.ustar, a.Gp, a.out, a.g, a.dt, a.rho, t); }
+  static __device__ void apply(const Arg& a, int t, int) { k_nodal_rhs_at<D>(a.ustar, a.Gp, a.out, a.g, a.k, t); }
 };
 
 template <int D>
@@ -140,10 +137,10 @@ struct OpProjectUpdate {
     double* u;
     const double *Gp, *phi;
     Geom g;
-    double dt, rho;
+    StepC k;
   };
   static __device__ void apply(const Arg& a, int t, int) {
-    k_project_update_at<D>(a.u, a.Gp, a.phi, a.g, a.dt, a.rho, t);
+    k_project_update_at<D>(a.u, a.Gp, a.phi, a.g, a.k, t);
   }
 };
 
@@ -174,22 +171,22 @@ static void build_tables(hbf_batch* B, ExplicitTables& T) {
   std::vector<typename OpProjectUpdate<D>::Arg> a11;
   for (int i = 0; i < B->ncav; ++i) {
     hbf_ctx* c = B->cav[i];
-    const double dt = B->dt[i];
+    const StepC k = step_consts(c->g, D, B->dt[i], c->rho);
     Force fo{{c->f[0], c->f[1], c->f[2]}};
     a1.push_back({c->u, c->eta, c->g, c->rheo});
     a2.push_back({c->eta, {c->lv[0].ef[0], c->lv[0].ef[1], c->lv[0].ef[2]}, c->g});
     a3.push_back({c->p, c->Gp, c->g});
     a4.push_back({c->u, c->slopes, c->g});
-    a5.push_back({c->u, c->slopes, c->hats, c->g, dt});
-    a6.push_back({c->u, c->slopes, c->hats, c->Gp, c->Lu, fo, c->rho, c->predictor_visc,
+    a5.push_back({c->u, c->slopes, c->hats, c->g, k});
+    a6.push_back({c->u, c->slopes, c->hats, c->Gp, c->Lu, fo, c->predictor_visc,
                   {c->uL[0], c->uL[1], c->uL[2]}, {c->uR[0], c->uR[1], c->uR[2]},
-                  {c->uadv[0], c->uadv[1], c->uadv[2]}, c->g, dt});
+                  {c->uadv[0], c->uadv[1], c->uadv[2]}, c->g, k});
     a7.push_back({{c->uadv[0], c->uadv[1], c->uadv[2]}, c->mrhs, c->g});
     a8.push_back({{c->uadv[0], c->uadv[1], c->uadv[2]}, c->phi_mac, {c->umac[0], c->umac[1], c->umac[2]}, c->g});
     a9.push_back({c->u, {c->uL[0], c->uL[1], c->uL[2]}, {c->uR[0], c->uR[1], c->uR[2]},
-                  {c->umac[0], c->umac[1], c->umac[2]}, c->Gp, c->Lu, fo, c->rho, c->rhs, c->g, dt});
-    a10.push_back({c->ustar, c->Gp, c->nrhs, c->g, dt, c->rho});
-    a11.push_back({c->ustar, c->Gp, c->p, c->g, dt, c->rho});
+                  {c->umac[0], c->umac[1], c->umac[2]}, c->Gp, c->Lu, fo, c->rhs, c->g, k});
+    a10.push_back({c->ustar, c->Gp, c->nrhs, c->g, k});
+    a11.push_back({c->ustar, c->Gp, c->p, c->g, k});
   }
   T.eta = table<OpEta<D>>(B, a1);
   T.ef = table<OpEtaFaces<D>>(B, a2);

@@ -40,10 +40,11 @@ int launch_predict(hbf_ctx* c, double dt) {
   if (st) return st;
   if ((st = tensor_lu(c, c->u, c->Lu))) return st;
   HB_DISPATCH(c->dim, k_slopes, grid_for(g.ncell), c->u, c->slopes, g);
-  HB_DISPATCH(c->dim, k_hats, grid_for(g.ncell), c->u, c->slopes, c->hats, g, dt);
+  const StepC k = step_consts(g, c->dim, dt, c->rho);
+  HB_DISPATCH(c->dim, k_hats, grid_for(g.ncell), c->u, c->slopes, c->hats, g, k);
   for (int a = 0; a < c->dim; ++a)
     HB_DISPATCH(c->dim, k_traces, grid_for(g.nface[a]), c->u, c->slopes, c->hats, c->Gp, c->Lu, fo,
-                c->rho, c->predictor_visc, a, c->uL[a], c->uR[a], c->uadv[a], g, dt);
+                c->predictor_visc, a, c->uL[a], c->uR[a], c->uadv[a], g, k);
   return cuda_check(c, cudaGetLastError(), "predict kernels");
 }
 
@@ -61,20 +62,22 @@ int launch_mac_correct(hbf_ctx* c, const double* phi) {
 int launch_advect_rhs(hbf_ctx* c, double dt) {
   Force fo{{c->f[0], c->f[1], c->f[2]}};
   HB_DISPATCH(c->dim, k_advect_rhs, grid_for(c->g.ncell), c->u, c->uL[0], c->uL[1], c->uL[2], c->uR[0],
-              c->uR[1], c->uR[2], c->umac[0], c->umac[1], c->umac[2], c->Gp, c->Lu, fo, c->rho,
-              c->rhs, c->g, dt);
+              c->uR[1], c->uR[2], c->umac[0], c->umac[1], c->umac[2], c->Gp, c->Lu, fo, c->rhs, c->g,
+              step_consts(c->g, c->dim, dt, c->rho));
   return cuda_check(c, cudaGetLastError(), "k_advect_rhs");
 }
 
 int launch_nodal_rhs(hbf_ctx* c, double dt, const double* ustar, const double* p, double* out) {
   HB_DISPATCH(c->dim, k_grad_p, grid_for(c->g.ncell), p, c->Gp, c->g);
-  HB_DISPATCH(c->dim, k_nodal_rhs, grid_for(c->g.nnode), ustar, c->Gp, out, c->g, dt, c->rho);
+  HB_DISPATCH(c->dim, k_nodal_rhs, grid_for(c->g.nnode), ustar, c->Gp, out, c->g,
+              step_consts(c->g, c->dim, dt, c->rho));
   return cuda_check(c, cudaGetLastError(), "k_nodal_rhs");
 }
 
 int launch_project_update(hbf_ctx* c, double dt, double* u, const double* p_old, const double* phi) {
   (void)p_old;  // G p^{m-1/2} is still in c->Gp from launch_nodal_rhs
-  HB_DISPATCH(c->dim, k_project_update, grid_for(c->g.ncell), u, c->Gp, phi, c->g, dt, c->rho);
+  HB_DISPATCH(c->dim, k_project_update, grid_for(c->g.ncell), u, c->Gp, phi, c->g,
+              step_consts(c->g, c->dim, dt, c->rho));
   return cuda_check(c, cudaGetLastError(), "k_project_update");
 }
 

@@ -4,10 +4,76 @@
 // include it are compiled without FMA contraction (see hb_explicit.cu).
 #pragma once
 #include <cmath>
+#include <cstring>
 
 #include "hb_internal.h"
 
 namespace hb {
+
+// ---------------------------------------------------------------------------
+// FP64 comparisons on the integer pipe.  GB300 issues FP64 instructions at a
+// small fraction of its FP32/INT32 rate, and the limiter and upwind choices of
+// the predictor are comparisons: on the bit patterns they give the IEEE answer
+// for every non-NaN operand (+0 and -0 both count as zero).
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kSignBit = 1ull << 63;
+
+__host__ __device__ __forceinline__ unsigned long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  std::memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double dfrom(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  std::memcpy(&x, &b, sizeof x);
+  return x;
+#endif
+}
+
+// x > 0, x < 0, x == 0
+__host__ __device__ __forceinline__ bool dpos(double x) { return (long long)dbits(x) > 0; }
+__host__ __device__ __forceinline__ bool dneg(double x) { return dbits(x) > kSignBit; }
+__host__ __device__ __forceinline__ bool dzero(double x) { return (dbits(x) << 1) == 0; }
+
+// min(|a|, |b|)
+__host__ __device__ __forceinline__ double dminabs(double a, double b) {
+  const unsigned long long ma = dbits(a) & ~kSignBit, mb = dbits(b) & ~kSignBit;
+  return dfrom(ma < mb ? ma : mb);
+}
+
+// The time-step constants of the explicit stages, rounded once on the host
+// (the stages multiply by them where the plain formulas divide).
+struct StepC {
+  double dt;    // time step
+  double dt2h;  // dt / (2h)
+  double hdt;   // dt / 2
+  double rho;   // density
+  double irho;  // 1 / rho
+  double dtr;   // dt / rho
+  double idt;   // 1 / dt
+  double inrm;  // 1 / (2^(D-1) h): the nodal divergence's normalisation
+};
+
+inline StepC step_consts(const Geom& g, int dim, double dt, double rho) {
+  StepC k;
+  k.dt = dt;
+  k.dt2h = dt / (2.0 * g.h);
+  k.hdt = 0.5 * dt;
+  k.rho = rho;
+  k.irho = 1.0 / rho;
+  k.dtr = dt / rho;
+  k.idt = 1.0 / dt;
+  k.inrm = 1.0 / ((double)(1 << (dim - 1)) * g.h);
+  return k;
+}
 
 // ---------------------------------------------------------------------------
 // Stage 1: strain rate and regularised viscosity (Eqs. 1, 21-23)
@@ -114,7 +180,7 @@ __host__ __device__ inline double grad_nodal(const double* __restrict__ p, const
       if (D == 3) q[o2] += s2;
       int qh[3] = {q[0], q[1], q[2]};
       qh[a] += 1;
-      v[s1][s2] = (p[nidx(g, qh[0], qh[1], qh[2])] - p[nidx(g, q[0], q[1], q[2])]) / g.h;
+      v[s1][s2] = (p[nidx(g, qh[0], qh[1], qh[2])] - p[nidx(g, q[0], q[1], q[2])]) * g.ih;
     }
   if (D == 2) return 0.5 * (v[0][0] + v[1][0]);
   // average over o1 first, then o2
@@ -143,10 +209,10 @@ __global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, 
 // Stage 3: Godunov edge states (Eqs. 11-14)
 // ---------------------------------------------------------------------------
 __host__ __device__ inline double sgn_min(double v, double lim) {
-  // sign(v) * min(|v|, lim) with sign(0) = 0
-  if (v == 0.0) return 0.0;
-  double m = fmin(fabs(v), lim);
-  return v > 0.0 ? m : -m;
+  // sign(v) * min(|v|, lim) with sign(0) = 0, for lim >= +0: the magnitude
+  // is the smaller bit pattern, the sign bit is v's
+  if (dzero(v)) return 0.0;
+  return dfrom(dbits(dminabs(v, lim)) | (dbits(v) & kSignBit));
 }
 
 // Colella's slope from the five values w[0..4] at offsets -2..2
@@ -157,7 +223,10 @@ __host__ __device__ inline double slope5(const double* w) {
     double dL = w[s + 1] - w[s];
     double dR = w[s + 2] - w[s + 1];
     dC[s] = 0.5 * (w[s + 2] - w[s]);
-    dlim[s] = (dL * dR > 0.0) ? 2.0 * fmin(fabs(dL), fabs(dR)) : 0.0;
+    // dL dR > 0 as a sign test (it differs from the product only where
+    // |dL dR| underflows, below 1e-300, and then by less than 1e-150)
+    const bool same = !dzero(dL) && !dzero(dR) && !((dbits(dL) ^ dbits(dR)) & kSignBit);
+    dlim[s] = same ? 2.0 * dminabs(dL, dR) : 0.0;
     df[s] = sgn_min(dC[s], dlim[s]);
   }
   double d4 = (4.0 / 3.0) * dC[1] - (1.0 / 6.0) * (df[2] + df[0]);
@@ -203,14 +272,14 @@ __global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slop
 
 __host__ __device__ inline double riemann(double uL, double uR) {
   double s = uL + uR;
-  if (uL > 0.0 && s > 0.0) return uL;
-  if (uR < 0.0 && s < 0.0) return uR;
+  if (dpos(uL) && dpos(s)) return uL;
+  if (dneg(uR) && dneg(s)) return uR;
   return 0.0;
 }
 
 __host__ __device__ inline double upwind(double uL, double uR, double v) {
-  if (v > 0.0) return uL;
-  if (v < 0.0) return uR;
+  if (dpos(v)) return uL;
+  if (dneg(v)) return uR;
   return 0.5 * (uL + uR);
 }
 
@@ -218,7 +287,7 @@ __host__ __device__ inline double upwind(double uL, double uR, double v) {
 // st[c] returns the upwinded state of each component, vb the normal velocity.
 template <int D>
 __host__ __device__ inline void prestate_face(const double* __restrict__ u, const double* __restrict__ slopes,
-                                     const Geom& g, double dt, int b, const int* L, double* st,
+                                     const Geom& g, const StepC& k, int b, const int* L, double* st,
                                      double& vb) {
   int R[3] = {L[0], L[1], L[2]};
   R[b] += 1;
@@ -230,8 +299,8 @@ __host__ __device__ inline void prestate_face(const double* __restrict__ u, cons
   } else {
     int tl = cidx<D>(g, L[0], L[1], L[2]), tr = cidx<D>(g, R[0], R[1], R[2]);
     double ubL = u[(size_t)b * g.ncell + tl], ubR = u[(size_t)b * g.ncell + tr];
-    double facL = 0.5 - ubL * dt / (2.0 * g.h);
-    double facR = 0.5 + ubR * dt / (2.0 * g.h);
+    double facL = 0.5 - ubL * k.dt2h;
+    double facR = 0.5 + ubR * k.dt2h;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       sL[c] = u[(size_t)c * g.ncell + tl] + facL * slopes[(size_t)(b * D + c) * g.ncell + tl];
@@ -245,28 +314,28 @@ __host__ __device__ inline void prestate_face(const double* __restrict__ u, cons
 
 template <int D>
 __host__ __device__ __forceinline__ void k_hats_at(const double* __restrict__ u, const double* __restrict__ slopes,
-                       double* __restrict__ hats, const Geom& g, double dt, int t) {
+                       double* __restrict__ hats, const Geom& g, const StepC& k, int t) {
   
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
 #pragma unroll
     for (int b = 0; b < D; ++b) {
       double stHi[3], stLo[3], vHi, vLo;
-      prestate_face<D>(u, slopes, g, dt, b, p, stHi, vHi);
+      prestate_face<D>(u, slopes, g, k, b, p, stHi, vHi);
       int Lm[3] = {p[0], p[1], p[2]};
       Lm[b] -= 1;
-      prestate_face<D>(u, slopes, g, dt, b, Lm, stLo, vLo);
+      prestate_face<D>(u, slopes, g, k, b, Lm, stLo, vLo);
 #pragma unroll
       for (int c = 0; c < D; ++c)
-        hats[(size_t)(b * D + c) * g.ncell + t] = 0.5 * (vHi + vLo) * (stHi[c] - stLo[c]) / g.h;
+        hats[(size_t)(b * D + c) * g.ncell + t] = 0.5 * (vHi + vLo) * (stHi[c] - stLo[c]) * g.ih;
     }
   }
 
 template <int D>
 __global__ void k_hats(const double* __restrict__ u, const double* __restrict__ slopes,
-                       double* __restrict__ hats, const __grid_constant__ Geom g, double dt) {
+                       double* __restrict__ hats, const __grid_constant__ Geom g, const StepC k) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    k_hats_at<D>(u, slopes, hats, g, dt, t);
+    k_hats_at<D>(u, slopes, hats, g, k, t);
   }
 }
 
@@ -275,22 +344,22 @@ __global__ void k_hats(const double* __restrict__ u, const double* __restrict__ 
 template <int D>
 __host__ __device__ inline double trace(const double* __restrict__ u, const double* __restrict__ slopes,
                                const double* __restrict__ hats, const double* __restrict__ Gp,
-                               const double* __restrict__ Lu, const double* f, double rho, int pv,
-                               const Geom& g, double dt, int a, int c, int tq, bool left) {
+                               const double* __restrict__ Lu, const double* f, int pv,
+                               const Geom& g, const StepC& k, int a, int c, int tq, bool left) {
   double trans = 0.0;
 #pragma unroll
   for (int b = 0; b < D; ++b)
     if (b != a) trans += hats[(size_t)(b * D + c) * g.ncell + tq];
-  double F = (-Gp[(size_t)c * g.ncell + tq] + (pv ? Lu[(size_t)c * g.ncell + tq] : 0.0) + f[c]) / rho;
-  double common = -0.5 * dt * trans + 0.5 * dt * F;
+  double F = (-Gp[(size_t)c * g.ncell + tq] + (pv ? Lu[(size_t)c * g.ncell + tq] : 0.0) + f[c]) * k.irho;
+  double common = -k.hdt * trans + k.hdt * F;
   double ua = u[(size_t)a * g.ncell + tq];
   double s = slopes[(size_t)(a * D + c) * g.ncell + tq];
   double uc = u[(size_t)c * g.ncell + tq];
   if (left) {
-    double fac = 0.5 - ua * dt / (2.0 * g.h);
+    double fac = 0.5 - ua * k.dt2h;
     return uc + fac * s + common;
   }
-  double fac = 0.5 + ua * dt / (2.0 * g.h);
+  double fac = 0.5 + ua * k.dt2h;
   return uc - fac * s + common;
 }
 
@@ -301,9 +370,9 @@ struct Force {
 template <int D>
 __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ u, const double* __restrict__ slopes,
                          const double* __restrict__ hats, const double* __restrict__ Gp,
-                         const double* __restrict__ Lu, Force fo, double rho, int pv, int a,
+                         const double* __restrict__ Lu, Force fo, int pv, int a,
                          double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
-                         const Geom& g, double dt, int t) {
+                         const Geom& g, const StepC& k, int t) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
   
@@ -325,8 +394,8 @@ __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ 
     double vl = 0, vr = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      double l = trace<D>(u, slopes, hats, Gp, Lu, fo.f, rho, pv, g, dt, a, c, tl, true);
-      double rr = trace<D>(u, slopes, hats, Gp, Lu, fo.f, rho, pv, g, dt, a, c, tr, false);
+      double l = trace<D>(u, slopes, hats, Gp, Lu, fo.f, pv, g, k, a, c, tl, true);
+      double rr = trace<D>(u, slopes, hats, Gp, Lu, fo.f, pv, g, k, a, c, tr, false);
       uL[(size_t)c * nf + t] = l;
       uR[(size_t)c * nf + t] = rr;
       if (c == a) {
@@ -340,13 +409,13 @@ __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ 
 template <int D>
 __global__ void k_traces(const double* __restrict__ u, const double* __restrict__ slopes,
                          const double* __restrict__ hats, const double* __restrict__ Gp,
-                         const double* __restrict__ Lu, Force fo, double rho, int pv, int a,
+                         const double* __restrict__ Lu, Force fo, int pv, int a,
                          double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
-                         const __grid_constant__ Geom g, double dt) {
+                         const __grid_constant__ Geom g, const StepC k) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
-    k_traces_at<D>(u, slopes, hats, Gp, Lu, fo, rho, pv, a, uL, uR, uadv, g, dt, t);
+    k_traces_at<D>(u, slopes, hats, Gp, Lu, fo, pv, a, uL, uR, uadv, g, k, t);
   }
 }
 
@@ -367,7 +436,7 @@ __host__ __device__ __forceinline__ void k_mac_rhs_at(const double* ua0, const d
       double lo = ua[a][fidx(g, a, q[0], q[1], q[2])];
       q[a] += 1;
       double hi = ua[a][fidx(g, a, q[0], q[1], q[2])];
-      acc += (hi - lo) / g.h;
+      acc += (hi - lo) * g.ih;
     }
     rhs[t] = acc;
   }
@@ -394,7 +463,7 @@ __host__ __device__ __forceinline__ void k_mac_correct_at(const double* __restri
     }
     int L[3] = {R[0], R[1], R[2]};
     L[a] -= 1;
-    double gr = (phi[cidx<D>(g, R[0], R[1], R[2])] - phi[cidx<D>(g, L[0], L[1], L[2])]) / g.h;
+    double gr = (phi[cidx<D>(g, R[0], R[1], R[2])] - phi[cidx<D>(g, L[0], L[1], L[2])]) * g.ih;
     umac[t] = uadv[t] - gr;
   }
 
@@ -416,8 +485,8 @@ __host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restric
                              const double* uL2, const double* uR0, const double* uR1,
                              const double* uR2, const double* um0, const double* um1,
                              const double* um2, const double* __restrict__ Gp,
-                             const double* __restrict__ Lu, Force fo, double rho,
-                             double* __restrict__ rhs, const Geom& g, double dt, int t) {
+                             const double* __restrict__ Lu, Force fo,
+                             double* __restrict__ rhs, const Geom& g, const StepC& k, int t) {
   const double* uL[3] = {uL0, uL1, uL2};
   const double* uR[3] = {uR0, uR1, uR2};
   const double* um[3] = {um0, um1, um2};
@@ -438,13 +507,13 @@ __host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restric
       for (int c = 0; c < D; ++c) {
         double thi = upwind(uL[a][(size_t)c * nf + fhi], uR[a][(size_t)c * nf + fhi], vhi);
         double tlo = upwind(uL[a][(size_t)c * nf + flo], uR[a][(size_t)c * nf + flo], vlo);
-        A[c] += vbar * (thi - tlo) / g.h;
+        A[c] += vbar * (thi - tlo) * g.ih;
       }
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       size_t o = (size_t)c * g.ncell + t;
-      rhs[o] = u[o] - dt * A[c] + (dt / rho) * (-Gp[o] + 0.5 * Lu[o] + fo.f[c]);
+      rhs[o] = u[o] - k.dt * A[c] + k.dtr * (-Gp[o] + 0.5 * Lu[o] + fo.f[c]);
     }
   }
 
@@ -453,13 +522,13 @@ __global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, co
                              const double* uL2, const double* uR0, const double* uR1,
                              const double* uR2, const double* um0, const double* um1,
                              const double* um2, const double* __restrict__ Gp,
-                             const double* __restrict__ Lu, Force fo, double rho,
-                             double* __restrict__ rhs, const __grid_constant__ Geom g, double dt) {
+                             const double* __restrict__ Lu, Force fo,
+                             double* __restrict__ rhs, const __grid_constant__ Geom g, const StepC k) {
   const double* uL[3] = {uL0, uL1, uL2};
   const double* uR[3] = {uR0, uR1, uR2};
   const double* um[3] = {um0, um1, um2};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    k_advect_rhs_at<D>(u, uL0, uL1, uL2, uR0, uR1, uR2, um0, um1, um2, Gp, Lu, fo, rho, rhs, g, dt, t);
+    k_advect_rhs_at<D>(u, uL0, uL1, uL2, uR0, uR1, uR2, um0, um1, um2, Gp, Lu, fo, rhs, g, k, t);
   }
 }
 
@@ -468,7 +537,7 @@ __global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, co
 // ---------------------------------------------------------------------------
 template <int D>
 __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict__ ustar, const double* __restrict__ Gp,
-                            double* __restrict__ out, const Geom& g, double dt, double rho, int t) {
+                            double* __restrict__ out, const Geom& g, const StepC& k, int t) {
   int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
   
     int p[3];
@@ -495,29 +564,31 @@ __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict
                   (D == 2 || (q[2] >= 0 && q[2] < g.n[2]));
         if (!in) continue;
         size_t o = (size_t)a * g.ncell + cidx<D>(g, q[0], q[1], q[2]);
-        double v = ustar[o] / dt + Gp[o] / rho;
+        double v = ustar[o] * k.idt + Gp[o] * k.irho;
         acc += cb[a] ? v : -v;
       }
     }
-    double w = 1.0;
+    // 1 / (w 2^(D-1) h) with w the node's weight (1/2 per wall axis): the
+    // power of two 1/w is exact
+    double iw = 1.0;
 #pragma unroll
     for (int a = 0; a < D; ++a)
-      if (p[a] == 0 || p[a] == g.n[a]) w *= 0.5;
-    out[t] = rho * (acc / (w * (double)(1 << (D - 1)) * g.h));
+      if (p[a] == 0 || p[a] == g.n[a]) iw *= 2.0;
+    out[t] = k.rho * (acc * (iw * k.inrm));
   }
 
 template <int D>
 __global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __restrict__ Gp,
-                            double* __restrict__ out, const __grid_constant__ Geom g, double dt, double rho) {
+                            double* __restrict__ out, const __grid_constant__ Geom g, const StepC k) {
   int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
-    k_nodal_rhs_at<D>(ustar, Gp, out, g, dt, rho, t);
+    k_nodal_rhs_at<D>(ustar, Gp, out, g, k, t);
   }
 }
 
 template <int D>
 __host__ __device__ __forceinline__ void k_project_update_at(double* __restrict__ u, const double* __restrict__ Gp,
-                                 const double* __restrict__ phi, const Geom& g, double dt, double rho, int t) {
+                                 const double* __restrict__ phi, const Geom& g, const StepC& sc, int t) {
   
     int i, j, k;
     cell_coords<D>(g, t, i, j, k);
@@ -525,15 +596,15 @@ __host__ __device__ __forceinline__ void k_project_update_at(double* __restrict_
     for (int a = 0; a < D; ++a) {
       size_t o = (size_t)a * g.ncell + t;
       double gphi = grad_nodal<D>(phi, g, a, i, j, k);
-      u[o] = u[o] + (dt / rho) * (Gp[o] - gphi);
+      u[o] = u[o] + sc.dtr * (Gp[o] - gphi);
     }
   }
 
 template <int D>
 __global__ void k_project_update(double* __restrict__ u, const double* __restrict__ Gp,
-                                 const double* __restrict__ phi, const __grid_constant__ Geom g, double dt, double rho) {
+                                 const double* __restrict__ phi, const __grid_constant__ Geom g, const StepC k) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    k_project_update_at<D>(u, Gp, phi, g, dt, rho, t);
+    k_project_update_at<D>(u, Gp, phi, g, k, t);
   }
 }
 

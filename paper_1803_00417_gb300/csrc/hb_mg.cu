@@ -579,7 +579,7 @@ struct ViscProblem : Problem<T> {
     Level& L = c->lv[l];
     const int slot = l == 0 ? kSlotViscSmooth : kSlotCoarse;
     const dim3 blk(kThreads, 1, 1);
-    const dim3 grd((unsigned)grid_for(rb_count<D>(L.g), 152 * 24), 1, 1);
+    const dim3 grd((unsigned)grid_for(rbx_count<D>(L.g), 152 * 24), 1, 1);
     const T* e0 = View<T>::ef(L, 0);
     const T* e1 = View<T>::ef(L, 1);
     const T* e2 = View<T>::ef(L, 2);
@@ -595,8 +595,8 @@ struct ViscProblem : Problem<T> {
   }
   void resid(int l) override {
     Level& L = c->lv[l];
-    const dim3 blk(32, 8, 1);
-    const dim3 grd((unsigned)(L.g.n[0] + 31) / 32, (unsigned)(L.g.n[1] + 7) / 8, (unsigned)L.g.n[2]);
+    const dim3 blk(256, 1, 1);
+    const dim3 grd(op3_blocks<D>(L.g), 1, 1);
     launch3(c, l == 0 ? kSlotViscResid : kSlotCoarse, k_visc_op3<D, T>, grd, blk, (const T*)x(l), (const T*)b(l), r(l),
             (const T*)View<T>::ef(L, 0), (const T*)View<T>::ef(L, 1), (const T*)View<T>::ef(L, 2), L.g, (T)beta,
             (int)this->hom(l));
@@ -865,8 +865,8 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
     launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, z, n);
     vcycle(Pz, 0, cfg);
   };
-  const dim3 blk(32, 8, 1);
-  const dim3 grd((unsigned)(L0.g.n[0] + 31) / 32, (unsigned)(L0.g.n[1] + 7) / 8, (unsigned)L0.g.n[2]);
+  const dim3 blk(256, 1, 1);
+  const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
   auto apply0 = [&](const float* q, float* o) {
     launch3(c, kSlotViscResid, k_visc_op3<D, float>, grd, blk, q, (const float*)nullptr, o, (const float*)L0.fef[0],
             (const float*)L0.fef[1], (const float*)L0.fef[2], L0.g, fbeta, 1);
@@ -966,8 +966,8 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
     }
   };
   auto apply0 = [&](const double* q, double* out_) {
-    const dim3 blk(32, 8, 1);
-    const dim3 grd((unsigned)(L0.g.n[0] + 31) / 32, (unsigned)(L0.g.n[1] + 7) / 8, (unsigned)L0.g.n[2]);
+    const dim3 blk(256, 1, 1);
+    const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
     launch3(c, l0slot(), k_visc_op3<D, double>, grd, blk, q, (const double*)nullptr, out_, (const double*)L0.ef[0],
             (const double*)L0.ef[1], (const double*)L0.ef[2], L0.g, beta, 1);
   };
@@ -1086,10 +1086,10 @@ void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, l
 int tensor_lu(hbf_ctx* c, const double* u, double* out) {
   const Level& L = c->lv[0];
   if (c->dim == 2)
-    launch(c, kSlotExplicit, k_tensor_lu<2, double>, grid_for(L.g.ncell, 152 * 24), kThreads, u, out,
+    launch(c, kSlotExplicit, k_tensor_lu<2, double>, grid_for(xi_count<2>(L.g), 152 * 24), kThreads, u, out,
            (const double*)L.ef[0], (const double*)L.ef[1], (const double*)L.ef[2], L.g, 0);
   else
-    launch(c, kSlotExplicit, k_tensor_lu<3, double>, grid_for(L.g.ncell, 152 * 24), kThreads, u, out,
+    launch(c, kSlotExplicit, k_tensor_lu<3, double>, grid_for(xi_count<3>(L.g), 152 * 24), kThreads, u, out,
            (const double*)L.ef[0], (const double*)L.ef[1], (const double*)L.ef[2], L.g, 0);
   return cuda_check(c, cudaGetLastError(), "k_tensor_lu");
 }

@@ -237,34 +237,113 @@ __host__ __device__ inline int rb_count(const Geom& g) {
   return ((g.n[0] + 1) / 2) * g.n[1] * (D == 3 ? g.n[2] : 1);
 }
 
-// Grid-stride over the cells of one colour; the component is a template
-// parameter so every a == C decision folds at compile time.  (A grid-stride
-// launch of about 24 blocks per SM measured faster than one thread per cell.)
+// Gauss-Seidel update of component C at cell p of the current colour
+template <int D, typename T, int C>
+__host__ __device__ __forceinline__ void visc_smooth_cell(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
+                                                          const T* ef1, const T* ef2, const Geom& g, T beta, int hom,
+                                                          const int* p) {
+  const T* ef[3] = {ef0, ef1, ef2};
+  T v;
+  if (interior<D>(g, p)) {
+    const Strides S = make_strides(g);
+    v = visc_gs_interior<D, T>(u, b, ef, g, S, C, p, beta);
+  } else {
+    v = visc_gs_point<D, T>(u, b, ef, g, C, p, beta, hom != 0);
+  }
+  u[(size_t)C * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
+}
+
 template <int D, typename T, int C>
 __host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
-                                                      const T* ef1, const T* ef2, const Geom& g, int col, T beta, int hom, int t) {
-  const T* ef[3] = {ef0, ef1, ef2};
-  const int nt = rb_count<D>(g);
-  
-    int p[3];
-    if (!rb_cell<D>(g, t, col, p)) return;
-    T v;
-    if (interior<D>(g, p)) {
-      const Strides S = make_strides(g);
-      v = visc_gs_interior<D, T>(u, b, ef, g, S, C, p, beta);
-    } else {
-      v = visc_gs_point<D, T>(u, b, ef, g, C, p, beta, hom != 0);
-    }
-    u[(size_t)C * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
-  }
+                                                           const T* ef1, const T* ef2, const Geom& g, int col, T beta,
+                                                           int hom, int t) {
+  int p[3];
+  if (!rb_cell<D>(g, t, col, p)) return;
+  visc_smooth_cell<D, T, C>(u, b, ef0, ef1, ef2, g, beta, hom, p);
+}
 
+// Thread -> cell maps that keep the x-wall cells out of the warps of x-interior
+// cells.  A warp holding one wall cell issues the wall stencil (ghost values,
+// many branches) on top of the interior one; in a row-major map a quarter of
+// the warps along a 256-cell row hold one.  Here the x-interior cells
+// (1 <= i <= n0 - 2) of every row come first, then the two x-wall cells of
+// every row.  Rows with j or k on a wall are whole warps of wall cells.
+template <int D>
+__host__ __device__ inline int map_rows(const Geom& g) {
+  return g.n[1] * (D == 3 ? g.n[2] : 1);
+}
+
+template <int D>
+__host__ __device__ inline void row_jk(const Geom& g, int r, int* p) {
+  if (D == 3) {
+    p[2] = divm(r, g.n[1], g.m_n1);
+    p[1] = r - p[2] * g.n[1];
+  } else {
+    p[1] = r;
+    p[2] = 0;
+  }
+}
+
+// the wall slot w of the row list: side w & 1 of row w >> 1
+template <int D>
+__host__ __device__ inline bool xwall_cell(const Geom& g, int w, int* p) {
+  row_jk<D>(g, w >> 1, p);
+  p[0] = (w & 1) ? g.n[0] - 1 : 0;
+  return !((w & 1) && g.n[0] < 2);
+}
+
+// every cell: n0 - 2 interior slots per row, then the wall slots
+template <int D>
+__host__ __device__ inline int xi_count(const Geom& g) {
+  return ((g.n[0] > 2 ? g.n[0] - 2 : 0) + 2) * map_rows<D>(g);
+}
+
+template <int D>
+__host__ __device__ inline bool xi_cell(const Geom& g, int t, int* p) {
+  const int M = g.n[0] > 2 ? g.n[0] - 2 : 0;
+  const int ni = M * map_rows<D>(g);
+  if (t < ni) {
+    const int r = divm(t, M, g.m_xi);
+    row_jk<D>(g, r, p);
+    p[0] = 1 + t - r * M;
+    return true;
+  }
+  return xwall_cell<D>(g, t - ni, p);
+}
+
+// the cells of red-black colour col: (n0 - 1) / 2 interior slots per row
+// (i = 2 + 2m - q with q = (j + k + col) & 1, so that i + j + k + col is even),
+// then the wall slots, each taken when its cell has the colour
+template <int D>
+__host__ __device__ inline int rbx_count(const Geom& g) {
+  return ((g.n[0] - 1) / 2 + 2) * map_rows<D>(g);
+}
+
+template <int D>
+__host__ __device__ inline bool rbx_cell(const Geom& g, int t, int col, int* p) {
+  const int M = (g.n[0] - 1) / 2;
+  const int ni = M * map_rows<D>(g);
+  if (t < ni) {
+    const int r = divm(t, M, g.m_rbx);
+    row_jk<D>(g, r, p);
+    p[0] = 2 + 2 * (t - r * M) - ((p[1] + p[2] + col) & 1);
+    return p[0] <= g.n[0] - 2;
+  }
+  if (!xwall_cell<D>(g, t - ni, p)) return false;
+  return ((p[0] + p[1] + p[2] + col) & 1) == 0;
+}
+
+// Grid-stride over the cells of one colour (x-interior cells first); the
+// component is a template parameter so every a == C decision folds at compile
+// time.  (A grid-stride launch of about 24 blocks per SM measured faster than
+// one thread per cell.)
 template <int D, typename T, int C>
 __global__ void __launch_bounds__(256, 8) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
                                                       const T* ef1, const T* ef2, const __grid_constant__ Geom g, int col, T beta, int hom) {
-  const T* ef[3] = {ef0, ef1, ef2};
-  const int nt = rb_count<D>(g);
+  const int nt = rbx_count<D>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-    k_visc_smooth_c_at<D, T, C>(u, b, ef0, ef1, ef2, g, col, beta, hom, t);
+    int p[3];
+    if (rbx_cell<D>(g, t, col, p)) visc_smooth_cell<D, T, C>(u, b, ef0, ef1, ef2, g, beta, hom, p);
   }
 }
 
@@ -305,28 +384,32 @@ __host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, c
   visc_op_cell<D, T>(u, b, out, ef, g, beta, hom, p, t);
 }
 
-// out = u - beta L u, or r = b - (u - beta L u) when b != nullptr; 3D grid over cells
+// out = u - beta L u, or r = b - (u - beta L u) when b != nullptr; one thread
+// per cell, x-interior cells first (xi_cell), op3_blocks(g) blocks of 256
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_visc_op3(const T* __restrict__ u, const T* __restrict__ b,
                                                  T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
                                                  const __grid_constant__ Geom g, T beta, int hom) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= g.n[0] || j >= g.n[1]) return;
-  const int p[3] = {i, j, k};
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int p[3];
+  if (t >= xi_count<D>(g) || !xi_cell<D>(g, t, p)) return;
   const T* ef[3] = {ef0, ef1, ef2};
-  visc_op_cell<D, T>(u, b, out, ef, g, beta, hom, p, cidx<D>(g, i, j, k));
+  visc_op_cell<D, T>(u, b, out, ef, g, beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
 }
 
-// out = L_eta u (the stress divergence alone) at cell t; interior and wall
+template <int D>
+inline unsigned op3_blocks(const Geom& g) {
+  return (unsigned)((xi_count<D>(g) + 255) / 256);
+}
+
+// out = L_eta u (the stress divergence alone) at cell p; interior and wall
 // cells in separate branches as in visc_op_cell
 template <int D, typename T>
-__host__ __device__ __forceinline__ void k_tensor_lu_at(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
-                                                        const T* ef1, const T* ef2, const Geom& g, int hom, int t) {
+__host__ __device__ __forceinline__ void tensor_lu_cell(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
+                                                        const T* ef1, const T* ef2, const Geom& g, int hom,
+                                                        const int* p) {
   const T* ef[3] = {ef0, ef1, ef2};
-  int p[3];
-  cell_coords<D>(g, t, p[0], p[1], p[2]);
+  const int t = cidx<D>(g, p[0], p[1], p[2]);
   if (interior<D>(g, p)) {
     const Strides S = make_strides(g);
 #pragma unroll
@@ -337,13 +420,23 @@ __host__ __device__ __forceinline__ void k_tensor_lu_at(const T* __restrict__ u,
   }
 }
 
+// the same at flat cell index t (row-major map)
+template <int D, typename T>
+__host__ __device__ __forceinline__ void k_tensor_lu_at(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
+                                                        const T* ef1, const T* ef2, const Geom& g, int hom, int t) {
+  int p[3];
+  cell_coords<D>(g, t, p[0], p[1], p[2]);
+  tensor_lu_cell<D, T>(u, out, ef0, ef1, ef2, g, hom, p);
+}
+
+// grid-stride, x-interior cells first (xi_cell)
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_tensor_lu(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
                                                   const T* ef1, const T* ef2, const __grid_constant__ Geom g, int hom) {
-  const T* ef[3] = {ef0, ef1, ef2};
-  const Strides S = make_strides(g);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    k_tensor_lu_at<D, T>(u, out, ef0, ef1, ef2, g, hom, t);
+  const int nt = xi_count<D>(g);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    int p[3];
+    if (xi_cell<D>(g, t, p)) tensor_lu_cell<D, T>(u, out, ef0, ef1, ef2, g, hom, p);
   }
 }
 
