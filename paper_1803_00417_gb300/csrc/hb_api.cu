@@ -96,6 +96,7 @@ static int allocate(hbf_ctx* c) {
   A(c->mrhs, g.ncell);
   A(c->slopes, (long long)D * D * g.ncell);
   A(c->hats, (long long)D * D * g.ncell);
+  A(c->tcom, (long long)D * D * g.ncell);
   for (int a = 0; a < D; ++a) {
     A(c->uL[a], (long long)D * g.nface[a]);
     A(c->uR[a], (long long)D * g.nface[a]);
@@ -257,6 +258,7 @@ int hbf_init_grid(hbf_ctx** out, int dim, const int64_t n[3], double h, const do
   c->rheo.tau = 0.0;
   c->rheo.m = 1e4;
   c->rheo.reg_power = 1;
+  c->rheo.e2 = rheo_e2(1.0, 1);
   int st = allocate(c);
   if (st) {
     hbf_destroy(c);
@@ -321,6 +323,7 @@ int hbf_set_rheology(hbf_ctx* c, double K, double n, double tau_y, double m, int
   c->rheo.tau = tau_y;
   c->rheo.m = m;
   c->rheo.reg_power = reg_power ? 1 : 0;
+  c->rheo.e2 = rheo_e2(n, c->rheo.reg_power);
   return HBF_OK;
 }
 

@@ -54,28 +54,29 @@ struct OpSlopes {
 template <int D>
 struct OpHats {
   struct Arg {
-    const double* u;
-    const double* slopes;
-    double* hats;
+    const double *u, *slopes, *Gp, *Lu;
+    Force fo;
+    int pv;
+    double *hats, *tcom;
     Geom g;
     StepC k;
   };
-  static __device__ void apply(const Arg& a, int t, int) { k_hats_at<D>(a.u, a.slopes, a.hats, a.g, a.k, t); }
+  static __device__ void apply(const Arg& a, int t, int) {
+    k_hats_at<D>(a.u, a.slopes, a.Gp, a.Lu, a.fo, a.pv, a.hats, a.tcom, a.g, a.k, t);
+  }
 };
 
 template <int D>
 struct OpTraces {
   struct Arg {
-    const double *u, *slopes, *hats, *Gp, *Lu;
-    Force fo;
-    int pv;
+    const double *u, *slopes, *tcom;
     double *uL[3], *uR[3], *uadv[3];
     Geom g;
     StepC k;
   };
   static __device__ void apply(const Arg& a, int t, int) {
     const int ax = face_axis(a.g, t);
-    k_traces_at<D>(a.u, a.slopes, a.hats, a.Gp, a.Lu, a.fo, a.pv, ax, a.uL[ax], a.uR[ax], a.uadv[ax], a.g, a.k, t);
+    k_traces_at<D>(a.u, a.slopes, a.tcom, ax, a.uL[ax], a.uR[ax], a.uadv[ax], a.g, a.k, t);
   }
 };
 
@@ -177,9 +178,8 @@ static void build_tables(hbf_batch* B, ExplicitTables& T) {
     a2.push_back({c->eta, {c->lv[0].ef[0], c->lv[0].ef[1], c->lv[0].ef[2]}, c->g});
     a3.push_back({c->p, c->Gp, c->g});
     a4.push_back({c->u, c->slopes, c->g});
-    a5.push_back({c->u, c->slopes, c->hats, c->g, k});
-    a6.push_back({c->u, c->slopes, c->hats, c->Gp, c->Lu, fo, c->predictor_visc,
-                  {c->uL[0], c->uL[1], c->uL[2]}, {c->uR[0], c->uR[1], c->uR[2]},
+    a5.push_back({c->u, c->slopes, c->Gp, c->Lu, fo, c->predictor_visc, c->hats, c->tcom, c->g, k});
+    a6.push_back({c->u, c->slopes, c->tcom, {c->uL[0], c->uL[1], c->uL[2]}, {c->uR[0], c->uR[1], c->uR[2]},
                   {c->uadv[0], c->uadv[1], c->uadv[2]}, c->g, k});
     a7.push_back({{c->uadv[0], c->uadv[1], c->uadv[2]}, c->mrhs, c->g});
     a8.push_back({{c->uadv[0], c->uadv[1], c->uadv[2]}, c->phi_mac, {c->umac[0], c->umac[1], c->umac[2]}, c->g});

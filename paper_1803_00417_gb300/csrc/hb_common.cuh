@@ -113,7 +113,18 @@ struct Rheo {
   double tau;    // yield stress tau_y
   double m;      // Papanastasiou exponent 1/epsilon
   int reg_power; // 1: regularise the whole bracket (Eq. 23); 0: yield term only
+  int e2;        // twice the power-law exponent (n, or n - 1 without reg_power)
+                 // when it is an integer of magnitude <= 8, else kGeneralPow
 };
+
+constexpr int kGeneralPow = 1 << 20;
+
+// e2 of a flow index (host side, set with the rheology)
+inline int rheo_e2(double n, int reg_power) {
+  const double e2 = 2.0 * (reg_power ? n : n - 1.0);
+  const double r = (double)(long long)e2;
+  return (r == e2 && e2 >= -8.0 && e2 <= 8.0) ? (int)r : kGeneralPow;
+}
 
 template <int D>
 __host__ __device__ inline int cidx(const Geom& g, int i, int j, int k) {

@@ -41,10 +41,11 @@ int launch_predict(hbf_ctx* c, double dt) {
   if ((st = tensor_lu(c, c->u, c->Lu))) return st;
   HB_DISPATCH(c->dim, k_slopes, grid_for(g.ncell), c->u, c->slopes, g);
   const StepC k = step_consts(g, c->dim, dt, c->rho);
-  HB_DISPATCH(c->dim, k_hats, grid_for(g.ncell), c->u, c->slopes, c->hats, g, k);
+  HB_DISPATCH(c->dim, k_hats, grid_for(g.ncell), c->u, c->slopes, c->Gp, c->Lu, fo, c->predictor_visc, c->hats,
+              c->tcom, g, k);
   for (int a = 0; a < c->dim; ++a)
-    HB_DISPATCH(c->dim, k_traces, grid_for(g.nface[a]), c->u, c->slopes, c->hats, c->Gp, c->Lu, fo,
-                c->predictor_visc, a, c->uL[a], c->uR[a], c->uadv[a], g, k);
+    HB_DISPATCH(c->dim, k_traces, grid_for(g.nface[a]), c->u, c->slopes, c->tcom, a, c->uL[a], c->uR[a],
+                c->uadv[a], g, k);
   return cuda_check(c, cudaGetLastError(), "predict kernels");
 }
 

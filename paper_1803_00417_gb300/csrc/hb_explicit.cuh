@@ -6,48 +6,10 @@
 #include <cmath>
 #include <cstring>
 
+#include "hb_fp64bits.cuh"
 #include "hb_internal.h"
 
 namespace hb {
-
-// ---------------------------------------------------------------------------
-// FP64 comparisons on the integer pipe.  GB300 issues FP64 instructions at a
-// small fraction of its FP32/INT32 rate, and the limiter and upwind choices of
-// the predictor are comparisons: on the bit patterns they give the IEEE answer
-// for every non-NaN operand (+0 and -0 both count as zero).
-// ---------------------------------------------------------------------------
-constexpr unsigned long long kSignBit = 1ull << 63;
-
-__host__ __device__ __forceinline__ unsigned long long dbits(double x) {
-#ifdef __CUDA_ARCH__
-  return (unsigned long long)__double_as_longlong(x);
-#else
-  unsigned long long b;
-  std::memcpy(&b, &x, sizeof b);
-  return b;
-#endif
-}
-
-__host__ __device__ __forceinline__ double dfrom(unsigned long long b) {
-#ifdef __CUDA_ARCH__
-  return __longlong_as_double((long long)b);
-#else
-  double x;
-  std::memcpy(&x, &b, sizeof x);
-  return x;
-#endif
-}
-
-// x > 0, x < 0, x == 0
-__host__ __device__ __forceinline__ bool dpos(double x) { return (long long)dbits(x) > 0; }
-__host__ __device__ __forceinline__ bool dneg(double x) { return dbits(x) > kSignBit; }
-__host__ __device__ __forceinline__ bool dzero(double x) { return (dbits(x) << 1) == 0; }
-
-// min(|a|, |b|)
-__host__ __device__ __forceinline__ double dminabs(double a, double b) {
-  const unsigned long long ma = dbits(a) & ~kSignBit, mb = dbits(b) & ~kSignBit;
-  return dfrom(ma < mb ? ma : mb);
-}
 
 // The time-step constants of the explicit stages, rounded once on the host
 // (the stages multiply by them where the plain formulas divide).
@@ -78,6 +40,16 @@ inline StepC step_consts(const Geom& g, int dim, double dt, double rho) {
 // ---------------------------------------------------------------------------
 // Stage 1: strain rate and regularised viscosity (Eqs. 1, 21-23)
 // ---------------------------------------------------------------------------
+// g^(e2 / 2) for a half-integer exponent: products and one square root
+// (within 2 ulp; pow, which the general exponent takes, costs several times
+// as many FP64 instructions)
+__host__ __device__ inline double half_pow(double g, int e2) {
+  const int m = e2 < 0 ? -e2 : e2;
+  double v = (m & 1) ? sqrt(g) : 1.0;
+  for (int q = 0; q < (m >> 1); ++q) v *= g;
+  return e2 < 0 ? 1.0 / v : v;
+}
+
 __host__ __device__ inline double viscosity(double g, const Rheo& r) {
   double x = r.m * g;
   double F;
@@ -87,8 +59,9 @@ __host__ __device__ inline double viscosity(double g, const Rheo& r) {
   } else {
     F = -expm1(-x) / g;
   }
-  if (r.reg_power) return (r.c2 * pow(g, r.n) + 0.5 * r.tau) * F;
-  return r.c2 * pow(g, r.n - 1.0) + 0.5 * r.tau * F;
+  const bool half = r.e2 != kGeneralPow;
+  if (r.reg_power) return (r.c2 * (half ? half_pow(g, r.e2) : pow(g, r.n)) + 0.5 * r.tau) * F;
+  return r.c2 * (half ? half_pow(g, r.e2) : pow(g, r.n - 1.0)) + 0.5 * r.tau * F;
 }
 
 template <int D>
@@ -118,10 +91,10 @@ __host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, 
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int b = 0; b < D; ++b) {
-        double Dab = 0.5 * (G[a][b] + G[b][a]);
+        double Dab = dhalf(G[a][b] + G[b][a]);
         s += Dab * Dab;
       }
-    double gn = sqrt(0.5 * s);
+    double gn = sqrt(dhalf(s));
     eta[t] = viscosity(gn, r);
   }
 
@@ -143,7 +116,7 @@ __host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict
     L[a] -= 1;
     if (L[a] < 0) L[a] = 0;
     if (R[a] >= g.n[a]) R[a] = g.n[a] - 1;
-    ef[t] = 0.5 * (eta[cidx<D>(g, L[0], L[1], L[2])] + eta[cidx<D>(g, R[0], R[1], R[2])]);
+    ef[t] = dhalf(eta[cidx<D>(g, L[0], L[1], L[2])] + eta[cidx<D>(g, R[0], R[1], R[2])]);
   }
 
 template <int D>
@@ -182,11 +155,11 @@ __host__ __device__ inline double grad_nodal(const double* __restrict__ p, const
       qh[a] += 1;
       v[s1][s2] = (p[nidx(g, qh[0], qh[1], qh[2])] - p[nidx(g, q[0], q[1], q[2])]) * g.ih;
     }
-  if (D == 2) return 0.5 * (v[0][0] + v[1][0]);
+  if (D == 2) return dhalf(v[0][0] + v[1][0]);
   // average over o1 first, then o2
-  double w0 = 0.5 * (v[0][0] + v[1][0]);
-  double w1 = 0.5 * (v[0][1] + v[1][1]);
-  return 0.5 * (w0 + w1);
+  double w0 = dhalf(v[0][0] + v[1][0]);
+  double w1 = dhalf(v[0][1] + v[1][1]);
+  return dhalf(w0 + w1);
 }
 
 template <int D>
@@ -208,13 +181,6 @@ __global__ void k_grad_p(const double* __restrict__ p, double* __restrict__ Gp, 
 // ---------------------------------------------------------------------------
 // Stage 3: Godunov edge states (Eqs. 11-14)
 // ---------------------------------------------------------------------------
-__host__ __device__ inline double sgn_min(double v, double lim) {
-  // sign(v) * min(|v|, lim) with sign(0) = 0, for lim >= +0: the magnitude
-  // is the smaller bit pattern, the sign bit is v's
-  if (dzero(v)) return 0.0;
-  return dfrom(dbits(dminabs(v, lim)) | (dbits(v) & kSignBit));
-}
-
 // Colella's slope from the five values w[0..4] at offsets -2..2
 __host__ __device__ inline double slope5(const double* w) {
   double dlim[3], dC[3], df[3];
@@ -222,15 +188,14 @@ __host__ __device__ inline double slope5(const double* w) {
   for (int s = 0; s < 3; ++s) {  // cells p-1, p, p+1
     double dL = w[s + 1] - w[s];
     double dR = w[s + 2] - w[s + 1];
-    dC[s] = 0.5 * (w[s + 2] - w[s]);
+    dC[s] = dhalf(w[s + 2] - w[s]);
     // dL dR > 0 as a sign test (it differs from the product only where
     // |dL dR| underflows, below 1e-300, and then by less than 1e-150)
-    const bool same = !dzero(dL) && !dzero(dR) && !((dbits(dL) ^ dbits(dR)) & kSignBit);
-    dlim[s] = same ? 2.0 * dminabs(dL, dR) : 0.0;
-    df[s] = sgn_min(dC[s], dlim[s]);
+    dlim[s] = dsame_sign(dL, dR) ? dtwice(dminabs(dL, dR)) : 0.0;
+    df[s] = dsgn_min(dC[s], dlim[s]);
   }
   double d4 = (4.0 / 3.0) * dC[1] - (1.0 / 6.0) * (df[2] + df[0]);
-  return sgn_min(d4, dlim[1]);
+  return dsgn_min(d4, dlim[1]);
 }
 
 template <int D>
@@ -280,7 +245,7 @@ __host__ __device__ inline double riemann(double uL, double uR) {
 __host__ __device__ inline double upwind(double uL, double uR, double v) {
   if (dpos(v)) return uL;
   if (dneg(v)) return uR;
-  return 0.5 * (uL + uR);
+  return dhalf(uL + uR);
 }
 
 // Slope-only pre-states on the b-face between L and L+e_b (or wall values);
@@ -312,30 +277,60 @@ __host__ __device__ inline void prestate_face(const double* __restrict__ u, cons
   for (int c = 0; c < D; ++c) st[c] = (c == b) ? vb : upwind(sL[c], sR[c], vb);
 }
 
+struct Force {
+  double f[3];
+};
+
+// The transverse terms hat_{bc} of the cell (Eq. 13), and from them the part of
+// the cell's traces on its a-faces that does not depend on the face,
+// tcom_{ac} = -dt/2 sum_{b != a} hat_{bc} + dt/2 F_c with F the cell's force
+// (-G p [+ L_eta u] + f) / rho (Eq. 12).
 template <int D>
 __host__ __device__ __forceinline__ void k_hats_at(const double* __restrict__ u, const double* __restrict__ slopes,
-                       double* __restrict__ hats, const Geom& g, const StepC& k, int t) {
-  
-    int p[3];
-    cell_coords<D>(g, t, p[0], p[1], p[2]);
+                                                   const double* __restrict__ Gp, const double* __restrict__ Lu,
+                                                   const Force& fo, int pv, double* __restrict__ hats,
+                                                   double* __restrict__ tcom, const Geom& g, const StepC& k, int t) {
+  int p[3];
+  cell_coords<D>(g, t, p[0], p[1], p[2]);
+  double hat[3][3];
 #pragma unroll
-    for (int b = 0; b < D; ++b) {
-      double stHi[3], stLo[3], vHi, vLo;
-      prestate_face<D>(u, slopes, g, k, b, p, stHi, vHi);
-      int Lm[3] = {p[0], p[1], p[2]};
-      Lm[b] -= 1;
-      prestate_face<D>(u, slopes, g, k, b, Lm, stLo, vLo);
+  for (int b = 0; b < D; ++b) {
+    double stHi[3], stLo[3], vHi, vLo;
+    prestate_face<D>(u, slopes, g, k, b, p, stHi, vHi);
+    int Lm[3] = {p[0], p[1], p[2]};
+    Lm[b] -= 1;
+    prestate_face<D>(u, slopes, g, k, b, Lm, stLo, vLo);
 #pragma unroll
-      for (int c = 0; c < D; ++c)
-        hats[(size_t)(b * D + c) * g.ncell + t] = 0.5 * (vHi + vLo) * (stHi[c] - stLo[c]) * g.ih;
+    for (int c = 0; c < D; ++c) {
+      hat[b][c] = dhalf(vHi + vLo) * (stHi[c] - stLo[c]) * g.ih;
+      hats[(size_t)(b * D + c) * g.ncell + t] = hat[b][c];
     }
   }
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const size_t o = (size_t)c * g.ncell + t;
+    const double F = (-Gp[o] + (pv ? Lu[o] : 0.0) + fo.f[c]) * k.irho;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      // the sum over b != a in increasing b (with no leading 0.0 + : that
+      // changes at most the sign of a zero sum, which no later step sees)
+      const int b0 = a == 0 ? 1 : 0;
+      double trans = hat[b0][c];
+#pragma unroll
+      for (int b = b0 + 1; b < D; ++b)
+        if (b != a) trans += hat[b][c];
+      tcom[(size_t)(a * D + c) * g.ncell + t] = -k.hdt * trans + k.hdt * F;
+    }
+  }
+}
 
 template <int D>
 __global__ void k_hats(const double* __restrict__ u, const double* __restrict__ slopes,
-                       double* __restrict__ hats, const __grid_constant__ Geom g, const StepC k) {
+                       const double* __restrict__ Gp, const double* __restrict__ Lu, Force fo, int pv,
+                       double* __restrict__ hats, double* __restrict__ tcom, const __grid_constant__ Geom g,
+                       const StepC k) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    k_hats_at<D>(u, slopes, hats, g, k, t);
+    k_hats_at<D>(u, slopes, Gp, Lu, fo, pv, hats, tcom, g, k, t);
   }
 }
 
@@ -343,15 +338,9 @@ __global__ void k_hats(const double* __restrict__ u, const double* __restrict__ 
 // side = -1 (left state: face above q) or +1 (right state: face below q)
 template <int D>
 __host__ __device__ inline double trace(const double* __restrict__ u, const double* __restrict__ slopes,
-                               const double* __restrict__ hats, const double* __restrict__ Gp,
-                               const double* __restrict__ Lu, const double* f, int pv,
-                               const Geom& g, const StepC& k, int a, int c, int tq, bool left) {
-  double trans = 0.0;
-#pragma unroll
-  for (int b = 0; b < D; ++b)
-    if (b != a) trans += hats[(size_t)(b * D + c) * g.ncell + tq];
-  double F = (-Gp[(size_t)c * g.ncell + tq] + (pv ? Lu[(size_t)c * g.ncell + tq] : 0.0) + f[c]) * k.irho;
-  double common = -k.hdt * trans + k.hdt * F;
+                                        const double* __restrict__ tcom, const Geom& g, const StepC& k, int a, int c,
+                                        int tq, bool left) {
+  double common = tcom[(size_t)(a * D + c) * g.ncell + tq];
   double ua = u[(size_t)a * g.ncell + tq];
   double s = slopes[(size_t)(a * D + c) * g.ncell + tq];
   double uc = u[(size_t)c * g.ncell + tq];
@@ -363,14 +352,9 @@ __host__ __device__ inline double trace(const double* __restrict__ u, const doub
   return uc - fac * s + common;
 }
 
-struct Force {
-  double f[3];
-};
-
 template <int D>
 __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ u, const double* __restrict__ slopes,
-                         const double* __restrict__ hats, const double* __restrict__ Gp,
-                         const double* __restrict__ Lu, Force fo, int pv, int a,
+                         const double* __restrict__ tcom, int a,
                          double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
                          const Geom& g, const StepC& k, int t) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
@@ -394,8 +378,8 @@ __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ 
     double vl = 0, vr = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      double l = trace<D>(u, slopes, hats, Gp, Lu, fo.f, pv, g, k, a, c, tl, true);
-      double rr = trace<D>(u, slopes, hats, Gp, Lu, fo.f, pv, g, k, a, c, tr, false);
+      double l = trace<D>(u, slopes, tcom, g, k, a, c, tl, true);
+      double rr = trace<D>(u, slopes, tcom, g, k, a, c, tr, false);
       uL[(size_t)c * nf + t] = l;
       uR[(size_t)c * nf + t] = rr;
       if (c == a) {
@@ -408,14 +392,13 @@ __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ 
 
 template <int D>
 __global__ void k_traces(const double* __restrict__ u, const double* __restrict__ slopes,
-                         const double* __restrict__ hats, const double* __restrict__ Gp,
-                         const double* __restrict__ Lu, Force fo, int pv, int a,
+                         const double* __restrict__ tcom, int a,
                          double* __restrict__ uL, double* __restrict__ uR, double* __restrict__ uadv,
                          const __grid_constant__ Geom g, const StepC k) {
   int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   int nf = ex[0] * ex[1] * ex[2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf; t += gridDim.x * blockDim.x) {
-    k_traces_at<D>(u, slopes, hats, Gp, Lu, fo, pv, a, uL, uR, uadv, g, k, t);
+    k_traces_at<D>(u, slopes, tcom, a, uL, uR, uadv, g, k, t);
   }
 }
 
@@ -502,7 +485,7 @@ __host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restric
       q[a] += 1;
       int fhi = fidx(g, a, q[0], q[1], q[2]);
       double vlo = um[a][flo], vhi = um[a][fhi];
-      double vbar = 0.5 * (vhi + vlo);
+      double vbar = dhalf(vhi + vlo);
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         double thi = upwind(uL[a][(size_t)c * nf + fhi], uR[a][(size_t)c * nf + fhi], vhi);
@@ -513,7 +496,7 @@ __host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restric
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       size_t o = (size_t)c * g.ncell + t;
-      rhs[o] = u[o] - k.dt * A[c] + k.dtr * (-Gp[o] + 0.5 * Lu[o] + fo.f[c]);
+      rhs[o] = u[o] - k.dt * A[c] + k.dtr * (-Gp[o] + dhalf(Lu[o]) + fo.f[c]);
     }
   }
 

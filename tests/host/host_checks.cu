@@ -1,0 +1,135 @@
+// Host-side checks of integer helpers shared by the CUDA kernels, built and
+// run by tests/test_host_helpers.py (no GPU needed; the same functions run on
+// the device with the hi/lo register intrinsics in place of memcpy):
+//  * the FP64 sign tests, magnitude minimum, limiter clamp and exact x/2, 2x
+//    on bit patterns against plain IEEE arithmetic, bit for bit;
+//  * the thread -> cell maps that put x-wall cells in warps of their own:
+//    every cell (every cell of a red-black colour) exactly once, in range.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "hb_internal.h"
+#include "hb_fp64bits.cuh"
+#include "hb_mg_kernels.cuh"
+
+using namespace hb;
+
+static uint64_t bits(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, 8);
+  return b;
+}
+
+static int fails = 0;
+static void expect(bool ok, const char* what, double a, double b) {
+  if (!ok && fails++ < 20) std::printf("FAIL %s a=%a b=%a\n", what, a, b);
+}
+
+static double sample(std::mt19937_64& rng) {
+  std::uniform_int_distribution<int> kind(0, 9);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  std::uniform_int_distribution<uint64_t> any;
+  switch (kind(rng)) {
+    case 0: return 0.0;
+    case 1: return -0.0;
+    case 2: {  // subnormal
+      uint64_t b = any(rng) & 0x000fffffffffffffull;
+      if (any(rng) & 1) b |= 1ull << 63;
+      double x;
+      std::memcpy(&x, &b, 8);
+      return x;
+    }
+    case 3: return std::ldexp(nd(rng), -1022 + (int)(any(rng) % 3));  // around the normal boundary
+    case 4: return std::ldexp(nd(rng), 1020 + (int)(any(rng) % 4));   // near overflow
+    case 5: return (any(rng) & 1) ? INFINITY : -INFINITY;
+    case 6: {  // any finite pattern
+      uint64_t b;
+      double x;
+      do {
+        b = any(rng);
+        std::memcpy(&x, &b, 8);
+      } while (!std::isfinite(x));
+      return x;
+    }
+    default: return nd(rng) * std::ldexp(1.0, (int)(any(rng) % 40) - 20);
+  }
+}
+
+static void check_fp64bits() {
+  std::mt19937_64 rng(12345);
+  for (int it = 0; it < 2000000; ++it) {
+    const double a = sample(rng), b = (it & 7) == 0 ? a : ((it & 7) == 1 ? -a : sample(rng));
+    expect(dzero(a) == (a == 0.0), "dzero", a, 0);
+    expect(dpos(a) == (a > 0.0), "dpos", a, 0);
+    expect(dneg(a) == (a < 0.0), "dneg", a, 0);
+    expect(bits(dhalf(a)) == bits(a * 0.5), "dhalf", a, 0);
+    expect(bits(dtwice(a)) == bits(a * 2.0), "dtwice", a, 0);
+    if (std::isfinite(a) && std::isfinite(b)) {
+      expect(bits(dminabs(a, b)) == bits(std::fmin(std::fabs(a), std::fabs(b))), "dminabs", a, b);
+      const double p = a * b;
+      if (!(p == 0.0 && a != 0.0 && b != 0.0))  // the product underflowed
+        expect(dsame_sign(a, b) == (p > 0.0), "dsame_sign", a, b);
+      const double lim = std::fabs(b);
+      double want;
+      if (a == 0.0) {
+        want = 0.0;
+      } else {
+        const double m = std::fmin(std::fabs(a), lim);
+        want = a > 0.0 ? m : -m;
+      }
+      expect(bits(dsgn_min(a, lim)) == bits(want), "dsgn_min", a, lim);
+    }
+  }
+}
+
+template <int D>
+static void check_maps(int n0, int n1, int n2) {
+  Geom g{};
+  g.n[0] = n0;
+  g.n[1] = n1;
+  g.n[2] = D == 3 ? n2 : 1;
+  g.h = 1.0;
+  g.ncell = g.n[0] * g.n[1] * g.n[2];
+  geom_finish(g);
+  auto inside = [&](const int* p) {
+    return p[0] >= 0 && p[0] < g.n[0] && p[1] >= 0 && p[1] < g.n[1] && p[2] >= 0 && p[2] < g.n[2];
+  };
+  for (int col = 0; col < 2; ++col) {
+    std::vector<int> seen(g.ncell, 0);
+    for (int t = 0; t < rbx_count<D>(g); ++t) {
+      int p[3];
+      if (!rbx_cell<D>(g, t, col, p)) continue;
+      expect(inside(p), "rbx_cell range", n0, n1);
+      if (inside(p)) seen[cidx<D>(g, p[0], p[1], p[2])]++;
+    }
+    for (int k = 0; k < g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int i = 0; i < g.n[0]; ++i)
+          expect(seen[cidx<D>(g, i, j, k)] == (((i + j + k + col) & 1) == 0 ? 1 : 0), "rbx_cell colour", n0, n1);
+  }
+  std::vector<int> seen(g.ncell, 0);
+  for (int t = 0; t < xi_count<D>(g); ++t) {
+    int p[3];
+    if (!xi_cell<D>(g, t, p)) continue;
+    expect(inside(p), "xi_cell range", n0, n1);
+    if (inside(p)) seen[cidx<D>(g, p[0], p[1], p[2])]++;
+  }
+  for (int c = 0; c < g.ncell; ++c) expect(seen[c] == 1, "xi_cell once", n0, n1);
+}
+
+int main() {
+  check_fp64bits();
+  const int sizes[] = {1, 2, 3, 4, 5, 7, 8, 9, 16, 17, 33, 64};
+  for (int a : sizes)
+    for (int b : sizes) check_maps<2>(a, b, 1);
+  for (int a : sizes)
+    for (int b : {1, 2, 3, 8, 9})
+      for (int c : {1, 2, 5, 8}) check_maps<3>(a, b, c);
+  check_maps<3>(256, 256, 3);
+  std::printf("%s (%d failures)\n", fails ? "FAILED" : "ok", fails);
+  return fails ? 1 : 0;
+}
