@@ -29,7 +29,8 @@ struct Geom {
   float fih, fihh, fq4, fhh;
   float fwu[3][2][3];  // FP32 wall velocities
   unsigned long long m_n0, m_n1, m_e0, m_e1, m_rb, m_mc0[2], m_mc1[2];
-  unsigned long long m_rbx, m_xi;  // (n0 - 1) / 2 and n0 - 2: the x-interior cell maps
+  unsigned long long m_rbx, m_xi;    // (n0 - 1) / 2 and n0 - 2: the x-interior cell maps
+  unsigned long long m_rbxg, m_xig;  // their row-group sizes 16 M + 32
 };
 
 // Multiplier M for the exact quotient t / d = floor(t * M / 2^64) of any
@@ -68,6 +69,8 @@ __host__ __device__ inline void geom_finish(Geom& g) {
   g.m_rb = div_magic((unsigned)((g.n[0] + 1) / 2));
   g.m_rbx = div_magic((unsigned)((g.n[0] - 1) / 2));
   g.m_xi = div_magic((unsigned)(g.n[0] > 2 ? g.n[0] - 2 : 0));
+  g.m_rbxg = div_magic((unsigned)(16 * ((g.n[0] - 1) / 2) + 32));
+  g.m_xig = div_magic((unsigned)(16 * (g.n[0] > 2 ? g.n[0] - 2 : 0) + 32));
   for (int b = 0; b < 2; ++b) {
     g.m_mc0[b] = div_magic((unsigned)((g.n[0] + 1 - b + 1) / 2));
     g.m_mc1[b] = div_magic((unsigned)((g.n[1] + 1 - b + 1) / 2));

@@ -265,9 +265,15 @@ __host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, c
 // Thread -> cell maps that keep the x-wall cells out of the warps of x-interior
 // cells.  A warp holding one wall cell issues the wall stencil (ghost values,
 // many branches) on top of the interior one; in a row-major map a quarter of
-// the warps along a 256-cell row hold one.  Here the x-interior cells
-// (1 <= i <= n0 - 2) of every row come first, then the two x-wall cells of
-// every row.  Rows with j or k on a wall are whole warps of wall cells.
+// the warps along a 256-cell row hold one.  Rows are taken in groups of
+// kMapRows: the x-interior slots (1 <= i <= n0 - 2) of the group's rows, M per
+// row, then the group's 2 kMapRows wall slots (one warp's worth), so that a
+// wall cell is visited soon after the interior cells of its row, while their
+// cache lines are still in L2.  Rows with j or k on a wall are whole warps of
+// wall cells.  (The multipliers of M and of the group size 16 M + 32 are in
+// Geom; kMapRows is fixed at 16 to match.)
+constexpr int kMapRows = 16;
+
 template <int D>
 __host__ __device__ inline int map_rows(const Geom& g) {
   return g.n[1] * (D == 3 ? g.n[2] : 1);
@@ -284,52 +290,69 @@ __host__ __device__ inline void row_jk(const Geom& g, int r, int* p) {
   }
 }
 
-// the wall slot w of the row list: side w & 1 of row w >> 1
 template <int D>
-__host__ __device__ inline bool xwall_cell(const Geom& g, int w, int* p) {
-  row_jk<D>(g, w >> 1, p);
-  p[0] = (w & 1) ? g.n[0] - 1 : 0;
-  return !((w & 1) && g.n[0] < 2);
+__host__ __device__ inline int grouped_count(const Geom& g, int M) {
+  return (map_rows<D>(g) + kMapRows - 1) / kMapRows * (kMapRows * M + 2 * kMapRows);
 }
 
-// every cell: n0 - 2 interior slots per row, then the wall slots
+// slot t -> row and m: an interior slot 0 <= m < M, or the wall slot of side
+// -1 - m (x = 0 for m = -1, x = n0 - 1 for m = -2); false past the last row
+template <int D>
+__host__ __device__ inline bool grouped_slot(const Geom& g, int t, int M, unsigned long long mS,
+                                             unsigned long long mM, int& row, int& m) {
+  const int S = kMapRows * M + 2 * kMapRows;
+  const int grp = divm(t, S, mS);
+  int rem = t - grp * S;
+  if (rem < kMapRows * M) {
+    const int r = divm(rem, M, mM);
+    row = grp * kMapRows + r;
+    m = rem - r * M;
+  } else {
+    rem -= kMapRows * M;
+    row = grp * kMapRows + (rem >> 1);
+    m = -1 - (rem & 1);
+  }
+  return row < map_rows<D>(g);
+}
+
+// every cell: M = n0 - 2 interior slots per row (i = 1 + m)
 template <int D>
 __host__ __device__ inline int xi_count(const Geom& g) {
-  return ((g.n[0] > 2 ? g.n[0] - 2 : 0) + 2) * map_rows<D>(g);
+  return grouped_count<D>(g, g.n[0] > 2 ? g.n[0] - 2 : 0);
 }
 
 template <int D>
 __host__ __device__ inline bool xi_cell(const Geom& g, int t, int* p) {
-  const int M = g.n[0] > 2 ? g.n[0] - 2 : 0;
-  const int ni = M * map_rows<D>(g);
-  if (t < ni) {
-    const int r = divm(t, M, g.m_xi);
-    row_jk<D>(g, r, p);
-    p[0] = 1 + t - r * M;
+  int row, m;
+  if (!grouped_slot<D>(g, t, g.n[0] > 2 ? g.n[0] - 2 : 0, g.m_xig, g.m_xi, row, m)) return false;
+  row_jk<D>(g, row, p);
+  if (m >= 0) {
+    p[0] = 1 + m;
     return true;
   }
-  return xwall_cell<D>(g, t - ni, p);
+  p[0] = m == -1 ? 0 : g.n[0] - 1;
+  return !(m == -2 && g.n[0] < 2);
 }
 
-// the cells of red-black colour col: (n0 - 1) / 2 interior slots per row
-// (i = 2 + 2m - q with q = (j + k + col) & 1, so that i + j + k + col is even),
-// then the wall slots, each taken when its cell has the colour
+// the cells of red-black colour col: M = (n0 - 1) / 2 interior slots per row
+// (i = 2 + 2m - q with q = (j + k + col) & 1, so that i + j + k + col is
+// even), and the wall slots, each taken when its cell has the colour
 template <int D>
 __host__ __device__ inline int rbx_count(const Geom& g) {
-  return ((g.n[0] - 1) / 2 + 2) * map_rows<D>(g);
+  return grouped_count<D>(g, (g.n[0] - 1) / 2);
 }
 
 template <int D>
 __host__ __device__ inline bool rbx_cell(const Geom& g, int t, int col, int* p) {
-  const int M = (g.n[0] - 1) / 2;
-  const int ni = M * map_rows<D>(g);
-  if (t < ni) {
-    const int r = divm(t, M, g.m_rbx);
-    row_jk<D>(g, r, p);
-    p[0] = 2 + 2 * (t - r * M) - ((p[1] + p[2] + col) & 1);
+  int row, m;
+  if (!grouped_slot<D>(g, t, (g.n[0] - 1) / 2, g.m_rbxg, g.m_rbx, row, m)) return false;
+  row_jk<D>(g, row, p);
+  if (m >= 0) {
+    p[0] = 2 + 2 * m - ((p[1] + p[2] + col) & 1);
     return p[0] <= g.n[0] - 2;
   }
-  if (!xwall_cell<D>(g, t - ni, p)) return false;
+  p[0] = m == -1 ? 0 : g.n[0] - 1;
+  if (m == -2 && g.n[0] < 2) return false;
   return ((p[0] + p[1] + p[2] + col) & 1) == 0;
 }
 
@@ -387,7 +410,7 @@ __host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, c
 // out = u - beta L u, or r = b - (u - beta L u) when b != nullptr; one thread
 // per cell, x-interior cells first (xi_cell), op3_blocks(g) blocks of 256
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_visc_op3(const T* __restrict__ u, const T* __restrict__ b,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_visc_op3(const T* __restrict__ u, const T* __restrict__ b,
                                                  T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
                                                  const __grid_constant__ Geom g, T beta, int hom) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
