@@ -152,6 +152,7 @@ static int allocate(hbf_ctx* c) {
       A(L.fnb, gl.nnode);
       A(L.fnr, gl.nnode);
       for (int a = 0; a < D; ++a) A(L.fef[a], gl.nface[a]);
+      if (l == 0) A(L.feta, gl.ncell);
     }
     A(L.vb, (long long)D * gl.ncell);
     A(L.vr, (long long)D * gl.ncell);

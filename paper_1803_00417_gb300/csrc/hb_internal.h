@@ -30,6 +30,7 @@ struct Level {
   float* fvb = nullptr;
   float* fvr = nullptr;
   float* fef[3] = {nullptr, nullptr, nullptr};
+  float* feta = nullptr;  // level 0: the cell viscosity, whose face means the FP32 kernels form
   float* fcx = nullptr;
   float* fcb = nullptr;
   float* fcr = nullptr;

@@ -580,10 +580,25 @@ struct ViscProblem : Problem<T> {
     const int slot = l == 0 ? kSlotViscSmooth : kSlotCoarse;
     const dim3 blk(kThreads, 1, 1);
     const dim3 grd((unsigned)grid_for(rbx_count<D>(L.g), 152 * 24), 1, 1);
+    const int hm = (int)this->hom(l);
+    if (cell_eta(l)) {
+      // FP32 finest level: face viscosities from the cell viscosity
+      const T* e0 = (const T*)L.feta;
+      for (int col = 0; col < 2; ++col)
+        launch3(c, slot, k_visc_smooth_c<D, T, 0, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+                (T)beta, hm);
+      for (int col = 0; col < 2; ++col)
+        launch3(c, slot, k_visc_smooth_c<D, T, 1, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+                (T)beta, hm);
+      if (D == 3)
+        for (int col = 0; col < 2; ++col)
+          launch3(c, slot, k_visc_smooth_c<D, T, 2, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+                  (T)beta, hm);
+      return;
+    }
     const T* e0 = View<T>::ef(L, 0);
     const T* e1 = View<T>::ef(L, 1);
     const T* e2 = View<T>::ef(L, 2);
-    const int hm = (int)this->hom(l);
     for (int col = 0; col < 2; ++col)
       launch3(c, slot, k_visc_smooth_c<D, T, 0>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
     for (int col = 0; col < 2; ++col)
@@ -593,10 +608,18 @@ struct ViscProblem : Problem<T> {
         launch3(c, slot, k_visc_smooth_c<D, T, 2>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta,
                 hm);
   }
+  // the FP32 finest level forms its face viscosities from the cell viscosity
+  bool cell_eta(int l) const { return l == 0 && sizeof(T) == 4 && c->lv[0].feta != nullptr; }
   void resid(int l) override {
     Level& L = c->lv[l];
     const dim3 blk(256, 1, 1);
     const dim3 grd(op3_blocks<D>(L.g), 1, 1);
+    if (cell_eta(l)) {
+      const T* e0 = (const T*)L.feta;
+      launch3(c, kSlotViscResid, k_visc_op3<D, T, true>, grd, blk, (const T*)x(l), (const T*)b(l), r(l), e0, e0, e0,
+              L.g, (T)beta, (int)this->hom(l));
+      return;
+    }
     launch3(c, l == 0 ? kSlotViscResid : kSlotCoarse, k_visc_op3<D, T>, grd, blk, (const T*)x(l), (const T*)b(l), r(l),
             (const T*)View<T>::ef(L, 0), (const T*)View<T>::ef(L, 1), (const T*)View<T>::ef(L, 2), L.g, (T)beta,
             (int)this->hom(l));
@@ -819,11 +842,19 @@ static void build_eta_levels(hbf_ctx* c) {
       launch(c, kSlotTransfer, k_restrict_faces<D, double>, grid_for(C.g.nface[a]), kThreads, (const double*)F.ef[a],
              C.ef[a], a, F.g, C.g);
   }
-  if (c->precision == HBF_MIXED)
-    for (auto& L : c->lv)
+  if (c->precision == HBF_MIXED) {
+    for (size_t l = 1; l < c->lv.size(); ++l) {
+      Level& L = c->lv[l];
       for (int a = 0; a < D; ++a)
         launch(c, kSlotTransfer, k_convert<float, double>, grid_for(L.g.nface[a]), kThreads, L.fef[a],
                (const double*)L.ef[a], (long long)L.g.nface[a]);
+    }
+    // the finest level of the FP32 V-cycles reads the cell viscosity (the
+    // level-0 faces are the means of its cells, wall faces the interior cell)
+    Level& L0 = c->lv[0];
+    launch(c, kSlotTransfer, k_convert<float, double>, grid_for(L0.g.ncell), kThreads, L0.feta,
+           (const double*)c->eta, (long long)L0.g.ncell);
+  }
 }
 
 // BiCGStab (van der Vorst 1992) on (I - beta L_eta) u = b, right-preconditioned
@@ -868,8 +899,9 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
   const dim3 blk(256, 1, 1);
   const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
   auto apply0 = [&](const float* q, float* o) {
-    launch3(c, kSlotViscResid, k_visc_op3<D, float>, grd, blk, q, (const float*)nullptr, o, (const float*)L0.fef[0],
-            (const float*)L0.fef[1], (const float*)L0.fef[2], L0.g, fbeta, 1);
+    const float* e0 = L0.feta;
+    launch3(c, kSlotViscResid, k_visc_op3<D, float, true>, grd, blk, q, (const float*)nullptr, o, e0, e0, e0, L0.g,
+            fbeta, 1);
   };
   if ((st = cuda_check(c, cudaMemcpyAsync(kb, b_in, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy rhs")))
     return st;

@@ -18,6 +18,36 @@ namespace hb {
 // ---------------------------------------------------------------------------
 // tensor viscous operator pieces (mirrors the explicit-stage operator)
 // ---------------------------------------------------------------------------
+struct Strides;
+
+// The face viscosities of a level, stored per face (FaceEta), or, on the
+// finest level of the FP32 V-cycles, formed where they are used as the mean
+// of the two cells' viscosities (CellEta: the rule that makes the stored
+// finest-level faces, wall faces taking the interior cell; one cell array is
+// read instead of D face arrays).
+//   lo / hi: the face of axis a below / above interior cell p (flat index id)
+//   at:      the face of axis a whose upper cell is q (q[a] may be n[a])
+template <typename T>
+struct FaceEta {
+  const T* const* ef;
+  __host__ __device__ T lo(const Geom& g, const Strides& S, int a, const int* p, int id) const;
+  __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
+  __host__ __device__ T at(const Geom& g, int a, const int* q) const { return ef[a][fidx(g, a, q[0], q[1], q[2])]; }
+};
+
+template <typename T>
+struct CellEta {
+  const T* eta;
+  __host__ __device__ T lo(const Geom& g, const Strides& S, int a, const int* p, int id) const;
+  __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
+  __host__ __device__ T at(const Geom& g, int a, const int* q) const {
+    int L[3] = {q[0], q[1], q[2]}, R[3] = {q[0], q[1], q[2]};
+    L[a] = q[a] > 0 ? q[a] - 1 : 0;
+    R[a] = q[a] < g.n[a] ? q[a] : g.n[a] - 1;
+    return T(0.5) * (eta[cidx<3>(g, L[0], L[1], L[2])] + eta[cidx<3>(g, R[0], R[1], R[2])]);
+  }
+};
+
 template <int D, typename T>
 __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
                                   bool hom) {
@@ -33,8 +63,8 @@ __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom&
   return (dL + dR) * g_q4<T>(g);
 }
 
-template <int D, typename T>
-__host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const T* const* ef, const Geom& g, int c,
+template <int D, typename T, typename EF>
+__host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& ef, const Geom& g, int c,
                                     const int* p, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
   T acc = T(0);
@@ -48,7 +78,7 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const T* c
       L[a] += s - 1;
       int R[3] = {L[0], L[1], L[2]};
       R[a] += 1;
-      T e = ef[a][fidx(g, a, R[0], R[1], R[2])];
+      T e = ef.at(g, a, R);
       T nrm = (uget<D>(uc, g, c, R[0], R[1], R[2], hom) - uget<D>(uc, g, c, L[0], L[1], L[2], hom)) * ih;
       if (a == c)
         flux[s] = e * (T(2) * nrm);
@@ -61,8 +91,8 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const T* c
 }
 
 // Gauss-Seidel update of component c at cell p (all other values frozen)
-template <int D, typename T>
-__host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
+template <int D, typename T, typename EF>
+__host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const EF& ef,
                                   const Geom& g, int c, const int* p, T beta, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
   const T ih = g_ih<T>(g);
@@ -81,7 +111,7 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
         q[a] += 1;
         fq[a] += 1;
       }
-      T wf = kappa * ef[a][fidx(g, a, fq[0], fq[1], fq[2])] * ihh;
+      T wf = kappa * ef.at(g, a, fq) * ihh;
       bool wall = (s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1);
       if (wall) {
         T ub = hom ? T(0) : g_wu<T>(g, a, s, c);
@@ -102,8 +132,8 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
     Llo[a] -= 1;
     int fhi[3] = {p[0], p[1], p[2]};
     fhi[a] += 1;
-    T fluxhi = ef[a][fidx(g, a, fhi[0], fhi[1], fhi[2])] * mg_face_cross<D, T>(ua, g, a, c, p, hom);
-    T fluxlo = ef[a][fidx(g, a, p[0], p[1], p[2])] * mg_face_cross<D, T>(ua, g, a, c, Llo, hom);
+    T fluxhi = ef.at(g, a, fhi) * mg_face_cross<D, T>(ua, g, a, c, p, hom);
+    T fluxlo = ef.at(g, a, p) * mg_face_cross<D, T>(ua, g, a, c, Llo, hom);
     cross += (fluxhi - fluxlo) * ih;
   }
   return (b[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] + beta * (offd + cross)) /
@@ -130,6 +160,30 @@ __host__ __device__ inline Strides make_strides(const Geom& g) {
   return st;
 }
 
+template <typename T>
+__host__ __device__ __forceinline__ T FaceEta<T>::lo(const Geom& g, const Strides& S, int a, const int* p, int id) const {
+  (void)S;
+  (void)id;
+  return ef[a][fidx(g, a, p[0], p[1], p[2])];
+}
+template <typename T>
+__host__ __device__ __forceinline__ T FaceEta<T>::hi(const Geom& g, const Strides& S, int a, const int* p, int id) const {
+  (void)id;
+  return ef[a][fidx(g, a, p[0], p[1], p[2]) + S.fs[a][a]];
+}
+template <typename T>
+__host__ __device__ __forceinline__ T CellEta<T>::lo(const Geom& g, const Strides& S, int a, const int* p, int id) const {
+  (void)g;
+  (void)p;
+  return T(0.5) * (eta[id - S.s[a]] + eta[id]);
+}
+template <typename T>
+__host__ __device__ __forceinline__ T CellEta<T>::hi(const Geom& g, const Strides& S, int a, const int* p, int id) const {
+  (void)g;
+  (void)p;
+  return T(0.5) * (eta[id] + eta[id + S.s[a]]);
+}
+
 template <int D>
 __host__ __device__ inline bool interior(const Geom& g, const int* p) {
   bool in = p[0] >= 1 && p[0] <= g.n[0] - 2 && p[1] >= 1 && p[1] <= g.n[1] - 2;
@@ -139,25 +193,28 @@ __host__ __device__ inline bool interior(const Geom& g, const int* p) {
 
 // The same Gauss-Seidel update as visc_gs_point for a cell whose whole
 // stencil is inside the domain: direct strided indexing, no ghost logic.
-template <int D, typename T>
-__host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, const T* __restrict__ b, const T* const* ef,
+template <int D, typename T, typename EF>
+__host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, const T* __restrict__ b, const EF& ef,
                                               const Geom& g, const Strides& S, int c, const int* p, T beta) {
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
   const T ih = g_ih<T>(g);
   const T ihh = g_ihh<T>(g);
   const T q = g_q4<T>(g);
-  int fid[3];
+  T elo[3], ehi[3];
 #pragma unroll
-  for (int a = 0; a < D; ++a) fid[a] = fidx(g, a, p[0], p[1], p[2]);
+  for (int a = 0; a < D; ++a) {
+    elo[a] = ef.lo(g, S, a, p, id);
+    ehi[a] = ef.hi(g, S, a, p, id);
+  }
   T offd = T(0), diag = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T kappa = (a == c) ? T(2) : T(1);
-    T wlo = kappa * ef[a][fid[a]] * ihh;
+    T wlo = kappa * elo[a] * ihh;
     offd += wlo * uc[id - S.s[a]];
     diag += wlo;
-    T whi = kappa * ef[a][fid[a] + S.fs[a][a]] * ihh;
+    T whi = kappa * ehi[a] * ihh;
     offd += whi * uc[id + S.s[a]];
     diag += whi;
   }
@@ -170,8 +227,8 @@ __host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, 
     T mid = ua[id + sc] - ua[id - sc];
     T xhi = (mid + (ua[id + sa + sc] - ua[id + sa - sc])) * q;
     T xlo = ((ua[id - sa + sc] - ua[id - sa - sc]) + mid) * q;
-    T fluxhi = ef[a][fid[a] + S.fs[a][a]] * xhi;
-    T fluxlo = ef[a][fid[a]] * xlo;
+    T fluxhi = ehi[a] * xhi;
+    T fluxlo = elo[a] * xlo;
     cross += (fluxhi - fluxlo) * ih;
   }
   return (b[(size_t)c * g.ncell + id] + beta * (offd + cross)) / (T(1) + beta * diag);
@@ -180,8 +237,8 @@ __host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, 
 // (L_eta u)_c for an interior cell: the operator of mg_tensor_point with the
 // 1/h of the differences and of the divergence taken out as one factor 1/h^2
 // (fewer multiplications; the FP64 residuals are bound by GB300's FP64 rate)
-template <int D, typename T>
-__host__ __device__ __forceinline__ T tensor_interior(const T* __restrict__ u, const T* const* ef, const Geom& g,
+template <int D, typename T, typename EF>
+__host__ __device__ __forceinline__ T tensor_interior(const T* __restrict__ u, const EF& ef, const Geom& g,
                                              const Strides& S, int c, const int* p) {
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
@@ -189,22 +246,22 @@ __host__ __device__ __forceinline__ T tensor_interior(const T* __restrict__ u, c
   T acc = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const int fid = fidx(g, a, p[0], p[1], p[2]);
     const int sa = S.s[a];
+    const T elo = ef.lo(g, S, a, p, id), ehi = ef.hi(g, S, a, p, id);
     const T dlo = u0 - uc[id - sa];
     const T dhi = uc[id + sa] - u0;
     T flo, fhi;
     if (a == c) {
-      flo = ef[a][fid] * (T(2) * dlo);
-      fhi = ef[a][fid + S.fs[a][a]] * (T(2) * dhi);
+      flo = elo * (T(2) * dlo);
+      fhi = ehi * (T(2) * dhi);
     } else {
       const T* ua = u + (size_t)a * g.ncell;
       const int sc = S.s[c];
       const T mid = ua[id + sc] - ua[id - sc];
       const T xhi = mid + (ua[id + sa + sc] - ua[id + sa - sc]);
       const T xlo = (ua[id - sa + sc] - ua[id - sa - sc]) + mid;
-      flo = ef[a][fid] * (dlo + T(0.25) * xlo);
-      fhi = ef[a][fid + S.fs[a][a]] * (dhi + T(0.25) * xhi);
+      flo = elo * (dlo + T(0.25) * xlo);
+      fhi = ehi * (dhi + T(0.25) * xhi);
     }
     acc += fhi - flo;
   }
@@ -238,11 +295,9 @@ __host__ __device__ inline int rb_count(const Geom& g) {
 }
 
 // Gauss-Seidel update of component C at cell p of the current colour
-template <int D, typename T, int C>
-__host__ __device__ __forceinline__ void visc_smooth_cell(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
-                                                          const T* ef1, const T* ef2, const Geom& g, T beta, int hom,
-                                                          const int* p) {
-  const T* ef[3] = {ef0, ef1, ef2};
+template <int D, typename T, int C, typename EF>
+__host__ __device__ __forceinline__ void visc_smooth_cell(T* __restrict__ u, const T* __restrict__ b, const EF& ef,
+                                                          const Geom& g, T beta, int hom, const int* p) {
   T v;
   if (interior<D>(g, p)) {
     const Strides S = make_strides(g);
@@ -259,7 +314,8 @@ __host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, c
                                                            int hom, int t) {
   int p[3];
   if (!rb_cell<D>(g, t, col, p)) return;
-  visc_smooth_cell<D, T, C>(u, b, ef0, ef1, ef2, g, beta, hom, p);
+  const T* ef[3] = {ef0, ef1, ef2};
+  visc_smooth_cell<D, T, C>(u, b, FaceEta<T>{ef}, g, beta, hom, p);
 }
 
 // Thread -> cell maps that keep the x-wall cells out of the warps of x-interior
@@ -359,23 +415,29 @@ __host__ __device__ inline bool rbx_cell(const Geom& g, int t, int col, int* p) 
 // Grid-stride over the cells of one colour (x-interior cells first); the
 // component is a template parameter so every a == C decision folds at compile
 // time.  (A grid-stride launch of about 24 blocks per SM measured faster than
-// one thread per cell.)
-template <int D, typename T, int C>
-__global__ void __launch_bounds__(256, 8) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
+// one thread per cell.)  CE: ef0 is the cell viscosity (CellEta), else the
+// face arrays.
+template <int D, typename T, int C, bool CE = false>
+__global__ void __launch_bounds__(256, CE ? 6 : 8) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
                                                       const T* ef1, const T* ef2, const __grid_constant__ Geom g, int col, T beta, int hom) {
   const int nt = rbx_count<D>(g);
+  const T* ef[3] = {ef0, ef1, ef2};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
     int p[3];
-    if (rbx_cell<D>(g, t, col, p)) visc_smooth_cell<D, T, C>(u, b, ef0, ef1, ef2, g, beta, hom, p);
+    if (!rbx_cell<D>(g, t, col, p)) continue;
+    if (CE)
+      visc_smooth_cell<D, T, C>(u, b, CellEta<T>{ef0}, g, beta, hom, p);
+    else
+      visc_smooth_cell<D, T, C>(u, b, FaceEta<T>{ef}, g, beta, hom, p);
   }
 }
 
 // out = u - beta L u, or r = b - (u - beta L u) when b != nullptr, for every
 // component of cell p (flat index t).  Interior cells and wall cells are two
 // separate branches (warps are almost always uniform).
-template <int D, typename T>
+template <int D, typename T, typename EF>
 __host__ __device__ __forceinline__ void visc_op_cell(const T* __restrict__ u, const T* __restrict__ b,
-                                                     T* __restrict__ out, const T* const* ef, const Geom& g, T beta,
+                                                     T* __restrict__ out, const EF& ef, const Geom& g, T beta,
                                                      int hom, const int* p, int t) {
   if (interior<D>(g, p)) {
     const Strides S = make_strides(g);
@@ -404,20 +466,24 @@ __host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, c
   const T* ef[3] = {ef0, ef1, ef2};
   int p[3];
   cell_coords<D>(g, t, p[0], p[1], p[2]);
-  visc_op_cell<D, T>(u, b, out, ef, g, beta, hom, p, t);
+  visc_op_cell<D, T>(u, b, out, FaceEta<T>{ef}, g, beta, hom, p, t);
 }
 
 // out = u - beta L u, or r = b - (u - beta L u) when b != nullptr; one thread
-// per cell, x-interior cells first (xi_cell), op3_blocks(g) blocks of 256
-template <int D, typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_visc_op3(const T* __restrict__ u, const T* __restrict__ b,
+// per cell, x-interior cells first (xi_cell), op3_blocks(g) blocks of 256.
+// CE: ef0 is the cell viscosity (CellEta), else the face arrays.
+template <int D, typename T, bool CE = false>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CE ? 4 : 5) : 4) k_visc_op3(const T* __restrict__ u, const T* __restrict__ b,
                                                  T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
                                                  const __grid_constant__ Geom g, T beta, int hom) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   int p[3];
   if (t >= xi_count<D>(g) || !xi_cell<D>(g, t, p)) return;
   const T* ef[3] = {ef0, ef1, ef2};
-  visc_op_cell<D, T>(u, b, out, ef, g, beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
+  if (CE)
+    visc_op_cell<D, T>(u, b, out, CellEta<T>{ef0}, g, beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
+  else
+    visc_op_cell<D, T>(u, b, out, FaceEta<T>{ef}, g, beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
 }
 
 template <int D>
@@ -431,7 +497,8 @@ template <int D, typename T>
 __host__ __device__ __forceinline__ void tensor_lu_cell(const T* __restrict__ u, T* __restrict__ out, const T* ef0,
                                                         const T* ef1, const T* ef2, const Geom& g, int hom,
                                                         const int* p) {
-  const T* ef[3] = {ef0, ef1, ef2};
+  const T* efa[3] = {ef0, ef1, ef2};
+  const FaceEta<T> ef{efa};
   const int t = cidx<D>(g, p[0], p[1], p[2]);
   if (interior<D>(g, p)) {
     const Strides S = make_strides(g);
@@ -475,7 +542,7 @@ __global__ void k_visc_bottom(T* __restrict__ u, const T* __restrict__ b, const 
         for (int t = threadIdx.x; t < nt; t += blockDim.x) {
           int p[3];
           if (!rb_cell<D>(g, t, col, p)) continue;
-          T v = visc_gs_point<D, T>(u, b, ef, g, c, p, beta, hom != 0);
+          T v = visc_gs_point<D, T>(u, b, FaceEta<T>{ef}, g, c, p, beta, hom != 0);
           u[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
         }
         __syncthreads();
@@ -955,7 +1022,7 @@ __device__ inline void dense_build_col(int kind, double* __restrict__ X, double*
     if (kind == 0) {
       const int c = i / g.ncell, t = i % g.ncell;
       cell_coords<D>(g, t, p[0], p[1], p[2]);
-      v = e[i] - beta * mg_tensor_point<D, double>(e, ef, g, c, p, true);
+      v = e[i] - beta * mg_tensor_point<D, double>(e, FaceEta<double>{ef}, g, c, p, true);
     } else if (kind == 1) {
       cell_coords<D>(g, i, p[0], p[1], p[2]);
       v = cell_lap_point<D, double>(e, g, p);
