@@ -97,6 +97,7 @@ static int allocate(hbf_ctx* c) {
   A(c->slopes, (long long)D * D * g.ncell);
   A(c->hats, (long long)D * D * g.ncell);
   A(c->tcom, (long long)D * D * g.ncell);
+  A(c->wn, (long long)D * g.ncell);
   for (int a = 0; a < D; ++a) {
     A(c->uL[a], (long long)D * g.nface[a]);
     A(c->uR[a], (long long)D * g.nface[a]);

@@ -122,14 +122,25 @@ struct OpAdvectRhs {
 };
 
 template <int D>
+struct OpGradPW {
+  struct Arg {
+    const double *p, *ustar;
+    double *Gp, *w;
+    Geom g;
+    StepC k;
+  };
+  static __device__ void apply(const Arg& a, int t, int) { k_grad_p_w_at<D>(a.p, a.ustar, a.Gp, a.w, a.g, a.k, t); }
+};
+
+template <int D>
 struct OpNodalRhs {
   struct Arg {
-    const double *ustar, *Gp;
+    const double* w;
     double* out;
     Geom g;
     StepC k;
   };
-  static __device__ void apply(const Arg& a, int t, int) { k_nodal_rhs_at<D>(a.ustar, a.Gp, a.out, a.g, a.k, t); }
+  static __device__ void apply(const Arg& a, int t, int) { k_nodal_rhs_at<D>(a.w, a.out, a.g, a.k, t); }
 };
 
 template <int D>
@@ -154,7 +165,7 @@ static void* table(hbf_batch* B, const std::vector<typename Op::Arg>& h) {
 }
 
 struct ExplicitTables {
-  void *eta, *ef, *gp, *slopes, *hats, *traces, *macrhs, *maccorr, *advect, *nrhs, *update;
+  void *eta, *ef, *gp, *gpw, *slopes, *hats, *traces, *macrhs, *maccorr, *advect, *nrhs, *update;
 };
 
 template <int D>
@@ -169,6 +180,7 @@ static void build_tables(hbf_batch* B, ExplicitTables& T) {
   std::vector<typename OpMacCorrect<D>::Arg> a8;
   std::vector<typename OpAdvectRhs<D>::Arg> a9;
   std::vector<typename OpNodalRhs<D>::Arg> a10;
+  std::vector<typename OpGradPW<D>::Arg> a12;
   std::vector<typename OpProjectUpdate<D>::Arg> a11;
   for (int i = 0; i < B->ncav; ++i) {
     hbf_ctx* c = B->cav[i];
@@ -185,7 +197,8 @@ static void build_tables(hbf_batch* B, ExplicitTables& T) {
     a8.push_back({{c->uadv[0], c->uadv[1], c->uadv[2]}, c->phi_mac, {c->umac[0], c->umac[1], c->umac[2]}, c->g});
     a9.push_back({c->u, {c->uL[0], c->uL[1], c->uL[2]}, {c->uR[0], c->uR[1], c->uR[2]},
                   {c->umac[0], c->umac[1], c->umac[2]}, c->Gp, c->Lu, fo, c->rhs, c->g, k});
-    a10.push_back({c->ustar, c->Gp, c->nrhs, c->g, k});
+    a10.push_back({c->wn, c->nrhs, c->g, k});
+    a12.push_back({c->p, c->ustar, c->Gp, c->wn, c->g, k});
     a11.push_back({c->ustar, c->Gp, c->p, c->g, k});
   }
   T.eta = table<OpEta<D>>(B, a1);
@@ -198,6 +211,7 @@ static void build_tables(hbf_batch* B, ExplicitTables& T) {
   T.maccorr = table<OpMacCorrect<D>>(B, a8);
   T.advect = table<OpAdvectRhs<D>>(B, a9);
   T.nrhs = table<OpNodalRhs<D>>(B, a10);
+  T.gpw = table<OpGradPW<D>>(B, a12);
   T.update = table<OpProjectUpdate<D>>(B, a11);
 }
 
@@ -241,7 +255,7 @@ static void post(hbf_batch* B, BatchExplicit* E) {
 
 template <int D>
 static void nodal_rhs(hbf_batch* B, BatchExplicit* E) {
-  run<OpGradP<D>>(B, E->t.gp, B->H[0][kCells], B->mask_all);
+  run<OpGradPW<D>>(B, E->t.gpw, B->H[0][kCells], B->mask_all);
   run<OpNodalRhs<D>>(B, E->t.nrhs, B->H[0][kNodes], B->mask_all);
 }
 

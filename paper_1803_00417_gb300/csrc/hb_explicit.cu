@@ -69,9 +69,9 @@ int launch_advect_rhs(hbf_ctx* c, double dt) {
 }
 
 int launch_nodal_rhs(hbf_ctx* c, double dt, const double* ustar, const double* p, double* out) {
-  HB_DISPATCH(c->dim, k_grad_p, grid_for(c->g.ncell), p, c->Gp, c->g);
-  HB_DISPATCH(c->dim, k_nodal_rhs, grid_for(c->g.nnode), ustar, c->Gp, out, c->g,
-              step_consts(c->g, c->dim, dt, c->rho));
+  const StepC k = step_consts(c->g, c->dim, dt, c->rho);
+  HB_DISPATCH(c->dim, k_grad_p_w, grid_for(c->g.ncell), p, ustar, c->Gp, c->wn, c->g, k);
+  HB_DISPATCH(c->dim, k_nodal_rhs, grid_for(c->g.nnode), (const double*)c->wn, out, c->g, k);
   return cuda_check(c, cudaGetLastError(), "k_nodal_rhs");
 }
 

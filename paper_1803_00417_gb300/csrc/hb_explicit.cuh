@@ -518,9 +518,36 @@ __global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, co
 // ---------------------------------------------------------------------------
 // Stage 7: nodal divergence of u*/dt + G p/rho, projection update
 // ---------------------------------------------------------------------------
+// G p of the cell from the nodes, and the cell field the nodal divergence
+// takes, w = u*/dt + (G p)/rho, formed once per cell instead of at each of
+// the cell's 2^D nodes
 template <int D>
-__host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict__ ustar, const double* __restrict__ Gp,
-                            double* __restrict__ out, const Geom& g, const StepC& k, int t) {
+__host__ __device__ __forceinline__ void k_grad_p_w_at(const double* __restrict__ p, const double* __restrict__ ustar,
+                                                       double* __restrict__ Gp, double* __restrict__ w, const Geom& g,
+                                                       const StepC& k, int t) {
+  int i, j, kk;
+  cell_coords<D>(g, t, i, j, kk);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const size_t o = (size_t)a * g.ncell + t;
+    const double gp = grad_nodal<D>(p, g, a, i, j, kk);
+    Gp[o] = gp;
+    w[o] = ustar[o] * k.idt + gp * k.irho;
+  }
+}
+
+template <int D>
+__global__ void k_grad_p_w(const double* __restrict__ p, const double* __restrict__ ustar, double* __restrict__ Gp,
+                           double* __restrict__ w, const __grid_constant__ Geom g, const StepC k) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
+    k_grad_p_w_at<D>(p, ustar, Gp, w, g, k, t);
+  }
+}
+
+// the nodal right-hand side: the divergence of w over the node's 2^D cells
+template <int D>
+__host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict__ w, double* __restrict__ out,
+                                                        const Geom& g, const StepC& k, int t) {
   int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
   
     int p[3];
@@ -546,8 +573,7 @@ __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict
         bool in = q[0] >= 0 && q[0] < g.n[0] && q[1] >= 0 && q[1] < g.n[1] &&
                   (D == 2 || (q[2] >= 0 && q[2] < g.n[2]));
         if (!in) continue;
-        size_t o = (size_t)a * g.ncell + cidx<D>(g, q[0], q[1], q[2]);
-        double v = ustar[o] * k.idt + Gp[o] * k.irho;
+        const double v = w[(size_t)a * g.ncell + cidx<D>(g, q[0], q[1], q[2])];
         acc += cb[a] ? v : -v;
       }
     }
@@ -561,11 +587,10 @@ __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict
   }
 
 template <int D>
-__global__ void k_nodal_rhs(const double* __restrict__ ustar, const double* __restrict__ Gp,
-                            double* __restrict__ out, const __grid_constant__ Geom g, const StepC k) {
-  int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
+__global__ void k_nodal_rhs(const double* __restrict__ w, double* __restrict__ out, const __grid_constant__ Geom g,
+                            const StepC k) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
-    k_nodal_rhs_at<D>(ustar, Gp, out, g, k, t);
+    k_nodal_rhs_at<D>(w, out, g, k, t);
   }
 }
 

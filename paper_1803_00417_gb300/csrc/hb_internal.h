@@ -110,7 +110,8 @@ struct hbf_ctx {
   double* Lu = nullptr;     // d*ncell
   double* slopes = nullptr; // d*d*ncell  [a][c]
   double* hats = nullptr;   // d*d*ncell  [b][c]
-  double* tcom = nullptr;   // d*d*ncell  [a][c]: the cell's share of the a-face traces
+  double* tcom = nullptr;
+  double* wn = nullptr;     // d*ncell: u*/dt + G p/rho, the nodal divergence's cell field   // d*d*ncell  [a][c]: the cell's share of the a-face traces
   double* uL[3] = {nullptr, nullptr, nullptr};   // per axis: d*nface[a]
   double* uR[3] = {nullptr, nullptr, nullptr};
   double* uadv[3] = {nullptr, nullptr, nullptr}; // per axis: nface[a]
