@@ -194,13 +194,14 @@ def run_reference(args):
 SMOOTHER_DRAM_BYTES_PER_CELL = (201.2e6 + 18.8e6) / 192 ** 3
 
 
-def visc_smoother_bytes(d, ncell, elem):
+def visc_smoother_bytes(d, ncell, elem, cell_eta):
     """Algorithmic bytes of one finest-level launch of the viscous smoother
     (one component, one colour): reads the other colour of u_c (ncell/2), the
     other components for the cross terms ((d-1) ncell), b_c of the colour
-    (ncell/2) and every face eta once (d ncell); writes u_c of the colour
-    (ncell/2)."""
-    return elem * ncell * (0.5 + (d - 1) + 0.5 + d + 0.5)
+    (ncell/2) and the viscosity, as the cell array (ncell; the FP32 finest
+    level forms the face means itself) or every face eta once (d ncell);
+    writes u_c of the colour (ncell/2)."""
+    return elem * ncell * (0.5 + (d - 1) + 0.5 + (1 if cell_eta else d) + 0.5)
 
 
 def run_batch_sweep(args, clocks=None):
@@ -479,7 +480,7 @@ def run_ours(args):
     roofline = None
     if sm_n > 0:
         per_launch_s = sm_ms / sm_n / 1e3
-        algo = visc_smoother_bytes(d, ncell, elem)
+        algo = visc_smoother_bytes(d, ncell, elem, prec == MIXED)
         ach = algo / per_launch_s / 1e9
         # DRAM bytes per cell of this kernel from one full ncu capture at 192^3
         # (profiles/k_visc_smooth_cavity192.md), scaled to this grid; valid

@@ -25,10 +25,12 @@ struct Strides;
 // of the two cells' viscosities (CellEta: the rule that makes the stored
 // finest-level faces, wall faces taking the interior cell; one cell array is
 // read instead of D face arrays).
-//   lo / hi: the face of axis a below / above interior cell p (flat index id)
+//   lo / hi: the face of axis a below / above interior cell p (flat index id),
+//            up to the factor kScale (CellEta returns the two cells' sum)
 //   at:      the face of axis a whose upper cell is q (q[a] may be n[a])
 template <typename T>
 struct FaceEta {
+  static constexpr double kScale = 1.0;
   const T* const* ef;
   __host__ __device__ T lo(const Geom& g, const Strides& S, int a, const int* p, int id) const;
   __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
@@ -37,6 +39,7 @@ struct FaceEta {
 
 template <typename T>
 struct CellEta {
+  static constexpr double kScale = 0.5;
   const T* eta;
   __host__ __device__ T lo(const Geom& g, const Strides& S, int a, const int* p, int id) const;
   __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
@@ -175,13 +178,13 @@ template <typename T>
 __host__ __device__ __forceinline__ T CellEta<T>::lo(const Geom& g, const Strides& S, int a, const int* p, int id) const {
   (void)g;
   (void)p;
-  return T(0.5) * (eta[id - S.s[a]] + eta[id]);
+  return eta[id - S.s[a]] + eta[id];
 }
 template <typename T>
 __host__ __device__ __forceinline__ T CellEta<T>::hi(const Geom& g, const Strides& S, int a, const int* p, int id) const {
   (void)g;
   (void)p;
-  return T(0.5) * (eta[id] + eta[id + S.s[a]]);
+  return eta[id] + eta[id + S.s[a]];
 }
 
 template <int D>
@@ -196,11 +199,11 @@ __host__ __device__ inline bool interior(const Geom& g, const int* p) {
 template <int D, typename T, typename EF>
 __host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, const T* __restrict__ b, const EF& ef,
                                               const Geom& g, const Strides& S, int c, const int* p, T beta) {
+  // every term of the update is linear in the face viscosities: they enter
+  // unscaled, and 1/h^2 with the accessor's factor goes into beta
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
-  const T ih = g_ih<T>(g);
-  const T ihh = g_ihh<T>(g);
-  const T q = g_q4<T>(g);
+  const T bs = beta * (g_ihh<T>(g) * T(EF::kScale));
   T elo[3], ehi[3];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -210,13 +213,9 @@ __host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, 
   T offd = T(0), diag = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    T kappa = (a == c) ? T(2) : T(1);
-    T wlo = kappa * elo[a] * ihh;
-    offd += wlo * uc[id - S.s[a]];
-    diag += wlo;
-    T whi = kappa * ehi[a] * ihh;
-    offd += whi * uc[id + S.s[a]];
-    diag += whi;
+    const T kappa = (a == c) ? T(2) : T(1);
+    offd += kappa * (elo[a] * uc[id - S.s[a]] + ehi[a] * uc[id + S.s[a]]);
+    diag += kappa * (elo[a] + ehi[a]);
   }
   T cross = T(0);
 #pragma unroll
@@ -224,14 +223,12 @@ __host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, 
     if (a == c) continue;
     const T* ua = u + (size_t)a * g.ncell;
     const int sa = S.s[a], sc = S.s[c];
-    T mid = ua[id + sc] - ua[id - sc];
-    T xhi = (mid + (ua[id + sa + sc] - ua[id + sa - sc])) * q;
-    T xlo = ((ua[id - sa + sc] - ua[id - sa - sc]) + mid) * q;
-    T fluxhi = ehi[a] * xhi;
-    T fluxlo = elo[a] * xlo;
-    cross += (fluxhi - fluxlo) * ih;
+    const T mid = ua[id + sc] - ua[id - sc];
+    const T xhi = mid + (ua[id + sa + sc] - ua[id + sa - sc]);
+    const T xlo = (ua[id - sa + sc] - ua[id - sa - sc]) + mid;
+    cross += ehi[a] * xhi - elo[a] * xlo;
   }
-  return (b[(size_t)c * g.ncell + id] + beta * (offd + cross)) / (T(1) + beta * diag);
+  return (b[(size_t)c * g.ncell + id] + bs * (offd + T(0.25) * cross)) / (T(1) + bs * diag);
 }
 
 // (L_eta u)_c for an interior cell: the operator of mg_tensor_point with the
@@ -265,7 +262,7 @@ __host__ __device__ __forceinline__ T tensor_interior(const T* __restrict__ u, c
     }
     acc += fhi - flo;
   }
-  return acc * g_ihh<T>(g);
+  return acc * (g_ihh<T>(g) * T(EF::kScale));
 }
 
 // thread t -> cell of red-black colour col (x index stride 2)
