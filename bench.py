@@ -191,7 +191,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
-SMOOTHER_DRAM_BYTES_PER_CELL = (201.2e6 + 18.8e6) / 192 ** 3
+SMOOTHER_DRAM_BYTES_PER_CELL = (144.2e6 + 15.8e6) / 192 ** 3
 
 
 def visc_smoother_bytes(d, ncell, elem, cell_eta):
@@ -487,7 +487,7 @@ def run_ours(args):
         # for the FP32 kernel version recorded there
         traffic = SMOOTHER_DRAM_BYTES_PER_CELL * ncell if prec == MIXED else None
         roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                    "traffic": traffic, "traffic_source": "ncu at 192^3, 31.1 B/cell, scaled by cells"
+                    "traffic": traffic, "traffic_source": "ncu at 192^3, 22.6 B/cell, scaled by cells"
                     if traffic else None, "kernel": "k_visc_smooth (finest level)",
                     "launches": sm_n, "avg_launch_us": per_launch_s * 1e6,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
