@@ -16,6 +16,7 @@ namespace hb {
 struct StepC {
   double dt;    // time step
   double dt2h;  // dt / (2h)
+  double dth;   // dt / h
   double hdt;   // dt / 2
   double rho;   // density
   double irho;  // 1 / rho
@@ -28,6 +29,7 @@ inline StepC step_consts(const Geom& g, int dim, double dt, double rho) {
   StepC k;
   k.dt = dt;
   k.dt2h = dt / (2.0 * g.h);
+  k.dth = dt / g.h;
   k.hdt = 0.5 * dt;
   k.rho = rho;
   k.irho = 1.0 / rho;
@@ -86,15 +88,19 @@ __host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, 
                   i2h;
       }
     }
-    double s = 0.0;
+    // tr(D D^T) with D = (G + G^T)/2 symmetric: the diagonal D_aa = G_aa,
+    // each off-diagonal pair counted twice
+    double s = 0.0, so = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) s += G[a][a] * G[a][a];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int b = 0; b < D; ++b) {
-        double Dab = dhalf(G[a][b] + G[b][a]);
-        s += Dab * Dab;
+      for (int b = a + 1; b < D; ++b) {
+        const double Dab = dhalf(G[a][b] + G[b][a]);
+        so += Dab * Dab;
       }
-    double gn = sqrt(dhalf(s));
+    double gn = sqrt(dhalf(s + dtwice(so)));
     eta[t] = viscosity(gn, r);
   }
 
@@ -476,7 +482,7 @@ __host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restric
   
     int p[3];
     cell_coords<D>(g, t, p[0], p[1], p[2]);
-    double A[3] = {0.0, 0.0, 0.0};
+    double A[3] = {0.0, 0.0, 0.0};  // h times the convective term (1/h goes into dt/h)
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       int nf = g.nface[a];
@@ -490,13 +496,13 @@ __host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restric
       for (int c = 0; c < D; ++c) {
         double thi = upwind(uL[a][(size_t)c * nf + fhi], uR[a][(size_t)c * nf + fhi], vhi);
         double tlo = upwind(uL[a][(size_t)c * nf + flo], uR[a][(size_t)c * nf + flo], vlo);
-        A[c] += vbar * (thi - tlo) * g.ih;
+        A[c] += vbar * (thi - tlo);
       }
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       size_t o = (size_t)c * g.ncell + t;
-      rhs[o] = u[o] - k.dt * A[c] + k.dtr * (-Gp[o] + dhalf(Lu[o]) + fo.f[c]);
+      rhs[o] = u[o] - k.dth * A[c] + k.dtr * (-Gp[o] + dhalf(Lu[o]) + fo.f[c]);
     }
   }
 
