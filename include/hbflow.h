@@ -117,6 +117,13 @@ int hbf_set_predictor_viscous(hbf_ctx* ctx, int on);
  * max_cycles V-cycles; nu1/nu2 pre/post smoothing sweeps; nu_bottom sweeps on
  * the coarsest level.  Defaults 1e-10, 200, 2, 2, 40. */
 int hbf_set_solver(hbf_ctx* ctx, double rtol, int max_cycles, int nu1, int nu2, int nu_bottom);
+/* The fused tail of the V-cycles (the multigrid scheme of Sec. III B): from
+ * the first level with at most max_cells cells down to the exact bottom solve
+ * and back runs as one launch of one thread block, with block barriers
+ * between the colour sweeps; the arithmetic and its order are those of the
+ * level-by-level launches.  0 disables it; default 512.  HBF_ERR_ARG for a
+ * negative count. */
+int hbf_set_tail(hbf_ctx* ctx, int max_cells);
 
 /* Number of doubles of a field (see enum hbf_field), or a negative status. */
 int64_t hbf_field_size(const hbf_ctx* ctx, int which);

@@ -360,6 +360,18 @@ int hbf_set_solver(hbf_ctx* c, double rtol, int max_cycles, int nu1, int nu2, in
   return HBF_OK;
 }
 
+int hbf_set_tail(hbf_ctx* c, int max_cells) {
+  if (!c) return HBF_ERR_ARG;
+  if (max_cells < 0) return fail(c, HBF_ERR_ARG, "negative tail size");
+  if (max_cells != c->tail_cells) {
+    c->tail_cells = max_cells;
+    c->tail_lf = -1;  // recomputed, and the tail records rebuilt, at the next cycle
+    for (auto& k : c->tail_host)
+      for (auto& h : k) h.clear();
+  }
+  return HBF_OK;
+}
+
 int64_t hbf_field_size(const hbf_ctx* c, int which) {
   if (!c) return HBF_ERR_ARG;
   FieldView v;

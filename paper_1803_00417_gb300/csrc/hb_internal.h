@@ -143,6 +143,7 @@ struct hbf_ctx {
   hb::Dense dense[3];  // viscous, MAC, nodal
   // fused V-cycle tail of the solves: levels >= tail_lf run in one block
   int tail_lf = -1;                         // -1: not set up; >= levels: none
+  int tail_cells = 512;                     // the tail starts at the first level with at most this many cells
   void* tail_dev[3][2] = {};                // device argument records [kind][FP32?]
   std::vector<unsigned char> tail_host[3][2];
   double tail_beta[2] = {0.0, 0.0};         // beta of the uploaded viscous records

@@ -456,10 +456,9 @@ static void bottom_fp64(Problem<T>& P, int l, double* xd, double* bd, void (*run
 
 // ---------------------------------------------------------------------------
 // fused tail of the V-cycle (k_vcycle_tail): from the first level with at
-// most kTailCells cells down to the exact bottom solve and back in one launch
-// of one block, instead of about twenty launches per level
+// most c->tail_cells cells (hbf_set_tail) down to the exact bottom solve and
+// back in one launch of one block, instead of about twenty launches per level
 // ---------------------------------------------------------------------------
-constexpr int kTailCells = 512;
 
 static int tail_level(hbf_ctx* c) {
   if (c->tail_lf >= 0) return c->tail_lf;
@@ -469,7 +468,7 @@ static int tail_level(hbf_ctx* c) {
   int lf = nl;
   if (dense)
     for (int l = 1; l < nl; ++l)
-      if (c->lv[l].g.ncell <= kTailCells) {
+      if (c->lv[l].g.ncell <= c->tail_cells) {
         lf = l;
         break;
       }

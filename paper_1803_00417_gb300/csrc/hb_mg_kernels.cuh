@@ -51,18 +51,39 @@ struct CellEta {
   }
 };
 
+// component comp at cell q, which lies inside the domain on every axis but
+// ax: uget with the one reflection test that can apply
+template <int D, typename T>
+__host__ __device__ __forceinline__ T uget_axis(const T* __restrict__ uc, const Geom& g, int comp, int i, int j, int k,
+                                                int ax, bool hom) {
+  int q[3] = {i, j, k};
+  int side = -1;
+  if (q[ax] < 0) {
+    side = 0;
+    q[ax] = -q[ax] - 1;
+  } else if (q[ax] >= g.n[ax]) {
+    side = 1;
+    q[ax] = 2 * g.n[ax] - 1 - q[ax];
+  }
+  const T v = uc[cidx<D>(g, q[0], q[1], q[2])];
+  if (side < 0) return v;
+  const T ub = hom ? T(0) : g_wu<T>(g, ax, side, comp);
+  return T(2) * ub - v;
+}
+
 template <int D, typename T>
 __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
                                   bool hom) {
-  // mean of the two cells' central differences, (dL + dR)/2 with dL, dR over 2h
+  // mean of the two cells' central differences, (dL + dR)/2 with dL, dR over 2h;
+  // L and L + e_a are inside the domain, so only the c offsets can cross a wall
   if (L[a] < 0 || L[a] >= g.n[a] - 1) return T(0);
   int p1[3] = {L[0], L[1], L[2]}, p0[3] = {L[0], L[1], L[2]};
   p1[c] += 1;
   p0[c] -= 1;
-  T dL = uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom);
+  T dL = uget_axis<D>(ua, g, a, p1[0], p1[1], p1[2], c, hom) - uget_axis<D>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
   p1[a] += 1;
   p0[a] += 1;
-  T dR = uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom);
+  T dR = uget_axis<D>(ua, g, a, p1[0], p1[1], p1[2], c, hom) - uget_axis<D>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
   return (dL + dR) * g_q4<T>(g);
 }
 
@@ -82,7 +103,8 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& 
       int R[3] = {L[0], L[1], L[2]};
       R[a] += 1;
       T e = ef.at(g, a, R);
-      T nrm = (uget<D>(uc, g, c, R[0], R[1], R[2], hom) - uget<D>(uc, g, c, L[0], L[1], L[2], hom)) * ih;
+      // L and R differ from the cell p only along a
+      T nrm = (uget_axis<D>(uc, g, c, R[0], R[1], R[2], a, hom) - uget_axis<D>(uc, g, c, L[0], L[1], L[2], a, hom)) * ih;
       if (a == c)
         flux[s] = e * (T(2) * nrm);
       else

@@ -4,7 +4,9 @@
 //  * the FP64 sign tests, magnitude minimum, limiter clamp and exact x/2, 2x
 //    on bit patterns against plain IEEE arithmetic, bit for bit;
 //  * the thread -> cell maps that put x-wall cells in warps of their own:
-//    every cell (every cell of a red-black colour) exactly once, in range.
+//    every cell (every cell of a red-black colour) exactly once, in range;
+//  * the wall stencil of the viscous operator with its one-axis reflections
+//    against the general reflection accessor, bit for bit.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -121,8 +123,103 @@ static void check_maps(int n0, int n1, int n2) {
   for (int c = 0; c < g.ncell; ++c) expect(seen[c] == 1, "xi_cell once", n0, n1);
 }
 
+// the wall stencil's pieces against the same formulas with the general
+// reflection accessor uget (every axis tested), bit for bit
+template <int D, typename T>
+static T ref_face_cross(const T* ua, const Geom& g, int a, int c, const int* L, bool hom) {
+  if (L[a] < 0 || L[a] >= g.n[a] - 1) return T(0);
+  int p1[3] = {L[0], L[1], L[2]}, p0[3] = {L[0], L[1], L[2]};
+  p1[c] += 1;
+  p0[c] -= 1;
+  T dL = uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom);
+  p1[a] += 1;
+  p0[a] += 1;
+  T dR = uget<D>(ua, g, a, p1[0], p1[1], p1[2], hom) - uget<D>(ua, g, a, p0[0], p0[1], p0[2], hom);
+  return (dL + dR) * g_q4<T>(g);
+}
+
+template <int D, typename T>
+static T ref_tensor_point(const T* u, const T* const* ef, const Geom& g, int c, const int* p, bool hom) {
+  const T* uc = u + (size_t)c * g.ncell;
+  T acc = T(0);
+  const T ih = g_ih<T>(g);
+  for (int a = 0; a < D; ++a) {
+    T flux[2];
+    for (int s = 0; s < 2; ++s) {
+      int L[3] = {p[0], p[1], p[2]};
+      L[a] += s - 1;
+      int R[3] = {L[0], L[1], L[2]};
+      R[a] += 1;
+      T e = ef[a][fidx(g, a, R[0], R[1], R[2])];
+      T nrm = (uget<D>(uc, g, c, R[0], R[1], R[2], hom) - uget<D>(uc, g, c, L[0], L[1], L[2], hom)) * ih;
+      if (a == c)
+        flux[s] = e * (T(2) * nrm);
+      else
+        flux[s] = e * (nrm + ref_face_cross<D, T>(u + (size_t)a * g.ncell, g, a, c, L, hom));
+    }
+    acc += (flux[1] - flux[0]) * ih;
+  }
+  return acc;
+}
+
+template <int D, typename T>
+static void check_wall_stencil(int n0, int n1, int n2) {
+  Geom g{};
+  g.n[0] = n0;
+  g.n[1] = n1;
+  g.n[2] = D == 3 ? n2 : 1;
+  g.h = 1.0 / 7.0;
+  g.ncell = g.n[0] * g.n[1] * g.n[2];
+  for (int a = 0; a < 3; ++a) g.nface[a] = (g.n[0] + (a == 0)) * (g.n[1] + (a == 1)) * (g.n[2] + (a == 2 && D == 3));
+  std::mt19937_64 rng(7 + n0 + 10 * n1 + 100 * n2);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (int a = 0; a < 3; ++a)
+    for (int sd = 0; sd < 2; ++sd)
+      for (int q = 0; q < 3; ++q) g.wu[a][sd][q] = nd(rng);
+  geom_finish(g);
+  std::vector<T> u((size_t)D * g.ncell), e[3];
+  for (auto& v : u) v = (T)nd(rng);
+  const T* ef[3] = {nullptr, nullptr, nullptr};
+  for (int a = 0; a < D; ++a) {
+    e[a].resize(g.nface[a]);
+    for (auto& v : e[a]) v = (T)(1.0 + std::fabs(nd(rng)));
+    ef[a] = e[a].data();
+  }
+  for (int hom = 0; hom < 2; ++hom)
+    for (int k = 0; k < g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int i = 0; i < g.n[0]; ++i) {
+          const int p[3] = {i, j, k};
+          for (int c = 0; c < D; ++c) {
+            const T got = mg_tensor_point<D, T>(u.data(), FaceEta<T>{ef}, g, c, p, hom != 0);
+            const T want = ref_tensor_point<D, T>(u.data(), ef, g, c, p, hom != 0);
+            expect(std::memcmp(&got, &want, sizeof(T)) == 0, "mg_tensor_point", (double)got, (double)want);
+            for (int a = 0; a < D; ++a) {
+              if (a == c) continue;
+              for (int s = 0; s < 2; ++s) {
+                int L[3] = {i, j, k};
+                L[a] -= s;
+                const T* ua = u.data() + (size_t)a * g.ncell;
+                const T x = mg_face_cross<D, T>(ua, g, a, c, L, hom != 0);
+                const T y = ref_face_cross<D, T>(ua, g, a, c, L, hom != 0);
+                expect(std::memcmp(&x, &y, sizeof(T)) == 0, "mg_face_cross", (double)x, (double)y);
+              }
+            }
+          }
+        }
+}
+
 int main() {
   check_fp64bits();
+  for (int a : {1, 2, 3, 5})
+    for (int b : {1, 2, 4}) {
+      check_wall_stencil<2, double>(a, b, 1);
+      check_wall_stencil<2, float>(a, b, 1);
+      for (int c : {1, 3}) {
+        check_wall_stencil<3, double>(a, b, c);
+        check_wall_stencil<3, float>(a, b, c);
+      }
+    }
   const int sizes[] = {1, 2, 3, 4, 5, 7, 8, 9, 16, 17, 33, 64};
   for (int a : sizes)
     for (int b : sizes) check_maps<2>(a, b, 1);

@@ -37,8 +37,8 @@ def rel_l2(a, b):
     ((48, 32), 32, dict(Re=1000.0, Bi=5.0, Pa=1e5, nexp=0.5)),
     ((16, 16, 16), 33, dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)),
     ((24, 20, 12), 34, dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)),
-    # wide enough for the shared-memory staged smoother on two levels, with
-    # ragged x tiles and a ragged z chunk
+    # ragged for the thread -> cell maps: rows not a multiple of the 16-row
+    # groups on the coarse levels, x extents that leave partial warps
     ((64, 32, 40), 35, dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)),
 ])
 def test_mixed_step_matches_fp64_oracle(n, seed, over):
@@ -86,3 +86,30 @@ def test_mixed_from_rest():
         sim.set_velocity(u)
         sim.set_pressure(p)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n", [(48, 32), (24, 20, 12)])
+def test_fused_tail_matches_level_by_level(precision, n):
+    """The fused V-cycle tail (one block over the small levels) performs the
+    level-by-level launches' operations in the same order: two steps agree
+    to rounding with the tail off, from the default level, from a coarser
+    level, and over every level."""
+    from paper_1803_00417_gb300.hbflow import HBFlow
+
+    cfg = cavity(n, Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)
+    u, p = random_state(cfg["n"], seed=36)
+    outs = []
+    for cells in (0, 64, 512, 1 << 20):
+        sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=precision)
+        sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+        sim.set_tail(cells)
+        sim.set_velocity(u)
+        sim.set_pressure(p)
+        for _ in range(2):
+            st = sim.step(cfg["dt"])
+            assert all(st[k]["converged"] for k in ("mac", "visc", "nodal")), st
+        outs.append(np.concatenate([sim.get_field("U"), sim.get_field("P")]))
+        sim.close()
+    for other in outs[1:]:
+        assert np.linalg.norm(other - outs[0]) <= 1e-12 * np.linalg.norm(outs[0])
