@@ -6,7 +6,10 @@
 //  * the thread -> cell maps that put x-wall cells in warps of their own:
 //    every cell (every cell of a red-black colour) exactly once, in range;
 //  * the wall stencil of the viscous operator with its one-axis reflections
-//    against the general reflection accessor, bit for bit.
+//    against the general reflection accessor, bit for bit;
+//  * the interior smoother and operator (stored faces, and faces formed from
+//    the cell viscosity) against the general point forms, and the cell-mean
+//    face accessor against the finest-level face rule.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -15,6 +18,7 @@
 #include <vector>
 
 #include "hb_internal.h"
+#include "hb_explicit.cuh"
 #include "hb_fp64bits.cuh"
 #include "hb_mg_kernels.cuh"
 
@@ -209,8 +213,71 @@ static void check_wall_stencil(int n0, int n1, int n2) {
         }
 }
 
+// the interior fast paths against the general (wall-aware) point forms on
+// interior cells, with stored faces and with faces formed from cell
+// viscosities; the cell-mean accessor against the finest-level face rule
+template <int D>
+static void check_interior_paths(int n0, int n1, int n2) {
+  Geom g{};
+  g.n[0] = n0;
+  g.n[1] = n1;
+  g.n[2] = D == 3 ? n2 : 1;
+  g.h = 1.0 / 9.0;
+  g.ncell = g.n[0] * g.n[1] * g.n[2];
+  for (int a = 0; a < 3; ++a) g.nface[a] = (g.n[0] + (a == 0)) * (g.n[1] + (a == 1)) * (g.n[2] + (a == 2 && D == 3));
+  geom_finish(g);
+  std::mt19937_64 rng(11 + n0 + 10 * n1 + 100 * n2);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  std::vector<double> u((size_t)D * g.ncell), b((size_t)D * g.ncell), eta(g.ncell), e[3];
+  for (auto& v : u) v = nd(rng);
+  for (auto& v : b) v = nd(rng);
+  for (auto& v : eta) v = std::exp(2.0 * nd(rng));
+  const double* ef[3] = {nullptr, nullptr, nullptr};
+  for (int a = 0; a < D; ++a) {
+    e[a].resize(g.nface[a]);
+    for (int t = 0; t < g.nface[a]; ++t) k_eta_faces_at<D>(eta.data(), e[a].data(), a, g, t);
+    ef[a] = e[a].data();
+  }
+  const FaceEta<double> fa{ef};
+  const CellEta<double> ce{eta.data()};
+  const Strides S = make_strides(g);
+  const double beta = 0.37;
+  auto close = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * (1.0 + std::fabs(y)); };
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        const int p[3] = {i, j, k};
+        // every face through both accessors
+        for (int a = 0; a < D; ++a)
+          for (int s = 0; s < 2; ++s) {
+            int q[3] = {i, j, k};
+            q[a] += s;
+            expect(fa.at(g, a, q) == ce.at(g, a, q), "CellEta::at", fa.at(g, a, q), ce.at(g, a, q));
+          }
+        if (!interior<D>(g, p)) continue;
+        const int id = cidx<D>(g, i, j, k);
+        for (int a = 0; a < D; ++a) {
+          expect(CellEta<double>::kScale * ce.lo(g, S, a, p, id) == fa.lo(g, S, a, p, id), "CellEta::lo", 0, 0);
+          expect(CellEta<double>::kScale * ce.hi(g, S, a, p, id) == fa.hi(g, S, a, p, id), "CellEta::hi", 0, 0);
+        }
+        for (int c = 0; c < D; ++c) {
+          for (int hom = 0; hom < 2; ++hom) {
+            const double w = visc_gs_point<D, double>(u.data(), b.data(), fa, g, c, p, beta, hom != 0);
+            expect(close(visc_gs_interior<D, double>(u.data(), b.data(), fa, g, S, c, p, beta), w), "gs faces", w, 0);
+            expect(close(visc_gs_interior<D, double>(u.data(), b.data(), ce, g, S, c, p, beta), w), "gs cells", w, 0);
+            const double l = mg_tensor_point<D, double>(u.data(), fa, g, c, p, hom != 0);
+            expect(close(tensor_interior<D, double>(u.data(), fa, g, S, c, p), l), "L faces", l, 0);
+            expect(close(tensor_interior<D, double>(u.data(), ce, g, S, c, p), l), "L cells", l, 0);
+          }
+        }
+      }
+}
+
 int main() {
   check_fp64bits();
+  check_interior_paths<2>(7, 5, 1);
+  check_interior_paths<3>(6, 5, 4);
+  check_interior_paths<3>(3, 3, 3);
   for (int a : {1, 2, 3, 5})
     for (int b : {1, 2, 4}) {
       check_wall_stencil<2, double>(a, b, 1);

@@ -1,7 +1,10 @@
-"""Host-side checks of the integer helpers the CUDA kernels share: the FP64
+"""Host-side checks of device code that also compiles for the host: the FP64
 comparisons and exact scalings done on bit patterns (against IEEE arithmetic,
-bit for bit) and the thread -> cell maps of the smoother and operator kernels
-(every cell once).  Built with nvcc as a host program; no GPU needed."""
+bit for bit), the thread -> cell maps of the smoother and operator kernels
+(every cell once), the viscous wall stencil's one-axis reflections (against
+the general accessor, bit for bit), and the interior smoother and operator
+with stored or cell-formed face viscosities (against the general point
+forms).  Built with nvcc as a host program; no GPU needed."""
 
 import os
 import shutil
