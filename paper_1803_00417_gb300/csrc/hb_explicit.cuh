@@ -114,7 +114,6 @@ __global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, co
 // face eta on level 0: mean of the two cells, wall faces take the interior cell
 template <int D>
 __host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict__ eta, double* __restrict__ ef, int a, const Geom& g, int t) {
-  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   
     int p[3];
     face_coords(g, a, t, p[0], p[1], p[2]);
@@ -235,7 +234,6 @@ __host__ __device__ __forceinline__ void k_slopes_at(const double* __restrict__ 
 
 template <int D>
 __global__ void k_slopes(const double* __restrict__ u, double* __restrict__ slopes, const __grid_constant__ Geom g) {
-  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_slopes_at<D>(u, slopes, g, t);
   }
@@ -433,7 +431,6 @@ __host__ __device__ __forceinline__ void k_mac_rhs_at(const double* ua0, const d
 template <int D>
 __global__ void k_mac_rhs(const double* ua0, const double* ua1, const double* ua2,
                           double* __restrict__ rhs, const __grid_constant__ Geom g) {
-  const double* ua[3] = {ua0, ua1, ua2};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_mac_rhs_at<D>(ua0, ua1, ua2, rhs, g, t);
   }
@@ -442,7 +439,6 @@ __global__ void k_mac_rhs(const double* ua0, const double* ua1, const double* ua
 template <int D>
 __host__ __device__ __forceinline__ void k_mac_correct_at(const double* __restrict__ uadv, const double* __restrict__ phi,
                               double* __restrict__ umac, int a, const Geom& g, int t) {
-  int ex[3] = {g.n[0] + (a == 0), g.n[1] + (a == 1), g.n[2] + (a == 2 && D == 3)};
   
     int R[3];
     face_coords(g, a, t, R[0], R[1], R[2]);
@@ -513,9 +509,6 @@ __global__ void k_advect_rhs(const double* __restrict__ u, const double* uL0, co
                              const double* um2, const double* __restrict__ Gp,
                              const double* __restrict__ Lu, Force fo,
                              double* __restrict__ rhs, const __grid_constant__ Geom g, const StepC k) {
-  const double* uL[3] = {uL0, uL1, uL2};
-  const double* uR[3] = {uR0, uR1, uR2};
-  const double* um[3] = {um0, um1, um2};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
     k_advect_rhs_at<D>(u, uL0, uL1, uL2, uR0, uR1, uR2, um0, um1, um2, Gp, Lu, fo, rhs, g, k, t);
   }
@@ -554,7 +547,6 @@ __global__ void k_grad_p_w(const double* __restrict__ p, const double* __restric
 template <int D>
 __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict__ w, double* __restrict__ out,
                                                         const Geom& g, const StepC& k, int t) {
-  int ex[3] = {g.n[0] + 1, g.n[1] + 1, D == 3 ? g.n[2] + 1 : 1};
   
     int p[3];
     node_coords(g, t, p[0], p[1], p[2]);
