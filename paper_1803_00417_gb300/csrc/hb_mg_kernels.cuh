@@ -751,7 +751,6 @@ __global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, const
 
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_nodal_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const Geom& g, int t) {
-  int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
   const T ihh = g_ihh<T>(g);
   
     int p[3];
@@ -761,7 +760,6 @@ __host__ __device__ __forceinline__ void k_nodal_resid_at(const T* __restrict__ 
 
 template <int D, typename T>
 __global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const __grid_constant__ Geom g) {
-  int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
   const T ihh = g_ihh<T>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
     k_nodal_resid_at<D, T>(x, b, r, g, t);
@@ -830,7 +828,6 @@ __global__ void k_restrict_cells(const T* __restrict__ f, T* __restrict__ c, con
 // coarse a-face eta: mean of the fine a-faces tiling it (pairwise, axis order)
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_restrict_faces_at(const T* __restrict__ ff, T* __restrict__ fc, int a, const Geom& gf, const Geom& gc, int t) {
-  int ex[3] = {gc.n[0] + (a == 0), gc.n[1] + (a == 1), gc.n[2] + (a == 2 && D == 3)};
   
     int P[3];
     face_coords(gc, a, t, P[0], P[1], P[2]);
@@ -929,7 +926,6 @@ __global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec
 // full weighting onto coarse nodes (even reflection), axis by axis
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict__ rf, T* __restrict__ rc, const Geom& gf, const Geom& gc, int t) {
-  int e0 = gc.n[0] + 1, e1 = gc.n[1] + 1;
   
     int I, J, K;
     node_coords(gc, t, I, J, K);
@@ -951,7 +947,6 @@ __host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict
 
 template <int D, typename T>
 __global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc) {
-  int e0 = gc.n[0] + 1, e1 = gc.n[1] + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gc.nnode; t += gridDim.x * blockDim.x) {
     k_restrict_nodes_at<D, T>(rf, rc, gf, gc, t);
   }
@@ -960,7 +955,6 @@ __global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, c
 // x_f += P e_c, nodal multilinear, axis by axis
 template <int D, typename T>
 __host__ __device__ __forceinline__ void k_prolong_nodes_add_at(T* __restrict__ xf, const T* __restrict__ ec, const Geom& gf, const Geom& gc, int t) {
-  int e0 = gf.n[0] + 1, e1 = gf.n[1] + 1;
   
     int i, j, k;
     node_coords(gf, t, i, j, k);
@@ -990,7 +984,6 @@ __host__ __device__ __forceinline__ void k_prolong_nodes_add_at(T* __restrict__ 
 
 template <int D, typename T>
 __global__ void k_prolong_nodes_add(T* __restrict__ xf, const T* __restrict__ ec, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc) {
-  int e0 = gf.n[0] + 1, e1 = gf.n[1] + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gf.nnode; t += gridDim.x * blockDim.x) {
     k_prolong_nodes_add_at<D, T>(xf, ec, gf, gc, t);
   }
