@@ -255,6 +255,7 @@ int hbf_init_grid(hbf_ctx** out, int dim, const int64_t n[3], double h, const do
         return HBF_ERR_ARG;
       }
   }
+  geom_finish(c->g);  // again: the FP32 copies of the wall velocities
   c->rheo.c2 = 1.0;
   c->rheo.n = 1.0;
   c->rheo.tau = 0.0;
