@@ -53,3 +53,20 @@ def test_argument_errors_need_no_gpu(lib):
     assert L.hbf_init_grid(ctypes.byref(ctx), 2, n_bad, 0.1, None, 0, None) == -1
     assert L.hbf_init_grid(ctypes.byref(ctx), 2, n, -1.0, None, 0, None) == -1
     assert L.hbf_step(None, 0.1, None) == -1
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C header: it compiles as C99 and as C++ on its own."""
+    import shutil
+    import subprocess
+
+    src = tmp_path / "use.c"
+    src.write_text('#include "hbflow.h"\nint main(void) { return hbf_set_tail((hbf_ctx*)0, 0) == 0; }\n')
+    inc = os.path.join(ROOT, "include")
+    for cc, std in (("gcc", "-std=c99"), ("g++", "-std=c++17")):
+        if shutil.which(cc) is None:
+            pytest.skip(cc + " not found")
+        lang = ["-x", "c++"] if cc == "g++" else []
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, *lang, "-c", str(src),
+                            "-o", str(tmp_path / ("use_" + cc + ".o"))], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
