@@ -10,7 +10,9 @@
 //         x after one cell sweep; bn - L xn; xn after one nodal sweep;
 //         restricted u (d ncell_c); coarse faces (sum of nface_c);
 //         u + P ev (odd ghosts, d ncell); x + P ec (even ghosts);
-//         restricted xn (nnode_c); xn + P en (nnode)
+//         restricted xn (nnode_c); xn + P en (nnode); then in FP32 with
+//         the finest-level maps and cell viscosity: A u (d ncell) and u after
+//         one viscous sweep (d ncell), written as float64
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -36,6 +38,16 @@ static void visc_colour_sweep(std::vector<double>& u, const std::vector<double>&
   for (int col = 0; col < 2; ++col)
     for (int t = 0; t < rb_count<D>(g); ++t)
       k_visc_smooth_c_at<D, double, C>(u.data(), b.data(), ef[0], ef[1], ef[2], g, col, beta, hom, t);
+}
+
+template <int D, int C>
+static void fsweep(std::vector<float>& u, const std::vector<float>& b, const CellEta<float>& ce, const Geom& g,
+                   float beta, int hom) {
+  for (int col = 0; col < 2; ++col)
+    for (int t = 0; t < rbx_count<D>(g); ++t) {
+      int p[3];
+      if (rbx_cell<D>(g, t, col, p)) visc_smooth_cell<D, float, C>(u.data(), b.data(), ce, g, beta, hom, p);
+    }
 }
 
 template <int D>
@@ -124,6 +136,21 @@ static int run(FILE* in, FILE* out, const int* n, int hom) {
   std::vector<double> np_ = xn;
   for (int t = 0; t < g.nnode; ++t) k_prolong_nodes_add_at<D, double>(np_.data(), en.data(), g, gc, t);
   wr(out, np_);
+  // the FP32 finest level of the mixed V-cycles as its kernels walk it: the
+  // x-interior-first maps, face viscosities formed from the cell viscosity
+  std::vector<float> fu(u.begin(), u.end()), fb(bv.begin(), bv.end()), feta(eta.begin(), eta.end());
+  std::vector<float> fAu(D * nc);
+  const CellEta<float> ce{feta.data()};
+  for (int t = 0; t < xi_count<D>(g); ++t) {
+    int p[3];
+    if (xi_cell<D>(g, t, p))
+      visc_op_cell<D, float>(fu.data(), nullptr, fAu.data(), ce, g, (float)beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
+  }
+  wr(out, std::vector<double>(fAu.begin(), fAu.end()));
+  fsweep<D, 0>(fu, fb, ce, g, (float)beta, hom);
+  fsweep<D, 1>(fu, fb, ce, g, (float)beta, hom);
+  if (D == 3) fsweep<D, (D == 3 ? 2 : 0)>(fu, fb, ce, g, (float)beta, hom);
+  wr(out, std::vector<double>(fu.begin(), fu.end()));
   return 0;
 }
 

@@ -105,4 +105,9 @@ def test_multigrid_pieces_match_oracle(harness, tmp_path, n, hom, seed):
     assert rel(take(n, 1), [x + prolong_cells(ec, gc, "neumann")]) < TOL
     assert rel(take(gc.node_shape, 1), [restrict_nodes(xn, g)]) < TOL
     assert rel(take(g.node_shape, 1), [xn + prolong_nodes(en, gc)]) < TOL
+    # the FP32 finest level of the mixed mode (x-interior-first maps, face
+    # viscosities formed from the cell viscosity): FP32 rounding of the same
+    # operator and sweep
+    assert rel(take(n, d), visc.apply(0, u)) < 1e-5
+    assert rel(take(n, d), us) < 1e-5
     assert pos == out.size
