@@ -12,7 +12,8 @@
 //         u + P ev (odd ghosts, d ncell); x + P ec (even ghosts);
 //         restricted xn (nnode_c); xn + P en (nnode); then in FP32 with
 //         the finest-level maps and cell viscosity: A u (d ncell) and u after
-//         one viscous sweep (d ncell), written as float64
+//         one viscous sweep (d ncell); x after one FP32 cell sweep; xn after
+//         one FP32 nodal sweep; all written as float64
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -151,6 +152,15 @@ static int run(FILE* in, FILE* out, const int* n, int hom) {
   fsweep<D, 1>(fu, fb, ce, g, (float)beta, hom);
   if (D == 3) fsweep<D, (D == 3 ? 2 : 0)>(fu, fb, ce, g, (float)beta, hom);
   wr(out, std::vector<double>(fu.begin(), fu.end()));
+  // the FP32 cell and nodal Poisson sweeps of the mixed MAC and nodal solves
+  std::vector<float> fx(x.begin(), x.end()), fbc(bc.begin(), bc.end());
+  for (int col = 0; col < 2; ++col)
+    for (int t = 0; t < rb_count<D>(g); ++t) k_cell_smooth_at<D, float>(fx.data(), fbc.data(), g, col, t);
+  wr(out, std::vector<double>(fx.begin(), fx.end()));
+  std::vector<float> fxn(xn.begin(), xn.end()), fbn(bn.begin(), bn.end());
+  for (int col = 0; col < (1 << D); ++col)
+    for (int t = 0; t < mc_count<D>(g, col); ++t) k_nodal_smooth_at<D, float>(fxn.data(), fbn.data(), g, col, t);
+  wr(out, std::vector<double>(fxn.begin(), fxn.end()));
   return 0;
 }
 

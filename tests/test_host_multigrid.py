@@ -110,4 +110,6 @@ def test_multigrid_pieces_match_oracle(harness, tmp_path, n, hom, seed):
     # operator and sweep
     assert rel(take(n, d), visc.apply(0, u)) < 1e-5
     assert rel(take(n, d), us) < 1e-5
+    assert rel(take(n, 1), xs) < 1e-5
+    assert rel(take(g.node_shape, 1), xns) < 1e-5
     assert pos == out.size
