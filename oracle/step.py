@@ -83,23 +83,34 @@ def step(grid, u, p, dt, rheo, rho=1.0, f=None, params=None, keep=False, predict
     visc = TensorViscous(grid, eta, dt / (2.0 * rho))
     ustar, st_visc = bicgstab_solve(visc, [uc.copy() for uc in u], rhs, params)
 
-    w = node_weights(grid)
-    v = [ustar[c] / dt + Gp[c] / rho for c in range(d)]
-    rhs_nod = rho * nodal_div(v, grid, w)
-    phi, st_nod = mg_solve(NodalPoisson(grid), [p_u.copy()], [rhs_nod], params)
-    Gphi = cell_grad_nodal(phi[0], grid)
-    unew = [ustar[c] + (dt / rho) * (Gp[c] - Gphi[c]) for c in range(d)]
+    unew, phi, rhs_nod, st_nod = nodal_project(grid, ustar, p_u, Gp, dt, rho, params)
 
     res.u = unew
-    res.p = nodes_full(phi[0], grid)
+    res.p = nodes_full(phi, grid)
     res.stats = {"mac": st_mac, "visc": st_visc, "nodal": st_nod}
     if keep:
         res.eta, res.Gp, res.Lu, res.F = eta, Gp, Lu, F
         res.uL, res.uR, res.uadv = uL, uR, uadv
         res.rhs_mac, res.phi_mac, res.umac = rhs_mac, phi_mac[0], umac
         res.A, res.rhs, res.ustar = A, rhs, ustar
-        res.rhs_nod, res.phi = rhs_nod, phi[0]
+        res.rhs_nod, res.phi = rhs_nod, phi
     return res
+
+
+def nodal_project(grid, ustar, p_u, Gp, dt, rho=1.0, params=None):
+    """Stage 7 (Eqs. 17-19): solve L phi = rho D(u*/dt + G p/rho) with the
+    warm start p, then u^{m+1} = u* + dt/rho (G p - G phi) and p^{m+1/2} = phi.
+    ``p_u`` holds the unique nodes of p^{m-1/2}, ``Gp`` its cell gradient.
+    Returns (u^{m+1}, phi on the unique nodes, the right-hand side, stats)."""
+    params = params or SolverParams()
+    d = grid.d
+    w = node_weights(grid)
+    v = [ustar[c] / dt + Gp[c] / rho for c in range(d)]
+    rhs_nod = rho * nodal_div(v, grid, w)
+    phi, st_nod = mg_solve(NodalPoisson(grid), [p_u.copy()], [rhs_nod], params)
+    Gphi = cell_grad_nodal(phi[0], grid)
+    unew = [ustar[c] + (dt / rho) * (Gp[c] - Gphi[c]) for c in range(d)]
+    return unew, phi[0], rhs_nod, st_nod
 
 
 def cfl_dt(grid, u, cfl, u_ref=1.0):
