@@ -169,7 +169,9 @@ int hbf_project(hbf_ctx* ctx, double dt, double* u_dev, double* p_dev, hbf_solve
  * NULL.  Returns HBF_ERR_NOT_CONVERGED if any solve did not converge. */
 int hbf_step(hbf_ctx* ctx, double dt, hbf_step_stats* stats);
 
-/* dt = cfl h / max(max|u|, 1) for the current U (synchronises). */
+/* dt = cfl h / max(max|u|, 1) for the current U (synchronises).  Returns NaN
+ * (and hbf_last_error says why) when U holds a NaN or an Inf or a CUDA call
+ * failed. */
 double hbf_cfl_dt(hbf_ctx* ctx, double cfl);
 
 /* Event timing of launches, per kernel class (slot):
@@ -209,7 +211,13 @@ int64_t hbf_launch_count(const hbf_ctx* ctx);
  * capture.  All calls share the one array and each overwrites the slots it
  * reads, so nothing carries over between calls, but calls whose GPU work
  * overlaps (different streams, or concurrent host threads) race on it.
- * Returns HBF_OK, HBF_ERR_ARG or HBF_ERR_CUDA. */
+ *
+ * A NaN or Inf in u_dev makes *dt_dev NaN.  The call cannot report that in
+ * its return value without waiting for the GPU, which a caller inside a
+ * stream capture may not do; check the written dt (isnan) where that matters.
+ * Returns HBF_OK, HBF_ERR_ARG, or HBF_ERR_CUDA (a launch failed, or an error
+ * from earlier work was already pending: it is left for the caller to read
+ * and nothing is launched). */
 #define HBF_NOALLOC_MAX_N 67108864LL
 int hbf_cfl_dt_noalloc(const double* u_dev, int64_t n, double h, double cfl, double* dt_dev, void* stream);
 
@@ -252,7 +260,10 @@ int hbf_unet_tensor_status(hbf_unet* net);
 /* y = net(x); y_dev may be NULL (the output stays inside the network) */
 int hbf_unet_forward(hbf_unet* net, const float* x_dev, float* y_dev);
 /* masked mean squared error of the last forward output against t; writes the
- * output gradient to gy_dev and the loss to *loss (synchronises) */
+ * output gradient to gy_dev and the loss to *loss (synchronises).  Returns
+ * HBF_ERR_TIMEOUT (and clears the flag) when a tcgen05 convolution gave up
+ * waiting for the tensor cores since the flag was last cleared: the forward
+ * output, the loss and the gradient are then not valid. */
 int hbf_unet_loss(hbf_unet* net, const float* t_dev, const float* mask_dev, float* gy_dev, double* loss);
 /* accumulate parameter gradients of the last forward for output gradient gy */
 int hbf_unet_backward(hbf_unet* net, const float* gy_dev);
@@ -263,7 +274,9 @@ int hbf_unet_adam(hbf_unet* net, double lr, double beta1, double beta2, double e
 /* Use net (NULL disables) for the initial guess of every nodal projection
  * solve of ctx: with r0 = b - L p the warm-start residual, the candidate guess
  * is p + |r0|_inf net(r0 / |r0|_inf); it is kept only if its residual is
- * smaller than |r0|_inf, otherwise the solve starts from p.  The network's
+ * smaller than |r0|_inf, otherwise the solve starts from p (also when a
+ * tcgen05 convolution of that forward pass gave up waiting for the tensor
+ * cores, whose flag the step then clears).  The network's
  * box must hold the (n+1)^d nodes: each of its sizes >= n[a] + 1. */
 int hbf_set_guess_model(hbf_ctx* ctx, hbf_unet* net);
 /* The same with the network on the nodes of multigrid level `level` (0 = the

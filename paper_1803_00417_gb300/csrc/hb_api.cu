@@ -489,6 +489,10 @@ double hbf_cfl_dt(hbf_ctx* c, double cfl) {
   int st = 0;
   double umax = reduce_max_abs(c, c->u, (long long)c->dim * c->g.ncell, &st);
   if (st) return NAN;
+  if (!std::isfinite(umax)) {  // the reduction maps NaN and Inf to +inf
+    fail(c, HBF_ERR_NONFINITE, "non-finite velocity");
+    return NAN;
+  }
   return cfl * c->g.h / std::fmax(umax, 1.0);
 }
 

@@ -8,6 +8,7 @@
 // Singular problems (MAC and nodal potentials) remove the (weighted) mean of
 // the right-hand side and pin the mean of the iterate after each cycle and the
 // bottom solve.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <cstdio>
@@ -206,33 +207,41 @@ __global__ void k_noalloc_cfl_final(const double* __restrict__ part, int nb, dou
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (int)(blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
     for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-    if (threadIdx.x == 0) *dt_out = cfl * h / fmax(v, 1.0);
+    // every finite |u| is below +inf, so +inf marks a non-finite input: dt
+    // becomes NaN rather than a silent 0
+    if (threadIdx.x == 0) *dt_out = isinf(v) ? (double)NAN : cfl * h / fmax(v, 1.0);
   }
 }
 
 // Device address of g_noalloc_partial per device, looked up once per device
 // (with that device current) and cached; the name itself is only a host-side
-// stand-in and must never be handed to a kernel.
+// stand-in and must never be handed to a kernel.  The cache entries are
+// atomics: host threads making their first calls on one device at the same
+// time may each look the address up, and all of them store the same value.
+// A cudaDeviceReset unloads the module, after which a cached address is
+// stale; the library's contexts do not survive a reset either.
 static double* noalloc_scratch(int* st) {
   constexpr int kMaxDevices = 64;
-  static double* addr[kMaxDevices] = {nullptr};
+  static std::atomic<double*> addr[kMaxDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     *st = HBF_ERR_CUDA;
     return nullptr;
   }
-  if (!addr[dev]) {
+  double* a = addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partial);
     if (e != cudaSuccess || !p) {
       *st = HBF_ERR_CUDA;
       return nullptr;
     }
-    addr[dev] = (double*)p;
+    a = (double*)p;
+    addr[dev].store(a, std::memory_order_release);
   }
   *st = HBF_OK;
-  return addr[dev];
+  return a;
 }
 
 // ---------------------------------------------------------------------------
@@ -1151,6 +1160,9 @@ extern "C" int hbf_cfl_dt_noalloc(const double* u_dev, int64_t n, double h, doub
   int st = 0;
   double* part = noalloc_scratch(&st);
   if (st) return st;
+  // an error left pending by earlier work of the caller is not this call's:
+  // leave it for the caller to read and launch nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return HBF_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   int nb = (int)((n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
   k_noalloc_maxabs_partial<<<nb, kThreads, 0, s>>>(u_dev, (long long)n, part);

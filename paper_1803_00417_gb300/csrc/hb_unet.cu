@@ -502,6 +502,18 @@ __global__ void k_net_to_nodes(const float* __restrict__ y, int e0, int e1, int 
 
 namespace hb {
 
+// 1 if a tcgen05 convolution of N gave up waiting for the tensor cores
+// since the flag was last cleared (then clears it); synchronises stream s
+int take_tc_err(hbf_unet* N, cudaStream_t s) {
+  if (!N->tc_err) return 0;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, N->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return 1;
+  if (h) cudaMemsetAsync(N->tc_err, 0, sizeof(int), s);
+  return h != 0;
+}
+
 void release_guess(hbf_ctx* c) {
   if (c->ntry) cudaFree(c->ntry);
   if (c->nzero) cudaFree(c->nzero);
@@ -560,6 +572,10 @@ int apply_guess(hbf_ctx* c, const double* b, double* p, int* used) {
   const double ww = reduce_dot(c, w, w, nn, &st);
   if (st) return st;
   if (!(ww > 0.0) || !std::isfinite(rw)) return HBF_OK;
+  // a tcgen05 convolution that gave up waiting left part of the output
+  // unwritten: discard the candidate (the solve starts from p) and clear
+  // the flag (the reductions above have synchronised the stream)
+  if (take_tc_err(N, c->stream)) return HBF_OK;
   const double alpha = -rw / ww;
   axmy(c, rtry, c->nres0, -alpha, w, nn);
   const double n1 = reduce_max_abs(c, rtry, nn, &st);
@@ -795,6 +811,12 @@ int hbf_unet_loss(hbf_unet* N, const float* t_dev, const float* mask_dev, float*
   double s = 0.0;
   for (int q = 0; q < nb; ++q) s += N->hpart[q];
   *loss = s;
+  // the loss is the first synchronising call after a training forward pass:
+  // a tensor-core wait that gave up there invalidates this output
+  if (hb::take_tc_err(N, N->stream)) {
+    N->err = "a tcgen05 convolution gave up waiting for the tensor cores";
+    return HBF_ERR_TIMEOUT;
+  }
   return check(N, "unet loss");
 }
 

@@ -18,7 +18,15 @@ namespace hb {
 namespace nn {
 
 constexpr int kTcM = 128;                 // points per CTA (the MMA's M)
-constexpr long long kTcWaitLimit = 1 << 24;  // mbarrier polls before giving up
+// mbarrier polls before a wait on the tensor cores gives up.  A CTA that
+// gives up sets the network's error flag (the host then reports
+// HBF_ERR_TIMEOUT and discards every output of that forward pass), waits
+// again on the same phase for up to kTcDrainLimit polls so that no MMA it
+// issued is still writing its TMEM columns or reading its shared memory, and
+// only then frees its TMEM and exits.  Completion of one CTA's MMAs takes
+// microseconds, so neither limit is reached in normal operation.
+constexpr long long kTcWaitLimit = 1 << 24;
+constexpr long long kTcDrainLimit = 1 << 27;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -44,8 +52,9 @@ __host__ __device__ constexpr int tc_cols(int n) {
   return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512)));
 }
 
-__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kTcWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity,
+                                                 long long limit = kTcWaitLimit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -144,8 +153,8 @@ __global__ void __launch_bounds__(kTcM, 1) k_conv_fwd_tc(const bf16* __restrict_
     // every thread waits for the MMAs before the operands are overwritten;
     // the block agrees on the outcome so that all threads leave together
     const bool mine = mbar_wait_parity(bar, parity);
-    parity ^= 1u;
     ok = __syncthreads_and(mine ? 1 : 0) != 0;
+    if (ok) parity ^= 1u;  // on failure parity keeps the phase still pending
   }
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (ok) {
@@ -177,8 +186,10 @@ __global__ void __launch_bounds__(kTcM, 1) k_conv_fwd_tc(const bf16* __restrict_
         dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
       }
     }
-  } else if (tid == 0) {
-    atomicExch(err, 1);
+  } else {
+    if (tid == 0) atomicExch(err, 1);
+    // drain: the MMAs of the pending phase must finish before TMEM is freed
+    mbar_wait_parity(bar, parity, kTcDrainLimit);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -325,8 +336,9 @@ __global__ void __launch_bounds__(kTcM, 1) k_conv_fwd_tc_halo(const bf16* __rest
         dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
       }
     }
-  } else if (tid == 0) {
-    atomicExch(err, 1);
+  } else {
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait_parity(bar, 0u, kTcDrainLimit);  // drain before TMEM is freed
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
