@@ -293,6 +293,104 @@ const char* hbf_last_error(const hbf_ctx* ctx);
 void hbf_destroy(hbf_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
+ * Start-up, steady state and cessation of the lid-driven cavity (Sec. III A:
+ * the steady criterion; Sec. IV: start-up from rest, steady state, the lid
+ * stopped and the fluid brought to rest in finite time; yield surfaces,
+ * stagnant and plug zones; Sec. IV and V: centre-line profiles and vortex
+ * centres), and the checkpoint record of a context.  The diagnostics read
+ * the context's current U and synchronise its stream.
+ * ------------------------------------------------------------------------- */
+
+/* Everything hbf_step reads besides U and P, plus the time and step count. */
+typedef struct {
+  int32_t dim;               /* 2 or 3 */
+  int32_t precision;         /* an hbf_precision (informative on restore) */
+  int64_t n[3];              /* cells per axis (n[2] = 1 in 2D) */
+  double h;                  /* cell size */
+  double t;                  /* time: sum of the dt of the steps taken */
+  int64_t step;              /* steps taken (hbf_step, hbf_batch_step) */
+  double K, nexp, tau_y, m;  /* as given to hbf_set_rheology */
+  int32_t reg_power;
+  int32_t predictor_viscous; /* hbf_set_predictor_viscous */
+  double rho;                /* hbf_set_density */
+  double f[3];               /* hbf_set_body_force */
+  double wall_u[18];         /* layout of hbf_init_grid */
+} hbf_state;
+
+/* Fill *state and, where not NULL, copy U (d*ncell doubles) and P (nnode
+ * doubles) out to host or device memory.  Synchronises. */
+int hbf_get_state(hbf_ctx* ctx, hbf_state* state, double* u, double* p);
+/* Restore a record of hbf_get_state: dim, n and h must be the context's
+ * (HBF_ERR_ARG otherwise; the precision may differ); sets the rheology,
+ * density, body force, predictor form, walls, time and step count, and copies
+ * U and P in where not NULL (host or device).  Synchronises. */
+int hbf_set_state(hbf_ctx* ctx, const hbf_state* state, const double* u, const double* p);
+
+/* Replace the wall velocities (layout and rules of hbf_init_grid): the
+ * cessation study stops the lid this way.  HBF_ERR_ARG for a non-zero normal
+ * component.  Also valid on a batch cavity (its tables are rebuilt). */
+int hbf_set_walls(hbf_ctx* ctx, const double wall_u[18]);
+
+/* The steady criterion of Sec. III A for the last hbf_step:
+ * max|u^{m+1} - u^m| / max|u^m|.  The paper's pointwise quotient is undefined
+ * where u^m = 0, so the two maxima are taken separately; +inf when u^m = 0.
+ * HBF_ERR_ARG when U was set, or a batched step taken, since that step. */
+int hbf_step_change(hbf_ctx* ctx, double* change);
+
+typedef struct {
+  double tau_max;     /* max over cells of |tau| = 2 eta |gamma_dot| (tau = 2 eta gamma_dot; norm of Eq. 1) */
+  int64_t yielded;    /* cells with |tau| > tau_y */
+  int64_t cells[3];   /* unyielded cells in stagnant [0], plug [1] and attached [2] zones */
+  int64_t zones[3];   /* number of zones of each kind */
+} hbf_yield_info;
+/* Yield state of the current U, with eta(|gamma_dot|) of Eq. 23: a cell is
+ * unyielded where |tau| <= tau_y (Sec. IV: the yield surface is the contour
+ * |tau| = tau_0).  Unyielded cells sharing a face form zones: a zone touching
+ * a wall at rest is stagnant, one touching no wall a plug (Sec. IV), one
+ * touching moving walls only attached.  labels: NULL, or ncell int32 (host or
+ * device, cell layout): -1 for a yielded cell, else the smallest cell index
+ * of its zone. */
+int hbf_yield(hbf_ctx* ctx, hbf_yield_info* info, int32_t* labels);
+
+typedef struct {
+  int64_t steps;          /* steps taken by the call */
+  double t;               /* the context's time after the call */
+  double change;          /* hbf_run_steady: the last step's change */
+  double tau_ratio;       /* hbf_run_cessation: max |tau| / tau_y after the last step */
+  double t_c;             /* hbf_run_cessation: time from the call to the first state with no yielded cell */
+  double t_c_interp;      /* the same with max|tau|/tau_y = 1 interpolated linearly between the last two steps */
+  int32_t reached;        /* 1 if the criterion was met within max_steps */
+  int32_t not_converged;  /* steps at which a solve stopped at its cycle cap */
+} hbf_run_info;
+
+/* Start-up (Sec. IV): hbf_step(dt) until hbf_step_change falls below tol
+ * (1e-5 in the paper) or max_steps steps were taken (then reached = 0).  An
+ * error of a step other than HBF_ERR_NOT_CONVERGED ends the run and is
+ * returned. */
+int hbf_run_steady(hbf_ctx* ctx, double dt, double tol, int64_t max_steps, hbf_run_info* info);
+/* Cessation (Sec. IV): set every wall at rest, then hbf_step(dt) until no
+ * cell is yielded (t_c) or max_steps steps were taken.  HBF_ERR_ARG without a
+ * yield stress.  Errors as for hbf_run_steady. */
+int hbf_run_cessation(hbf_ctx* ctx, double dt, int64_t max_steps, hbf_run_info* info);
+
+/* Velocity component comp along the line parallel to axis `along` through
+ * the box centre (Sec. IV and V centre-line profiles): n[along] values; across
+ * each other axis the mean of the two middle cells for an even count, the
+ * middle cell for an odd one.  out: host or device. */
+int hbf_centreline(hbf_ctx* ctx, int comp, int along, double* out);
+/* Stream function of the centre plane and the primary vortex centre
+ * (Sec. IV, V A).  The plane is the box in 2D and the plane normal to y
+ * through the centre in 3D (u_x averaged across y as for hbf_centreline);
+ * (a, b) = (x, y) in 2D, (x, z) in 3D.  psi: NULL or (n_a+1)(n_b+1) doubles,
+ * a fastest: psi = 0 on the low b wall and psi(i, j+1) = psi(i, j) + h u_x
+ * with u_x on the a-face i of cell row j the mean of its two cells (0 on the
+ * walls normal to a).  centre: the node where |psi| is largest (the smallest
+ * index among ties), refined by a parabola through its two neighbours along
+ * each in-plane axis, in coordinates of the plane (node k at k h); psi_c: psi
+ * at that node. */
+int hbf_vortex(hbf_ctx* ctx, double* psi, double centre[2], double* psi_c);
+
+/* ---------------------------------------------------------------------------
  * Batched sweep: ncav independent cavities (sizes, rheology and time steps of
  * their own) each advanced by the step of hbf_step (Sec. III A) in one call.
  * The paper runs one problem at a time; batching is a service of this

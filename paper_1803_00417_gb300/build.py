@@ -23,6 +23,7 @@ UNITS = {
     "hb_unet.cu": [],
     "hb_batch_explicit.cu": ["-fmad=false"],
     "hb_batch.cu": [],
+    "hb_drive.cu": ["-fmad=false"],
 }
 
 

@@ -321,6 +321,7 @@ int hbf_set_rheology(hbf_ctx* c, double K, double n, double tau_y, double m, int
   if (!c) return HBF_ERR_ARG;
   if (!(K >= 0.0) || !(n > 0.0) || !(tau_y >= 0.0) || !(m > 0.0)) return fail(c, HBF_ERR_ARG, "bad rheology");
   if (!reg_power && n < 1.0) return fail(c, HBF_ERR_ARG, "reg_power = 0 needs n >= 1 (eta bounded at g = 0)");
+  c->K = K;
   c->rheo.c2 = std::pow(2.0, n - 1.0) * K;
   c->rheo.n = n;
   c->rheo.tau = tau_y;
@@ -398,6 +399,7 @@ static int copy_field(hbf_ctx* c, int which, double* host_or_dev, bool in) {
 }
 
 int hbf_set_field(hbf_ctx* c, int which, const double* src) {
+  if (c && (which == HBF_U || which == HBF_USTAR)) c->prev_valid = false;
   return copy_field(c, which, const_cast<double*>(src), true);
 }
 
@@ -480,7 +482,10 @@ int hbf_step(hbf_ctx* c, double dt, hbf_step_stats* stats) {
   if (st) worst = st;
   double* t = c->u;
   c->u = c->ustar;
-  c->ustar = t;
+  c->ustar = t;  // now u^m, which hbf_step_change compares with
+  c->prev_valid = true;
+  c->t += dt;
+  ++c->nstep;
   return worst;
 }
 

@@ -1215,6 +1215,7 @@ Sig sig_of(hbf_batch* B, int c) {
   s.u = x->u;
   s.ustar = x->ustar;
   s.p = x->p;
+  s.walls_version = x->walls_version;
   return s;
 }
 
@@ -1223,7 +1224,8 @@ bool sig_eq(const Sig& a, const Sig& b) {
          a.rheo.reg_power == b.rheo.reg_power && a.rho == b.rho && a.f[0] == b.f[0] && a.f[1] == b.f[1] &&
          a.f[2] == b.f[2] && a.dt == b.dt && a.pv == b.pv && a.cfg.rtol == b.cfg.rtol &&
          a.cfg.max_cycles == b.cfg.max_cycles && a.cfg.nu1 == b.cfg.nu1 && a.cfg.nu2 == b.cfg.nu2 &&
-         a.cfg.nu_bottom == b.cfg.nu_bottom && a.u == b.u && a.ustar == b.ustar && a.p == b.p;
+         a.cfg.nu_bottom == b.cfg.nu_bottom && a.u == b.u && a.ustar == b.ustar && a.p == b.p &&
+         a.walls_version == b.walls_version;
 }
 
 void release_prepared(hbf_batch* B) {
@@ -1447,7 +1449,14 @@ int hbf_batch_step(hbf_batch* B, hbf_step_stats* stats) {
   if (!B) return HBF_ERR_ARG;
   int st = ensure_prepared(B);
   if (st) return st;
-  return B->sol->step(B, stats);
+  st = B->sol->step(B, stats);
+  if (st == HBF_OK || st == HBF_ERR_NOT_CONVERGED)
+    for (int c = 0; c < B->ncav; ++c) {
+      B->cav[c]->t += B->dt[c];
+      ++B->cav[c]->nstep;
+      B->cav[c]->prev_valid = false;  // the batch keeps no copy of u^m
+    }
+  return st;
 }
 
 int hbf_batch_autotune(hbf_batch* B, int reps, int* best_tile, int* best_bps, double* best_ms) {

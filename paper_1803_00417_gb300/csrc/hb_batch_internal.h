@@ -30,6 +30,7 @@ struct Sig {
   int pv;
   SolverCfg cfg;
   const double *u, *ustar, *p;
+  int walls_version;
 };
 
 struct Solvers;  // device argument tables of the solvers (hb_batch.cu)

@@ -66,43 +66,48 @@ __host__ __device__ inline double viscosity(double g, const Rheo& r) {
   return r.c2 * (half ? half_pow(g, r.e2) : pow(g, r.n - 1.0)) + 0.5 * r.tau * F;
 }
 
+// |gamma_dot| = sqrt(1/2 tr(D D^T)) at cell t (Eq. 1), D = (grad u + grad u^T)/2
+// from central differences with the wall ghosts
+template <int D>
+__host__ __device__ __forceinline__ double strain_norm_at(const double* __restrict__ u, const Geom& g, int t) {
+  int i, j, k;
+  cell_coords<D>(g, t, i, j, k);
+  int p[3] = {i, j, k};
+  double G[3][3];
+  const double i2h = 0.5 * g.ih;  // 1/(2h), rounded once on the host
+  // (grad u)_{ab} = d u_b / d x_a by central differences
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    const double* ub = u + (size_t)b * g.ncell;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int q1[3] = {p[0], p[1], p[2]}, q0[3] = {p[0], p[1], p[2]};
+      q1[a] += 1;
+      q0[a] -= 1;
+      G[a][b] = (uget<D>(ub, g, b, q1[0], q1[1], q1[2], false) -
+                 uget<D>(ub, g, b, q0[0], q0[1], q0[2], false)) *
+                i2h;
+    }
+  }
+  // tr(D D^T) with D = (G + G^T)/2 symmetric: the diagonal D_aa = G_aa,
+  // each off-diagonal pair counted twice
+  double s = 0.0, so = 0.0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) s += G[a][a] * G[a][a];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = a + 1; b < D; ++b) {
+      const double Dab = dhalf(G[a][b] + G[b][a]);
+      so += Dab * Dab;
+    }
+  return sqrt(dhalf(s + dtwice(so)));
+}
+
 template <int D>
 __host__ __device__ __forceinline__ void k_eta_at(const double* __restrict__ u, double* __restrict__ eta, const Geom& g, Rheo r, int t) {
-  
-    int i, j, k;
-    cell_coords<D>(g, t, i, j, k);
-    int p[3] = {i, j, k};
-    double G[3][3];
-    const double i2h = 0.5 * g.ih;  // 1/(2h), rounded once on the host
-    // (grad u)_{ab} = d u_b / d x_a by central differences
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      const double* ub = u + (size_t)b * g.ncell;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        int q1[3] = {p[0], p[1], p[2]}, q0[3] = {p[0], p[1], p[2]};
-        q1[a] += 1;
-        q0[a] -= 1;
-        G[a][b] = (uget<D>(ub, g, b, q1[0], q1[1], q1[2], false) -
-                   uget<D>(ub, g, b, q0[0], q0[1], q0[2], false)) *
-                  i2h;
-      }
-    }
-    // tr(D D^T) with D = (G + G^T)/2 symmetric: the diagonal D_aa = G_aa,
-    // each off-diagonal pair counted twice
-    double s = 0.0, so = 0.0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) s += G[a][a] * G[a][a];
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int b = a + 1; b < D; ++b) {
-        const double Dab = dhalf(G[a][b] + G[b][a]);
-        so += Dab * Dab;
-      }
-    double gn = sqrt(dhalf(s + dtwice(so)));
-    eta[t] = viscosity(gn, r);
-  }
+  eta[t] = viscosity(strain_norm_at<D>(u, g, t), r);
+}
 
 template <int D>
 __global__ void k_eta(const double* __restrict__ u, double* __restrict__ eta, const __grid_constant__ Geom g, Rheo r) {

@@ -97,6 +97,15 @@ struct hbf_ctx {
   double rho = 1.0;
   double f[3] = {0, 0, 0};
   int predictor_visc = 0;
+  double K = 1.0;           // the consistency K as given to hbf_set_rheology
+  double t = 0.0;           // time: the sum of the dt of every step taken
+  long long nstep = 0;      // steps taken
+  int walls_version = 0;    // bumped by hbf_set_walls (batched tables rebuild)
+  bool prev_valid = false;  // ustar holds u^m of the last hbf_step (hbf_step_change)
+  // diagnostics scratch, allocated on first use: d*ncell doubles, 2*ncell ints
+  double* dscr = nullptr;
+  int* dlab = nullptr;
+  unsigned long long* dcnt = nullptr;  // 8 counters
   hb::SolverCfg cfg;
   std::string err;
 

@@ -40,6 +40,53 @@ class StepStats(ctypes.Structure):
         return dict(mac=self.mac.as_dict(), visc=self.visc.as_dict(), nodal=self.nodal.as_dict())
 
 
+class State(ctypes.Structure):
+    """hbf_state: the checkpoint record of a context."""
+    _fields_ = [("dim", ctypes.c_int32), ("precision", ctypes.c_int32), ("n", ctypes.c_int64 * 3),
+                ("h", ctypes.c_double), ("t", ctypes.c_double), ("step", ctypes.c_int64),
+                ("K", ctypes.c_double), ("nexp", ctypes.c_double), ("tau_y", ctypes.c_double),
+                ("m", ctypes.c_double), ("reg_power", ctypes.c_int32), ("predictor_viscous", ctypes.c_int32),
+                ("rho", ctypes.c_double), ("f", ctypes.c_double * 3), ("wall_u", ctypes.c_double * 18)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+    @classmethod
+    def from_dict(cls, d):
+        s = cls()
+        for name, typ in cls._fields_:
+            v = d[name]
+            if isinstance(v, list):
+                getattr(s, name)[:] = v
+            else:
+                setattr(s, name, v)
+        return s
+
+
+class YieldInfo(ctypes.Structure):
+    _fields_ = [("tau_max", ctypes.c_double), ("yielded", ctypes.c_int64), ("cells", ctypes.c_int64 * 3),
+                ("zones", ctypes.c_int64 * 3)]
+
+    def as_dict(self):
+        kinds = ("stagnant", "plug", "attached")
+        return dict(tau_max=self.tau_max, yielded=self.yielded,
+                    cells={k: self.cells[i] for i, k in enumerate(kinds)},
+                    zones={k: self.zones[i] for i, k in enumerate(kinds)})
+
+
+class RunInfo(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("t", ctypes.c_double), ("change", ctypes.c_double),
+                ("tau_ratio", ctypes.c_double), ("t_c", ctypes.c_double), ("t_c_interp", ctypes.c_double),
+                ("reached", ctypes.c_int32), ("not_converged", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 SIGNATURES = {
@@ -92,6 +139,18 @@ SIGNATURES = {
                                      ctypes.c_double]),
     "hbf_set_guess_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hbf_set_guess_model_level": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "hbf_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(State), ctypes.c_void_p, ctypes.c_void_p]),
+    "hbf_set_walls": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "hbf_step_change": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "hbf_yield": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(YieldInfo), ctypes.c_void_p]),
+    "hbf_run_steady": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                      ctypes.POINTER(RunInfo)]),
+    "hbf_run_cessation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64,
+                                         ctypes.POINTER(RunInfo)]),
+    "hbf_centreline": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "hbf_vortex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]),
     "hbf_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hbf_destroy": (None, [ctypes.c_void_p]),
@@ -156,7 +215,7 @@ def _ptr(x):
     if hasattr(x, "data_ptr"):
         return ctypes.c_void_p(x.data_ptr())
     if isinstance(x, np.ndarray):
-        assert x.dtype == np.float64 and x.flags.c_contiguous
+        assert x.dtype in (np.float64, np.int32) and x.flags.c_contiguous
         return ctypes.c_void_p(x.ctypes.data)
     return ctypes.c_void_p(int(x))
 
@@ -318,6 +377,87 @@ class HBFlow:
 
     def cfl_dt(self, cfl):
         return float(self.lib.hbf_cfl_dt(self.ctx, cfl))
+
+    # ---- checkpoint, walls and the start-up / steady / cessation study -----------
+    def get_state(self, with_fields=True):
+        """(record dict, flat U, flat P) of hbf_get_state."""
+        s = State()
+        u = np.empty(self.d * self.ncell) if with_fields else None
+        p = np.empty(int(np.prod(self.node_shape))) if with_fields else None
+        self._check(self.lib.hbf_get_state(self.ctx, ctypes.byref(s), _ptr(u) if u is not None else None,
+                                           _ptr(p) if p is not None else None))
+        return s.as_dict(), u, p
+
+    def set_state(self, record, u=None, p=None):
+        s = State.from_dict(record)
+        self._check(self.lib.hbf_set_state(self.ctx, ctypes.byref(s), _ptr(u) if u is not None else None,
+                                           _ptr(p) if p is not None else None))
+
+    def save_checkpoint(self, path):
+        """``path``.json (the record) and ``path``.bin (U then P, float64)."""
+        import json
+        rec, u, p = self.get_state()
+        with open(path + ".json", "w") as f:
+            json.dump(rec, f)
+        np.concatenate([u, p]).tofile(path + ".bin")
+
+    def load_checkpoint(self, path):
+        import json
+        with open(path + ".json") as f:
+            rec = json.load(f)
+        data = np.fromfile(path + ".bin", dtype=np.float64)
+        nu = self.d * self.ncell
+        self.set_state(rec, np.ascontiguousarray(data[:nu]), np.ascontiguousarray(data[nu:]))
+        return rec
+
+    def set_walls(self, wall_u):
+        wu = np.zeros((3, 2, 3))
+        w = np.asarray(wall_u, dtype=np.float64).reshape(self.d, 2, self.d)
+        wu[:self.d, :, :self.d] = w
+        self._check(self.lib.hbf_set_walls(self.ctx, (ctypes.c_double * 18)(*wu.ravel())))
+
+    def step_change(self):
+        v = ctypes.c_double()
+        self._check(self.lib.hbf_step_change(self.ctx, ctypes.byref(v)))
+        return v.value
+
+    def yield_info(self, labels=False):
+        info = YieldInfo()
+        lab = np.empty(self.ncell, dtype=np.int32) if labels else None
+        self._check(self.lib.hbf_yield(self.ctx, ctypes.byref(info), _ptr(lab) if labels else None))
+        out = info.as_dict()
+        if labels:
+            out["labels"] = from_device_layout(lab, self.n, 1)[0]
+        return out
+
+    def run_steady(self, dt, tol=1e-5, max_steps=100000):
+        r = RunInfo()
+        self._check(self.lib.hbf_run_steady(self.ctx, dt, tol, int(max_steps), ctypes.byref(r)))
+        return r.as_dict()
+
+    def run_cessation(self, dt, max_steps=100000):
+        r = RunInfo()
+        self._check(self.lib.hbf_run_cessation(self.ctx, dt, int(max_steps), ctypes.byref(r)))
+        return r.as_dict()
+
+    def centreline(self, comp, along):
+        out = np.empty(self.n[along])
+        self._check(self.lib.hbf_centreline(self.ctx, int(comp), int(along), _ptr(out)))
+        return out
+
+    def vortex(self, with_psi=False):
+        """(x, y) of the primary vortex centre in the centre plane, psi there,
+        and optionally psi on the plane's nodes (array indexed [a, b])."""
+        na = self.n[0]
+        nb = self.n[2] if self.d == 3 else self.n[1]
+        psi = np.empty((na + 1) * (nb + 1)) if with_psi else None
+        c = (ctypes.c_double * 2)()
+        pc = ctypes.c_double()
+        self._check(self.lib.hbf_vortex(self.ctx, _ptr(psi) if with_psi else None, c, ctypes.byref(pc)))
+        out = dict(centre=(c[0], c[1]), psi=pc.value)
+        if with_psi:
+            out["field"] = psi.reshape(nb + 1, na + 1).T
+        return out
 
     PROFILE_SLOTS = dict(visc_smooth=0, visc_resid=1, nodal_smooth=2, nodal_resid=3, mac_smooth=4,
                          mac_resid=5, explicit=6, bottom=7, transfer=8, reduce=9, vector=10, coarse=11)
