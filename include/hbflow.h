@@ -113,6 +113,14 @@ int hbf_set_body_force(hbf_ctx* ctx, const double f[3]);
  * (1) or leave it out (0, default; see the library documentation). */
 int hbf_set_predictor_viscous(hbf_ctx* ctx, int on);
 
+/* Implicit weight theta of the viscous term: the solve of stage 6 is
+ * (I - theta dt/rho L_eta) u* = u^m - dt [u.grad u] + dt/rho (-G p +
+ * (1 - theta) L_eta u^m + f).  theta = 1/2 (default) is the Crank-Nicolson
+ * form of Eqs. 15-16; theta = 1 is backward Euler, which damps the modes
+ * with dt eta / (rho h^2) >> 1 that Crank-Nicolson leaves oscillating.
+ * HBF_ERR_ARG outside [1/2, 1]. */
+int hbf_set_theta(hbf_ctx* ctx, double theta);
+
 /* Multigrid controls: stop when ||b - A x||_inf <= rtol ||b||_inf or after
  * max_cycles V-cycles; nu1/nu2 pre/post smoothing sweeps; nu_bottom sweeps on
  * the coarsest level.  Defaults 1e-10, 200, 2, 2, 40. */
@@ -151,8 +159,8 @@ int hbf_mac_project(hbf_ctx* ctx, hbf_solve_stats* stats);
  * term and the viscous right-hand side RHS. */
 int hbf_advect_rhs(hbf_ctx* ctx, double dt);
 
-/* Stage 6 (Eq. 16): solve (I - dt/(2 rho) L_eta) u = rhs with the context's
- * current ETA, L_eta u = div(eta (grad u + grad u^T)), walls at their
+/* Stage 6 (Eq. 16): solve (I - theta dt/rho L_eta) u = rhs (theta = 1/2
+ * unless hbf_set_theta changed it) with the context's current ETA, L_eta u = div(eta (grad u + grad u^T)), walls at their
  * velocity.  rhs_dev, u_dev: device arrays of d*ncell doubles; u_dev holds the
  * initial guess on entry and the solution on exit.  stats may be NULL. */
 int hbf_solve_viscous(hbf_ctx* ctx, double dt, const double* rhs_dev, double* u_dev,
@@ -312,6 +320,7 @@ typedef struct {
   double K, nexp, tau_y, m;  /* as given to hbf_set_rheology */
   int32_t reg_power;
   int32_t predictor_viscous; /* hbf_set_predictor_viscous */
+  double theta;              /* hbf_set_theta */
   double rho;                /* hbf_set_density */
   double f[3];               /* hbf_set_body_force */
   double wall_u[18];         /* layout of hbf_init_grid */
@@ -369,9 +378,14 @@ typedef struct {
  * returned. */
 int hbf_run_steady(hbf_ctx* ctx, double dt, double tol, int64_t max_steps, hbf_run_info* info);
 /* Cessation (Sec. IV): set every wall at rest, then hbf_step(dt) until no
- * cell is yielded (t_c) or max_steps steps were taken.  HBF_ERR_ARG without a
- * yield stress.  Errors as for hbf_run_steady. */
-int hbf_run_cessation(hbf_ctx* ctx, double dt, int64_t max_steps, hbf_run_info* info);
+ * cell is yielded (t_c) or max_steps steps were taken.  The first damp_steps
+ * steps use theta = 1 (backward Euler in the viscous term, see
+ * hbf_set_theta), the rest the context's theta: stopping the lid excites
+ * modes with dt eta / (rho h^2) >> 1, which Crank-Nicolson carries on with
+ * an amplification factor near -1 (Rannacher's damped start after a
+ * discontinuity; 0 keeps the context's scheme throughout).  HBF_ERR_ARG
+ * without a yield stress.  Errors as for hbf_run_steady. */
+int hbf_run_cessation(hbf_ctx* ctx, double dt, int64_t max_steps, int damp_steps, hbf_run_info* info);
 
 /* Velocity component comp along the line parallel to axis `along` through
  * the box centre (Sec. IV and V centre-line profiles): n[along] values; across

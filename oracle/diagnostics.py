@@ -116,8 +116,10 @@ def resting(grid):
     return Grid(grid.n, grid.h, grid.periodic, np.zeros_like(grid.wall_u))
 
 
-def run_cessation(grid, u, p, dt, rheo, max_steps=1000, params=None):
-    """Hold every wall at rest and step until max |tau| <= tau_y.  Returns
+def run_cessation(grid, u, p, dt, rheo, max_steps=1000, params=None, damp_steps=0):
+    """Hold every wall at rest and step until max |tau| <= tau_y, the first
+    ``damp_steps`` steps with theta = 1 (backward Euler), the rest with the
+    Crank-Nicolson weighting.  Returns
     (u, p, steps, t_c, t_c_interp, history of max |tau| / tau_y): t_c is the
     time of the first step at which no cell is yielded, t_c_interp the
     linear interpolation of max |tau| / tau_y = 1 between the last two
@@ -128,7 +130,7 @@ def run_cessation(grid, u, p, dt, rheo, max_steps=1000, params=None):
     if hist[0] <= 1.0:
         return u, p, 0, 0.0, 0.0, hist
     for m in range(1, max_steps + 1):
-        r = step(g0, u, p, dt, rheo, params=params)
+        r = step(g0, u, p, dt, rheo, params=params, theta=1.0 if m <= damp_steps else 0.5)
         u, p = r.u, r.p
         hist.append(float(np.max(stress_norm(u, g0, rheo))) / rheo.tau_y)
         if hist[-1] <= 1.0:

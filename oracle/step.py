@@ -13,7 +13,10 @@ Order of the step:
     b = u^m - dt [u^MAC . grad u~] + dt/rho (-G p + 1/2 L_eta u^m + f).
  6. (I - dt/(2 rho) L_eta^m) u* = b, walls at their (constant) velocity
     (Eq. 16; L_eta u = 2 div(eta gamma_dot)), by V-cycle-preconditioned
-    BiCGStab (the paper leaves the solver to AMReX).
+    BiCGStab (the paper leaves the solver to AMReX).  This is the
+    Crank-Nicolson weighting of Eq. 15; ``theta`` generalises it to
+    (I - theta dt/rho L_eta) u* = ... + (1 - theta) dt/rho L_eta u^m
+    (theta = 1: backward Euler).
  7. nodal projection L phi = rho D(u*/dt + G p^{m-1/2}/rho) (Eq. 17),
     u^{m+1} = u* + dt/rho (G p^{m-1/2} - G phi), p^{m+1/2} = phi.
     Eq. 18 prints u^{m+1} = u* - dt/rho G phi, which is inconsistent with the
@@ -48,7 +51,7 @@ class StepResult:
     pass
 
 
-def step(grid, u, p, dt, rheo, rho=1.0, f=None, params=None, keep=False, predictor_visc=False):
+def step(grid, u, p, dt, rheo, rho=1.0, f=None, params=None, keep=False, predictor_visc=False, theta=0.5):
     """Advance (u^m, p^{m-1/2}) by dt.  ``u`` is a list of d cell arrays, ``p``
     a nodal array of shape n+1 per axis.  Returns a StepResult with u, p and the
     solve statistics (and every intermediate field when ``keep``)."""
@@ -78,9 +81,11 @@ def step(grid, u, p, dt, rheo, rho=1.0, f=None, params=None, keep=False, predict
         umac.append(um)
 
     A = advective_term(uL, uR, umac, grid)
-    rhs = [u[c] - dt * A[c] + (dt / rho) * (-Gp[c] + 0.5 * Lu[c] + f[c]) for c in range(d)]
+    wl = 1.0 - theta  # weight of the explicit viscous term (1/2 in Eq. 15)
+    rhs = [u[c] - dt * A[c] + (dt / rho) * (-Gp[c] + wl * Lu[c] + f[c]) for c in range(d)]
 
-    visc = TensorViscous(grid, eta, dt / (2.0 * rho))
+    beta = dt / (2.0 * rho) if theta == 0.5 else theta * dt / rho
+    visc = TensorViscous(grid, eta, beta)
     ustar, st_visc = bicgstab_solve(visc, [uc.copy() for uc in u], rhs, params)
 
     unew, phi, rhs_nod, st_nod = nodal_project(grid, ustar, p_u, Gp, dt, rho, params)

@@ -344,6 +344,13 @@ int hbf_set_body_force(hbf_ctx* c, const double f[3]) {
   return HBF_OK;
 }
 
+int hbf_set_theta(hbf_ctx* c, double theta) {
+  if (!c) return HBF_ERR_ARG;
+  if (!(theta >= 0.5 && theta <= 1.0)) return fail(c, HBF_ERR_ARG, "theta must lie in [1/2, 1]");
+  c->theta = theta;
+  return HBF_OK;
+}
+
 int hbf_set_predictor_viscous(hbf_ctx* c, int on) {
   if (!c) return HBF_ERR_ARG;
   c->predictor_visc = on ? 1 : 0;
@@ -438,7 +445,7 @@ int hbf_advect_rhs(hbf_ctx* c, double dt) {
 int hbf_solve_viscous(hbf_ctx* c, double dt, const double* rhs_dev, double* u_dev, hbf_solve_stats* s) {
   if (!c || !rhs_dev || !u_dev) return HBF_ERR_ARG;
   if (!(dt > 0.0)) return fail(c, HBF_ERR_ARG, "dt must be positive");
-  return solve_viscous(c, dt / (2.0 * c->rho), rhs_dev, u_dev, s);
+  return solve_viscous(c, visc_beta(dt, c->rho, c->theta), rhs_dev, u_dev, s);
 }
 
 int hbf_project(hbf_ctx* c, double dt, double* u_dev, double* p_dev, hbf_solve_stats* s) {
@@ -474,7 +481,7 @@ int hbf_step(hbf_ctx* c, double dt, hbf_step_stats* stats) {
                                           cudaMemcpyDeviceToDevice, c->stream),
                        "guess copy")))
     return st;
-  st = solve_viscous(c, dt / (2.0 * c->rho), c->rhs, c->ustar, &s->visc);
+  st = solve_viscous(c, visc_beta(dt, c->rho, c->theta), c->rhs, c->ustar, &s->visc);
   if (st && st != HBF_ERR_NOT_CONVERGED) return st;
   if (st) worst = st;
   st = hbf_project(c, dt, c->ustar, c->p, &s->nodal);

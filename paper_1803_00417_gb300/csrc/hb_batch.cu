@@ -507,7 +507,7 @@ static void build_inst(hbf_batch* B, Inst& I, int kind, bool hom0, T* (*x0)(hbf_
         a.out = R(c, l);
         for (int d = 0; d < 3; ++d) a.ef[d] = d < D ? V::ef(L, d) : nullptr;
         a.g = L.g;
-        a.beta = (T)(B->dt[q] / (2.0 * c->rho));
+        a.beta = (T)visc_beta(B->dt[q], c->rho, c->theta);
         a.hom = (l > 0 || hom0) ? 1 : 0;
         return a;
       });
@@ -776,7 +776,7 @@ struct SolversT : Solvers {
       a.n = a.m = D * L.g.ncell;
       for (int d = 0; d < D; ++d) a.ef[d] = L.ef[d];
       a.g = L.g;
-      a.beta = B->dt[q] / (2.0 * c->rho);
+      a.beta = visc_beta(B->dt[q], c->rho, c->theta);
       return a;
     });
     // MAC and nodal solves
@@ -823,7 +823,7 @@ struct SolversT : Solvers {
       a.out = c->kr;
       for (int d = 0; d < D; ++d) a.ef[d] = c->lv[0].ef[d];
       a.g = c->g;
-      a.beta = B->dt[q] / (2.0 * c->rho);
+      a.beta = visc_beta(B->dt[q], c->rho, c->theta);
       a.hom = 0;
       return a;
     });
@@ -836,7 +836,7 @@ struct SolversT : Solvers {
         a.out = outp(c);
         for (int d = 0; d < D; ++d) a.ef[d] = LvView<T>::ef(c->lv[0], d);
         a.g = c->g;
-        a.beta = (T)(B->dt[q] / (2.0 * c->rho));
+        a.beta = (T)visc_beta(B->dt[q], c->rho, c->theta);
         a.hom = 1;
         return a;
       });
@@ -1216,6 +1216,7 @@ Sig sig_of(hbf_batch* B, int c) {
   s.ustar = x->ustar;
   s.p = x->p;
   s.walls_version = x->walls_version;
+  s.theta = x->theta;
   return s;
 }
 
@@ -1225,7 +1226,7 @@ bool sig_eq(const Sig& a, const Sig& b) {
          a.f[2] == b.f[2] && a.dt == b.dt && a.pv == b.pv && a.cfg.rtol == b.cfg.rtol &&
          a.cfg.max_cycles == b.cfg.max_cycles && a.cfg.nu1 == b.cfg.nu1 && a.cfg.nu2 == b.cfg.nu2 &&
          a.cfg.nu_bottom == b.cfg.nu_bottom && a.u == b.u && a.ustar == b.ustar && a.p == b.p &&
-         a.walls_version == b.walls_version;
+         a.walls_version == b.walls_version && a.theta == b.theta;
 }
 
 void release_prepared(hbf_batch* B) {

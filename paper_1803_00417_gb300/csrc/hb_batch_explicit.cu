@@ -184,7 +184,7 @@ static void build_tables(hbf_batch* B, ExplicitTables& T) {
   std::vector<typename OpProjectUpdate<D>::Arg> a11;
   for (int i = 0; i < B->ncav; ++i) {
     hbf_ctx* c = B->cav[i];
-    const StepC k = step_consts(c->g, D, B->dt[i], c->rho);
+    const StepC k = step_consts(c->g, D, B->dt[i], c->rho, c->theta);
     Force fo{{c->f[0], c->f[1], c->f[2]}};
     a1.push_back({c->u, c->eta, c->g, c->rheo});
     a2.push_back({c->eta, {c->lv[0].ef[0], c->lv[0].ef[1], c->lv[0].ef[2]}, c->g});

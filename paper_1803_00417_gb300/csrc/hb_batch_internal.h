@@ -31,6 +31,7 @@ struct Sig {
   SolverCfg cfg;
   const double *u, *ustar, *p;
   int walls_version;
+  double theta;
 };
 
 struct Solvers;  // device argument tables of the solvers (hb_batch.cu)

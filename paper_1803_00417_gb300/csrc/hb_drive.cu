@@ -296,6 +296,7 @@ int hbf_get_state(hbf_ctx* c, hbf_state* s, double* u, double* p) {
   s->m = c->rheo.m;
   s->reg_power = c->rheo.reg_power;
   s->predictor_viscous = c->predictor_visc;
+  s->theta = c->theta;
   s->rho = c->rho;
   for (int a = 0; a < 3; ++a) s->f[a] = c->f[a];
   for (int a = 0; a < 3; ++a)
@@ -317,6 +318,7 @@ int hbf_set_state(hbf_ctx* c, const hbf_state* s, const double* u, const double*
   if ((st = hbf_set_density(c, s->rho))) return st;
   if ((st = hbf_set_body_force(c, s->f))) return st;
   if ((st = hbf_set_predictor_viscous(c, s->predictor_viscous))) return st;
+  if ((st = hbf_set_theta(c, s->theta))) return st;
   if ((st = hbf_set_walls(c, s->wall_u))) return st;
   if (u && (st = hbf_set_field(c, HBF_U, u))) return st;
   if (p && (st = hbf_set_field(c, HBF_P, p))) return st;
@@ -431,8 +433,8 @@ int hbf_run_steady(hbf_ctx* c, double dt, double tol, int64_t max_steps, hbf_run
   return HBF_OK;
 }
 
-int hbf_run_cessation(hbf_ctx* c, double dt, int64_t max_steps, hbf_run_info* info) {
-  if (!c || !info || !(dt > 0.0) || max_steps < 1) return HBF_ERR_ARG;
+int hbf_run_cessation(hbf_ctx* c, double dt, int64_t max_steps, int damp_steps, hbf_run_info* info) {
+  if (!c || !info || !(dt > 0.0) || max_steps < 1 || damp_steps < 0) return HBF_ERR_ARG;
   if (!(c->rheo.tau > 0.0)) return fail(c, HBF_ERR_ARG, "cessation needs a yield stress");
   std::memset(info, 0, sizeof *info);
   const double rest[18] = {0};
@@ -449,8 +451,11 @@ int hbf_run_cessation(hbf_ctx* c, double dt, int64_t max_steps, hbf_run_info* in
     return HBF_OK;
   }
   const double t0 = c->t;
+  const double theta = c->theta;
   for (int64_t m = 1; m <= max_steps; ++m) {
+    c->theta = m <= damp_steps ? 1.0 : theta;  // backward Euler for the first damp_steps steps
     st = hbf_step(c, dt, nullptr);
+    c->theta = theta;
     if (st == HBF_ERR_NOT_CONVERGED)
       ++info->not_converged;
     else if (st)

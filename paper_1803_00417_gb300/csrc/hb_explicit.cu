@@ -40,7 +40,7 @@ int launch_predict(hbf_ctx* c, double dt) {
   if (st) return st;
   if ((st = tensor_lu(c, c->u, c->Lu))) return st;
   HB_DISPATCH(c->dim, k_slopes, grid_for(g.ncell), c->u, c->slopes, g);
-  const StepC k = step_consts(g, c->dim, dt, c->rho);
+  const StepC k = step_consts(g, c->dim, dt, c->rho, c->theta);
   HB_DISPATCH(c->dim, k_hats, grid_for(g.ncell), c->u, c->slopes, c->Gp, c->Lu, fo, c->predictor_visc, c->hats,
               c->tcom, g, k);
   for (int a = 0; a < c->dim; ++a)
@@ -64,12 +64,12 @@ int launch_advect_rhs(hbf_ctx* c, double dt) {
   Force fo{{c->f[0], c->f[1], c->f[2]}};
   HB_DISPATCH(c->dim, k_advect_rhs, grid_for(c->g.ncell), c->u, c->uL[0], c->uL[1], c->uL[2], c->uR[0],
               c->uR[1], c->uR[2], c->umac[0], c->umac[1], c->umac[2], c->Gp, c->Lu, fo, c->rhs, c->g,
-              step_consts(c->g, c->dim, dt, c->rho));
+              step_consts(c->g, c->dim, dt, c->rho, c->theta));
   return cuda_check(c, cudaGetLastError(), "k_advect_rhs");
 }
 
 int launch_nodal_rhs(hbf_ctx* c, double dt, const double* ustar, const double* p, double* out) {
-  const StepC k = step_consts(c->g, c->dim, dt, c->rho);
+  const StepC k = step_consts(c->g, c->dim, dt, c->rho, c->theta);
   HB_DISPATCH(c->dim, k_grad_p_w, grid_for(c->g.ncell), p, ustar, c->Gp, c->wn, c->g, k);
   HB_DISPATCH(c->dim, k_nodal_rhs, grid_for(c->g.nnode), (const double*)c->wn, out, c->g, k);
   return cuda_check(c, cudaGetLastError(), "k_nodal_rhs");
@@ -78,7 +78,7 @@ int launch_nodal_rhs(hbf_ctx* c, double dt, const double* ustar, const double* p
 int launch_project_update(hbf_ctx* c, double dt, double* u, const double* p_old, const double* phi) {
   (void)p_old;  // G p^{m-1/2} is still in c->Gp from launch_nodal_rhs
   HB_DISPATCH(c->dim, k_project_update, grid_for(c->g.ncell), u, c->Gp, phi, c->g,
-              step_consts(c->g, c->dim, dt, c->rho));
+              step_consts(c->g, c->dim, dt, c->rho, c->theta));
   return cuda_check(c, cudaGetLastError(), "k_project_update");
 }
 

@@ -23,10 +23,12 @@ struct StepC {
   double dtr;   // dt / rho
   double idt;   // 1 / dt
   double inrm;  // 1 / (2^(D-1) h): the nodal divergence's normalisation
+  double wl;    // 1 - theta: the weight of the explicit viscous term L_eta u^m
 };
 
-inline StepC step_consts(const Geom& g, int dim, double dt, double rho) {
+inline StepC step_consts(const Geom& g, int dim, double dt, double rho, double theta = 0.5) {
   StepC k;
+  k.wl = 1.0 - theta;
   k.dt = dt;
   k.dt2h = dt / (2.0 * g.h);
   k.dth = dt / g.h;
@@ -503,7 +505,8 @@ __host__ __device__ __forceinline__ void k_advect_rhs_at(const double* __restric
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       size_t o = (size_t)c * g.ncell + t;
-      rhs[o] = u[o] - k.dth * A[c] + k.dtr * (-Gp[o] + dhalf(Lu[o]) + fo.f[c]);
+      const double lw = k.wl == 0.5 ? dhalf(Lu[o]) : k.wl * Lu[o];  // (1 - theta) L_eta u^m
+      rhs[o] = u[o] - k.dth * A[c] + k.dtr * (-Gp[o] + lw + fo.f[c]);
     }
   }
 

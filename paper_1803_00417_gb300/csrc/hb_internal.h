@@ -98,6 +98,7 @@ struct hbf_ctx {
   double f[3] = {0, 0, 0};
   int predictor_visc = 0;
   double K = 1.0;           // the consistency K as given to hbf_set_rheology
+  double theta = 0.5;       // implicit weight of the viscous term (1/2: Crank-Nicolson, Eq. 15)
   double t = 0.0;           // time: the sum of the dt of every step taken
   long long nstep = 0;      // steps taken
   int walls_version = 0;    // bumped by hbf_set_walls (batched tables rebuild)
@@ -162,6 +163,12 @@ struct hbf_ctx {
 namespace hb {
 
 constexpr int kRedBlocks = 1024;
+
+// beta = theta dt / rho of the viscous solve; theta = 1/2 is computed as
+// dt / (2 rho), the Crank-Nicolson form of Eq. 15
+inline double visc_beta(double dt, double rho, double theta) {
+  return theta == 0.5 ? dt / (2.0 * rho) : theta * dt / rho;
+}
 
 void prof_mark(hbf_ctx* c, int slot, bool start);
 

@@ -46,7 +46,7 @@ class State(ctypes.Structure):
                 ("h", ctypes.c_double), ("t", ctypes.c_double), ("step", ctypes.c_int64),
                 ("K", ctypes.c_double), ("nexp", ctypes.c_double), ("tau_y", ctypes.c_double),
                 ("m", ctypes.c_double), ("reg_power", ctypes.c_int32), ("predictor_viscous", ctypes.c_int32),
-                ("rho", ctypes.c_double), ("f", ctypes.c_double * 3), ("wall_u", ctypes.c_double * 18)]
+                ("theta", ctypes.c_double), ("rho", ctypes.c_double), ("f", ctypes.c_double * 3), ("wall_u", ctypes.c_double * 18)]
 
     def as_dict(self):
         out = {}
@@ -146,8 +146,9 @@ SIGNATURES = {
     "hbf_yield": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(YieldInfo), ctypes.c_void_p]),
     "hbf_run_steady": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                       ctypes.POINTER(RunInfo)]),
-    "hbf_run_cessation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64,
+    "hbf_run_cessation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
                                          ctypes.POINTER(RunInfo)]),
+    "hbf_set_theta": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "hbf_centreline": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "hbf_vortex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]),
@@ -290,6 +291,9 @@ class HBFlow:
     def set_body_force(self, f):
         ff = (ctypes.c_double * 3)(*(list(f) + [0.0] * (3 - len(f))))
         self._check(self.lib.hbf_set_body_force(self.ctx, ff))
+
+    def set_theta(self, theta):
+        self._check(self.lib.hbf_set_theta(self.ctx, float(theta)))
 
     def set_predictor_viscous(self, on):
         self._check(self.lib.hbf_set_predictor_viscous(self.ctx, int(bool(on))))
@@ -435,9 +439,9 @@ class HBFlow:
         self._check(self.lib.hbf_run_steady(self.ctx, dt, tol, int(max_steps), ctypes.byref(r)))
         return r.as_dict()
 
-    def run_cessation(self, dt, max_steps=100000):
+    def run_cessation(self, dt, max_steps=100000, damp_steps=0):
         r = RunInfo()
-        self._check(self.lib.hbf_run_cessation(self.ctx, dt, int(max_steps), ctypes.byref(r)))
+        self._check(self.lib.hbf_run_cessation(self.ctx, dt, int(max_steps), int(damp_steps), ctypes.byref(r)))
         return r.as_dict()
 
     def centreline(self, comp, along):

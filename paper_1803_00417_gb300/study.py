@@ -11,6 +11,8 @@ only: every step and every diagnostic runs in the CUDA library).
   evaluated after every step; at the time the paper stops the lid
   (t = 0.0205552) the state is checkpointed, the lid is stopped and the run
   continues until no cell is yielded: t_c, beside the paper's 1.2844e-3.
+  Each cessation runs with the Crank-Nicolson weighting throughout and with
+  the first steps after the stop taken by backward Euler (``--damp``).
   Yield zones (stagnant / plug) are reported at the paper's snapshot times
   of the start-up and of the cessation.
 * ``sweep`` (Sec. IV, V A): steady states of 2D cavities (Bingham at several
@@ -90,26 +92,30 @@ def startup(sim, dt, t_stop, snapshots, tol=1e-5):
                 wall_s=time.time() - t0, snapshots=snaps)
 
 
-def cessation_from(sim, dt, snapshots, max_steps):
+def cessation_from(sim, dt, snapshots, max_steps, damp_steps=0):
     """t_c from the current state (native driver), then the zones at the
-    snapshot times from the same state restored from a checkpoint."""
+    snapshot times from the same state restored from a checkpoint; the
+    state is restored again at the end.  damp_steps: backward-Euler steps
+    right after the lid stops (see hbf_run_cessation)."""
     rec, u, p = sim.get_state()
     t0 = time.time()
-    r = sim.run_cessation(dt, max_steps=max_steps)
+    r = sim.run_cessation(dt, max_steps=max_steps, damp_steps=damp_steps)
     wall = time.time() - t0
     sim.set_state(rec, u, p)
     d = sim.d
-    rest = np.zeros((d, 2, d))
-    sim.set_walls(rest)
+    sim.set_walls(np.zeros((d, 2, d)))
     snaps, done = [], 0
     for t in snapshots:
         k = steps_for(t, dt)
         while done < k:
+            sim.set_theta(1.0 if done < damp_steps else 0.5)
             sim.step(dt)
             done += 1
+        sim.set_theta(0.5)
         snaps.append(dict(t_paper=t, t=done * dt, **zone_summary(sim)))
-    return dict(steps=r["steps"], t_c=r["t_c"], t_c_interp=r["t_c_interp"], reached=bool(r["reached"]),
-                tau_ratio=r["tau_ratio"], wall_s=wall, snapshots=snaps)
+    sim.set_state(rec, u, p)
+    return dict(damp_steps=damp_steps, steps=r["steps"], t_c=r["t_c"], t_c_interp=r["t_c_interp"],
+                reached=bool(r["reached"]), tau_ratio=r["tau_ratio"], wall_s=wall, snapshots=snaps)
 
 
 def run_cessation_study(args):
@@ -118,11 +124,12 @@ def run_cessation_study(args):
         st = startup(sim, dt, T_STOP, STARTUP_SNAPSHOTS)
         at_stop = zone_summary(sim)
         vort = sim.vortex()
-        ce = cessation_from(sim, dt, CESSATION_SNAPSHOTS, max_steps=steps_for(20 * T_C_PAPER, dt))
+        ces = [cessation_from(sim, dt, CESSATION_SNAPSHOTS, steps_for(20 * T_C_PAPER, dt), k) for k in args.damp]
+        for ce in ces:
+            ce["t_c_rel_diff"] = (ce["t_c_interp"] - T_C_PAPER) / T_C_PAPER if ce["reached"] else None
         emit(dict(study="cessation", workload=f"cavity{args.n}_bingham_Re1_Bi10_Pa400", dt=dt,
-                  startup=st, at_lid_stop=dict(vortex=vort, **at_stop), cessation=ce,
-                  t_c_paper=T_C_PAPER,
-                  t_c_rel_diff=(ce["t_c_interp"] - T_C_PAPER) / T_C_PAPER if ce["reached"] else None), args.out)
+                  startup=st, at_lid_stop=dict(vortex=vort, **at_stop), cessation=ces,
+                  t_c_paper=T_C_PAPER), args.out)
         sim.close()
 
 
@@ -155,7 +162,7 @@ def run_cessation3d(args):
     st = startup(sim, dt, T_STOP, STARTUP_SNAPSHOTS)
     at_stop = zone_summary(sim)
     vort = sim.vortex()
-    ce = cessation_from(sim, dt, CESSATION_SNAPSHOTS, max_steps=steps_for(20 * T_C_PAPER, dt))
+    ce = [cessation_from(sim, dt, CESSATION_SNAPSHOTS, steps_for(20 * T_C_PAPER, dt), k) for k in args.damp]
     emit(dict(study="cessation3d", workload=f"cavity{args.n}^3_bingham_Re1_Bi10_Pa400", dt=dt,
               precision="mixed" if args.mixed else "fp64", startup=st,
               at_lid_stop=dict(vortex_centre_plane_y_half=vort, **at_stop), cessation=ce), args.out)
@@ -195,6 +202,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--mixed", action="store_true")
+    ap.add_argument("--damp", type=str, default="0,2",
+                    help="cessation variants: backward-Euler steps right after the lid stops")
     ap.add_argument("--out", type=str, default="")
     args = ap.parse_args(argv)
     from . import build
@@ -207,6 +216,7 @@ def main(argv=None):
     if args.study == "sweep":
         args.dt = args.dt[0]
     args.sizes = [int(v) for v in args.sizes.split(",")]
+    args.damp = [int(v) for v in args.damp.split(",")]
     dict(cessation=run_cessation_study, sweep=run_sweep, cessation3d=run_cessation3d, rate=run_rate)[args.study](args)
     return 0
 

@@ -152,10 +152,18 @@ def test_steady_and_cessation_drivers_match_oracle():
     # cessation from that state
     _, _, csteps, tc, tci, hist = dg.run_cessation(g, u1, p1, dt, rh, max_steps=600)
     assert np.isfinite(tc)
+    rec, us, ps = sim.get_state()
     c = sim.run_cessation(dt, max_steps=600)
     assert c["reached"] == 1 and c["steps"] == csteps
     assert c["t_c"] == pytest.approx(tc, rel=1e-12)
     assert c["t_c_interp"] == pytest.approx(tci, rel=1e-6)
     info = sim.yield_info()
     assert info["yielded"] == 0
+    # the same cessation with two backward-Euler steps after the lid stops
+    _, _, dsteps, dtc, _, _ = dg.run_cessation(g, u1, p1, dt, rh, max_steps=600, damp_steps=2)
+    sim.set_state(rec, us, ps)
+    c2 = sim.run_cessation(dt, max_steps=600, damp_steps=2)
+    assert c2["reached"] == 1 and c2["steps"] == dsteps
+    assert c2["t_c"] == pytest.approx(dtc, rel=1e-12)
+    assert sim.get_state(False)[0]["theta"] == 0.5  # restored after the damped steps
     sim.close()

@@ -175,6 +175,23 @@ def test_smallest_grid_and_odd_sizes():
         sim.close()
 
 
+@pytest.mark.parametrize("n,seed,theta", [((48, 32), 33, 1.0), ((16, 16, 12), 34, 0.75)])
+def test_theta_weighting_matches_oracle(n, seed, theta):
+    # the viscous term weighted theta (implicit) / 1 - theta (explicit)
+    # instead of Crank-Nicolson's 1/2 / 1/2
+    sim, g, rh, cfg, u, p = setup(n, seed, Re=1.0, Bi=10.0, Pa=400.0, nexp=1.0)
+    sim.set_theta(theta)
+    for _ in range(2):
+        ref = step(g, u, p, cfg["dt"], rh, theta=theta)
+        sim.step(cfg["dt"])
+        assert rel_l2(sim.velocity(), ref.u) < TOL_STEP
+        assert rel_max(sim.velocity(), ref.u) < 10 * TOL_STEP
+        u, p = ref.u, ref.p
+        sim.set_velocity(u)
+        sim.set_pressure(p)
+    sim.close()
+
+
 @pytest.mark.parametrize("n,seed", [((40, 24), 31), ((16, 12, 10), 32)])
 def test_paper_form_predictor_matches_oracle(n, seed):
     # Eq. 14 as printed: the edge-state forcing includes the explicit stress

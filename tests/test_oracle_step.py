@@ -130,3 +130,32 @@ def test_rest_state_and_mac_divergence(d):
     div_adv = np.max(np.abs(mac_div(r.uadv, g)))
     div_mac = np.max(np.abs(mac_div(r.umac, g)))
     assert div_adv > 1e-3 and div_mac <= 1e-9 * div_adv
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.75, 1.0])
+def test_viscous_decay_of_a_shear_wave_has_the_theta_amplification(theta):
+    # u = (0, v(x)) with v = sin(2 pi k x) on a doubly periodic box and a
+    # constant viscosity: divergence-free, no advection (u_x = 0, v does not
+    # vary along y), no pressure.  The step is the viscous solve alone, whose
+    # discrete operator acts on the mode by -nu 4 sin^2(pi k h) / h^2, so one
+    # step multiplies v by R(z) = (1 - (1 - theta) z) / (1 + theta z),
+    # z = dt nu 4 sin^2(pi k h) / h^2 (the theta-scheme's amplification).
+    N, k, nu, dt = 16, 3, 0.8, 0.05
+    h = 1.0 / N
+    g = Grid((N, N), h, periodic=(True, True))
+    x = (np.arange(N) + 0.5) * h
+    v = np.tile(np.sin(2 * np.pi * k * x)[:, None], (1, N))
+    u = [np.zeros((N, N)), v]
+    p = np.zeros((N + 1, N + 1))
+    rh = Rheology(K=nu, n=1.0, tau_y=0.0, m=1e4, reg_power=False)
+    r = step(g, u, p, dt, rh, params=SolverParams(rtol=1e-13), theta=theta)
+    z = dt * nu * 4.0 * np.sin(np.pi * k * h) ** 2 / h ** 2
+    R = (1.0 - (1.0 - theta) * z) / (1.0 + theta * z)
+    np.testing.assert_allclose(r.u[1], R * v, atol=1e-11)
+    np.testing.assert_allclose(r.u[0], 0.0, atol=1e-12)
+    # Crank-Nicolson keeps this stiff mode flipping sign with |R| near 1,
+    # backward Euler damps it
+    if theta == 0.5:
+        assert R < -0.5
+    if theta == 1.0:
+        assert 0.0 < R < 0.1
