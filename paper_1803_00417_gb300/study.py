@@ -92,9 +92,15 @@ def startup(sim, dt, t_stop, snapshots, tol=1e-5):
                 wall_s=time.time() - t0, snapshots=snaps)
 
 
+FRACTIONS = (1e-2, 1e-3, 1e-4)
+
+
 def cessation_from(sim, dt, snapshots, max_steps, damp_steps=0):
-    """t_c from the current state (native driver), then the zones at the
-    snapshot times from the same state restored from a checkpoint; the
+    """t_c from the current state (native driver); then, from the same state
+    restored from a checkpoint, the zones at the snapshot times and the first
+    times at which the yielded cells fall below the FRACTIONS of the box
+    (the strict criterion, no yielded cell at all, turns on the last few
+    cells, whose |tau| can hover within 0.1% of tau_y for many steps).  The
     state is restored again at the end.  damp_steps: backward-Euler steps
     right after the lid stops (see hbf_run_cessation)."""
     rec, u, p = sim.get_state()
@@ -104,18 +110,27 @@ def cessation_from(sim, dt, snapshots, max_steps, damp_steps=0):
     sim.set_state(rec, u, p)
     d = sim.d
     sim.set_walls(np.zeros((d, 2, d)))
-    snaps, done = [], 0
-    for t in snapshots:
-        k = steps_for(t, dt)
-        while done < k:
-            sim.set_theta(1.0 if done < damp_steps else 0.5)
-            sim.step(dt)
-            done += 1
+    marks = {steps_for(t, dt): t for t in snapshots}
+    last = max(max(marks), r["steps"] if r["reached"] else max_steps)
+    snaps, t_frac, hist = [], {}, []
+    for m in range(1, last + 1):
+        sim.set_theta(1.0 if m <= damp_steps else 0.5)
+        sim.step(dt)
         sim.set_theta(0.5)
-        snaps.append(dict(t_paper=t, t=done * dt, **zone_summary(sim)))
+        z = zone_summary(sim)
+        hist.append((z["yielded_frac"], z["tau_max"]))
+        for f in FRACTIONS:
+            if f not in t_frac and z["yielded_frac"] < f:
+                t_frac[f] = m * dt
+        if m in marks:
+            snaps.append(dict(t_paper=marks[m], t=m * dt, **z))
     sim.set_state(rec, u, p)
+    every = max(1, len(hist) // 200)
     return dict(damp_steps=damp_steps, steps=r["steps"], t_c=r["t_c"], t_c_interp=r["t_c_interp"],
-                reached=bool(r["reached"]), tau_ratio=r["tau_ratio"], wall_s=wall, snapshots=snaps)
+                reached=bool(r["reached"]), tau_ratio=r["tau_ratio"], wall_s=wall, snapshots=snaps,
+                t_yielded_below={str(f): t_frac.get(f) for f in FRACTIONS},
+                history=dict(every_steps=every, yielded_frac=[h[0] for h in hist[::every]],
+                             tau_max=[h[1] for h in hist[::every]]))
 
 
 def run_cessation_study(args):
@@ -127,6 +142,8 @@ def run_cessation_study(args):
         ces = [cessation_from(sim, dt, CESSATION_SNAPSHOTS, steps_for(20 * T_C_PAPER, dt), k) for k in args.damp]
         for ce in ces:
             ce["t_c_rel_diff"] = (ce["t_c_interp"] - T_C_PAPER) / T_C_PAPER if ce["reached"] else None
+            ce["t_1e-3_rel_diff"] = ((ce["t_yielded_below"]["0.001"] - T_C_PAPER) / T_C_PAPER
+                                     if ce["t_yielded_below"]["0.001"] else None)
         emit(dict(study="cessation", workload=f"cavity{args.n}_bingham_Re1_Bi10_Pa400", dt=dt,
                   startup=st, at_lid_stop=dict(vortex=vort, **at_stop), cessation=ces,
                   t_c_paper=T_C_PAPER), args.out)
@@ -202,7 +219,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--mixed", action="store_true")
-    ap.add_argument("--damp", type=str, default="0,2",
+    ap.add_argument("--damp", type=str, default="0,2,100000",
                     help="cessation variants: backward-Euler steps right after the lid stops")
     ap.add_argument("--out", type=str, default="")
     args = ap.parse_args(argv)
