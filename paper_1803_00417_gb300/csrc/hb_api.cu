@@ -154,6 +154,7 @@ static int allocate(hbf_ctx* c) {
       A(L.fnr, gl.nnode);
       for (int a = 0; a < D; ++a) A(L.fef[a], gl.nface[a]);
       if (l == 0) A(L.feta, gl.ncell);
+      if (l == 0 && D == 3) A(L.fvx2, (long long)D * gl.ncell);
     }
     A(L.vb, (long long)D * gl.ncell);
     A(L.vr, (long long)D * gl.ncell);
@@ -366,6 +367,12 @@ int hbf_set_solver(hbf_ctx* c, double rtol, int max_cycles, int nu1, int nu2, in
   c->cfg.nu1 = nu1;
   c->cfg.nu2 = nu2;
   c->cfg.nu_bottom = nu_bottom;
+  return HBF_OK;
+}
+
+int hbf_set_fused_sweep(hbf_ctx* c, int on) {
+  if (!c) return HBF_ERR_ARG;
+  c->fused_sweep = on ? 1 : 0;
   return HBF_OK;
 }
 

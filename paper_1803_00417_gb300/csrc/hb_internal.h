@@ -31,6 +31,7 @@ struct Level {
   float* fvr = nullptr;
   float* fef[3] = {nullptr, nullptr, nullptr};
   float* feta = nullptr;  // level 0: the cell viscosity, whose face means the FP32 kernels form
+  float* fvx2 = nullptr;  // level 0 in 3D: the second array of the fused red-black sweeps
   float* fcx = nullptr;
   float* fcb = nullptr;
   float* fcr = nullptr;
@@ -97,6 +98,7 @@ struct hbf_ctx {
   double rho = 1.0;
   double f[3] = {0, 0, 0};
   int predictor_visc = 0;
+  int fused_sweep = 1;      // FP32 finest-level viscous sweeps in one launch per component (3D)
   double K = 1.0;           // the consistency K as given to hbf_set_rheology
   double theta = 0.5;       // implicit weight of the viscous term (1/2: Crank-Nicolson, Eq. 15)
   double t = 0.0;           // time: the sum of the dt of every step taken
@@ -188,6 +190,15 @@ inline void launch3(hbf_ctx* c, int slot, K kern, dim3 grid, dim3 block, Args...
   const bool rec = prof_wants(c->prof, slot);
   if (rec) prof_mark(c, slot, true);
   kern<<<grid, block, 0, c->stream>>>(args...);
+  if (rec) prof_mark(c, slot, false);
+  ++c->nlaunch;
+}
+
+template <typename K, typename... Args>
+inline void launch_smem(hbf_ctx* c, int slot, K kern, dim3 grid, dim3 block, size_t smem, Args... args) {
+  const bool rec = prof_wants(c->prof, slot);
+  if (rec) prof_mark(c, slot, true);
+  kern<<<grid, block, smem, c->stream>>>(args...);
   if (rec) prof_mark(c, slot, false);
   ++c->nlaunch;
 }

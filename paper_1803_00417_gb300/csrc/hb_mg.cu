@@ -17,6 +17,7 @@
 #include "hb_internal.h"
 #include "hb_mg_kernels.cuh"
 #include "hb_vcycle_tail.cuh"
+#include "hb_visc_fused.cuh"
 
 namespace hb {
 
@@ -414,6 +415,10 @@ struct Problem {
   virtual T* r(int l) = 0;
   virtual long long count(int l) = 0;
   virtual void smooth(int l) = 0;
+  // count sweeps (a problem may fuse or pipeline them)
+  virtual void smooth_n(int l, int count) {
+    for (int s = 0; s < count; ++s) smooth(l);
+  }
   virtual void resid(int l) = 0;
   virtual void restrict_to(int l) = 0;  // b(l+1) = R r(l), x(l+1) = 0
   virtual void prolong_add(int l) = 0;  // x(l) += P x(l+1)
@@ -618,6 +623,16 @@ struct ViscProblem : Problem<T> {
   }
   // the FP32 finest level forms its face viscosities from the cell viscosity
   bool cell_eta(int l) const { return l == 0 && sizeof(T) == 4 && c->lv[0].feta != nullptr; }
+  // 3D FP32 finest level: each component's red-black sweep in one launch
+  // (hb_visc_fused.cuh), alternating between x and the level's second array
+  void smooth_n(int l, int count) override {
+    if (!(D == 3 && cell_eta(l) && c->fused_sweep && c->lv[0].fvx2)) {
+      Problem<T>::smooth_n(l, count);
+      return;
+    }
+    fused_sweeps(l, count);
+  }
+  void fused_sweeps(int l, int count);
   void resid(int l) override {
     Level& L = c->lv[l];
     const dim3 blk(256, 1, 1);
@@ -656,6 +671,47 @@ struct ViscProblem : Problem<T> {
     bottom_fp64<D, T>(*this, l, xd, bd, &run_bottom);
   }
 };
+
+template <int D, typename T>
+void ViscProblem<D, T>::fused_sweeps(int l, int count) {
+  if constexpr (D == 3 && std::is_same<T, float>::value) {
+    Level& L = c->lv[l];
+    const long long n = L.g.ncell;
+    static bool attr[3] = {false, false, false};
+    void (*kern[3])(const float*, const float*, const float*, const float*, const float*, float*, const Geom, float,
+                    int) = {fused::k_visc_sweep_rb<0>, fused::k_visc_sweep_rb<1>, fused::k_visc_sweep_rb<2>};
+    for (int q = 0; q < 3; ++q)
+      if (!attr[q]) {
+        cudaFuncSetAttribute(kern[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(fused::Smem));
+        attr[q] = true;
+      }
+    T* home = x(l);
+    T* cur = home;
+    T* oth = L.fvx2;
+    const T* bb = b(l);
+    const float* e0 = L.feta;
+    const int hm = (int)this->hom(l);
+    const dim3 grd = fused::sweep_grid(L.g);
+    for (int s = 0; s < count; ++s) {
+      // component q reads the components before it from oth (already swept)
+      // and those after it from cur
+      for (int q = 0; q < 3; ++q) {
+        const int a0 = q == 0 ? 1 : 0, a1 = q == 2 ? 1 : 2;
+        const float* pa = (a0 < q ? oth : cur) + a0 * n;
+        const float* pb = (a1 < q ? oth : cur) + a1 * n;
+        launch_smem(c, kSlotViscSmooth, kern[q], grd, dim3(fused::NT), sizeof(fused::Smem), (const float*)cur + q * n,
+                    pa, pb, e0, bb + q * n, oth + q * n, L.g, (float)beta, hm);
+      }
+      T* t = cur;
+      cur = oth;
+      oth = t;
+    }
+    if (cur != home)
+      cudaMemcpyAsync(home, cur, (size_t)3 * n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+  } else {
+    Problem<T>::smooth_n(l, count);
+  }
+}
 
 template <int D, typename T>
 struct MacProblem : Problem<T> {
@@ -771,12 +827,12 @@ static void vcycle(Problem<T>& P, int l, const SolverCfg& cfg) {
     P.bottom(l);
     return;
   }
-  for (int s = 0; s < cfg.nu1; ++s) P.smooth(l);
+  P.smooth_n(l, cfg.nu1);
   P.resid(l);
   P.restrict_to(l);
   vcycle(P, l + 1, cfg);
   P.prolong_add(l);
-  for (int s = 0; s < cfg.nu2; ++s) P.smooth(l);
+  P.smooth_n(l, cfg.nu2);
 }
 
 static inline int l0slot() { return kSlotViscResid; }

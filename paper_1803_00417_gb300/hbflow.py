@@ -101,6 +101,7 @@ SIGNATURES = {
     "hbf_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int]),
     "hbf_set_tail": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hbf_set_fused_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_field_size": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "hbf_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -300,6 +301,9 @@ class HBFlow:
 
     def set_solver(self, rtol=1e-10, max_cycles=200, nu1=2, nu2=2, nu_bottom=40):
         self._check(self.lib.hbf_set_solver(self.ctx, rtol, max_cycles, nu1, nu2, nu_bottom))
+
+    def set_fused_sweep(self, on):
+        self._check(self.lib.hbf_set_fused_sweep(self.ctx, int(bool(on))))
 
     def set_tail(self, max_cells):
         """Levels from the first one with at most max_cells cells run as one
