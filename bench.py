@@ -87,6 +87,8 @@ def parse():
                     help="steps from rest (mixed method, untimed) before the warm-up; develop + warm-up = 100 "
                          "with the default warm-up, the paper's protocol")
     ap.add_argument("--prof-steps", type=int, default=5, help="steps of the instrumented pass")
+    ap.add_argument("--two-launch-sweeps", action="store_true",
+                    help="smooth the FP32 finest level with the red and black launches instead of the fused sweep")
     ap.add_argument("--breakdown", action="store_true",
                     help="also time bottom solves, transfers, reductions, vector updates and coarse levels")
     ap.add_argument("--profiler-range", action="store_true",
@@ -211,6 +213,13 @@ def visc_smoother_bytes(d, ncell, elem, cell_eta):
     level forms the face means itself) or every face eta once (d ncell);
     writes u_c of the colour (ncell/2)."""
     return elem * ncell * (0.5 + (d - 1) + 0.5 + (1 if cell_eta else d) + 0.5)
+
+
+def fused_sweep_bytes(d, ncell, elem):
+    """Algorithmic bytes of one launch of the fused red-black sweep (one
+    component, both colours; 3D FP32 finest level): reads u_c, the d - 1 other
+    components, the cell viscosity and b_c once, writes u_c once."""
+    return elem * ncell * (1 + (d - 1) + 1 + 1 + 1)
 
 
 def run_batch_sweep(args, clocks=None):
@@ -367,6 +376,7 @@ def run_ours(args):
     sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=prec)
     sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
     sim.set_solver(rtol=1e-10, max_cycles=200)
+    sim.set_fused_sweep(not args.two_launch_sweeps)
     zeros_u = np.zeros(d * ncell)
     zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
     sim.set_field("U", zeros_u)
@@ -513,19 +523,23 @@ def run_ours(args):
     roofline = None
     if sm_n > 0:
         per_launch_s = sm_ms / sm_n / 1e3
-        algo = visc_smoother_bytes(d, ncell, elem, prec == MIXED)
+        fused = prec == MIXED and d == 3 and not args.two_launch_sweeps
+        algo = fused_sweep_bytes(d, ncell, elem) if fused else visc_smoother_bytes(d, ncell, elem, prec == MIXED)
         ach = algo / per_launch_s / 1e9
         # DRAM bytes per cell of this kernel from one full ncu capture at 192^3
         # (profiles/k_visc_smooth_cavity192.md), scaled to this grid.  The
         # kernel's arithmetic has changed since that capture (its loads have
         # not), so the figure is reported beside the roofline, and "traffic"
         # stays null until the kernel is captured again.
-        last = SMOOTHER_DRAM_BYTES_PER_CELL * ncell if prec == MIXED else None
+        last = SMOOTHER_DRAM_BYTES_PER_CELL * ncell if (prec == MIXED and not fused) else None
         roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                     "traffic": None, "traffic_last_capture": last,
                     "traffic_source": "ncu at 192^3 before the last arithmetic-only change, 22.6 B/cell, "
-                    "scaled by cells" if last else None, "kernel": "k_visc_smooth (finest level)",
+                    "scaled by cells" if last else None,
+                    "kernel": "k_visc_sweep_rb (fused red-black sweep, finest level)" if fused
+                    else "k_visc_smooth (finest level)",
                     "launches": sm_n, "avg_launch_us": per_launch_s * 1e6,
+                    "algorithmic_bytes_per_launch": algo,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
     cpu = None
