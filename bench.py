@@ -87,8 +87,8 @@ def parse():
                     help="steps from rest (mixed method, untimed) before the warm-up; develop + warm-up = 100 "
                          "with the default warm-up, the paper's protocol")
     ap.add_argument("--prof-steps", type=int, default=5, help="steps of the instrumented pass")
-    ap.add_argument("--two-launch-sweeps", action="store_true",
-                    help="smooth the FP32 finest level with the red and black launches instead of the fused sweep")
+    ap.add_argument("--fused-sweeps", action="store_true",
+                    help="smooth the 3D FP32 finest level with the one-launch red-black sweep (hbf_set_fused_sweep)")
     ap.add_argument("--breakdown", action="store_true",
                     help="also time bottom solves, transfers, reductions, vector updates and coarse levels")
     ap.add_argument("--profiler-range", action="store_true",
@@ -376,7 +376,7 @@ def run_ours(args):
     sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=prec)
     sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
     sim.set_solver(rtol=1e-10, max_cycles=200)
-    sim.set_fused_sweep(not args.two_launch_sweeps)
+    sim.set_fused_sweep(args.fused_sweeps)
     zeros_u = np.zeros(d * ncell)
     zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
     sim.set_field("U", zeros_u)
@@ -523,7 +523,7 @@ def run_ours(args):
     roofline = None
     if sm_n > 0:
         per_launch_s = sm_ms / sm_n / 1e3
-        fused = prec == MIXED and d == 3 and not args.two_launch_sweeps
+        fused = prec == MIXED and d == 3 and args.fused_sweeps
         algo = fused_sweep_bytes(d, ncell, elem) if fused else visc_smoother_bytes(d, ncell, elem, prec == MIXED)
         ach = algo / per_launch_s / 1e9
         # DRAM bytes per cell of this kernel from one full ncu capture at 192^3

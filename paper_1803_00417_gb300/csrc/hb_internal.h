@@ -98,7 +98,7 @@ struct hbf_ctx {
   double rho = 1.0;
   double f[3] = {0, 0, 0};
   int predictor_visc = 0;
-  int fused_sweep = 1;      // FP32 finest-level viscous sweeps in one launch per component (3D)
+  int fused_sweep = 0;      // FP32 finest-level viscous sweeps in one launch per component (3D)
   double K = 1.0;           // the consistency K as given to hbf_set_rheology
   double theta = 0.5;       // implicit weight of the viscous term (1/2: Crank-Nicolson, Eq. 15)
   double t = 0.0;           // time: the sum of the dt of every step taken

@@ -1,5 +1,5 @@
-"""The one-launch red-black sweep of the 3D FP32 finest level (default)
-against the two-launch red/black sweeps it replaces: the same cavity steps
+"""The one-launch red-black sweep of the 3D FP32 finest level
+(hbf_set_fused_sweep) against the default two-launch red/black sweeps: the same cavity steps
 from the same seeded states agree to the mixed-precision tolerance (the
 per-cell updates are the same arithmetic; the sweep order is the same), on
 sizes that are not multiples of the tile (32 x 16 x 16) and on a full tile
