@@ -54,7 +54,8 @@ enum hbf_precision {
  * Sizes in doubles (hbf_field_size): U, USTAR, RHS, GP, LU: d*ncell; P: nnode;
  * ETA, PHI_MAC: ncell; UADV, UMAC: sum over axes a of nface[a] (axis-major);
  * UL, UR: sum over axes a of d*nface[a] (axis-major, then component);
- * ETA_FACES: sum over axes of nface[a]; SLOPES, HATS: d*d*ncell; NRES0: nnode. */
+ * ETA_FACES: sum over axes of nface[a]; SLOPES, HATS: d*d*ncell; NRES0: nnode;
+ * VRES0, VCORR: d*ncell. */
 enum hbf_field {
   HBF_U = 0,       /* cell velocity u^m (set) / u^{m+1} (after a step) */
   HBF_P = 1,       /* nodal pressure p^{m-1/2} / p^{m+1/2} */
@@ -71,7 +72,10 @@ enum hbf_field {
   HBF_ETA_FACES = 12, /* face eta of the finest level (axis-major) */
   HBF_SLOPES = 13, /* limited slopes, d*d*ncell, [axis][component] */
   HBF_HATS = 14,   /* transverse terms, d*d*ncell, [axis][component] */
-  HBF_NRES0 = 15   /* nodal projection: warm-start residual b - L p of the last hbf_project */
+  HBF_NRES0 = 15,  /* nodal projection: warm-start residual b - L p of the last hbf_project */
+  HBF_VRES0 = 16,  /* viscous solve: b - A x at the start of the last solve, after the initial guess
+                      (d*ncell; needs hbf_set_visc_record) */
+  HBF_VCORR = 17   /* viscous solve: u* minus that starting point (d*ncell; needs hbf_set_visc_record) */
 };
 
 typedef struct {
@@ -304,6 +308,40 @@ int hbf_set_guess_model(hbf_ctx* ctx, hbf_unet* net);
  * the correction it has to predict is the smooth part.  The box must hold
  * that level's nodes.  HBF_ERR_ARG if the level does not exist. */
 int hbf_set_guess_model_level(hbf_ctx* ctx, hbf_unet* net, int level);
+
+/* ---------------------------------------------------------------------------
+ * Initial guess of the viscous solve (Eq. 16) in HBF_MIXED contexts.  Not in
+ * the paper: the solve starts from u^m there, and here too with mode 0.  The
+ * guess only moves the starting point; the solve still runs to its FP64
+ * tolerance.  From x = u^m and its residual r = b - A x, minimal-residual
+ * steps along up to two directions d, each taken only if it lowers max |r|:
+ * w = A d (homogeneous walls), alpha = (r, w)/(w, w), x += alpha d.
+ *   mode 1: d = the previous step's increment u*^{m-1} - u^{m-1} (kept by
+ *           hbf_step; cleared when U is set).  Where dt eta / (rho h^2) >> 1
+ *           Crank-Nicolson leaves modes flipping sign from step to step, so
+ *           alpha comes out near -1.
+ *   mode 2: also the direction of the network set by
+ *           hbf_set_visc_guess_model for the remaining residual.
+ * hbf_solve_stats.guess of the viscous solve: bit 0 the increment's step was
+ * taken, bit 1 the network's.  HBF_ERR_ARG for another mode or an FP64
+ * context. */
+int hbf_set_visc_guess(hbf_ctx* ctx, int mode);
+/* The network of mode 2 (NULL disables): each velocity component of the
+ * residual, divided by its max norm over all components, is restricted to
+ * the cells of multigrid level `level` by averaging, mapped by one forward
+ * pass, and the output interpolated back to the finest cells (multilinear,
+ * odd reflection at the walls).  The network's box must hold that level's
+ * cells (each size >= n[a] >> level). */
+int hbf_set_visc_guess_model(hbf_ctx* ctx, hbf_unet* net, int level);
+/* Keep the fields HBF_VRES0 and HBF_VCORR of every viscous solve of hbf_step
+ * (training pairs for the network: the residual at the start and the
+ * correction the solver found).  HBF_MIXED contexts. */
+int hbf_set_visc_record(hbf_ctx* ctx, int on);
+/* One level of the multigrid restriction applied to caller data (device
+ * pointers): kind 0 a d-component cell field, 1 a cell scalar (mean of the
+ * 2^d children), 2 a nodal field (full weighting); from level `level` to
+ * level + 1.  HBF_ERR_ARG if level + 1 does not exist. */
+int hbf_restrict(hbf_ctx* ctx, int kind, int level, const double* src, double* dst);
 
 int hbf_sync(hbf_ctx* ctx);
 const char* hbf_last_error(const hbf_ctx* ctx);

@@ -193,6 +193,12 @@ static int field_view(hbf_ctx* c, int which, FieldView* v) {
     case HBF_SLOPES: v->ptr[0] = c->slopes; v->cnt[0] = (long long)D * D * g.ncell; return 0;
     case HBF_HATS: v->ptr[0] = c->hats; v->cnt[0] = (long long)D * D * g.ncell; return 0;
     case HBF_NRES0: v->ptr[0] = c->nres0; v->cnt[0] = g.nnode; return 0;
+    case HBF_VRES0:
+    case HBF_VCORR:
+      if (!c->vres0) return -1;
+      v->ptr[0] = which == HBF_VRES0 ? c->vres0 : c->vcorr;
+      v->cnt[0] = (long long)D * g.ncell;
+      return 0;
     case HBF_ETA_FACES:
       v->parts = D;
       for (int a = 0; a < D; ++a) {
@@ -277,6 +283,7 @@ void hbf_destroy(hbf_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   release_guess(c);
+  release_visc_guess(c);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hres) cudaFreeHost(c->hres);
   prof_release(c);
@@ -370,6 +377,54 @@ int hbf_set_solver(hbf_ctx* c, double rtol, int max_cycles, int nu1, int nu2, in
   return HBF_OK;
 }
 
+int hbf_set_visc_guess(hbf_ctx* c, int mode) {
+  if (!c) return HBF_ERR_ARG;
+  if (mode < 0 || mode > 2) return fail(c, HBF_ERR_ARG, "viscous guess mode must be 0, 1 or 2");
+  if (mode > 0 && c->precision != HBF_MIXED) return fail(c, HBF_ERR_ARG, "the viscous guess needs a mixed context");
+  if (mode > 0 && !c->vprev32) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, sizeof(float) * (size_t)c->dim * c->g.ncell) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, HBF_ERR_OOM, "viscous guess buffer");
+    }
+    c->allocs.push_back(q);
+    c->vprev32 = (float*)q;
+  }
+  c->vguess_mode = mode;
+  c->vprev_ok = false;
+  return HBF_OK;
+}
+
+int hbf_set_visc_record(hbf_ctx* c, int on) {
+  if (!c) return HBF_ERR_ARG;
+  if (on && c->precision != HBF_MIXED) return fail(c, HBF_ERR_ARG, "recording needs a mixed context");
+  if (on && !c->vres0) {
+    void *a = nullptr, *b = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)c->dim * c->g.ncell;
+    if (cudaMalloc(&a, bytes) != cudaSuccess || cudaMalloc(&b, bytes) != cudaSuccess) {
+      if (a) cudaFree(a);
+      cudaGetLastError();
+      return fail(c, HBF_ERR_OOM, "recording buffers");
+    }
+    c->allocs.push_back(a);
+    c->allocs.push_back(b);
+    c->vres0 = (double*)a;
+    c->vcorr = (double*)b;
+  }
+  c->vrecord = on ? 1 : 0;
+  return HBF_OK;
+}
+
+int hbf_restrict(hbf_ctx* c, int kind, int level, const double* src, double* dst) {
+  if (!c || !src || !dst || kind < 0 || kind > 2) return HBF_ERR_ARG;
+  if (level < 0 || level + 1 >= (int)c->lv.size()) return fail(c, HBF_ERR_ARG, "no coarser level");
+  if (kind == 2)
+    nodal_restrict(c, level, src, dst);
+  else
+    cell_restrict_d(c, level, src, dst, kind == 0 ? c->dim : 1);
+  return cuda_check(c, cudaGetLastError(), "restriction");
+}
+
 int hbf_set_fused_sweep(hbf_ctx* c, int on) {
   if (!c) return HBF_ERR_ARG;
   c->fused_sweep = on ? 1 : 0;
@@ -413,7 +468,10 @@ static int copy_field(hbf_ctx* c, int which, double* host_or_dev, bool in) {
 }
 
 int hbf_set_field(hbf_ctx* c, int which, const double* src) {
-  if (c && (which == HBF_U || which == HBF_USTAR)) c->prev_valid = false;
+  if (c && (which == HBF_U || which == HBF_USTAR)) {
+    c->prev_valid = false;
+    c->vprev_ok = false;
+  }
   return copy_field(c, which, const_cast<double*>(src), true);
 }
 
@@ -491,6 +549,7 @@ int hbf_step(hbf_ctx* c, double dt, hbf_step_stats* stats) {
   st = solve_viscous(c, visc_beta(dt, c->rho, c->theta), c->rhs, c->ustar, &s->visc);
   if (st && st != HBF_ERR_NOT_CONVERGED) return st;
   if (st) worst = st;
+  if ((c->vguess_mode > 0 || c->vrecord) && (st = visc_after_solve(c, c->ustar, c->u))) return st;
   st = hbf_project(c, dt, c->ustar, c->p, &s->nodal);
   if (st && st != HBF_ERR_NOT_CONVERGED) return st;
   if (st) worst = st;

@@ -132,6 +132,18 @@ struct hbf_ctx {
   double* mrhs = nullptr;     // ncell, MAC right-hand side
   double* nrhs = nullptr;     // nnode
   double* nres0 = nullptr;    // nnode: warm-start residual of the last nodal solve
+  // initial guess of the viscous solve (mixed precision): 0 u^m; 1 also a
+  // minimal-residual step along the previous step's increment; 2 also one
+  // along the learned network's direction
+  int vguess_mode = 0;
+  float* vprev32 = nullptr;   // d*ncell: u*^{m-1} - u^{m-1} of the last hbf_step
+  bool vprev_ok = false;
+  hbf_unet* vnet = nullptr;   // network of mode 2 and the level it runs on
+  int vnet_level = 0;
+  float* vnet_x = nullptr;
+  int vrecord = 0;            // keep the solve's starting residual and correction
+  double* vres0 = nullptr;    // d*ncell: b - A x at the start of the last solve (after the guess)
+  double* vcorr = nullptr;    // d*ncell: u* minus the starting point of the last solve
   // learned initial guess (optional)
   hbf_unet* guess = nullptr;
   int guess_level = 0;        // multigrid level whose nodes the network sees
@@ -239,5 +251,17 @@ void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, l
 // that lowers the residual; *used tells which
 int apply_guess(hbf_ctx* c, const double* b, double* p, int* used);
 void release_guess(hbf_ctx* c);
+void release_visc_guess(hbf_ctx* c);
+int take_tc_err(hbf_unet* N, cudaStream_t s);
+// the network's direction for the viscous residual r32 (FP32, d*ncell, finest
+// level) scaled by `scale`, into d32 (FP32, d*ncell); false if none
+bool visc_net_direction(hbf_ctx* c, const float* r32, double scale, float* d32);
+// FP32 cell transfers of d-component fields between levels l and l + 1
+void cell_restrict_f(hbf_ctx* c, int l, const float* fine, float* coarse);
+void cell_restrict_d(hbf_ctx* c, int l, const double* fine, double* coarse, int ncomp);
+void cell_prolong_add_f(hbf_ctx* c, int l, float* fine, const float* coarse);
+// after a viscous solve of hbf_step: the increment for the next step's
+// guess and the recorded correction
+int visc_after_solve(hbf_ctx* c, const double* ustar, const double* u);
 
 }  // namespace hb

@@ -934,6 +934,86 @@ static void build_eta_levels(hbf_ctx* c) {
 constexpr double kInnerRtol = 1e-3;
 constexpr int kInnerMax = 40;
 
+// x (FP64) += a d (FP32);  r (FP64) -= a w (FP32)
+__global__ void k_add_scaled_f32(double* __restrict__ x, double a, const float* __restrict__ d, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    x[t] += a * (double)d[t];
+}
+
+// y = x - y
+__global__ void k_rsub(const double* __restrict__ x, double* y, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = x[t] - y[t];
+}
+
+// out (FP32) = a - b (FP64)
+__global__ void k_diff_to_f32(float* __restrict__ out, const double* __restrict__ a, const double* __restrict__ b,
+                              long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = (float)(a[t] - b[t]);
+}
+
+// Initial guess of the mixed-precision viscous solve (not in the paper; the
+// solve still runs to its FP64 tolerance).  From x = u^m with FP64 residual
+// r = b - A x, minimal-residual steps along up to two directions d, each
+// taken only if it lowers max |r|:
+//   w = A_hom d (the FP32 operator, homogeneous walls: the operator of a
+//   correction), alpha = (r, w) / (w, w), x += alpha d, r -= alpha w.
+// The directions: the previous step's increment u*^{m-1} - u^{m-1} (mode 1;
+// where Crank-Nicolson leaves stiff modes flipping sign, alpha comes out
+// near -1), then the network's direction for the remaining residual
+// (mode 2).  *used: bit 0 the increment, bit 1 the network.
+template <int D>
+static int visc_guess(hbf_ctx* c, double beta, double* x, double* r, double* rn, int* used) {
+  Level& L0 = c->lv[0];
+  const long long n = (long long)D * L0.g.ncell;
+  const int nb = grid_for(n);
+  const float fbeta = (float)beta;
+  int st = 0;
+  float* cur = c->fkr;  // FP32 copy of the current residual
+  float* tmp = c->fkt;
+  float* w = c->fkv;
+  launch(c, kSlotVector, k_convert<float, double>, nb, kThreads, cur, (const double*)r, n);
+  double m = reduce_max_abs_f(c, cur, n, &st);
+  if (st) return st;
+  const dim3 blk(256, 1, 1);
+  const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
+  auto step_along = [&](const float* d, int bit) -> int {
+    const float* e0 = L0.feta;
+    launch3(c, kSlotVector, k_visc_op3<D, float, true>, grd, blk, d, (const float*)nullptr, w, e0, e0, e0, L0.g,
+            fbeta, 1);
+    const double rw = reduce_dot_f(c, cur, w, n, &st);
+    if (st) return st;
+    const double ww = reduce_dot_f(c, w, w, n, &st);
+    if (st) return st;
+    if (!(ww > 0.0) || !std::isfinite(rw)) return HBF_OK;
+    const double a = rw / ww;
+    launch(c, kSlotVector, k_axmy<float>, nb, kThreads, tmp, (const float*)cur, (float)a, (const float*)w, n);
+    const double m1 = reduce_max_abs_f(c, tmp, n, &st);
+    if (st) return st;
+    if (m1 < m) {
+      launch(c, kSlotVector, k_add_scaled_f32, nb, kThreads, x, a, d, n);
+      launch(c, kSlotVector, k_add_scaled_f32, nb, kThreads, r, -a, (const float*)w, n);
+      float* t = cur;
+      cur = tmp;
+      tmp = t;
+      m = m1;
+      *used |= bit;
+    }
+    return HBF_OK;
+  };
+  if (c->vprev_ok && c->vprev32 && (st = step_along(c->vprev32, 1))) return st;
+  if (c->vguess_mode >= 2 && c->vnet && m > 0.0 && visc_net_direction(c, cur, 1.0 / m, c->fke) &&
+      (st = step_along(c->fke, 2)))
+    return st;
+  if ((st = cuda_check(c, cudaGetLastError(), "viscous guess"))) return st;
+  *rn = reduce_max_abs(c, r, n, &st);
+  return st;
+}
+
 template <int D>
 static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, double* x, hbf_solve_stats* out) {
   const SolverCfg& cfg = c->cfg;
@@ -976,6 +1056,13 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
   double r0 = rn;
   if (bnorm == 0.0) bnorm = rn;
   const double tol = cfg.rtol * bnorm;
+  int used = 0;
+  if (c->vguess_mode > 0 && rn > tol && std::isfinite(rn) && (st = visc_guess<D>(c, beta, x, r, &rn, &used)))
+    return st;
+  if (c->vrecord && c->vres0) {
+    cudaMemcpyAsync(c->vres0, r, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->vcorr, x, bytes, cudaMemcpyDeviceToDevice, c->stream);  // the start; hbf_step subtracts
+  }
   int it = 0;
   while (rn > tol && it < cfg.max_cycles && std::isfinite(rn)) {
     launch(c, kSlotTransfer, k_convert<float, double>, nb, kThreads, fr, (const double*)r, n);
@@ -1022,7 +1109,9 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
     if (st) return st;
   }
   if ((st = cuda_check(c, cudaGetLastError(), "viscous solve"))) return st;
-  return finish(c, it, r0, rn, bnorm, tol, out);
+  st = finish(c, it, r0, rn, bnorm, tol, out);
+  if (out) out->guess = used;
+  return st;
 }
 
 template <int D>
@@ -1173,6 +1262,44 @@ void nodal_prolong_add(hbf_ctx* c, int l, double* fine, const double* coarse) {
     launch(c, kSlotTransfer, k_prolong_nodes_add<2, double>, grid_for(F.g.nnode), kThreads, fine, coarse, F.g, C.g);
   else
     launch(c, kSlotTransfer, k_prolong_nodes_add<3, double>, grid_for(F.g.nnode), kThreads, fine, coarse, F.g, C.g);
+}
+
+void cell_restrict_f(hbf_ctx* c, int l, const float* fine, float* coarse) {
+  const Level &F = c->lv[l], &C = c->lv[l + 1];
+  const long long n = (long long)c->dim * C.g.ncell;
+  if (c->dim == 2)
+    launch(c, kSlotTransfer, k_restrict_cells<2, float>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 2);
+  else
+    launch(c, kSlotTransfer, k_restrict_cells<3, float>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3);
+}
+
+void cell_restrict_d(hbf_ctx* c, int l, const double* fine, double* coarse, int ncomp) {
+  const Level &F = c->lv[l], &C = c->lv[l + 1];
+  const long long n = (long long)ncomp * C.g.ncell;
+  if (c->dim == 2)
+    launch(c, kSlotTransfer, k_restrict_cells<2, double>, grid_for(n), kThreads, fine, coarse, F.g, C.g, ncomp);
+  else
+    launch(c, kSlotTransfer, k_restrict_cells<3, double>, grid_for(n), kThreads, fine, coarse, F.g, C.g, ncomp);
+}
+
+void cell_prolong_add_f(hbf_ctx* c, int l, float* fine, const float* coarse) {
+  const Level &F = c->lv[l], &C = c->lv[l + 1];
+  const long long n = (long long)c->dim * F.g.ncell;
+  // odd reflection at the walls: a correction of the Dirichlet problem
+  if (c->dim == 2)
+    launch(c, kSlotTransfer, k_prolong_cells_add<2, float>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 2, -1.f);
+  else
+    launch(c, kSlotTransfer, k_prolong_cells_add<3, float>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3, -1.f);
+}
+
+int visc_after_solve(hbf_ctx* c, const double* ustar, const double* u) {
+  const long long n = (long long)c->dim * c->g.ncell;
+  if (c->vguess_mode > 0 && c->vprev32) {
+    launch(c, kSlotVector, k_diff_to_f32, grid_for(n), kThreads, c->vprev32, ustar, u, n);
+    c->vprev_ok = true;
+  }
+  if (c->vrecord && c->vcorr) launch(c, kSlotVector, k_rsub, grid_for(n), kThreads, ustar, c->vcorr, n);  // u* - start
+  return cuda_check(c, cudaGetLastError(), "viscous increment");
 }
 
 void axmy(hbf_ctx* c, double* out, const double* x, double a, const double* y, long long n) {

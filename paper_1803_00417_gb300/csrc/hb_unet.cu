@@ -514,6 +514,72 @@ int take_tc_err(hbf_unet* N, cudaStream_t s) {
   return h != 0;
 }
 
+// x[point] = r[cell] * scale (FP32 cells), 0 in the padding
+__global__ void k_cells_to_net_f(const float* __restrict__ r, float scale, int e0, int e1, int e2, Box box,
+                                 float* __restrict__ x) {
+  const long long P = (long long)box.X * box.Y * box.Z;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < P; t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    coords(box, t, i, j, k);
+    x[t] = (i < e0 && j < e1 && k < e2) ? r[i + (long long)e0 * (j + (long long)e1 * k)] * scale : 0.f;
+  }
+}
+
+__global__ void k_net_to_cells_f(const float* __restrict__ y, int e0, int e1, int e2, Box box, float* __restrict__ out) {
+  const long long n = (long long)e0 * e1 * e2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % e0);
+    const long long r = t / e0;
+    const int j = (int)(r % e1), k = (int)(r / e1);
+    out[t] = y[i + (long long)box.X * (j + (long long)box.Y * k)];
+  }
+}
+
+// The network's direction for the viscous residual: each velocity component
+// of r32 (scaled by `scale`) restricted to the network's level by cell
+// averaging, one forward pass per component, the outputs interpolated back
+// to the finest cells (multilinear, odd reflection at the walls).  The level
+// arrays of the FP32 V-cycles serve as scratch (the solve has not started).
+bool visc_net_direction(hbf_ctx* c, const float* r32, double scale, float* d32) {
+  hbf_unet* N = c->vnet;
+  if (!N || !c->vnet_x) return false;
+  const int L = c->vnet_level;
+  const float* src = r32;
+  for (int l = 0; l < L; ++l) {
+    cell_restrict_f(c, l, src, c->lv[l + 1].fvb);
+    src = c->lv[l + 1].fvb;
+  }
+  const Geom& gL = c->lv[L].g;
+  const int e0 = gL.n[0], e1 = gL.n[1], e2 = c->dim == 3 ? gL.n[2] : 1;
+  float* outL = L == 0 ? d32 : c->lv[L].fvx;
+  cudaStream_t saved = N->stream;
+  N->stream = c->stream;
+  for (int q = 0; q < c->dim; ++q) {
+    k_cells_to_net_f<<<grid(N->P[0]), kThreads, 0, c->stream>>>(src + (size_t)q * gL.ncell, (float)scale, e0, e1, e2,
+                                                                 N->box[0], c->vnet_x);
+    forward(N, c->vnet_x);
+    k_net_to_cells_f<<<grid((long long)gL.ncell), kThreads, 0, c->stream>>>(N->y, e0, e1, e2, N->box[0],
+                                                                           outL + (size_t)q * gL.ncell);
+    c->nlaunch += N->nlaunch_fwd + 2;
+  }
+  N->stream = saved;
+  for (int l = L - 1; l >= 0; --l) {
+    float* fine = l == 0 ? d32 : c->lv[l].fvx;
+    cudaMemsetAsync(fine, 0, sizeof(float) * (size_t)c->dim * c->lv[l].g.ncell, c->stream);
+    cell_prolong_add_f(c, l, fine, c->lv[l + 1].fvx);
+  }
+  if (cudaGetLastError() != cudaSuccess) return false;
+  // a convolution that gave up waiting on the tensor cores left its output
+  // partly unwritten: no direction this step
+  return !take_tc_err(N, c->stream);
+}
+
+void release_visc_guess(hbf_ctx* c) {
+  if (c->vnet_x) cudaFree(c->vnet_x);
+  c->vnet_x = nullptr;
+  c->vnet = nullptr;
+}
+
 void release_guess(hbf_ctx* c) {
   if (c->ntry) cudaFree(c->ntry);
   if (c->nzero) cudaFree(c->nzero);
@@ -835,6 +901,29 @@ int hbf_unet_adam(hbf_unet* N, double lr, double b1, double b2, double eps) {
   // (the first layer's padded input channels have zero gradient and stay zero)
   refresh_bf16(N);
   return check(N, "unet adam");
+}
+
+int hbf_set_visc_guess_model(hbf_ctx* c, hbf_unet* N, int level) {
+  if (!c) return HBF_ERR_ARG;
+  hb::release_visc_guess(c);
+  if (!N) return HBF_OK;
+  if (c->precision != HBF_MIXED) return hb::fail(c, HBF_ERR_ARG, "the viscous guess needs a mixed context");
+  if (N->d != c->dim) return hb::fail(c, HBF_ERR_ARG, "guess model dimension differs from the grid's");
+  if (level < 0 || level >= (int)c->lv.size())
+    return hb::fail(c, HBF_ERR_ARG, "guess level outside the multigrid hierarchy");
+  const hb::Geom& gL = c->lv[level].g;
+  const int e[3] = {gL.n[0], gL.n[1], c->dim == 3 ? gL.n[2] : 1};
+  const int b[3] = {N->box[0].X, N->box[0].Y, N->box[0].Z};
+  for (int a = 0; a < c->dim; ++a)
+    if (b[a] < e[a]) return hb::fail(c, HBF_ERR_ARG, "guess model box is smaller than the cell grid");
+  if (cudaMalloc((void**)&c->vnet_x, (size_t)N->P[0] * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    c->vnet_x = nullptr;
+    return hb::fail(c, HBF_ERR_OOM, "guess buffers");
+  }
+  c->vnet = N;
+  c->vnet_level = level;
+  return HBF_OK;
 }
 
 int hbf_set_guess_model(hbf_ctx* c, hbf_unet* N) { return hbf_set_guess_model_level(c, N, 0); }

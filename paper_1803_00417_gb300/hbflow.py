@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhbflow.so")
 HBF_OK = 0
 HBF_ERR_NOT_CONVERGED = -4
 FIELDS = dict(U=0, P=1, ETA=2, USTAR=3, UADV=4, UMAC=5, RHS=6, PHI_MAC=7, GP=8, LU=9, UL=10, UR=11,
-              ETA_FACES=12, SLOPES=13, HATS=14, NRES0=15)
+              ETA_FACES=12, SLOPES=13, HATS=14, NRES0=15, VRES0=16, VCORR=17)
 FP64, MIXED = 0, 1
 
 
@@ -30,7 +30,7 @@ class SolveStats(ctypes.Structure):
 
     def as_dict(self):
         return dict(cycles=self.cycles, converged=bool(self.converged), r0=self.r0, rnorm=self.rnorm,
-                    bnorm=self.bnorm, guess=bool(self.guess))
+                    bnorm=self.bnorm, guess=int(self.guess))
 
 
 class StepStats(ctypes.Structure):
@@ -153,6 +153,10 @@ SIGNATURES = {
     "hbf_centreline": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "hbf_vortex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]),
+    "hbf_set_visc_guess": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hbf_set_visc_guess_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "hbf_set_visc_record": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hbf_restrict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "hbf_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "hbf_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "hbf_destroy": (None, [ctypes.c_void_p]),
@@ -292,6 +296,17 @@ class HBFlow:
     def set_body_force(self, f):
         ff = (ctypes.c_double * 3)(*(list(f) + [0.0] * (3 - len(f))))
         self._check(self.lib.hbf_set_body_force(self.ctx, ff))
+
+    def set_visc_guess(self, mode):
+        self._check(self.lib.hbf_set_visc_guess(self.ctx, int(mode)))
+
+    def set_visc_record(self, on):
+        self._check(self.lib.hbf_set_visc_record(self.ctx, int(bool(on))))
+
+    def restrict(self, kind, level, src_dev, dst_dev):
+        """One level of the multigrid restriction (kind 0 cell vector, 1 cell
+        scalar, 2 nodes) of device arrays."""
+        self._check(self.lib.hbf_restrict(self.ctx, int(kind), int(level), _ptr(src_dev), _ptr(dst_dev)))
 
     def set_theta(self, theta):
         self._check(self.lib.hbf_set_theta(self.ctx, float(theta)))
@@ -564,6 +579,13 @@ class UNet:
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         self._check(self.lib.hbf_unet_adam(self.net, lr, beta1, beta2, eps))
+
+
+def set_visc_guess_model(sim, net, level=0):
+    """Use ``net`` (a UNet, or None) for the viscous solve's learned direction
+    (guess mode 2), evaluated on the cells of multigrid level ``level``."""
+    st = sim.lib.hbf_set_visc_guess_model(sim.ctx, net.net if net is not None else None, int(level))
+    sim._check(st)
 
 
 def set_guess_model(sim, net, level=0):

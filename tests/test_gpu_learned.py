@@ -1,12 +1,18 @@
-"""The learned initial guess in the nodal projection (Eq. 17): trained by the
-library's own kernels on (warm-start residual, correction) pairs the solver
-generates, it changes only the multigrid's starting point.  This test trains a
-small model, then advances held-out cavities in lockstep with and without it
-from identical states, and checks that (a) the solves still reach the same
-tolerance and agree, (b) the guess is accepted at most steps and (c) the total
-number of nodal V-cycles stays within a few per cent of the plain method's (a
-guess with a smaller residual need not save a whole cycle).  It prints the
-V-cycles saved."""
+"""The learned initial guesses (not in the paper; they change only the
+starting point of a solve, which still runs to its tolerance).
+
+Nodal projection (Eq. 17): a network trained by the library's own kernels on
+(warm-start residual, correction) pairs the solver generates.  Held-out
+cavities advance in lockstep with and without it from identical states: the
+solves reach the same tolerance and agree, the guess is accepted at most
+steps, and the nodal V-cycles do not grow.  The V-cycles saved are printed
+(measured: none; the network's guess lowers the residual by less than one
+V-cycle does).
+
+Viscous solve (Eq. 16): the minimal-residual step along the previous step's
+increment saves BiCGStab iterations (strictly fewer over ten steps of the
+3D Herschel-Bulkley cavity's parameters), and the learned direction on top of
+it keeps every solve at its tolerance; its iterations are printed."""
 
 import numpy as np
 import pytest
@@ -65,7 +71,7 @@ def test_learned_guess_gain_2d():
     print(f"nodal V-cycles without / with the learned guess: {without} / {with_} "
           f"(guess accepted at {used}/{total} steps)")
     assert used >= total // 2
-    assert with_ <= without + max(2, without // 20)
+    assert with_ <= without
 
 
 def test_learned_guess_on_a_coarse_level_2d():
@@ -114,4 +120,88 @@ def test_learned_guess_on_a_coarse_level_2d():
     a.close()
     b.close()
     print(f"level-1 guess: nodal V-cycles without / with: {without} / {with_} (accepted {used}/{total})")
-    assert with_ <= without + max(2, without // 20)
+    assert with_ <= without
+
+
+def _visc_pair(n, seed_params, develop, modes):
+    """Contexts with the given viscous guess modes, started from one state
+    developed from rest by a plain mixed context."""
+    from paper_1803_00417_gb300.hbflow import MIXED, HBFlow
+    from paper_1803_00417_gb300.inputs import cavity
+
+    cfg = cavity(n, **seed_params)
+    base = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=MIXED)
+    base.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+    d = len(n)
+    base.set_field("U", np.zeros(d * int(np.prod(n))))
+    base.set_field("P", np.zeros(int(np.prod([v + 1 for v in n]))))
+    for _ in range(develop):
+        base.step(cfg["dt"])
+    rec, u, p = base.get_state()
+    base.close()
+    sims = []
+    for mode in modes:
+        s = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=MIXED)
+        s.set_state(rec, u, p)
+        s.set_visc_guess(mode)
+        sims.append(s)
+    return sims, cfg
+
+
+def test_previous_increment_guess_saves_viscous_iterations():
+    over = dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)  # the 3D workload's parameters
+    (plain, hist), cfg = _visc_pair((48, 48, 48), over, 10, (0, 1))
+    its = [0, 0]
+    taken = 0
+    for k in range(10):
+        s0, s1 = plain.step(cfg["dt"]), hist.step(cfg["dt"])
+        for s in (s0, s1):
+            assert all(s[q]["converged"] for q in ("mac", "visc", "nodal"))
+        its[0] += s0["visc"]["cycles"]
+        its[1] += s1["visc"]["cycles"]
+        taken += s1["visc"]["guess"] & 1
+    u0, u1 = plain.get_field("U"), hist.get_field("U")
+    print(f"viscous iterations over 10 steps without / with the previous-increment step: {its[0]} / {its[1]} "
+          f"(step taken {taken}/10)")
+    assert its[1] < its[0]
+    assert taken >= 8  # the first step has no increment yet
+    assert np.max(np.abs(u1 - u0)) <= 1e-6 * np.max(np.abs(u0))
+    plain.close()
+    hist.close()
+
+
+def test_learned_viscous_direction_keeps_tolerance():
+    from paper_1803_00417_gb300.hbflow import UNet, set_visc_guess_model
+    from paper_1803_00417_gb300.learned import cell_box, cell_mask, coarse_cells, generate_visc_pairs, train
+
+    n, level = (32, 32, 32), 1
+    nL = coarse_cells(n, level)
+    xs, ys, info = generate_visc_pairs(n, seeds=range(3), steps=10, level=level)
+    assert len(xs) == 3 * 3 * 8
+    box = cell_box(nL)
+    net = UNet(box, train=True, seed=0)
+    hist = train(net, xs, ys, cell_mask(nL, box), epochs=8, lr=1e-3, batch=4)
+    assert hist[-1] < hist[0]
+    model = UNet(box, train=False)
+    model.set_params(net.get_params())
+    net.close()
+    over = dict(Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)
+    (m1, m2), cfg = _visc_pair(n, over, 10, (1, 2))
+    set_visc_guess_model(m2, model, level)
+    its = [0, 0]
+    used = 0
+    for k in range(8):
+        s1, s2 = m1.step(cfg["dt"]), m2.step(cfg["dt"])
+        for s in (s1, s2):
+            assert all(s[q]["converged"] for q in ("mac", "visc", "nodal"))
+        its[0] += s1["visc"]["cycles"]
+        its[1] += s2["visc"]["cycles"]
+        used += (s2["visc"]["guess"] >> 1) & 1
+    u1, u2 = m1.get_field("U"), m2.get_field("U")
+    print(f"viscous iterations over 8 steps, previous increment / + learned direction: {its[0]} / {its[1]} "
+          f"(learned step taken {used}/8)")
+    assert np.max(np.abs(u2 - u1)) <= 1e-6 * np.max(np.abs(u1))
+    set_visc_guess_model(m2, None)
+    model.close()
+    m1.close()
+    m2.close()
