@@ -67,6 +67,12 @@ def parse():
     ap.add_argument("--learn-seeds", type=int, default=6)
     ap.add_argument("--learn-steps", type=int, default=10)
     ap.add_argument("--learn-epochs", type=int, default=15)
+    ap.add_argument("--vlearn-level", type=int, default=2,
+                    help="multigrid level of the viscous network's training cavities (applied on the level of the "
+                         "timed grid with the same cell count)")
+    ap.add_argument("--vlearn-seeds", type=int, default=3)
+    ap.add_argument("--vlearn-steps", type=int, default=10)
+    ap.add_argument("--vlearn-epochs", type=int, default=8)
     ap.add_argument("--learn-level", type=int, default=2,
                     help="multigrid level whose nodes the network sees (0 = finest)")
     ap.add_argument("--no-fp64-compare", action="store_true",
@@ -349,6 +355,8 @@ def run_ours(args):
     prec = MIXED if args.precision == "mixed" else FP64
     learned = None
     model = None
+    vmodel = None
+    vlev = None
     if prec == MIXED and not args.no_learned:
         # offline part of the learned guess: solver-generated pairs on small
         # cavities of the same family, trained by the library's kernels
@@ -368,11 +376,32 @@ def run_ours(args):
         tnet.close()
         model = UNet(net_box(coarse_cells(cfg["n"], lv)), train=False)
         model.set_params(params)
-        learned = {"train_cavities": f"{args.learn_seeds} x {args.learn_n}^{d}, random Bi/n/Re",
-                   "train_pairs": int(len(xs)), "level": lv,
-                   "epochs": args.learn_epochs, "loss_first": hist[0], "loss_last": hist[-1],
-                   "offline_seconds": time.perf_counter() - t0,
-                   "box": list(net_box(coarse_cells(cfg["n"], lv)))}
+        learned = {"nodal": {"train_cavities": f"{args.learn_seeds} x {args.learn_n}^{d}, random Bi/n/Re",
+                             "train_pairs": int(len(xs)), "level": lv,
+                             "epochs": args.learn_epochs, "loss_first": hist[0], "loss_last": hist[-1],
+                             "box": list(net_box(coarse_cells(cfg["n"], lv)))}}
+        # the viscous network: pairs from cavities with the previous-increment
+        # step on, restricted to a level whose cell count the timed grid has
+        # one level further down (128^3 level 2 = 256^3 level 3 = 32^3 cells)
+        from paper_1803_00417_gb300.learned import cell_box, cell_mask, generate_visc_pairs
+
+        vl = args.vlearn_level
+        nvl = coarse_cells(ln, vl)
+        vlev = next((l for l in range(12) if coarse_cells(cfg["n"], l) == nvl), None)
+        if vlev is not None:
+            vxs, vys, _ = generate_visc_pairs(ln, seeds=range(args.vlearn_seeds), steps=args.vlearn_steps,
+                                              level=vl)
+            vbox = cell_box(nvl)
+            vnet = UNet(vbox, train=True, seed=1)
+            vhist = train(vnet, vxs, vys, cell_mask(nvl, vbox), epochs=args.vlearn_epochs, lr=1e-3, batch=4)
+            vmodel = UNet(vbox, train=False)
+            vmodel.set_params(vnet.get_params())
+            vnet.close()
+            learned["viscous"] = {"train_cavities": f"{args.vlearn_seeds} x {args.learn_n}^{d}, random Bi/n/Re",
+                                  "train_pairs": int(len(vxs)), "train_level": vl, "level": vlev,
+                                  "epochs": args.vlearn_epochs, "loss_first": vhist[0], "loss_last": vhist[-1],
+                                  "box": list(vbox)}
+        learned["offline_seconds"] = time.perf_counter() - t0
     sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=prec)
     sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
     sim.set_solver(rtol=1e-10, max_cycles=200)
@@ -390,9 +419,12 @@ def run_ours(args):
     developed = sim.get_state()
     develop_s = time.perf_counter() - t0
     if model is not None:
-        from paper_1803_00417_gb300.hbflow import set_guess_model
+        from paper_1803_00417_gb300.hbflow import set_guess_model, set_visc_guess_model
 
         set_guess_model(sim, model, args.learn_level)
+        sim.set_visc_guess(2 if vmodel is not None else 1)
+        if vmodel is not None:
+            set_visc_guess_model(sim, vmodel, vlev)
 
     def restart(sim_):
         rec, u_, p_ = developed
@@ -410,6 +442,7 @@ def run_ours(args):
         cyc = {"mac": 0, "visc": 0, "nodal": 0}
         conv = True
         used = 0
+        vused = [0, 0]
         torch.cuda.synchronize()
         if clocks_ is not None:
             clocks_.start()
@@ -424,6 +457,8 @@ def run_ours(args):
                 cyc[k] += st[k]["cycles"]
                 conv &= st[k]["converged"]
             used += int(st["nodal"]["guess"])
+            vused[0] += st["visc"]["guess"] & 1
+            vused[1] += (st["visc"]["guess"] >> 1) & 1
         e1.record(stream)
         torch.cuda.synchronize()
         if profiler_range:
@@ -435,13 +470,16 @@ def run_ours(args):
         sim_.profile_enable(0)
         ms_ = max_over_ranks(ms_, dist, "cuda")
         timed.guess_used = used
+        timed.vguess_used = vused
         return ms_, cyc, conv, nl, prof_, clk_
 
     clocks = Clocks(local)
     ms, cycles, converged, launches, _, clk = timed(sim, 0, clocks, args.profiler_range)
     value = job_rate(world, ncell * args.steps, ms / 1e3)
     if learned is not None:
-        learned["guess_accepted_steps"] = f"{timed.guess_used}/{args.steps}"
+        learned["nodal"]["guess_accepted_steps"] = f"{timed.guess_used}/{args.steps}"
+        learned["viscous_steps_taken"] = {"previous_increment": f"{timed.vguess_used[0]}/{args.steps}",
+                                          "network": f"{timed.vguess_used[1]}/{args.steps}"}
     # instrumented pass: CUDA events around every finest-level launch of the
     # main kernel classes (level 2: every class) for the roofline and the
     # stage breakdown, continuing from the timed steps' state
@@ -482,14 +520,28 @@ def run_ours(args):
                "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
 
     mixed_only = None
+    increment_only = None
     if model is not None:
-        # the same method without the learned guess, for the V-cycles saved
+        # the same method without the networks: the previous-increment step of
+        # the viscous guess alone, then no guess at all (the V-cycles and
+        # iterations saved, and what each part costs)
         set_guess_model(sim, None)
+        set_visc_guess_model(sim, None)
+        sim.set_visc_guess(1)
+        msi, cyci, convi, _, _, _ = timed(sim, 0)
+        increment_only = {"value": world * ncell * args.steps / (msi / 1e3), "unit": UNIT,
+                          "ms_per_step": msi / args.steps, "converged": bool(convi),
+                          "cycles_per_step": {k: v / args.steps for k, v in cyci.items()},
+                          "guess": "viscous solve: previous-increment step only; no network"}
+        sim.set_visc_guess(0)
         msm, cycm, convm, _, _, _ = timed(sim, 0)
         mixed_only = {"value": world * ncell * args.steps / (msm / 1e3), "unit": UNIT,
                       "ms_per_step": msm / args.steps, "converged": bool(convm),
-                      "cycles_per_step": {k: v / args.steps for k, v in cycm.items()}}
+                      "cycles_per_step": {k: v / args.steps for k, v in cycm.items()},
+                      "guess": "none (the solves start from u^m and p^{m-1/2})"}
         model.close()
+        if vmodel is not None:
+            vmodel.close()
 
     fp64 = None
     if prec == MIXED and not args.no_fp64_compare:
@@ -564,6 +616,7 @@ def run_ours(args):
                        "converged": bool(converged)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "fp64_method": fp64, "learned_guess": learned, "mixed_without_learned": mixed_only,
+            "mixed_previous_increment_only": increment_only,
             "batch_sweep": batch,
             "clocks": clk,
             "protocol": {"develop_steps": args.develop, "develop_seconds": develop_s, "warmup": args.warmup,
