@@ -9,6 +9,7 @@
 // the right-hand side and pin the mean of the iterate after each cycle and the
 // bottom solve.
 #include <atomic>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <cstdio>
@@ -121,9 +122,80 @@ __global__ void k_dot_partial(const double* __restrict__ a, const double* __rest
   }
 }
 
+// Vectorised partials of the frequent reductions: 16-byte loads, four
+// iterations unrolled so that each thread keeps several loads in flight.
+// Thread t takes the vectors t, t + T, t + 2T, ... (T threads in the grid) in
+// that order, the tail past the last whole vector goes to thread 0, and the
+// block and final sums run in a fixed order: the result is the same on every
+// run.  MODE 0: max |x| (non-finite -> +inf); 1: sum x.  x 16-byte aligned.
+template <int MODE>
+__device__ __forceinline__ double red_op(double acc, double v) {
+  if (MODE == 0) {
+    double a = fabs(v);
+    if (!isfinite(a)) a = INFINITY;
+    return fmax(acc, a);
+  }
+  return acc + v;
+}
+
+template <int MODE>
+__device__ __forceinline__ void block_partial(double acc, double* part) {
+  __shared__ double sh[kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    double o = __shfl_xor_sync(0xffffffffu, acc, off);
+    acc = MODE == 0 ? fmax(acc, o) : acc + o;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) {
+      double o = __shfl_xor_sync(0xffffffffu, v, off);
+      v = MODE == 0 ? fmax(v, o) : v + o;
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+template <int MODE>
+__global__ void k_reduce_partial_v(const double* __restrict__ x, long long n, double* __restrict__ part) {
+  const long long T = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n2 = n >> 1;
+  const double2* x2 = reinterpret_cast<const double2*>(x);
+  double acc = 0.0;
+#pragma unroll 4
+  for (long long q = tid; q < n2; q += T) {
+    const double2 v = x2[q];
+    acc = red_op<MODE>(red_op<MODE>(acc, v.x), v.y);
+  }
+  if (tid == 0 && (n & 1)) acc = red_op<MODE>(acc, x[n - 1]);
+  block_partial<MODE>(acc, part);
+}
+
+__global__ void k_dot_partial_v(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                                double* __restrict__ part) {
+  const long long T = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n2 = n >> 1;
+  const double2* a2 = reinterpret_cast<const double2*>(a);
+  const double2* b2 = reinterpret_cast<const double2*>(b);
+  double acc = 0.0;
+#pragma unroll 4
+  for (long long q = tid; q < n2; q += T) {
+    const double2 u = a2[q], v = b2[q];
+    acc += u.x * v.x + u.y * v.y;
+  }
+  if (tid == 0 && (n & 1)) acc += a[n - 1] * b[n - 1];
+  block_partial<1>(acc, part);
+}
+
+static inline bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 template <int MODE>
 static int reduce_to_device(hbf_ctx* c, const double* x, long long n, double* out) {
-  launch(c, kSlotReduce, k_reduce_partial<MODE>, kRedBlocks, kThreads, x, n, c->partial, c->g, c->dim);
+  if (MODE < 2 && aligned16(x))
+    launch(c, kSlotReduce, k_reduce_partial_v<MODE < 2 ? MODE : 0>, kRedBlocks, kThreads, x, n, c->partial);
+  else
+    launch(c, kSlotReduce, k_reduce_partial<MODE>, kRedBlocks, kThreads, x, n, c->partial, c->g, c->dim);
   launch(c, kSlotReduce, k_reduce_final<MODE>, 1, 1024, c->partial, kRedBlocks, out);
   return cuda_check(c, cudaGetLastError(), "reduction");
 }
@@ -145,7 +217,10 @@ double reduce_max_abs(hbf_ctx* c, const double* x, long long n, int* st) {
 }
 
 double reduce_dot(hbf_ctx* c, const double* a, const double* b, long long n, int* st) {
-  launch(c, kSlotReduce, k_dot_partial, kRedBlocks, kThreads, a, b, n, c->partial);
+  if (aligned16(a) && aligned16(b))
+    launch(c, kSlotReduce, k_dot_partial_v, kRedBlocks, kThreads, a, b, n, c->partial);
+  else
+    launch(c, kSlotReduce, k_dot_partial, kRedBlocks, kThreads, a, b, n, c->partial);
   launch(c, kSlotReduce, k_reduce_final<1>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
   *st = cuda_check(c, cudaGetLastError(), "dot");
   if (*st) return NAN;
@@ -340,8 +415,65 @@ __global__ void k_maxabs_partial_f(const float* __restrict__ x, long long n, dou
   }
 }
 
+// the FP32 partials with 16-byte loads: products summed in FP32 over runs of
+// kDotRun elements (kDotRun / 4 vectors), the runs in FP64; same order rules
+// as k_reduce_partial_v
+__global__ void k_dot_partial_f4(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                                 double* __restrict__ part) {
+  const long long T = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n4 = n >> 2;
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  double acc = 0.0;
+  float run = 0.f;
+  int k = 0;
+#pragma unroll 4
+  for (long long q = tid; q < n4; q += T) {
+    const float4 x = a4[q], y = b4[q];
+    run = fmaf(x.x, y.x, run);
+    run = fmaf(x.y, y.y, run);
+    run = fmaf(x.z, y.z, run);
+    run = fmaf(x.w, y.w, run);
+    if (++k == kDotRun / 4) {
+      acc += (double)run;
+      run = 0.f;
+      k = 0;
+    }
+  }
+  if (tid == 0)
+    for (long long e = n4 << 2; e < n; ++e) run = fmaf(a[e], b[e], run);
+  acc += (double)run;
+  block_partial<1>(acc, part);
+}
+
+__global__ void k_maxabs_partial_f4(const float* __restrict__ x, long long n, double* __restrict__ part) {
+  const long long T = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n4 = n >> 2;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  float m = 0.f;
+  auto upd = [&](float v) {
+    float a = fabsf(v);
+    if (!isfinite(a)) a = INFINITY;
+    m = fmaxf(m, a);
+  };
+#pragma unroll 4
+  for (long long q = tid; q < n4; q += T) {
+    const float4 v = x4[q];
+    upd(v.x);
+    upd(v.y);
+    upd(v.z);
+    upd(v.w);
+  }
+  if (tid == 0)
+    for (long long e = n4 << 2; e < n; ++e) upd(x[e]);
+  block_partial<0>((double)m, part);
+}
+
 static double reduce_dot_f(hbf_ctx* c, const float* a, const float* b, long long n, int* st) {
-  launch(c, kSlotReduce, k_dot_partial_f, kRedBlocks, kThreads, a, b, n, c->partial);
+  if (aligned16(a) && aligned16(b))
+    launch(c, kSlotReduce, k_dot_partial_f4, kRedBlocks, kThreads, a, b, n, c->partial);
+  else
+    launch(c, kSlotReduce, k_dot_partial_f, kRedBlocks, kThreads, a, b, n, c->partial);
   launch(c, kSlotReduce, k_reduce_final<1>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
   *st = cuda_check(c, cudaGetLastError(), "dot");
   if (*st) return NAN;
@@ -349,7 +481,10 @@ static double reduce_dot_f(hbf_ctx* c, const float* a, const float* b, long long
 }
 
 static double reduce_max_abs_f(hbf_ctx* c, const float* x, long long n, int* st) {
-  launch(c, kSlotReduce, k_maxabs_partial_f, kRedBlocks, kThreads, x, n, c->partial);
+  if (aligned16(x))
+    launch(c, kSlotReduce, k_maxabs_partial_f4, kRedBlocks, kThreads, x, n, c->partial);
+  else
+    launch(c, kSlotReduce, k_maxabs_partial_f, kRedBlocks, kThreads, x, n, c->partial);
   launch(c, kSlotReduce, k_reduce_final<0>, 1, 1024, (const double*)c->partial, kRedBlocks, c->dres);
   *st = cuda_check(c, cudaGetLastError(), "max");
   if (*st) return NAN;
@@ -579,13 +714,14 @@ template <int D, typename T>
 struct ViscProblem : Problem<T> {
   using Problem<T>::c;
   T* x0;
+  const T* b0 = nullptr;  // level-0 right-hand side in place of the level's own array (read only)
   double beta;
   ViscProblem(hbf_ctx* ctx, T* x_in, double bt, bool h0) : Problem<T>(ctx, false, h0), x0(x_in), beta(bt) {}
   int kind() const override { return 0; }
   double dense_beta() const override { return beta; }
   bool tail(int l) override { return run_tail<D, T, batch::kVisc>(c, l, beta); }
   T* x(int l) override { return l == 0 ? x0 : View<T>::vx(c->lv[l]); }
-  T* b(int l) override { return View<T>::vb(c->lv[l]); }
+  T* b(int l) override { return (l == 0 && b0) ? const_cast<T*>(b0) : View<T>::vb(c->lv[l]); }
   T* r(int l) override { return View<T>::vr(c->lv[l]); }
   long long count(int l) override { return (long long)D * c->lv[l].g.ncell; }
   void smooth(int l) override {
@@ -1034,9 +1170,12 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
     cudaMemcpyAsync(r, L0.vr, bytes, cudaMemcpyDeviceToDevice, c->stream);
     return reduce_max_abs(c, r, n, &st);
   };
+  // the V-cycle reads q as its level-0 right-hand side in place (the fused
+  // tail starts on level 1 or below, so its argument records never hold level
+  // 0's array)
   auto precond = [&](const float* q, float* z) {
     ViscProblem<D, float> Pz(c, z, beta, true);
-    cudaMemcpyAsync(L0.fvb, q, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    Pz.b0 = q;
     launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, z, n);
     vcycle(Pz, 0, cfg);
   };
@@ -1145,7 +1284,7 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
       launch(c, kSlotTransfer, k_convert<double, float>, nb, kThreads, z, (const float*)L0.fvx, n);
     } else {
       ViscProblem<D, double> Pz(c, z, beta, true);
-      cudaMemcpyAsync(L0.vb, q, bytes, cudaMemcpyDeviceToDevice, c->stream);
+      Pz.b0 = q;  // read in place, as in the mixed solve
       launch(c, kSlotTransfer, k_zero<double>, nb, kThreads, z, n);
       vcycle(Pz, 0, cfg);
     }
