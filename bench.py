@@ -208,7 +208,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
-SMOOTHER_DRAM_BYTES_PER_CELL = (144.2e6 + 15.8e6) / 192 ** 3
+SMOOTHER_DRAM_BYTES_PER_CELL = (144.18e6 + 15.14e6) / 192 ** 3  # profiles/k_visc_smooth_cavity192.md
 
 
 def visc_smoother_bytes(d, ncell, elem, cell_eta):
@@ -579,15 +579,14 @@ def run_ours(args):
         algo = fused_sweep_bytes(d, ncell, elem) if fused else visc_smoother_bytes(d, ncell, elem, prec == MIXED)
         ach = algo / per_launch_s / 1e9
         # DRAM bytes per cell of this kernel from one full ncu capture at 192^3
-        # (profiles/k_visc_smooth_cavity192.md), scaled to this grid.  The
-        # kernel's arithmetic has changed since that capture (its loads have
-        # not), so the figure is reported beside the roofline, and "traffic"
-        # stays null until the kernel is captured again.
-        last = SMOOTHER_DRAM_BYTES_PER_CELL * ncell if (prec == MIXED and not fused) else None
+        # of the current kernel (profiles/k_visc_smooth_cavity192.md), scaled
+        # to this grid by the cell count (the kernel reads the same arrays per
+        # cell at any size; the 256^3 workload is too large to capture)
+        traffic = SMOOTHER_DRAM_BYTES_PER_CELL * ncell if (prec == MIXED and not fused) else None
         roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                    "traffic": None, "traffic_last_capture": last,
-                    "traffic_source": "ncu at 192^3 before the last arithmetic-only change, 22.6 B/cell, "
-                    "scaled by cells" if last else None,
+                    "traffic": traffic,
+                    "traffic_source": "ncu capture of the same kernel at 192^3 (22.5 B/cell), scaled by cells"
+                    if traffic else None,
                     "kernel": "k_visc_sweep_rb (fused red-black sweep, finest level)" if fused
                     else "k_visc_smooth (finest level)",
                     "launches": sm_n, "avg_launch_us": per_launch_s * 1e6,

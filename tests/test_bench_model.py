@@ -24,4 +24,10 @@ def test_smoother_bytes_face_arrays():
 
 def test_traffic_per_cell_from_capture():
     # the DRAM bytes per cell taken from the 192^3 capture
-    assert bench.SMOOTHER_DRAM_BYTES_PER_CELL == pytest.approx(22.6, abs=0.05)
+    # (profiles/k_visc_smooth_cavity192.md: 144.2 MB read + 15.1 MB written)
+    assert bench.SMOOTHER_DRAM_BYTES_PER_CELL == pytest.approx(22.5, abs=0.05)
+
+
+def test_fused_sweep_bytes():
+    # u_c, two other components, eta, b_c read once, u_c written once
+    assert bench.fused_sweep_bytes(3, 1000, 4) == pytest.approx(24.0 * 1000)
