@@ -20,8 +20,9 @@
  *    element (c, i, j, k) of a d-component field sits at
  *    c*ncell + i + nx*(j + ny*k); nodal fields (pressure) have (nx+1)(ny+1)(nz+1)
  *    points, i + (nx+1)*(j + (ny+1)*k).  In 2D nz = 1 and k = 0.
- *  - only no-slip walls (with a prescribed tangential wall velocity) are
- *    supported; every face of the box is a wall.
+ *  - every face of the box is a no-slip wall with a prescribed tangential
+ *    velocity, except the faces normal to the axes made periodic by
+ *    hbf_set_periodic.
  */
 #ifndef HBFLOW_H
 #define HBFLOW_H
@@ -101,6 +102,16 @@ typedef struct {
  * pressure.) */
 int hbf_init_grid(hbf_ctx** out, int dim, const int64_t n[3], double h, const double wall_u[18],
                   int precision, void* stream);
+
+/* Make axis a periodic (periodic[a] != 0) or bounded by walls (0), for the
+ * channel flows with which the method is checked (plane Couette and Poiseuille
+ * flow between walls, periodic along the flow).  A periodic axis needs an even
+ * cell count; the walls normal to it are dropped (their velocities set to 0).
+ * Nodal fields keep n+1 points along a periodic axis, the last a copy of the
+ * first: fields set with hbf_set_field must repeat node 0 there (the library
+ * keeps the copy equal).  Call before stepping; the exact bottom inverses are
+ * rebuilt.  HBF_ERR_ARG for an odd count.  Not available in a batch. */
+int hbf_set_periodic(hbf_ctx* ctx, const int periodic[3]);
 
 /* Regularised Herschel-Bulkley law, Eq. 23 with mu -> K and 1/epsilon -> m:
  *   eta = (2^(n-1) K g^n + tau_y/2) F(g),  F(g) = (1 - exp(-m g))/g, F(0) = m,
@@ -368,6 +379,7 @@ typedef struct {
   int32_t reg_power;
   int32_t predictor_viscous; /* hbf_set_predictor_viscous */
   double theta;              /* hbf_set_theta */
+  int32_t periodic[3];       /* hbf_set_periodic */
   double rho;                /* hbf_set_density */
   double f[3];               /* hbf_set_body_force */
   double wall_u[18];         /* layout of hbf_init_grid */

@@ -377,6 +377,33 @@ int hbf_set_solver(hbf_ctx* c, double rtol, int max_cycles, int nu1, int nu2, in
   return HBF_OK;
 }
 
+int hbf_set_periodic(hbf_ctx* c, const int periodic[3]) {
+  if (!c || !periodic) return HBF_ERR_ARG;
+  int per[3] = {0, 0, 0};
+  for (int a = 0; a < c->dim; ++a) {
+    per[a] = periodic[a] ? 1 : 0;
+    if (per[a] && (c->g.n[a] % 2 != 0 || c->g.n[a] < 2))
+      return fail(c, HBF_ERR_ARG, "a periodic axis needs an even cell count");
+  }
+  for (int a = 0; a < 3; ++a) {
+    c->g.per[a] = per[a];
+    if (per[a])  // no walls normal to a periodic axis
+      for (int s = 0; s < 2; ++s)
+        for (int q = 0; q < 3; ++q) c->g.wu[a][s][q] = 0.0;
+  }
+  geom_finish(c->g);
+  c->lv[0].g = c->g;
+  for (size_t l = 1; l < c->lv.size(); ++l)
+    for (int a = 0; a < 3; ++a) c->lv[l].g.per[a] = per[a];
+  // operators changed: rebuild the exact bottom inverses and the tail records
+  for (auto& d : c->dense) d.valid = false;
+  c->tail_lf = -1;
+  for (auto& k : c->tail_host)
+    for (auto& h : k) h.clear();
+  ++c->walls_version;
+  return HBF_OK;
+}
+
 int hbf_set_visc_guess(hbf_ctx* c, int mode) {
   if (!c) return HBF_ERR_ARG;
   if (mode < 0 || mode > 2) return fail(c, HBF_ERR_ARG, "viscous guess mode must be 0, 1 or 2");

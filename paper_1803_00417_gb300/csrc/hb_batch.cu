@@ -1259,6 +1259,8 @@ int prepare(hbf_batch* B) {
     if (!(B->dt[c] > 0.0)) return bfail(B, HBF_ERR_ARG, "every cavity needs a positive time step (hbf_batch_set_dt)");
     if (x->cfg.nu1 != c0.nu1 || x->cfg.nu2 != c0.nu2)
       return bfail(B, HBF_ERR_ARG, "all cavities of a batch need the same smoothing counts nu1, nu2");
+    if (x->g.per[0] || x->g.per[1] || x->g.per[2])
+      return bfail(B, HBF_ERR_ARG, "the batched sweep has walls on every face (no periodic axes)");
     B->nlev[c] = (int)x->lv.size();
     if (B->nlev[c] > kMaxLev) return bfail(B, HBF_ERR_ARG, "too many multigrid levels");
     B->maxlev = std::max(B->maxlev, B->nlev[c]);

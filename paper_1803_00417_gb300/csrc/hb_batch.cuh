@@ -56,9 +56,7 @@ __host__ __device__ inline double node_weight(const Geom& g, int dim, int t) {
   int i, j, k;
   node_coords(g, t, i, j, k);
   double w = 1.0;
-  if (i == 0 || i == g.n[0]) w *= 0.5;
-  if (j == 0 || j == g.n[1]) w *= 0.5;
-  if (dim == 3 && (k == 0 || k == g.n[2])) w *= 0.5;
+  w = node_weight(g, i, j, k, dim);
   return w;
 }
 

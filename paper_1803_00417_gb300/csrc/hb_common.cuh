@@ -17,6 +17,7 @@ constexpr int kThreads = 256;
 
 struct Geom {
   int n[3];          // cells per axis (n[2] == 1 in 2D)
+  int per[3];        // 1: the axis is periodic (no walls normal to it), 0: walls
   double h;          // cell size (equal on all axes)
   double wu[3][2][3];  // wall velocity [axis][side][component]
   int ncell;
@@ -175,13 +176,40 @@ __host__ __device__ inline void face_coords(const Geom& g, int a, int t, int& i,
   j = r - k * ey;
 }
 
+// A periodic axis: a cell index within one period of [0, n) wrapped into it;
+// a node index within one period of [0, n] wrapped into it (node n is the
+// copy of node 0, kept so that nodal arrays have n+1 points on every axis).
+__host__ __device__ inline int wrap_cell(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+__host__ __device__ inline int wrap_node(int i, int n) { return i < 0 ? i + n : (i > n ? i - n : i); }
+
+// Weight of node (i, j, k) in the mean of a nodal field: the fraction of its
+// dual cell inside the domain (1/2 per wall axis on which the node lies on
+// the wall), 0 for the copy node n on a periodic axis (so that every distinct
+// node counts once)
+__host__ __device__ inline double node_weight(const Geom& g, int i, int j, int k, int dim) {
+  const int p[3] = {i, j, k};
+  double w = 1.0;
+  for (int a = 0; a < dim; ++a) {
+    if (g.per[a]) {
+      if (p[a] == g.n[a]) w = 0.0;
+    } else if (p[a] == 0 || p[a] == g.n[a]) {
+      w *= 0.5;
+    }
+  }
+  return w;
+}
+
 // Velocity component c at cell (i,j,k) where at most one axis is out of range
 // by one or two cells: odd reflection about the wall value of that face,
 // g = 2 u_b - u_mirror (homogeneous: u_b = 0).
 template <int D, typename T>
 __host__ __device__ inline T uget(const T* __restrict__ uc, const Geom& g, int c, int i, int j, int k,
                                   bool hom) {
-  // the first out-of-range axis (x, then y, then z) selects the reflection
+  // periodic axes wrap; then the first out-of-range axis (x, then y, then z)
+  // selects the reflection
+  if (g.per[0]) i = wrap_cell(i, g.n[0]);
+  if (g.per[1]) j = wrap_cell(j, g.n[1]);
+  if (D == 3 && g.per[2]) k = wrap_cell(k, g.n[2]);
   int ax = -1, side = 0;
   if (i < 0) {
     ax = 0; side = 0; i = -i - 1;
@@ -202,18 +230,26 @@ __host__ __device__ inline T uget(const T* __restrict__ uc, const Geom& g, int c
   return T(2) * ub - v;
 }
 
-// Scalar with even reflection across walls (Neumann ghosts; one layer).
+// Scalar with even reflection across walls (Neumann ghosts; one layer),
+// wrapped on periodic axes.
 template <int D, typename T>
 __host__ __device__ inline T nget(const T* __restrict__ x, const Geom& g, int i, int j, int k) {
+  if (g.per[0]) i = wrap_cell(i, g.n[0]);
+  if (g.per[1]) j = wrap_cell(j, g.n[1]);
+  if (D == 3 && g.per[2]) k = wrap_cell(k, g.n[2]);
   i = i < 0 ? -i - 1 : (i >= g.n[0] ? 2 * g.n[0] - 1 - i : i);
   j = j < 0 ? -j - 1 : (j >= g.n[1] ? 2 * g.n[1] - 1 - j : j);
   if (D == 3) k = k < 0 ? -k - 1 : (k >= g.n[2] ? 2 * g.n[2] - 1 - k : k);
   return x[cidx<D>(g, i, j, k)];
 }
 
-// Node value with even reflection across walls (node -1 -> 1, n+1 -> n-1).
+// Node value with even reflection across walls (node -1 -> 1, n+1 -> n-1),
+// wrapped on periodic axes (node -1 -> n-1, n+1 -> 1).
 template <int D, typename T>
 __host__ __device__ inline T ndget(const T* __restrict__ x, const Geom& g, int i, int j, int k) {
+  if (g.per[0]) i = wrap_node(i, g.n[0]);
+  if (g.per[1]) j = wrap_node(j, g.n[1]);
+  if (D == 3 && g.per[2]) k = wrap_node(k, g.n[2]);
   i = i < 0 ? -i : (i > g.n[0] ? 2 * g.n[0] - i : i);
   j = j < 0 ? -j : (j > g.n[1] ? 2 * g.n[1] - j : j);
   if (D == 3) k = k < 0 ? -k : (k > g.n[2] ? 2 * g.n[2] - k : k);

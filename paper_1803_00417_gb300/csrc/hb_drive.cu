@@ -64,12 +64,13 @@ __global__ void k_zone_step(int* __restrict__ lab, const __grid_constant__ Geom 
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const int stride = a == 0 ? 1 : (a == 1 ? g.n[0] : g.n[0] * g.n[1]);
-      if (p[a] > 0) {
-        const int q = lab[t - stride];
+      const int span = stride * g.n[a];  // a periodic axis wraps by one period
+      if (p[a] > 0 || g.per[a]) {
+        const int q = lab[p[a] > 0 ? t - stride : t - stride + span];
         if (q >= 0 && q < m) m = q;
       }
-      if (p[a] < g.n[a] - 1) {
-        const int q = lab[t + stride];
+      if (p[a] < g.n[a] - 1 || g.per[a]) {
+        const int q = lab[p[a] < g.n[a] - 1 ? t + stride : t + stride - span];
         if (q >= 0 && q < m) m = q;
       }
     }
@@ -97,7 +98,7 @@ __global__ void k_zone_touch(const int* __restrict__ lab, int* __restrict__ touc
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        if (p[a] != (s ? g.n[a] - 1 : 0)) continue;
+        if (g.per[a] || p[a] != (s ? g.n[a] - 1 : 0)) continue;
         const bool moving = g.wu[a][s][0] != 0.0 || g.wu[a][s][1] != 0.0 || g.wu[a][s][2] != 0.0;
         bits |= moving ? 2 : 1;
       }
@@ -297,6 +298,7 @@ int hbf_get_state(hbf_ctx* c, hbf_state* s, double* u, double* p) {
   s->reg_power = c->rheo.reg_power;
   s->predictor_viscous = c->predictor_visc;
   s->theta = c->theta;
+  for (int a = 0; a < 3; ++a) s->periodic[a] = c->g.per[a];
   s->rho = c->rho;
   for (int a = 0; a < 3; ++a) s->f[a] = c->f[a];
   for (int a = 0; a < 3; ++a)
@@ -319,6 +321,8 @@ int hbf_set_state(hbf_ctx* c, const hbf_state* s, const double* u, const double*
   if ((st = hbf_set_body_force(c, s->f))) return st;
   if ((st = hbf_set_predictor_viscous(c, s->predictor_viscous))) return st;
   if ((st = hbf_set_theta(c, s->theta))) return st;
+  const int per[3] = {s->periodic[0], s->periodic[1], s->periodic[2]};
+  if ((st = hbf_set_periodic(c, per))) return st;
   if ((st = hbf_set_walls(c, s->wall_u))) return st;
   if (u && (st = hbf_set_field(c, HBF_U, u))) return st;
   if (p && (st = hbf_set_field(c, HBF_P, p))) return st;
@@ -336,7 +340,7 @@ int hbf_set_walls(hbf_ctx* c, const double wall_u[18]) {
   for (int a = 0; a < 3; ++a)
     for (int sd = 0; sd < 2; ++sd)
       for (int q = 0; q < 3; ++q)
-        c->g.wu[a][sd][q] = (a < c->dim && q < c->dim) ? wall_u[(a * 2 + sd) * 3 + q] : 0.0;
+        c->g.wu[a][sd][q] = (a < c->dim && q < c->dim && !c->g.per[a]) ? wall_u[(a * 2 + sd) * 3 + q] : 0.0;
   geom_finish(c->g);
   // the finest multigrid level carries the wall velocities (coarse levels
   // solve for homogeneous errors); the fused tail records are rebuilt in

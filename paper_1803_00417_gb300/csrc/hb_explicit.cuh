@@ -126,8 +126,13 @@ __host__ __device__ __forceinline__ void k_eta_faces_at(const double* __restrict
     face_coords(g, a, t, p[0], p[1], p[2]);
     int L[3] = {p[0], p[1], p[2]}, R[3] = {p[0], p[1], p[2]};
     L[a] -= 1;
-    if (L[a] < 0) L[a] = 0;
-    if (R[a] >= g.n[a]) R[a] = g.n[a] - 1;
+    if (g.per[a]) {  // periodic: the cells across the face, wrapped
+      L[a] = wrap_cell(L[a], g.n[a]);
+      R[a] = wrap_cell(R[a], g.n[a]);
+    } else {
+      if (L[a] < 0) L[a] = 0;
+      if (R[a] >= g.n[a]) R[a] = g.n[a] - 1;
+    }
     ef[t] = dhalf(eta[cidx<D>(g, L[0], L[1], L[2])] + eta[cidx<D>(g, R[0], R[1], R[2])]);
   }
 
@@ -265,15 +270,20 @@ template <int D>
 __host__ __device__ inline void prestate_face(const double* __restrict__ u, const double* __restrict__ slopes,
                                      const Geom& g, const StepC& k, int b, const int* L, double* st,
                                      double& vb) {
+  int Lw[3] = {L[0], L[1], L[2]};
   int R[3] = {L[0], L[1], L[2]};
   R[b] += 1;
   double sL[3], sR[3];
-  if (L[b] < 0 || R[b] >= g.n[b]) {
+  if (g.per[b]) {
+    R[b] = wrap_cell(R[b], g.n[b]);
+    Lw[b] = wrap_cell(Lw[b], g.n[b]);
+  }
+  if (!g.per[b] && (L[b] < 0 || R[b] >= g.n[b])) {
     int side = L[b] < 0 ? 0 : 1;
 #pragma unroll
     for (int c = 0; c < D; ++c) sL[c] = sR[c] = g.wu[b][side][c];
   } else {
-    int tl = cidx<D>(g, L[0], L[1], L[2]), tr = cidx<D>(g, R[0], R[1], R[2]);
+    int tl = cidx<D>(g, Lw[0], Lw[1], Lw[2]), tr = cidx<D>(g, R[0], R[1], R[2]);
     double ubL = u[(size_t)b * g.ncell + tl], ubR = u[(size_t)b * g.ncell + tr];
     double facL = 0.5 - ubL * k.dt2h;
     double facR = 0.5 + ubR * k.dt2h;
@@ -375,7 +385,10 @@ __host__ __device__ __forceinline__ void k_traces_at(const double* __restrict__ 
     face_coords(g, a, t, R[0], R[1], R[2]);
     int L[3] = {R[0], R[1], R[2]};
     L[a] -= 1;
-    if (L[a] < 0 || R[a] >= g.n[a]) {
+    if (g.per[a]) {  // periodic: the cells across the face, wrapped (face n repeats face 0)
+      L[a] = wrap_cell(L[a], g.n[a]);
+      R[a] = wrap_cell(R[a], g.n[a]);
+    } else if (L[a] < 0 || R[a] >= g.n[a]) {
       int side = L[a] < 0 ? 0 : 1;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
@@ -449,12 +462,16 @@ __host__ __device__ __forceinline__ void k_mac_correct_at(const double* __restri
   
     int R[3];
     face_coords(g, a, t, R[0], R[1], R[2]);
-    if (R[a] == 0 || R[a] == g.n[a]) {
+    if (!g.per[a] && (R[a] == 0 || R[a] == g.n[a])) {
       umac[t] = 0.0;
       return;
     }
     int L[3] = {R[0], R[1], R[2]};
     L[a] -= 1;
+    if (g.per[a]) {
+      L[a] = wrap_cell(L[a], g.n[a]);
+      R[a] = wrap_cell(R[a], g.n[a]);
+    }
     double gr = (phi[cidx<D>(g, R[0], R[1], R[2])] - phi[cidx<D>(g, L[0], L[1], L[2])]) * g.ih;
     umac[t] = uadv[t] - gr;
   }
@@ -576,6 +593,9 @@ __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict
           cb[2] = 1;
         }
         int q[3] = {p[0] - 1 + cb[0], p[1] - 1 + cb[1], D == 3 ? p[2] - 1 + cb[2] : 0};
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+          if (g.per[b]) q[b] = wrap_cell(q[b], g.n[b]);
         bool in = q[0] >= 0 && q[0] < g.n[0] && q[1] >= 0 && q[1] < g.n[1] &&
                   (D == 2 || (q[2] >= 0 && q[2] < g.n[2]));
         if (!in) continue;
@@ -588,7 +608,7 @@ __host__ __device__ __forceinline__ void k_nodal_rhs_at(const double* __restrict
     double iw = 1.0;
 #pragma unroll
     for (int a = 0; a < D; ++a)
-      if (p[a] == 0 || p[a] == g.n[a]) iw *= 2.0;
+      if (!g.per[a] && (p[a] == 0 || p[a] == g.n[a])) iw *= 2.0;
     out[t] = k.rho * (acc * (iw * k.inrm));
   }
 

@@ -45,9 +45,7 @@ __global__ void k_reduce_partial(const double* __restrict__ x, long long n, doub
       int j = q % e1;
       int k = q / e1;
       double w = 1.0;
-      if (i == 0 || i == g.n[0]) w *= 0.5;
-      if (j == 0 || j == g.n[1]) w *= 0.5;
-      if (dim == 3 && (k == 0 || k == g.n[2])) w *= 0.5;
+      w = node_weight(g, i, j, k, dim);
       acc += w * v;
     }
   }
@@ -762,7 +760,8 @@ struct ViscProblem : Problem<T> {
   // 3D FP32 finest level: each component's red-black sweep in one launch
   // (hb_visc_fused.cuh), alternating between x and the level's second array
   void smooth_n(int l, int count) override {
-    if (!(D == 3 && cell_eta(l) && c->fused_sweep && c->lv[0].fvx2)) {
+    const bool walls = !c->g.per[0] && !c->g.per[1] && !c->g.per[2];
+    if (!(D == 3 && cell_eta(l) && c->fused_sweep && c->lv[0].fvx2 && walls)) {
       Problem<T>::smooth_n(l, count);
       return;
     }

@@ -45,8 +45,13 @@ struct CellEta {
   __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
   __host__ __device__ T at(const Geom& g, int a, const int* q) const {
     int L[3] = {q[0], q[1], q[2]}, R[3] = {q[0], q[1], q[2]};
-    L[a] = q[a] > 0 ? q[a] - 1 : 0;
-    R[a] = q[a] < g.n[a] ? q[a] : g.n[a] - 1;
+    if (g.per[a]) {  // periodic: the two cells across the face, wrapped
+      L[a] = wrap_cell(q[a] - 1, g.n[a]);
+      R[a] = wrap_cell(q[a], g.n[a]);
+    } else {
+      L[a] = q[a] > 0 ? q[a] - 1 : 0;
+      R[a] = q[a] < g.n[a] ? q[a] : g.n[a] - 1;
+    }
     return T(0.5) * (eta[cidx<3>(g, L[0], L[1], L[2])] + eta[cidx<3>(g, R[0], R[1], R[2])]);
   }
 };
@@ -57,6 +62,10 @@ template <int D, typename T>
 __host__ __device__ __forceinline__ T uget_axis(const T* __restrict__ uc, const Geom& g, int comp, int i, int j, int k,
                                                 int ax, bool hom) {
   int q[3] = {i, j, k};
+  if (g.per[ax]) {
+    q[ax] = wrap_cell(q[ax], g.n[ax]);
+    return uc[cidx<D>(g, q[0], q[1], q[2])];
+  }
   int side = -1;
   if (q[ax] < 0) {
     side = 0;
@@ -75,14 +84,20 @@ template <int D, typename T>
 __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
                                   bool hom) {
   // mean of the two cells' central differences, (dL + dR)/2 with dL, dR over 2h;
-  // L and L + e_a are inside the domain, so only the c offsets can cross a wall
-  if (L[a] < 0 || L[a] >= g.n[a] - 1) return T(0);
+  // on a wall axis L and L + e_a are inside the domain (a wall face gives 0),
+  // on a periodic axis they are wrapped, so only the c offsets can leave it
+  if (!g.per[a] && (L[a] < 0 || L[a] >= g.n[a] - 1)) return T(0);
   int p1[3] = {L[0], L[1], L[2]}, p0[3] = {L[0], L[1], L[2]};
+  if (g.per[a]) p1[a] = p0[a] = wrap_cell(L[a], g.n[a]);
   p1[c] += 1;
   p0[c] -= 1;
   T dL = uget_axis<D>(ua, g, a, p1[0], p1[1], p1[2], c, hom) - uget_axis<D>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
-  p1[a] += 1;
-  p0[a] += 1;
+  if (g.per[a]) {
+    p1[a] = p0[a] = wrap_cell(L[a] + 1, g.n[a]);
+  } else {
+    p1[a] += 1;
+    p0[a] += 1;
+  }
   T dR = uget_axis<D>(ua, g, a, p1[0], p1[1], p1[2], c, hom) - uget_axis<D>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
   return (dL + dR) * g_q4<T>(g);
 }
@@ -137,12 +152,13 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
         fq[a] += 1;
       }
       T wf = kappa * ef.at(g, a, fq) * ihh;
-      bool wall = (s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1);
+      bool wall = !g.per[a] && ((s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1));
       if (wall) {
         T ub = hom ? T(0) : g_wu<T>(g, a, s, c);
         offd += T(2) * wf * ub;
         diag += T(2) * wf;
       } else {
+        if (g.per[a]) q[a] = wrap_cell(q[a], g.n[a]);
         offd += wf * uc[cidx<D>(g, q[0], q[1], q[2])];
         diag += wf;
       }
@@ -579,15 +595,15 @@ __host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __r
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T lo = T(0), hi = T(0);
-    if (p[a] > 0) {
+    if (p[a] > 0 || g.per[a]) {
       int q[3] = {p[0], p[1], p[2]};
-      q[a] -= 1;
+      q[a] = g.per[a] ? wrap_cell(q[a] - 1, g.n[a]) : q[a] - 1;
       lo = x[cidx<D>(g, q[0], q[1], q[2])];
       ++cnt;
     }
-    if (p[a] < g.n[a] - 1) {
+    if (p[a] < g.n[a] - 1 || g.per[a]) {
       int q[3] = {p[0], p[1], p[2]};
-      q[a] += 1;
+      q[a] = g.per[a] ? wrap_cell(q[a] + 1, g.n[a]) : q[a] + 1;
       hi = x[cidx<D>(g, q[0], q[1], q[2])];
       ++cnt;
     }
@@ -625,14 +641,14 @@ __host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       T glo = T(0), ghi = T(0);
-      if (p[a] > 0) {
+      if (p[a] > 0 || g.per[a]) {
         int q[3] = {p[0], p[1], p[2]};
-        q[a] -= 1;
+        q[a] = g.per[a] ? wrap_cell(q[a] - 1, g.n[a]) : q[a] - 1;
         glo = (xc - x[cidx<D>(g, q[0], q[1], q[2])]) * ih;
       }
-      if (p[a] < g.n[a] - 1) {
+      if (p[a] < g.n[a] - 1 || g.per[a]) {
         int q[3] = {p[0], p[1], p[2]};
-        q[a] += 1;
+        q[a] = g.per[a] ? wrap_cell(q[a] + 1, g.n[a]) : q[a] + 1;
         ghi = (x[cidx<D>(g, q[0], q[1], q[2])] - xc) * ih;
       }
       acc += (ghi - glo) * ih;
@@ -870,6 +886,9 @@ __global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, i
 template <int D, typename T>
 __host__ __device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, int i, int j, int k, T sign) {
   T s = T(1);
+  if (g.per[0]) i = wrap_cell(i, g.n[0]);
+  if (g.per[1]) j = wrap_cell(j, g.n[1]);
+  if (D == 3 && g.per[2]) k = wrap_cell(k, g.n[2]);
   if (i < 0) { i = 0; s *= sign; }
   if (i >= g.n[0]) { i = g.n[0] - 1; s *= sign; }
   if (j < 0) { j = 0; s *= sign; }
@@ -1001,14 +1020,14 @@ __device__ inline T cell_lap_point(const T* __restrict__ x, const Geom& g, const
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T glo = T(0), ghi = T(0);
-    if (p[a] > 0) {
+    if (p[a] > 0 || g.per[a]) {
       int q[3] = {p[0], p[1], p[2]};
-      q[a] -= 1;
+      q[a] = g.per[a] ? wrap_cell(q[a] - 1, g.n[a]) : q[a] - 1;
       glo = (xc - x[cidx<D>(g, q[0], q[1], q[2])]) * ih;
     }
-    if (p[a] < g.n[a] - 1) {
+    if (p[a] < g.n[a] - 1 || g.per[a]) {
       int q[3] = {p[0], p[1], p[2]};
-      q[a] += 1;
+      q[a] = g.per[a] ? wrap_cell(q[a] + 1, g.n[a]) : q[a] + 1;
       ghi = (x[cidx<D>(g, q[0], q[1], q[2])] - xc) * ih;
     }
     acc += (ghi - glo) * ih;
@@ -1053,9 +1072,7 @@ __device__ inline void dense_build_col(int kind, double* __restrict__ X, double*
     if (kind == 2) {
       const int e0 = g.n[0] + 1, e1 = g.n[1] + 1;
       const int pi = k % e0, pj = (k / e0) % e1, pk = k / (e0 * e1);
-      if (pi == 0 || pi == g.n[0]) w *= 0.5;
-      if (pj == 0 || pj == g.n[1]) w *= 0.5;
-      if (D == 3 && (pk == 0 || pk == g.n[2])) w *= 0.5;
+      w = node_weight(g, pi, pj, pk, D);
     }
     M[(size_t)n * ld + k] = w;
     M[(size_t)k * ld + n] = w;

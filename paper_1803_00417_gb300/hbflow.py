@@ -46,7 +46,7 @@ class State(ctypes.Structure):
                 ("h", ctypes.c_double), ("t", ctypes.c_double), ("step", ctypes.c_int64),
                 ("K", ctypes.c_double), ("nexp", ctypes.c_double), ("tau_y", ctypes.c_double),
                 ("m", ctypes.c_double), ("reg_power", ctypes.c_int32), ("predictor_viscous", ctypes.c_int32),
-                ("theta", ctypes.c_double), ("rho", ctypes.c_double), ("f", ctypes.c_double * 3), ("wall_u", ctypes.c_double * 18)]
+                ("theta", ctypes.c_double), ("periodic", ctypes.c_int32 * 3), ("rho", ctypes.c_double), ("f", ctypes.c_double * 3), ("wall_u", ctypes.c_double * 18)]
 
     def as_dict(self):
         out = {}
@@ -150,6 +150,7 @@ SIGNATURES = {
     "hbf_run_cessation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
                                          ctypes.POINTER(RunInfo)]),
     "hbf_set_theta": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "hbf_set_periodic": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "hbf_centreline": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "hbf_vortex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]),
@@ -310,6 +311,10 @@ class HBFlow:
 
     def set_theta(self, theta):
         self._check(self.lib.hbf_set_theta(self.ctx, float(theta)))
+
+    def set_periodic(self, periodic):
+        per = (ctypes.c_int * 3)(*([int(bool(v)) for v in periodic] + [0] * (3 - len(periodic))))
+        self._check(self.lib.hbf_set_periodic(self.ctx, per))
 
     def set_predictor_viscous(self, on):
         self._check(self.lib.hbf_set_predictor_viscous(self.ctx, int(bool(on))))
