@@ -587,11 +587,28 @@ __global__ void k_visc_bottom(T* __restrict__ u, const T* __restrict__ b, const 
 // ---------------------------------------------------------------------------
 // cell-centred Poisson (MAC potential), Neumann walls
 // ---------------------------------------------------------------------------
+// Cell p and its 2D face neighbours lie inside the domain: no wall is
+// skipped and no periodic wrap is needed.
+template <int D>
+__host__ __device__ inline bool cell_inner(const Geom& g, const int* p) {
+  bool in = p[0] >= 1 && p[0] < g.n[0] - 1 && p[1] >= 1 && p[1] < g.n[1] - 1;
+  if (D == 3) in = in && p[2] >= 1 && p[2] < g.n[2] - 1;
+  return in;
+}
+
 template <int D, typename T>
 __host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __restrict__ b, const Geom& g,
                                   const int* p) {
   T s = T(0);
   int cnt = 0;
+  const int id = cidx<D>(g, p[0], p[1], p[2]);
+  if (cell_inner<D>(g, p)) {
+    // direct offsets, the same terms in the same order as the general path
+    const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+#pragma unroll
+    for (int a = 0; a < D; ++a) s += x[id - st[a]] + x[id + st[a]];
+    return (s - g_hh<T>(g) * b[id]) / T(2 * D);
+  }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T lo = T(0), hi = T(0);
@@ -638,6 +655,18 @@ __host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x
     cell_coords<D>(g, t, p[0], p[1], p[2]);
     T xc = x[t];
     T acc = T(0);
+    if (cell_inner<D>(g, p)) {
+      // direct offsets, the same terms in the same order as the general path
+      const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const T glo = (xc - x[t - st[a]]) * ih;
+        const T ghi = (x[t + st[a]] - xc) * ih;
+        acc += (ghi - glo) * ih;
+      }
+      r[t] = b[t] - acc;
+      return;
+    }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       T glo = T(0), ghi = T(0);
@@ -689,10 +718,43 @@ __host__ __device__ inline T fe_weight(int nz) {
   return nz == 1 ? T(0) : (nz == 2 ? T(1.0 / 6.0) : T(1.0 / 12.0));
 }
 
+// Node p and its whole 3^D neighbourhood lie in [0, n] on every axis, so no
+// stencil point needs a reflection or a periodic wrap.
+template <int D>
+__host__ __device__ inline bool node_inner(const Geom& g, const int* p) {
+  bool in = p[0] >= 1 && p[0] < g.n[0] && p[1] >= 1 && p[1] < g.n[1];
+  if (D == 3) in = in && p[2] >= 1 && p[2] < g.n[2];
+  return in;
+}
+
 template <int D, typename T>
 __host__ __device__ inline T nodal_lap_point(const T* __restrict__ x, const Geom& g, const int* p, bool skip_centre) {
   T s = T(0);
   const int K = D == 3 ? 27 : 9;
+  if (node_inner<D>(g, p)) {
+    // direct offsets, the same terms in the same order as the general path
+    const int sy = g.n[0] + 1, sz = (g.n[0] + 1) * (g.n[1] + 1);
+    const int id = nidx(g, p[0], p[1], p[2]);
+#pragma unroll
+    for (int o = 0; o < K; ++o) {
+      int oo[3];
+      if (D == 3) {
+        oo[0] = o / 9 - 1;
+        oo[1] = (o / 3) % 3 - 1;
+        oo[2] = o % 3 - 1;
+      } else {
+        oo[0] = o / 3 - 1;
+        oo[1] = o % 3 - 1;
+        oo[2] = 0;
+      }
+      int nz = (oo[0] != 0) + (oo[1] != 0) + (oo[2] != 0);
+      if (nz == 0 && skip_centre) continue;
+      if (D == 3 && nz == 1) continue;
+      T w = fe_weight<D, T>(nz);
+      s += w * x[id + oo[0] + oo[1] * sy + oo[2] * sz];
+    }
+    return s;
+  }
 #pragma unroll
   for (int o = 0; o < K; ++o) {
     int oo[3];
