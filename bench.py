@@ -93,6 +93,9 @@ def parse():
                     help="steps from rest (mixed method, untimed) before the warm-up; develop + warm-up = 100 "
                          "with the default warm-up, the paper's protocol")
     ap.add_argument("--prof-steps", type=int, default=5, help="steps of the instrumented pass")
+    ap.add_argument("--staged-sweep", default="0",
+                    help="TMA-staged finest-level viscous sweeps: 'TX,TZ' (tile width 64 or 128, planes per block) "
+                         "or 0 (hbf_set_staged_sweep)")
     ap.add_argument("--fused-sweeps", action="store_true",
                     help="smooth the 3D FP32 finest level with the one-launch red-black sweep (hbf_set_fused_sweep)")
     ap.add_argument("--breakdown", action="store_true",
@@ -406,6 +409,8 @@ def run_ours(args):
     sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
     sim.set_solver(rtol=1e-10, max_cycles=200)
     sim.set_fused_sweep(args.fused_sweeps)
+    staged = [int(v) for v in str(args.staged_sweep).split(",")] if args.staged_sweep != "0" else [0, 16]
+    sim.set_staged_sweep(staged[0], staged[1] if len(staged) > 1 else 16)
     zeros_u = np.zeros(d * ncell)
     zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
     sim.set_field("U", zeros_u)
@@ -611,6 +616,9 @@ def run_ours(args):
                        "precision": args.precision + ("+learned" if learned else ""),
                        "rtol": 1e-10, "dt": dt, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "no flush: every field (>= 134 MB) exceeds the 129 MB L2",
+                       "viscous_sweeps": ("one-launch fused" if args.fused_sweeps else
+                                          f"TMA-staged {staged[0]}x8 tiles, {staged[1]} planes per block"
+                                          if staged[0] else "two launches per component, unstaged"),
                        "cycles_per_step": {k: v / args.steps for k, v in cycles.items()},
                        "converged": bool(converged)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -156,6 +156,19 @@ int hbf_set_tail(hbf_ctx* ctx, int max_cells);
  * of 36 bytes per cell but measured slower on GB300 (370 against 2 x 110 us
  * per 256^3 component sweep). */
 int hbf_set_fused_sweep(hbf_ctx* ctx, int on);
+/* The same two-launch red-black sweeps of the 3D FP32 finest level with their
+ * operands staged in shared memory by the tensor memory accelerator: each
+ * block owns a tile_x x 8-cell tile of a plane (tile_x 64 or 128) and streams
+ * tile_z planes in z through a ring of shared-memory stages, so that the
+ * loads of the next planes are in flight while the block updates the current
+ * one.  Every interior cell's update is the same arithmetic on the same
+ * values as in the unstaged sweeps (bit for bit).  Taken when the level has
+ * walls on every axis and n[0] % 4 == 0 (the staged rows must start on
+ * 16-byte boundaries); otherwise the unstaged sweeps run.  tile_x = 0
+ * disables it (default).  A block whose bounded wait for its loads gives up
+ * stops updating and the viscous solve returns HBF_ERR_TIMEOUT.
+ * HBF_ERR_ARG for another width or tile_z outside [1, 4096]. */
+int hbf_set_staged_sweep(hbf_ctx* ctx, int tile_x, int tile_z);
 
 /* Number of doubles of a field (see enum hbf_field), or a negative status. */
 int64_t hbf_field_size(const hbf_ctx* ctx, int which);

@@ -130,6 +130,7 @@ static int allocate(hbf_ctx* c) {
   A(c->dA, (long long)(kDenseMax + 1) * 2 * (kDenseMax + 1));
   A(c->partial, kRedBlocks);
   A(c->dres, 8);
+  A(c->sweep_err, 1);
   if (cudaMallocHost((void**)&c->hres, 8 * sizeof(double)) != cudaSuccess)
     return fail(c, HBF_ERR_OOM, "cudaMallocHost");
   // multigrid hierarchy
@@ -455,6 +456,15 @@ int hbf_restrict(hbf_ctx* c, int kind, int level, const double* src, double* dst
 int hbf_set_fused_sweep(hbf_ctx* c, int on) {
   if (!c) return HBF_ERR_ARG;
   c->fused_sweep = on ? 1 : 0;
+  return HBF_OK;
+}
+
+int hbf_set_staged_sweep(hbf_ctx* c, int tile_x, int tile_z) {
+  if (!c) return HBF_ERR_ARG;
+  if ((tile_x != 0 && tile_x != 64 && tile_x != 128) || tile_z < 1 || tile_z > 4096)
+    return fail(c, HBF_ERR_ARG, "staged sweep tile: width 0, 64 or 128, 1 <= planes <= 4096");
+  c->staged_tx = tile_x;
+  c->staged_tz = tile_z;
   return HBF_OK;
 }
 

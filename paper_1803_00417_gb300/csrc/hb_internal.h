@@ -99,6 +99,9 @@ struct hbf_ctx {
   double f[3] = {0, 0, 0};
   int predictor_visc = 0;
   int fused_sweep = 0;      // FP32 finest-level viscous sweeps in one launch per component (3D)
+  int staged_tx = 0;        // FP32 finest-level viscous sweeps staged by TMA: tile width 64 or 128, 0 off (3D)
+  int staged_tz = 16;       // planes per block of the staged sweeps
+  int* sweep_err = nullptr; // set by a staged sweep whose bounded wait gave up
   double K = 1.0;           // the consistency K as given to hbf_set_rheology
   double theta = 0.5;       // implicit weight of the viscous term (1/2: Crank-Nicolson, Eq. 15)
   double t = 0.0;           // time: the sum of the dt of every step taken

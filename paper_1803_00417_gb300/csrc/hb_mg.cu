@@ -19,6 +19,9 @@
 #include "hb_mg_kernels.cuh"
 #include "hb_vcycle_tail.cuh"
 #include "hb_visc_fused.cuh"
+#include "hb_visc_tma.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace hb {
 
@@ -728,6 +731,7 @@ struct ViscProblem : Problem<T> {
     const dim3 blk(kThreads, 1, 1);
     const dim3 grd((unsigned)grid_for(rbx_count<D>(L.g), 152 * 24), 1, 1);
     const int hm = (int)this->hom(l);
+    if (cell_eta(l) && staged_sweeps(l, hm)) return;
     if (cell_eta(l)) {
       // FP32 finest level: face viscosities from the cell viscosity
       const T* e0 = (const T*)L.feta;
@@ -757,6 +761,11 @@ struct ViscProblem : Problem<T> {
   }
   // the FP32 finest level forms its face viscosities from the cell viscosity
   bool cell_eta(int l) const { return l == 0 && sizeof(T) == 4 && c->lv[0].feta != nullptr; }
+  // 3D FP32 finest level with walls on every axis: the sweeps of k_visc_smooth_c
+  // with the planes staged in shared memory by TMA (hb_visc_tma.cuh); false
+  // (nothing launched) when the staged sweep is off or the level does not
+  // meet its layout rules
+  bool staged_sweeps(int l, int hm);
   // 3D FP32 finest level: each component's red-black sweep in one launch
   // (hb_visc_fused.cuh), alternating between x and the level's second array
   void smooth_n(int l, int count) override {
@@ -806,6 +815,94 @@ struct ViscProblem : Problem<T> {
     bottom_fp64<D, T>(*this, l, xd, bd, &run_bottom);
   }
 };
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point, so that
+// the library links against the runtime only
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Tiled FP32 map of a cell array of level geometry g: rank 3 (n0, n1, n2), or
+// rank 4 with ncomp component arrays of ncell cells each.  Box bx x by x 1
+// (x bc components); coordinates outside the grid read zeros.  Needs
+// n0 % 4 == 0 (row strides in multiples of 16 bytes) and a 16-byte aligned
+// base.
+static bool encode_cells(CUtensorMap* m, const void* base, const Geom& g, int ncomp, int bx, int by, int bc) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)base & 15) || g.n[0] % 4) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], (cuuint64_t)ncomp};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.n[0] * 4, (cuuint64_t)g.n[0] * g.n[1] * 4, (cuuint64_t)g.ncell * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)bc};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ncomp > 0 ? 4 : 3, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// One colour sweep of every component, staged: tile TX x TY, ring of NS stages
+template <int TX, int TY, int NS>
+static bool staged_launches(hbf_ctx* c, int slot, float* u, const float* b, const float* eta, const Geom& g, float beta,
+                            int hm, int tz) {
+  using Lay = tma::Layout<TX, TY>;
+  CUtensorMap mu, me, mb;
+  if (!encode_cells(&mu, u, g, 3, Lay::PX, Lay::PY, 3) || !encode_cells(&me, eta, g, 0, Lay::PX, Lay::PY, 1) ||
+      !encode_cells(&mb, b, g, 3, TX, TY, 1))
+    return false;
+  void (*kern[3])(const CUtensorMap, const CUtensorMap, const CUtensorMap, float*, const float*, const float*,
+                  const Geom, const tma::SweepGrid, int, float, int, int*) = {
+      tma::k_visc_smooth_tma<0, TX, TY, NS>, tma::k_visc_smooth_tma<1, TX, TY, NS>,
+      tma::k_visc_smooth_tma<2, TX, TY, NS>};
+  static std::atomic<bool> attr{false};
+  const int smem = Lay::smem(NS);
+  if (!attr.load()) {
+    for (auto k : kern)
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
+    attr.store(true);
+  }
+  const tma::SweepGrid sg = tma::sweep_grid<TX, TY>(g, tz);
+  const dim3 grd((unsigned)sg.blocks(), 1, 1), blk(tma::kThreads, 1, 1);
+  for (int q = 0; q < 3; ++q)
+    for (int col = 0; col < 2; ++col)
+      launch_smem(c, slot, kern[q], grd, blk, (size_t)smem, mu, me, mb, u, b, eta, g, sg, col, beta, hm,
+                  c->sweep_err);
+  return true;
+}
+
+template <int D, typename T>
+bool ViscProblem<D, T>::staged_sweeps(int l, int hm) {
+  if constexpr (D == 3 && std::is_same<T, float>::value) {
+    const Geom& g = c->lv[l].g;
+    if (c->staged_tx == 0 || g.per[0] || g.per[1] || g.per[2] || !c->sweep_err) return false;
+    float* u = x(l);
+    const float* bb = b(l);
+    const float* e = c->lv[l].feta;
+    const int tz = c->staged_tz;
+    if (c->staged_tx == 64) return staged_launches<64, 8, 6>(c, kSlotViscSmooth, u, bb, e, g, (float)beta, hm, tz);
+    return staged_launches<128, 8, 4>(c, kSlotViscSmooth, u, bb, e, g, (float)beta, hm, tz);
+  }
+  (void)l;
+  (void)hm;
+  return false;
+}
+
+static int take_sweep_err(hbf_ctx* c) {
+  if (!c->sweep_err || c->staged_tx == 0) return HBF_OK;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->sweep_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "reading the sweep status");
+  if (!h) return HBF_OK;
+  cudaMemsetAsync(c->sweep_err, 0, sizeof(int), c->stream);
+  return fail(c, HBF_ERR_TIMEOUT, "a staged viscous sweep gave up waiting for its loads");
+}
 
 template <int D, typename T>
 void ViscProblem<D, T>::fused_sweeps(int l, int count) {
@@ -1347,7 +1444,9 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
 int solve_viscous(hbf_ctx* c, double beta, const double* rhs, double* u, hbf_solve_stats* s) {
   int st = launch_eta_faces(c);
   if (st) return st;
-  return c->dim == 2 ? solve_viscous_d<2>(c, beta, rhs, u, s) : solve_viscous_d<3>(c, beta, rhs, u, s);
+  st = c->dim == 2 ? solve_viscous_d<2>(c, beta, rhs, u, s) : solve_viscous_d<3>(c, beta, rhs, u, s);
+  const int se = take_sweep_err(c);
+  return st ? st : se;
 }
 
 template <int D>

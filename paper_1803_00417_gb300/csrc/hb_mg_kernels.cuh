@@ -11,6 +11,7 @@
 //    full weighting / multilinear interpolation on nodes, coarse face eta as
 //    the mean of the fine faces tiling each coarse face
 #pragma once
+#include <cmath>
 #include "hb_common.cuh"
 
 namespace hb {
@@ -130,6 +131,67 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& 
   return acc;
 }
 
+// Explicitly rounded operations (round to nearest): the compiler may not
+// contract or reorder them, so every kernel that inlines the Gauss-Seidel
+// point updates below (visc_gs_point, visc_gs_core) issues the same
+// operations in the same order and gets the same bits.  On the host (the
+// host-built checks) they are the plain operations and an exact fused
+// multiply-add.
+template <typename T>
+__host__ __device__ __forceinline__ T rn_mul(T a, T b);
+template <typename T>
+__host__ __device__ __forceinline__ T rn_add(T a, T b);
+template <typename T>
+__host__ __device__ __forceinline__ T rn_fma(T a, T b, T c);
+template <>
+__host__ __device__ __forceinline__ float rn_mul<float>(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ double rn_mul<double>(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ float rn_add<float>(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ double rn_add<double>(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ float rn_fma<float>(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ double rn_fma<double>(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+  return __fma_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+
 // Gauss-Seidel update of component c at cell p (all other values frozen)
 template <int D, typename T, typename EF>
 __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const EF& ef,
@@ -155,12 +217,12 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
       bool wall = !g.per[a] && ((s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1));
       if (wall) {
         T ub = hom ? T(0) : g_wu<T>(g, a, s, c);
-        offd += T(2) * wf * ub;
-        diag += T(2) * wf;
+        offd = rn_fma(rn_mul(T(2), wf), ub, offd);
+        diag = rn_fma(T(2), wf, diag);
       } else {
         if (g.per[a]) q[a] = wrap_cell(q[a], g.n[a]);
-        offd += wf * uc[cidx<D>(g, q[0], q[1], q[2])];
-        diag += wf;
+        offd = rn_fma(wf, uc[cidx<D>(g, q[0], q[1], q[2])], offd);
+        diag = rn_add(diag, wf);
       }
     }
   }
@@ -173,12 +235,13 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
     Llo[a] -= 1;
     int fhi[3] = {p[0], p[1], p[2]};
     fhi[a] += 1;
-    T fluxhi = ef.at(g, a, fhi) * mg_face_cross<D, T>(ua, g, a, c, p, hom);
-    T fluxlo = ef.at(g, a, p) * mg_face_cross<D, T>(ua, g, a, c, Llo, hom);
-    cross += (fluxhi - fluxlo) * ih;
+    T fluxhi = rn_mul(ef.at(g, a, fhi), mg_face_cross<D, T>(ua, g, a, c, p, hom));
+    T fluxlo = rn_mul(ef.at(g, a, p), mg_face_cross<D, T>(ua, g, a, c, Llo, hom));
+    cross = rn_fma(rn_add(fluxhi, -fluxlo), ih, cross);
   }
-  return (b[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])] + beta * (offd + cross)) /
-         (T(1) + beta * diag);
+  // explicitly rounded (see rn_fma): the same result wherever it is inlined
+  return rn_fma(beta, rn_add(offd, cross), b[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])]) /
+         rn_fma(beta, diag, T(1));
 }
 
 // Strides of the cell array and of the face arrays (face array a, axis b).
@@ -232,6 +295,43 @@ __host__ __device__ inline bool interior(const Geom& g, const int* p) {
   return in;
 }
 
+// The arithmetic of the interior Gauss-Seidel update of component c on
+// gathered values: elo / ehi the face viscosities below / above the cell on
+// each axis (up to the accessor's factor, which is folded into bs with
+// beta / h^2), ulo / uhi u_c at the two face neighbours on each axis, bc the
+// right-hand side, and for each axis a != c the six values of u_a that the
+// cross term reads, xa[a] = {u_a(p + e_c), u_a(p - e_c), u_a(p + e_a + e_c),
+// u_a(p + e_a - e_c), u_a(p - e_a + e_c), u_a(p - e_a - e_c)}.  The update is
+//   (bc + bs (offd + cross / 4)) / (1 + bs diag),
+//   offd = sum_a k_a (elo_a u_lo,a + ehi_a u_hi,a), diag = sum_a k_a (elo_a + ehi_a),
+//   cross = sum_{a != c} (ehi_a xhi_a - elo_a xlo_a), k_c = 2, k_a = 1 otherwise,
+// in explicitly rounded operations: every caller that gathers the same
+// values gets the same result bit for bit.
+template <int D, typename T>
+__host__ __device__ __forceinline__ T visc_gs_core(int c, const T* elo, const T* ehi, const T* ulo, const T* uhi,
+                                                   const T (*xa)[6], T bc, T bs) {
+  T offd = T(0), diag = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const T f = rn_fma(elo[a], ulo[a], rn_mul(ehi[a], uhi[a]));
+    const T w = rn_add(elo[a], ehi[a]);
+    offd = a == c ? rn_fma(T(2), f, offd) : rn_add(offd, f);
+    diag = a == c ? rn_fma(T(2), w, diag) : rn_add(diag, w);
+  }
+  T cross = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (a == c) continue;
+    const T mid = rn_add(xa[a][0], -xa[a][1]);
+    const T xhi = rn_add(mid, rn_add(xa[a][2], -xa[a][3]));
+    const T xlo = rn_add(rn_add(xa[a][4], -xa[a][5]), mid);
+    cross = rn_add(cross, rn_fma(ehi[a], xhi, -rn_mul(elo[a], xlo)));
+  }
+  const T num = rn_fma(bs, rn_fma(T(0.25), cross, offd), bc);
+  const T den = rn_fma(bs, diag, T(1));
+  return num / den;
+}
+
 // The same Gauss-Seidel update as visc_gs_point for a cell whose whole
 // stencil is inside the domain: direct strided indexing, no ghost logic.
 template <int D, typename T, typename EF>
@@ -242,31 +342,27 @@ __host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, 
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
   const T bs = beta * (g_ihh<T>(g) * T(EF::kScale));
-  T elo[3], ehi[3];
+  T elo[3], ehi[3], ulo[3], uhi[3], xa[3][6];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     elo[a] = ef.lo(g, S, a, p, id);
     ehi[a] = ef.hi(g, S, a, p, id);
+    ulo[a] = uc[id - S.s[a]];
+    uhi[a] = uc[id + S.s[a]];
   }
-  T offd = T(0), diag = T(0);
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const T kappa = (a == c) ? T(2) : T(1);
-    offd += kappa * (elo[a] * uc[id - S.s[a]] + ehi[a] * uc[id + S.s[a]]);
-    diag += kappa * (elo[a] + ehi[a]);
-  }
-  T cross = T(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     if (a == c) continue;
     const T* ua = u + (size_t)a * g.ncell;
     const int sa = S.s[a], sc = S.s[c];
-    const T mid = ua[id + sc] - ua[id - sc];
-    const T xhi = mid + (ua[id + sa + sc] - ua[id + sa - sc]);
-    const T xlo = (ua[id - sa + sc] - ua[id - sa - sc]) + mid;
-    cross += ehi[a] * xhi - elo[a] * xlo;
+    xa[a][0] = ua[id + sc];
+    xa[a][1] = ua[id - sc];
+    xa[a][2] = ua[id + sa + sc];
+    xa[a][3] = ua[id + sa - sc];
+    xa[a][4] = ua[id - sa + sc];
+    xa[a][5] = ua[id - sa - sc];
   }
-  return (b[(size_t)c * g.ncell + id] + bs * (offd + T(0.25) * cross)) / (T(1) + bs * diag);
+  return visc_gs_core<D, T>(c, elo, ehi, ulo, uhi, xa, b[(size_t)c * g.ncell + id], bs);
 }
 
 // (L_eta u)_c for an interior cell: the operator of mg_tensor_point with the
