@@ -128,7 +128,7 @@ static int allocate(hbf_ctx* c) {
   A(c->dX, (long long)kDenseMax * kDenseMax);
   A(c->dM, (long long)(kDenseMax + 1) * (kDenseMax + 1));
   A(c->dA, (long long)(kDenseMax + 1) * 2 * (kDenseMax + 1));
-  A(c->partial, kRedBlocks);
+  A(c->partial, 2 * kRedBlocks);  // two-result reductions use both halves
   A(c->dres, 8);
   A(c->sweep_err, 1);
   if (cudaMallocHost((void**)&c->hres, 8 * sizeof(double)) != cudaSuccess)

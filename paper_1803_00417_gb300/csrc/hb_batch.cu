@@ -51,25 +51,25 @@ struct OpTensorLu {
 template <int D, typename T>
 struct OpCellSmooth {
   using Arg = PoisArg<T>;
-  static __device__ void apply(const Arg& a, int t, int col) { k_cell_smooth_at<D, T>(a.x, a.b, a.g, col, t); }
+  static __device__ void apply(const Arg& a, int t, int col) { k_cell_smooth_at<D, T, false>(a.x, a.b, a.g, col, t); }
 };
 
 template <int D, typename T>
 struct OpCellResid {
   using Arg = PoisArg<T>;
-  static __device__ void apply(const Arg& a, int t, int) { k_cell_resid_at<D, T>(a.x, a.b, a.r, a.g, t); }
+  static __device__ void apply(const Arg& a, int t, int) { k_cell_resid_at<D, T, false>(a.x, a.b, a.r, a.g, t); }
 };
 
 template <int D, typename T>
 struct OpNodalSmooth {
   using Arg = PoisArg<T>;
-  static __device__ void apply(const Arg& a, int t, int col) { k_nodal_smooth_at<D, T>(a.x, a.b, a.g, col, t); }
+  static __device__ void apply(const Arg& a, int t, int col) { k_nodal_smooth_at<D, T, false>(a.x, a.b, a.g, col, t); }
 };
 
 template <int D, typename T>
 struct OpNodalResid {
   using Arg = PoisArg<T>;
-  static __device__ void apply(const Arg& a, int t, int) { k_nodal_resid_at<D, T>(a.x, a.b, a.r, a.g, t); }
+  static __device__ void apply(const Arg& a, int t, int) { k_nodal_resid_at<D, T, false>(a.x, a.b, a.r, a.g, t); }
 };
 
 template <int D, typename T>
@@ -85,7 +85,7 @@ template <int D, typename T>
 struct OpProlongCells {
   using Arg = XferArg<T>;
   static __device__ void apply(const Arg& a, int t, int) {
-    k_prolong_cells_add_at<D, T>(a.dst, a.src, a.gf, a.gc, a.ncomp, T(a.sign), t);
+    k_prolong_cells_add_at<D, T, false>(a.dst, a.src, a.gf, a.gc, a.ncomp, T(a.sign), t);
   }
 };
 
@@ -93,7 +93,7 @@ template <int D, typename T>
 struct OpRestrictNodes {
   using Arg = XferArg<T>;
   static __device__ void apply(const Arg& a, int t, int) {
-    k_restrict_nodes_at<D, T>(a.src, a.dst, a.gf, a.gc, t);
+    k_restrict_nodes_at<D, T, false>(a.src, a.dst, a.gf, a.gc, t);
     a.zero[t] = T(0);
   }
 };

@@ -245,11 +245,14 @@ __host__ __device__ inline T nget(const T* __restrict__ x, const Geom& g, int i,
 
 // Node value with even reflection across walls (node -1 -> 1, n+1 -> n-1),
 // wrapped on periodic axes (node -1 -> n-1, n+1 -> 1).
-template <int D, typename T>
+// PER = false compiles the wraps out (a level with walls on every axis).
+template <int D, typename T, bool PER = true>
 __host__ __device__ inline T ndget(const T* __restrict__ x, const Geom& g, int i, int j, int k) {
-  if (g.per[0]) i = wrap_node(i, g.n[0]);
-  if (g.per[1]) j = wrap_node(j, g.n[1]);
-  if (D == 3 && g.per[2]) k = wrap_node(k, g.n[2]);
+  if (PER) {
+    if (g.per[0]) i = wrap_node(i, g.n[0]);
+    if (g.per[1]) j = wrap_node(j, g.n[1]);
+    if (D == 3 && g.per[2]) k = wrap_node(k, g.n[2]);
+  }
   i = i < 0 ? -i : (i > g.n[0] ? 2 * g.n[0] - i : i);
   j = j < 0 ? -j : (j > g.n[1] ? 2 * g.n[1] - j : j);
   if (D == 3) k = k < 0 ? -k : (k > g.n[2] ? 2 * g.n[2] - k : k);

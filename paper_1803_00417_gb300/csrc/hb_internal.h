@@ -160,7 +160,7 @@ struct hbf_ctx {
   float *fkr = nullptr, *fkrh = nullptr, *fkp = nullptr, *fkv = nullptr, *fks = nullptr, *fkt = nullptr,
         *fkph = nullptr, *fksh = nullptr, *fke = nullptr;
   // reductions
-  double* partial = nullptr;  // kRedBlocks doubles
+  double* partial = nullptr;  // 2 kRedBlocks doubles
   double* dres = nullptr;     // device result slot(s)
   double* hres = nullptr;     // pinned host result
   std::vector<hb::Level> lv;

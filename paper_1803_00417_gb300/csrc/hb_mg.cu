@@ -191,6 +191,10 @@ __global__ void k_dot_partial_v(const double* __restrict__ a, const double* __re
 
 static inline bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
+// a periodic axis: the Poisson and transfer kernels take their PER = true
+// form (with the wraps); walls on every axis take PER = false
+static inline bool any_per(const Geom& g) { return g.per[0] || g.per[1] || g.per[2]; }
+
 template <int MODE>
 static int reduce_to_device(hbf_ctx* c, const double* x, long long n, double* out) {
   if (MODE < 2 && aligned16(x))
@@ -418,7 +422,42 @@ __global__ void k_maxabs_partial_f(const float* __restrict__ x, long long n, dou
 
 // the FP32 partials with 16-byte loads: products summed in FP32 over runs of
 // kDotRun elements (kDotRun / 4 vectors), the runs in FP64; same order rules
-// as k_reduce_partial_v
+// as k_reduce_partial_v.  A thread takes its vectors q0, q0 + T, ... one run
+// at a time (nested loops, so that a run's loads are issued together); a run
+// is added to the FP64 sum once it holds kDotRun / 4 vectors, and the last,
+// shorter one (with thread 0's tail past the last whole vector) at the end.
+constexpr int kRunVec = kDotRun / 4;
+
+// acc, run: the thread's FP64 sum of finished runs and its open FP32 run;
+// term(q, run) adds vector q's products to run
+template <typename F>
+__device__ __forceinline__ void dot_runs(long long tid, long long T, long long n4, double& acc, float& run, F term) {
+  for (long long q0 = tid; q0 < n4; q0 += (long long)kRunVec * T) {
+#pragma unroll 4
+    for (int k = 0; k < kRunVec; ++k) {
+      const long long q = q0 + (long long)k * T;
+      if (q < n4) run = term(q, run);
+    }
+    if (q0 + (long long)(kRunVec - 1) * T < n4) {
+      acc += (double)run;
+      run = 0.f;
+    }
+  }
+}
+
+__device__ __forceinline__ float dot4(const float4& x, const float4& y, float run) {
+  run = fmaf(x.x, y.x, run);
+  run = fmaf(x.y, y.y, run);
+  run = fmaf(x.z, y.z, run);
+  return fmaf(x.w, y.w, run);
+}
+
+__device__ __forceinline__ void max_abs(float& m, float v) {
+  float a = fabsf(v);
+  if (!isfinite(a)) a = INFINITY;
+  m = fmaxf(m, a);
+}
+
 __global__ void k_dot_partial_f4(const float* __restrict__ a, const float* __restrict__ b, long long n,
                                  double* __restrict__ part) {
   const long long T = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -427,24 +466,87 @@ __global__ void k_dot_partial_f4(const float* __restrict__ a, const float* __res
   const float4* b4 = reinterpret_cast<const float4*>(b);
   double acc = 0.0;
   float run = 0.f;
-  int k = 0;
-#pragma unroll 4
-  for (long long q = tid; q < n4; q += T) {
-    const float4 x = a4[q], y = b4[q];
-    run = fmaf(x.x, y.x, run);
-    run = fmaf(x.y, y.y, run);
-    run = fmaf(x.z, y.z, run);
-    run = fmaf(x.w, y.w, run);
-    if (++k == kDotRun / 4) {
-      acc += (double)run;
-      run = 0.f;
-      k = 0;
-    }
-  }
+  dot_runs(tid, T, n4, acc, run, [&](long long q, float r) { return dot4(a4[q], b4[q], r); });
   if (tid == 0)
     for (long long e = n4 << 2; e < n; ++e) run = fmaf(a[e], b[e], run);
   acc += (double)run;
   block_partial<1>(acc, part);
+}
+
+// x.x and x.y in one pass over x (BiCGStab's t.t and t.s): partials of the
+// first in part[0, gridDim), of the second in part[gridDim, 2 gridDim)
+__global__ void k_dot2_partial_f4(const float* __restrict__ x, const float* __restrict__ y, long long n,
+                                  double* __restrict__ part) {
+  const long long T = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n4 = n >> 2;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  double axx = 0.0, axy = 0.0;
+  float rxx = 0.f, rxy = 0.f;
+  for (long long q0 = tid; q0 < n4; q0 += (long long)kRunVec * T) {
+#pragma unroll 4
+    for (int k = 0; k < kRunVec; ++k) {
+      const long long q = q0 + (long long)k * T;
+      if (q < n4) {
+        const float4 u = x4[q], v = y4[q];
+        rxx = dot4(u, u, rxx);
+        rxy = dot4(u, v, rxy);
+      }
+    }
+    if (q0 + (long long)(kRunVec - 1) * T < n4) {
+      axx += (double)rxx;
+      axy += (double)rxy;
+      rxx = rxy = 0.f;
+    }
+  }
+  if (tid == 0)
+    for (long long e = n4 << 2; e < n; ++e) {
+      rxx = fmaf(x[e], x[e], rxx);
+      rxy = fmaf(x[e], y[e], rxy);
+    }
+  block_partial<1>(axx + (double)rxx, part);
+  __syncthreads();
+  block_partial<1>(axy + (double)rxy, part + gridDim.x);
+}
+
+// out = x - a y (BiCGStab's r = s - omega t) with max |out| (non-finite ->
+// +inf) and w.out (the next iteration's r^.r) in the same pass: partials of
+// the max in part[0, gridDim), of the dot in part[gridDim, 2 gridDim)
+__global__ void k_axmy_red_f4(float* __restrict__ out, const float* __restrict__ x, float a,
+                              const float* __restrict__ y, const float* __restrict__ w, long long n,
+                              double* __restrict__ part) {
+  const long long T = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n4 = n >> 2;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  float4* o4 = reinterpret_cast<float4*>(out);
+  double acc = 0.0;
+  float run = 0.f, m = 0.f;
+  dot_runs(tid, T, n4, acc, run, [&](long long q, float r) {
+    const float4 u = x4[q], v = y4[q];
+    float4 o;
+    o.x = u.x - a * v.x;
+    o.y = u.y - a * v.y;
+    o.z = u.z - a * v.z;
+    o.w = u.w - a * v.w;
+    o4[q] = o;
+    max_abs(m, o.x);
+    max_abs(m, o.y);
+    max_abs(m, o.z);
+    max_abs(m, o.w);
+    return dot4(w4[q], o, r);
+  });
+  if (tid == 0)
+    for (long long e = n4 << 2; e < n; ++e) {
+      const float o = x[e] - a * y[e];
+      out[e] = o;
+      max_abs(m, o);
+      run = fmaf(w[e], o, run);
+    }
+  block_partial<0>((double)m, part);
+  __syncthreads();
+  block_partial<1>(acc + (double)run, part + gridDim.x);
 }
 
 __global__ void k_maxabs_partial_f4(const float* __restrict__ x, long long n, double* __restrict__ part) {
@@ -452,22 +554,43 @@ __global__ void k_maxabs_partial_f4(const float* __restrict__ x, long long n, do
   const long long n4 = n >> 2;
   const float4* x4 = reinterpret_cast<const float4*>(x);
   float m = 0.f;
-  auto upd = [&](float v) {
-    float a = fabsf(v);
-    if (!isfinite(a)) a = INFINITY;
-    m = fmaxf(m, a);
-  };
 #pragma unroll 4
   for (long long q = tid; q < n4; q += T) {
     const float4 v = x4[q];
-    upd(v.x);
-    upd(v.y);
-    upd(v.z);
-    upd(v.w);
+    max_abs(m, v.x);
+    max_abs(m, v.y);
+    max_abs(m, v.z);
+    max_abs(m, v.w);
   }
   if (tid == 0)
-    for (long long e = n4 << 2; e < n; ++e) upd(x[e]);
+    for (long long e = n4 << 2; e < n; ++e) max_abs(m, x[e]);
   block_partial<0>((double)m, part);
+}
+
+// the two finals of a two-result partial kernel: block 0 reduces
+// part[0, nb) with MODE0 into out[0], block 1 part[nb, 2 nb) with MODE1 into
+// out[1]
+template <int MODE0, int MODE1>
+__global__ void k_reduce_final2(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int mode = blockIdx.x == 0 ? MODE0 : MODE1;
+  const double* p = part + (size_t)blockIdx.x * nb;
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) acc = mode == 0 ? fmax(acc, p[t]) : acc + p[t];
+  for (int off = 16; off > 0; off >>= 1) {
+    double o = __shfl_xor_sync(0xffffffffu, acc, off);
+    acc = mode == 0 ? fmax(acc, o) : acc + o;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (int)(blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) {
+      double o = __shfl_xor_sync(0xffffffffu, v, off);
+      v = mode == 0 ? fmax(v, o) : v + o;
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+  }
 }
 
 static double reduce_dot_f(hbf_ctx* c, const float* a, const float* b, long long n, int* st) {
@@ -479,6 +602,31 @@ static double reduce_dot_f(hbf_ctx* c, const float* a, const float* b, long long
   *st = cuda_check(c, cudaGetLastError(), "dot");
   if (*st) return NAN;
   return read_result(c, c->dres, st);
+}
+
+// both results of a two-result partial kernel (out[0], out[1]), one read
+static int read_results2(hbf_ctx* c, double* r0, double* r1) {
+  launch(c, kSlotReduce, k_reduce_final2<0, 1>, 2, 1024, (const double*)c->partial, kRedBlocks, c->dres);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->hres, c->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "reading a reduction");
+  *r0 = c->hres[0];
+  *r1 = c->hres[1];
+  return HBF_OK;
+}
+
+// (x.x, x.y) in one pass; sum-sum finals
+static int reduce_dot2_f(hbf_ctx* c, const float* x, const float* y, long long n, double* xx, double* xy) {
+  launch(c, kSlotReduce, k_dot2_partial_f4, kRedBlocks, kThreads, x, y, n, c->partial);
+  launch(c, kSlotReduce, k_reduce_final2<1, 1>, 2, 1024, (const double*)c->partial, kRedBlocks, c->dres);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->hres, c->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "reading a reduction");
+  *xx = c->hres[0];
+  *xy = c->hres[1];
+  return HBF_OK;
 }
 
 static double reduce_max_abs_f(hbf_ctx* c, const float* x, long long n, int* st) {
@@ -799,8 +947,14 @@ struct ViscProblem : Problem<T> {
   }
   void prolong_add(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotTransfer, k_prolong_cells_add<D, T>, grid_for((long long)D * F.g.ncell), kThreads, x(l), x(l + 1),
+    {
+      if (any_per(c->g))
+        launch(c, kSlotTransfer, k_prolong_cells_add_c<D, T, true>, grid_for((long long)D * C.g.ncell), kThreads, x(l), x(l + 1),
            F.g, C.g, D, T(-1));
+      else
+        launch(c, kSlotTransfer, k_prolong_cells_add_c<D, T, false>, grid_for((long long)D * C.g.ncell), kThreads, x(l), x(l + 1),
+           F.g, C.g, D, T(-1));
+    }
   }
   static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
     auto& S = static_cast<ViscProblem&>(P);
@@ -960,12 +1114,23 @@ struct MacProblem : Problem<T> {
     Level& L = c->lv[l];
     int nb = grid_for(rb_count<D>(L.g));
     for (int col = 0; col < 2; ++col)
-      launch(c, l == 0 ? kSlotCellSmooth : kSlotCoarse, k_cell_smooth<D, T>, nb, kThreads, x(l), b(l), L.g, col);
+      {
+        if (any_per(c->g))
+          launch(c, l == 0 ? kSlotCellSmooth : kSlotCoarse, k_cell_smooth<D, T, true>, nb, kThreads, x(l), b(l), L.g, col);
+        else
+          launch(c, l == 0 ? kSlotCellSmooth : kSlotCoarse, k_cell_smooth<D, T, false>, nb, kThreads, x(l), b(l), L.g, col);
+      }
   }
   void resid(int l) override {
     Level& L = c->lv[l];
-    launch(c, l == 0 ? kSlotCellResid : kSlotCoarse, k_cell_resid<D, T>, grid_for(L.g.ncell), kThreads, x(l), b(l),
+    {
+      if (any_per(c->g))
+        launch(c, l == 0 ? kSlotCellResid : kSlotCoarse, k_cell_resid<D, T, true>, grid_for(L.g.ncell), kThreads, x(l), b(l),
            r(l), L.g);
+      else
+        launch(c, l == 0 ? kSlotCellResid : kSlotCoarse, k_cell_resid<D, T, false>, grid_for(L.g.ncell), kThreads, x(l), b(l),
+           r(l), L.g);
+    }
   }
   void restrict_to(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
@@ -974,8 +1139,14 @@ struct MacProblem : Problem<T> {
   }
   void prolong_add(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotTransfer, k_prolong_cells_add<D, T>, grid_for(F.g.ncell), kThreads, x(l), x(l + 1), F.g, C.g, 1,
+    {
+      if (any_per(c->g))
+        launch(c, kSlotTransfer, k_prolong_cells_add_c<D, T, true>, grid_for(C.g.ncell), kThreads, x(l), x(l + 1), F.g, C.g, 1,
            T(1));
+      else
+        launch(c, kSlotTransfer, k_prolong_cells_add_c<D, T, false>, grid_for(C.g.ncell), kThreads, x(l), x(l + 1), F.g, C.g, 1,
+           T(1));
+    }
   }
   static void run_bottom(Problem<T>& P, int l, double* xd, double* bd) {
     Level& L = P.c->lv[l];
@@ -1011,17 +1182,34 @@ struct NodalProblem : Problem<T> {
   void smooth(int l) override {
     Level& L = c->lv[l];
     for (int col = 0; col < (1 << D); ++col)
-      launch(c, l == 0 ? kSlotNodalSmooth : kSlotCoarse, k_nodal_smooth<D, T>, grid_for(mc_count<D>(L.g, col)),
+      {
+        if (any_per(c->g))
+          launch(c, l == 0 ? kSlotNodalSmooth : kSlotCoarse, k_nodal_smooth<D, T, true>, grid_for(mc_count<D>(L.g, col)),
              kThreads, x(l), b(l), L.g, col);
+        else
+          launch(c, l == 0 ? kSlotNodalSmooth : kSlotCoarse, k_nodal_smooth<D, T, false>, grid_for(mc_count<D>(L.g, col)),
+             kThreads, x(l), b(l), L.g, col);
+      }
   }
   void resid(int l) override {
     Level& L = c->lv[l];
-    launch(c, l == 0 ? kSlotNodalResid : kSlotCoarse, k_nodal_resid<D, T>, grid_for(L.g.nnode), kThreads, x(l), b(l),
+    {
+      if (any_per(c->g))
+        launch(c, l == 0 ? kSlotNodalResid : kSlotCoarse, k_nodal_resid<D, T, true>, grid_for(L.g.nnode), kThreads, x(l), b(l),
            r(l), L.g);
+      else
+        launch(c, l == 0 ? kSlotNodalResid : kSlotCoarse, k_nodal_resid<D, T, false>, grid_for(L.g.nnode), kThreads, x(l), b(l),
+           r(l), L.g);
+    }
   }
   void restrict_to(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    launch(c, kSlotTransfer, k_restrict_nodes<D, T>, grid_for(C.g.nnode), kThreads, r(l), b(l + 1), F.g, C.g);
+    {
+      if (any_per(c->g))
+        launch(c, kSlotTransfer, k_restrict_nodes<D, T, true>, grid_for(C.g.nnode), kThreads, r(l), b(l + 1), F.g, C.g);
+      else
+        launch(c, kSlotTransfer, k_restrict_nodes<D, T, false>, grid_for(C.g.nnode), kThreads, r(l), b(l + 1), F.g, C.g);
+    }
     launch(c, kSlotTransfer, k_zero<T>, grid_for(C.g.nnode), kThreads, x(l + 1), (long long)C.g.nnode);
   }
   void prolong_add(int l) override {
@@ -1309,8 +1497,11 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
     if (st) return st;
     const double in_tol = kInnerRtol * in_norm;
     double rho = 1.0, alpha = 1.0, omega = 1.0;
+    // the fused vector kernels need 16-byte aligned vectors (cudaMalloc'd)
+    const bool fused = aligned16(fr) && aligned16(fs) && aligned16(ft) && aligned16(frh);
+    double rho_next = 0.0;  // r^.r of the updated r, from the fused update
     for (int k = 0; k < kInnerMax && it < cfg.max_cycles; ++k) {
-      double rho1 = reduce_dot_f(c, frh, fr, n, &st);
+      double rho1 = (fused && k > 0) ? rho_next : reduce_dot_f(c, frh, fr, n, &st);
       if (st) return st;
       if (rho1 == 0.0 || !std::isfinite(rho1)) break;
       double bt = (rho1 / rho) * (alpha / omega);
@@ -1325,18 +1516,31 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
       launch(c, kSlotVector, k_axmy<float>, nb, kThreads, fs, (const float*)fr, (float)alpha, (const float*)fv, n);
       precond(fs, fsh);
       apply0(fsh, ft);
-      double tt = reduce_dot_f(c, ft, ft, n, &st);
-      if (st) return st;
-      double ts = reduce_dot_f(c, ft, fs, n, &st);
-      if (st) return st;
+      double tt, ts;
+      if (fused) {
+        if ((st = reduce_dot2_f(c, ft, fs, n, &tt, &ts))) return st;
+      } else {
+        tt = reduce_dot_f(c, ft, ft, n, &st);
+        if (st) return st;
+        ts = reduce_dot_f(c, ft, fs, n, &st);
+        if (st) return st;
+      }
       omega = tt > 0.0 ? ts / tt : 0.0;
       launch(c, kSlotVector, k_bicg_x<float>, nb, kThreads, fe, (const float*)fph, (const float*)fsh, (float)alpha,
              (float)omega, n);
-      launch(c, kSlotVector, k_axmy<float>, nb, kThreads, fr, (const float*)fs, (float)omega, (const float*)ft, n);
+      double rr;
+      if (fused) {
+        // r = s - omega t with max |r| and r^.r of the new r in one pass
+        launch(c, kSlotVector, k_axmy_red_f4, kRedBlocks, kThreads, fr, (const float*)fs, (float)omega,
+               (const float*)ft, (const float*)frh, n, c->partial);
+        if ((st = read_results2(c, &rr, &rho_next))) return st;
+      } else {
+        launch(c, kSlotVector, k_axmy<float>, nb, kThreads, fr, (const float*)fs, (float)omega, (const float*)ft, n);
+        rr = reduce_max_abs_f(c, fr, n, &st);
+        if (st) return st;
+      }
       rho = rho1;
       ++it;
-      double rr = reduce_max_abs_f(c, fr, n, &st);
-      if (st) return st;
       if (rr <= in_tol || omega == 0.0 || !std::isfinite(rr)) break;
     }
     launch(c, kSlotTransfer, k_add_f32, nb, kThreads, x, (const float*)fe, n);
@@ -1478,19 +1682,33 @@ int solve_nodal(hbf_ctx* c, const double* rhs, double* phi, hbf_solve_stats* s) 
 }
 
 int nodal_residual(hbf_ctx* c, const double* b, const double* x, double* r) {
-  if (c->dim == 2)
-    launch(c, kSlotNodalResid, k_nodal_resid<2, double>, grid_for(c->g.nnode), kThreads, x, b, r, c->g);
-  else
-    launch(c, kSlotNodalResid, k_nodal_resid<3, double>, grid_for(c->g.nnode), kThreads, x, b, r, c->g);
+  if (c->dim == 2) {
+    if (any_per(c->g))
+      launch(c, kSlotNodalResid, k_nodal_resid<2, double, true>, grid_for(c->g.nnode), kThreads, x, b, r, c->g);
+    else
+      launch(c, kSlotNodalResid, k_nodal_resid<2, double, false>, grid_for(c->g.nnode), kThreads, x, b, r, c->g);
+  } else {
+    if (any_per(c->g))
+      launch(c, kSlotNodalResid, k_nodal_resid<3, double, true>, grid_for(c->g.nnode), kThreads, x, b, r, c->g);
+    else
+      launch(c, kSlotNodalResid, k_nodal_resid<3, double, false>, grid_for(c->g.nnode), kThreads, x, b, r, c->g);
+  }
   return cuda_check(c, cudaGetLastError(), "nodal residual");
 }
 
 void nodal_restrict(hbf_ctx* c, int l, const double* fine, double* coarse) {
   const Level &F = c->lv[l], &C = c->lv[l + 1];
-  if (c->dim == 2)
-    launch(c, kSlotTransfer, k_restrict_nodes<2, double>, grid_for(C.g.nnode), kThreads, fine, coarse, F.g, C.g);
-  else
-    launch(c, kSlotTransfer, k_restrict_nodes<3, double>, grid_for(C.g.nnode), kThreads, fine, coarse, F.g, C.g);
+  if (c->dim == 2) {
+    if (any_per(c->g))
+      launch(c, kSlotTransfer, k_restrict_nodes<2, double, true>, grid_for(C.g.nnode), kThreads, fine, coarse, F.g, C.g);
+    else
+      launch(c, kSlotTransfer, k_restrict_nodes<2, double, false>, grid_for(C.g.nnode), kThreads, fine, coarse, F.g, C.g);
+  } else {
+    if (any_per(c->g))
+      launch(c, kSlotTransfer, k_restrict_nodes<3, double, true>, grid_for(C.g.nnode), kThreads, fine, coarse, F.g, C.g);
+    else
+      launch(c, kSlotTransfer, k_restrict_nodes<3, double, false>, grid_for(C.g.nnode), kThreads, fine, coarse, F.g, C.g);
+  }
 }
 
 void nodal_prolong_add(hbf_ctx* c, int l, double* fine, const double* coarse) {
@@ -1521,12 +1739,19 @@ void cell_restrict_d(hbf_ctx* c, int l, const double* fine, double* coarse, int 
 
 void cell_prolong_add_f(hbf_ctx* c, int l, float* fine, const float* coarse) {
   const Level &F = c->lv[l], &C = c->lv[l + 1];
-  const long long n = (long long)c->dim * F.g.ncell;
+  const long long n = (long long)c->dim * C.g.ncell;
   // odd reflection at the walls: a correction of the Dirichlet problem
-  if (c->dim == 2)
-    launch(c, kSlotTransfer, k_prolong_cells_add<2, float>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 2, -1.f);
-  else
-    launch(c, kSlotTransfer, k_prolong_cells_add<3, float>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3, -1.f);
+  if (c->dim == 2) {
+    if (any_per(c->g))
+      launch(c, kSlotTransfer, k_prolong_cells_add_c<2, float, true>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 2, -1.f);
+    else
+      launch(c, kSlotTransfer, k_prolong_cells_add_c<2, float, false>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 2, -1.f);
+  } else {
+    if (any_per(c->g))
+      launch(c, kSlotTransfer, k_prolong_cells_add_c<3, float, true>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3, -1.f);
+    else
+      launch(c, kSlotTransfer, k_prolong_cells_add_c<3, float, false>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3, -1.f);
+  }
 }
 
 int visc_after_solve(hbf_ctx* c, const double* ustar, const double* u) {

@@ -683,40 +683,24 @@ __global__ void k_visc_bottom(T* __restrict__ u, const T* __restrict__ b, const 
 // ---------------------------------------------------------------------------
 // cell-centred Poisson (MAC potential), Neumann walls
 // ---------------------------------------------------------------------------
-// Cell p and its 2D face neighbours lie inside the domain: no wall is
-// skipped and no periodic wrap is needed.
-template <int D>
-__host__ __device__ inline bool cell_inner(const Geom& g, const int* p) {
-  bool in = p[0] >= 1 && p[0] < g.n[0] - 1 && p[1] >= 1 && p[1] < g.n[1] - 1;
-  if (D == 3) in = in && p[2] >= 1 && p[2] < g.n[2] - 1;
-  return in;
-}
-
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __restrict__ b, const Geom& g,
                                   const int* p) {
   T s = T(0);
   int cnt = 0;
-  const int id = cidx<D>(g, p[0], p[1], p[2]);
-  if (cell_inner<D>(g, p)) {
-    // direct offsets, the same terms in the same order as the general path
-    const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
-#pragma unroll
-    for (int a = 0; a < D; ++a) s += x[id - st[a]] + x[id + st[a]];
-    return (s - g_hh<T>(g) * b[id]) / T(2 * D);
-  }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T lo = T(0), hi = T(0);
-    if (p[a] > 0 || g.per[a]) {
+    const bool pa = PER && g.per[a];
+    if (p[a] > 0 || pa) {
       int q[3] = {p[0], p[1], p[2]};
-      q[a] = g.per[a] ? wrap_cell(q[a] - 1, g.n[a]) : q[a] - 1;
+      q[a] = pa ? wrap_cell(q[a] - 1, g.n[a]) : q[a] - 1;
       lo = x[cidx<D>(g, q[0], q[1], q[2])];
       ++cnt;
     }
-    if (p[a] < g.n[a] - 1 || g.per[a]) {
+    if (p[a] < g.n[a] - 1 || pa) {
       int q[3] = {p[0], p[1], p[2]};
-      q[a] = g.per[a] ? wrap_cell(q[a] + 1, g.n[a]) : q[a] + 1;
+      q[a] = pa ? wrap_cell(q[a] + 1, g.n[a]) : q[a] + 1;
       hi = x[cidx<D>(g, q[0], q[1], q[2])];
       ++cnt;
     }
@@ -726,66 +710,51 @@ __host__ __device__ inline T cell_gs_point(const T* __restrict__ x, const T* __r
   return (s - hh * b[cidx<D>(g, p[0], p[1], p[2])]) / T(cnt);
 }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ void k_cell_smooth_at(T* __restrict__ x, const T* __restrict__ b, const Geom& g, int col, int t) {
-  int nt = rb_count<D>(g);
-  
-    int p[3];
-    if (!rb_cell<D>(g, t, col, p)) return;
-    x[cidx<D>(g, p[0], p[1], p[2])] = cell_gs_point<D, T>(x, b, g, p);
-  }
+  int p[3];
+  if (!rb_cell<D>(g, t, col, p)) return;
+  x[cidx<D>(g, p[0], p[1], p[2])] = cell_gs_point<D, T, PER>(x, b, g, p);
+}
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __global__ void k_cell_smooth(T* __restrict__ x, const T* __restrict__ b, const __grid_constant__ Geom g, int col) {
   int nt = rb_count<D>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-    k_cell_smooth_at<D, T>(x, b, g, col, t);
+    k_cell_smooth_at<D, T, PER>(x, b, g, col, t);
   }
 }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ void k_cell_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const Geom& g, int t) {
   const T ih = g_ih<T>(g);
-  
-    int p[3];
-    cell_coords<D>(g, t, p[0], p[1], p[2]);
-    T xc = x[t];
-    T acc = T(0);
-    if (cell_inner<D>(g, p)) {
-      // direct offsets, the same terms in the same order as the general path
-      const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  int p[3];
+  cell_coords<D>(g, t, p[0], p[1], p[2]);
+  T xc = x[t];
+  T acc = T(0);
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T glo = (xc - x[t - st[a]]) * ih;
-        const T ghi = (x[t + st[a]] - xc) * ih;
-        acc += (ghi - glo) * ih;
-      }
-      r[t] = b[t] - acc;
-      return;
+  for (int a = 0; a < D; ++a) {
+    T glo = T(0), ghi = T(0);
+    const bool pa = PER && g.per[a];
+    if (p[a] > 0 || pa) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[a] = pa ? wrap_cell(q[a] - 1, g.n[a]) : q[a] - 1;
+      glo = (xc - x[cidx<D>(g, q[0], q[1], q[2])]) * ih;
     }
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      T glo = T(0), ghi = T(0);
-      if (p[a] > 0 || g.per[a]) {
-        int q[3] = {p[0], p[1], p[2]};
-        q[a] = g.per[a] ? wrap_cell(q[a] - 1, g.n[a]) : q[a] - 1;
-        glo = (xc - x[cidx<D>(g, q[0], q[1], q[2])]) * ih;
-      }
-      if (p[a] < g.n[a] - 1 || g.per[a]) {
-        int q[3] = {p[0], p[1], p[2]};
-        q[a] = g.per[a] ? wrap_cell(q[a] + 1, g.n[a]) : q[a] + 1;
-        ghi = (x[cidx<D>(g, q[0], q[1], q[2])] - xc) * ih;
-      }
-      acc += (ghi - glo) * ih;
+    if (p[a] < g.n[a] - 1 || pa) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[a] = pa ? wrap_cell(q[a] + 1, g.n[a]) : q[a] + 1;
+      ghi = (x[cidx<D>(g, q[0], q[1], q[2])] - xc) * ih;
     }
-    r[t] = b[t] - acc;
+    acc += (ghi - glo) * ih;
   }
+  r[t] = b[t] - acc;
+}
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __global__ void k_cell_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const __grid_constant__ Geom g) {
-  const T ih = g_ih<T>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.ncell; t += gridDim.x * blockDim.x) {
-    k_cell_resid_at<D, T>(x, b, r, g, t);
+    k_cell_resid_at<D, T, PER>(x, b, r, g, t);
   }
 }
 
@@ -814,43 +783,13 @@ __host__ __device__ inline T fe_weight(int nz) {
   return nz == 1 ? T(0) : (nz == 2 ? T(1.0 / 6.0) : T(1.0 / 12.0));
 }
 
-// Node p and its whole 3^D neighbourhood lie in [0, n] on every axis, so no
-// stencil point needs a reflection or a periodic wrap.
-template <int D>
-__host__ __device__ inline bool node_inner(const Geom& g, const int* p) {
-  bool in = p[0] >= 1 && p[0] < g.n[0] && p[1] >= 1 && p[1] < g.n[1];
-  if (D == 3) in = in && p[2] >= 1 && p[2] < g.n[2];
-  return in;
-}
-
-template <int D, typename T>
+// The kernels below take PER = false for a level with walls on every axis
+// (the periodic wraps compile out; the code is then the plain reflection
+// form) and PER = true otherwise.
+template <int D, typename T, bool PER = true>
 __host__ __device__ inline T nodal_lap_point(const T* __restrict__ x, const Geom& g, const int* p, bool skip_centre) {
   T s = T(0);
   const int K = D == 3 ? 27 : 9;
-  if (node_inner<D>(g, p)) {
-    // direct offsets, the same terms in the same order as the general path
-    const int sy = g.n[0] + 1, sz = (g.n[0] + 1) * (g.n[1] + 1);
-    const int id = nidx(g, p[0], p[1], p[2]);
-#pragma unroll
-    for (int o = 0; o < K; ++o) {
-      int oo[3];
-      if (D == 3) {
-        oo[0] = o / 9 - 1;
-        oo[1] = (o / 3) % 3 - 1;
-        oo[2] = o % 3 - 1;
-      } else {
-        oo[0] = o / 3 - 1;
-        oo[1] = o % 3 - 1;
-        oo[2] = 0;
-      }
-      int nz = (oo[0] != 0) + (oo[1] != 0) + (oo[2] != 0);
-      if (nz == 0 && skip_centre) continue;
-      if (D == 3 && nz == 1) continue;
-      T w = fe_weight<D, T>(nz);
-      s += w * x[id + oo[0] + oo[1] * sy + oo[2] * sz];
-    }
-    return s;
-  }
 #pragma unroll
   for (int o = 0; o < K; ++o) {
     int oo[3];
@@ -867,7 +806,7 @@ __host__ __device__ inline T nodal_lap_point(const T* __restrict__ x, const Geom
     if (nz == 0 && skip_centre) continue;
     if (D == 3 && nz == 1) continue;
     T w = fe_weight<D, T>(nz);
-    s += w * ndget<D>(x, g, p[0] + oo[0], p[1] + oo[1], p[2] + oo[2]);
+    s += w * ndget<D, T, PER>(x, g, p[0] + oo[0], p[1] + oo[1], p[2] + oo[2]);
   }
   return s;
 }
@@ -900,7 +839,7 @@ __host__ __device__ inline int mc_count(const Geom& g, int col) {
   return c;
 }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ void k_nodal_smooth_at(T* __restrict__ x, const T* __restrict__ b, const Geom& g, int col, int t) {
   int nt = mc_count<D>(g, col);
   const T hh = g_hh<T>(g);
@@ -909,34 +848,34 @@ __host__ __device__ __forceinline__ void k_nodal_smooth_at(T* __restrict__ x, co
     int p[3];
     if (!mc_node<D>(g, t, col, p)) return;
     int id = nidx(g, p[0], p[1], p[2]);
-    T s = nodal_lap_point<D, T>(x, g, p, true);
+    T s = nodal_lap_point<D, T, PER>(x, g, p, true);
     x[id] = (hh * b[id] - s) * is0;
   }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __global__ void k_nodal_smooth(T* __restrict__ x, const T* __restrict__ b, const __grid_constant__ Geom g, int col) {
   int nt = mc_count<D>(g, col);
   const T hh = g_hh<T>(g);
   const T is0 = T(-3.0 / 8.0);  // 1 / centre weight
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-    k_nodal_smooth_at<D, T>(x, b, g, col, t);
+    k_nodal_smooth_at<D, T, PER>(x, b, g, col, t);
   }
 }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ void k_nodal_resid_at(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const Geom& g, int t) {
   const T ihh = g_ihh<T>(g);
   
     int p[3];
     node_coords(g, t, p[0], p[1], p[2]);
-    r[t] = b[t] - nodal_lap_point<D, T>(x, g, p, false) * ihh;
+    r[t] = b[t] - nodal_lap_point<D, T, PER>(x, g, p, false) * ihh;
   }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __global__ void k_nodal_resid(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, const __grid_constant__ Geom g) {
   const T ihh = g_ihh<T>(g);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += gridDim.x * blockDim.x) {
-    k_nodal_resid_at<D, T>(x, b, r, g, t);
+    k_nodal_resid_at<D, T, PER>(x, b, r, g, t);
   }
 }
 
@@ -1041,12 +980,14 @@ __global__ void k_restrict_faces(const T* __restrict__ ff, T* __restrict__ fc, i
 }
 
 // coarse cell value with ghost by reflection: sign -1 (Dirichlet error), +1 (Neumann)
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, int i, int j, int k, T sign) {
   T s = T(1);
-  if (g.per[0]) i = wrap_cell(i, g.n[0]);
-  if (g.per[1]) j = wrap_cell(j, g.n[1]);
-  if (D == 3 && g.per[2]) k = wrap_cell(k, g.n[2]);
+  if (PER) {
+    if (g.per[0]) i = wrap_cell(i, g.n[0]);
+    if (g.per[1]) j = wrap_cell(j, g.n[1]);
+    if (D == 3 && g.per[2]) k = wrap_cell(k, g.n[2]);
+  }
   if (i < 0) { i = 0; s *= sign; }
   if (i >= g.n[0]) { i = g.n[0] - 1; s *= sign; }
   if (j < 0) { j = 0; s *= sign; }
@@ -1059,7 +1000,7 @@ __host__ __device__ inline T cget_refl(const T* __restrict__ e, const Geom& g, i
 }
 
 // x_f += P e_c, cell-centred multilinear (3/4, 1/4 per axis), axis by axis
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ xf, const T* __restrict__ ec, const Geom& gf, const Geom& gc,
                                     int ncomp, T sign, long long tt) {
   
@@ -1082,7 +1023,8 @@ __host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ 
       T ty[2];
       for (int jj = 0; jj < 2; ++jj) {
         int jc = jj ? Jn : J;
-        ty[jj] = T(0.75) * cget_refl<D>(e, gc, I, jc, kc, sign) + T(0.25) * cget_refl<D>(e, gc, In, jc, kc, sign);
+        ty[jj] = T(0.75) * cget_refl<D, T, PER>(e, gc, I, jc, kc, sign) +
+                 T(0.25) * cget_refl<D, T, PER>(e, gc, In, jc, kc, sign);
       }
       tz[kk] = T(0.75) * ty[0] + T(0.25) * ty[1];
     }
@@ -1090,18 +1032,107 @@ __host__ __device__ __forceinline__ void k_prolong_cells_add_at(T* __restrict__ 
     xf[(size_t)comp * gf.ncell + t] += v;
   }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __global__ void k_prolong_cells_add(T* __restrict__ xf, const T* __restrict__ ec, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc,
                                     int ncomp, T sign) {
   long long tot = (long long)gf.ncell * ncomp;
   for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
        tt += (long long)gridDim.x * blockDim.x) {
-    k_prolong_cells_add_at<D, T>(xf, ec, gf, gc, ncomp, sign, tt);
+    k_prolong_cells_add_at<D, T, PER>(xf, ec, gf, gc, ncomp, sign, tt);
   }
 }
 
+// The same prolongation with one thread per (coarse cell, component): the
+// 3^D coarse neighbourhood is read once (with cget_refl's wraps, clamps and
+// signs, which are exact: each sign is +-1) and each of the 2^D children is
+// updated with the terms of k_prolong_cells_add_at in the same order.  Every
+// level has even sizes (the hierarchy coarsens only even sizes), so each
+// coarse cell has exactly 2^D children.
+template <int D, typename T, bool PER = true>
+__host__ __device__ __forceinline__ void k_prolong_cells_add_c_at(T* __restrict__ xf, const T* __restrict__ ec,
+                                                                  const Geom& gf, const Geom& gc, T sign,
+                                                                  long long tt) {
+  int comp = 0;
+  int t = (int)tt;
+  while (t >= gc.ncell) {
+    t -= gc.ncell;
+    ++comp;
+  }
+  int P[3];
+  cell_coords<D>(gc, t, P[0], P[1], P[2]);
+  const T* e = ec + (size_t)comp * gc.ncell;
+  // per axis: coarse index and sign of the offsets -1, 0, +1
+  int ix[3][3];
+  T sg[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int q = (a < D) ? P[a] + d - 1 : 0;
+      T s = T(1);
+      if (a < D) {
+        if (PER && gc.per[a]) q = wrap_cell(q, gc.n[a]);
+        if (q < 0) {
+          q = 0;
+          s *= sign;
+        }
+        if (q >= gc.n[a]) {
+          q = gc.n[a] - 1;
+          s *= sign;
+        }
+      }
+      ix[a][d] = q;
+      sg[a][d] = s;
+    }
+  T v[D == 3 ? 3 : 1][3][3];
+#pragma unroll
+  for (int dz = 0; dz < (D == 3 ? 3 : 1); ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int kz = D == 3 ? dz : 0;
+        const T s = sg[0][dx] * sg[1][dy] * (D == 3 ? sg[2][kz] : T(1));
+        v[dz][dy][dx] = s * e[cidx<D>(gc, ix[0][dx], ix[1][dy], D == 3 ? ix[2][kz] : 0)];
+      }
+  T* x = xf + (size_t)comp * gf.ncell;
+#pragma unroll
+  for (int ck = 0; ck < (D == 3 ? 2 : 1); ++ck)
+#pragma unroll
+    for (int cj = 0; cj < 2; ++cj)
+#pragma unroll
+      for (int ci = 0; ci < 2; ++ci) {
+        // child (2I + ci, 2J + cj, 2K + ck): its own coarse cell (offset 1)
+        // and the neighbour on the child's side (offset 2 or 0)
+        const int nx = ci ? 2 : 0, ny = cj ? 2 : 0, nz = D == 3 ? (ck ? 2 : 0) : 0;
+        T tz[2];
+#pragma unroll
+        for (int kk = 0; kk < (D == 3 ? 2 : 1); ++kk) {
+          const int kz = D == 3 ? (kk ? nz : 1) : 0;
+          T ty[2];
+#pragma unroll
+          for (int jj = 0; jj < 2; ++jj) {
+            const int jy = jj ? ny : 1;
+            ty[jj] = T(0.75) * v[kz][jy][1] + T(0.25) * v[kz][jy][nx];
+          }
+          tz[kk] = T(0.75) * ty[0] + T(0.25) * ty[1];
+        }
+        const T val = D == 3 ? T(0.75) * tz[0] + T(0.25) * tz[1] : tz[0];
+        x[cidx<D>(gf, 2 * P[0] + ci, 2 * P[1] + cj, D == 3 ? 2 * P[2] + ck : 0)] += val;
+      }
+}
+
+template <int D, typename T, bool PER = true>
+__global__ void k_prolong_cells_add_c(T* __restrict__ xf, const T* __restrict__ ec, const __grid_constant__ Geom gf,
+                                      const __grid_constant__ Geom gc, int ncomp, T sign) {
+  const long long tot = (long long)gc.ncell * ncomp;
+  for (long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x; tt < tot;
+       tt += (long long)gridDim.x * blockDim.x)
+    k_prolong_cells_add_c_at<D, T, PER>(xf, ec, gf, gc, sign, tt);
+}
+
 // full weighting onto coarse nodes (even reflection), axis by axis
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict__ rf, T* __restrict__ rc, const Geom& gf, const Geom& gc, int t) {
   
     int I, J, K;
@@ -1112,9 +1143,9 @@ __host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict
       T yr[3];
       for (int jj = 0; jj < 3; ++jj) {
         int j = 2 * J + jj - 1;
-        T cen = ndget<D>(rf, gf, 2 * I, j, k);
-        T lo = ndget<D>(rf, gf, 2 * I - 1, j, k);
-        T hi = ndget<D>(rf, gf, 2 * I + 1, j, k);
+        T cen = ndget<D, T, PER>(rf, gf, 2 * I, j, k);
+        T lo = ndget<D, T, PER>(rf, gf, 2 * I - 1, j, k);
+        T hi = ndget<D, T, PER>(rf, gf, 2 * I + 1, j, k);
         yr[jj] = T(0.5) * cen + T(0.25) * (lo + hi);
       }
       zr[kk] = T(0.5) * yr[1] + T(0.25) * (yr[0] + yr[2]);
@@ -1122,10 +1153,10 @@ __host__ __device__ __forceinline__ void k_restrict_nodes_at(const T* __restrict
     rc[t] = D == 3 ? T(0.5) * zr[1] + T(0.25) * (zr[0] + zr[2]) : zr[0];
   }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __global__ void k_restrict_nodes(const T* __restrict__ rf, T* __restrict__ rc, const __grid_constant__ Geom gf, const __grid_constant__ Geom gc) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < gc.nnode; t += gridDim.x * blockDim.x) {
-    k_restrict_nodes_at<D, T>(rf, rc, gf, gc, t);
+    k_restrict_nodes_at<D, T, PER>(rf, rc, gf, gc, t);
   }
 }
 

@@ -124,12 +124,25 @@ static int run(FILE* in, FILE* out, const int* n, int hom) {
     for (int t = 0; t < gc.nface[a]; ++t) k_restrict_faces_at<D, double>(efp[a], fc.data(), a, g, gc, t);
     wr(out, fc);
   }
-  std::vector<double> up = u;
+  // prolongation: the coarse-centred form the level-by-level cycles launch,
+  // checked bit for bit against the per-fine-cell form of the fused tail
+  std::vector<double> up = u, up1 = u;
+  for (long long t = 0; t < (long long)D * gc.ncell; ++t)
+    k_prolong_cells_add_c_at<D, double>(up.data(), ev.data(), g, gc, -1.0, t);
   for (long long t = 0; t < (long long)D * g.ncell; ++t)
-    k_prolong_cells_add_at<D, double>(up.data(), ev.data(), g, gc, D, -1.0, t);
+    k_prolong_cells_add_at<D, double>(up1.data(), ev.data(), g, gc, D, -1.0, t);
+  if (std::memcmp(up.data(), up1.data(), up.size() * sizeof(double)) != 0) {
+    std::fprintf(stderr, "the two cell prolongations differ (Dirichlet)\n");
+    return 3;
+  }
   wr(out, up);
-  std::vector<double> xp = x;
-  for (long long t = 0; t < g.ncell; ++t) k_prolong_cells_add_at<D, double>(xp.data(), ec.data(), g, gc, 1, 1.0, t);
+  std::vector<double> xp = x, xp1 = x;
+  for (long long t = 0; t < gc.ncell; ++t) k_prolong_cells_add_c_at<D, double>(xp.data(), ec.data(), g, gc, 1.0, t);
+  for (long long t = 0; t < g.ncell; ++t) k_prolong_cells_add_at<D, double>(xp1.data(), ec.data(), g, gc, 1, 1.0, t);
+  if (std::memcmp(xp.data(), xp1.data(), xp.size() * sizeof(double)) != 0) {
+    std::fprintf(stderr, "the two cell prolongations differ (Neumann)\n");
+    return 3;
+  }
   wr(out, xp);
   std::vector<double> nr(nnc);
   for (int t = 0; t < gc.nnode; ++t) k_restrict_nodes_at<D, double>(xn.data(), nr.data(), g, gc, t);
