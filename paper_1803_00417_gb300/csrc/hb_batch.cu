@@ -26,7 +26,7 @@ template <int D, typename T, int C>
 struct OpViscSmooth {
   using Arg = ViscArg<T>;
   static __device__ void apply(const Arg& a, int t, int col) {
-    k_visc_smooth_c_at<D, T, C>(a.x, a.b, a.ef[0], a.ef[1], a.ef[2], a.g, col, a.beta, a.hom, t);
+    k_visc_smooth_c_at<D, T, C, false>(a.x, a.b, a.ef[0], a.ef[1], a.ef[2], a.g, col, a.beta, a.hom, t);
   }
 };
 
@@ -35,7 +35,7 @@ template <int D, typename T>
 struct OpViscOp {
   using Arg = ViscArg<T>;
   static __device__ void apply(const Arg& a, int t, int) {
-    k_visc_op_at<D, T>(a.x, a.b, a.out, a.ef[0], a.ef[1], a.ef[2], a.g, a.beta, a.hom, t);
+    k_visc_op_at<D, T, false>(a.x, a.b, a.out, a.ef[0], a.ef[1], a.ef[2], a.g, a.beta, a.hom, t);
   }
 };
 
@@ -612,11 +612,11 @@ static void vcycle(hbf_batch* B, Inst& I, const int* mask) {
   ++B->nlaunch;
   if (lf < B->maxlev) {
     if (I.kind == kVisc)
-      k_vcycle_tail<D, T, kVisc><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1, cfg.nu2);
+      k_vcycle_tail<D, T, kVisc, false><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1, cfg.nu2);
     else if (I.kind == kMac)
-      k_vcycle_tail<D, T, kMac><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1, cfg.nu2);
+      k_vcycle_tail<D, T, kMac, false><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1, cfg.nu2);
     else
-      k_vcycle_tail<D, T, kNodal><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1,
+      k_vcycle_tail<D, T, kNodal, false><<<B->ncav, 256, 0, B->stream>>>(I.tail, lf, B->ncav, mask, cfg.nu1,
                                                                          cfg.nu2);
     ++B->nlaunch;
   }

@@ -99,11 +99,55 @@ __global__ void k_sub_mean(T* __restrict__ x, long long n, const double* __restr
     x[t] -= m;
 }
 
+// Elementwise kernels touch four elements per step with 16-byte accesses
+// (one float4, or two double2) when every array is 16-byte aligned, which
+// keeps several loads in flight per thread on the capped grids; the elements
+// past the last whole group go to thread 0.  The arithmetic per element is
+// the one-element form's.
+template <typename T>
+struct V4 {
+  T v[4];
+};
+__device__ __forceinline__ V4<float> ld4(const float* p, long long q) {
+  const float4 f = reinterpret_cast<const float4*>(p)[q];
+  return {{f.x, f.y, f.z, f.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p, long long q) {
+  const double2 a = reinterpret_cast<const double2*>(p)[2 * q], b = reinterpret_cast<const double2*>(p)[2 * q + 1];
+  return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, long long q, const V4<float>& v) {
+  reinterpret_cast<float4*>(p)[q] = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, long long q, const V4<double>& v) {
+  reinterpret_cast<double2*>(p)[2 * q] = make_double2(v.v[0], v.v[1]);
+  reinterpret_cast<double2*>(p)[2 * q + 1] = make_double2(v.v[2], v.v[3]);
+}
+template <typename... P>
+__device__ __forceinline__ bool aligned16_all(const P*... p) {
+  return ((reinterpret_cast<uintptr_t>(p) | ...) & 15) == 0;
+}
+// grid-stride loop: f4(q) on the groups 4q .. 4q + 3 when vec, f1(e) on single
+// elements otherwise (and on the tail)
+template <typename F4, typename F1>
+__device__ __forceinline__ void for_each4(long long n, bool vec, F4 f4, F1 f1) {
+  const long long T = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (vec) {
+    const long long n4 = n >> 2;
+#pragma unroll 4
+    for (long long q = tid; q < n4; q += T) f4(q);
+    if (tid == 0)
+      for (long long e = n4 << 2; e < n; ++e) f1(e);
+  } else {
+    for (long long e = tid; e < n; e += T) f1(e);
+  }
+}
+
 template <typename T>
 __global__ void k_zero(T* __restrict__ x, long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    x[t] = T(0);
+  for_each4(
+      n, aligned16_all(x), [&](long long q) { st4(x, q, V4<T>{{T(0), T(0), T(0), T(0)}}); },
+      [&](long long e) { x[e] = T(0); });
 }
 
 __global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b, long long n,
@@ -330,42 +374,74 @@ static double* noalloc_scratch(int* st) {
 // ---------------------------------------------------------------------------
 template <typename TO, typename TI>
 __global__ void k_convert(TO* __restrict__ out, const TI* __restrict__ in, long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    out[t] = TO(in[t]);
+  for_each4(
+      n, aligned16_all(out, in),
+      [&](long long q) {
+        const V4<TI> a = ld4(in, q);
+        st4(out, q, V4<TO>{{TO(a.v[0]), TO(a.v[1]), TO(a.v[2]), TO(a.v[3])}});
+      },
+      [&](long long e) { out[e] = TO(in[e]); });
 }
 
 // x (FP64) += e (FP32): the defect-correction update
 __global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ e, long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    x[t] += (double)e[t];
+  for_each4(
+      n, aligned16_all(x, e),
+      [&](long long q) {
+        V4<double> a = ld4(x, q);
+        const V4<float> d = ld4(e, q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a.v[i] += (double)d.v[i];
+        st4(x, q, a);
+      },
+      [&](long long i) { x[i] += (double)e[i]; });
 }
 
 // p = r + beta (p - omega v)
 template <typename T>
 __global__ void k_bicg_p(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ v, T beta, T omega,
                          long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    p[t] = r[t] + beta * (p[t] - omega * v[t]);
+  for_each4(
+      n, aligned16_all(p, r, v),
+      [&](long long q) {
+        V4<T> a = ld4(p, q);
+        const V4<T> b = ld4(r, q), c = ld4(v, q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a.v[i] = b.v[i] + beta * (a.v[i] - omega * c.v[i]);
+        st4(p, q, a);
+      },
+      [&](long long e) { p[e] = r[e] + beta * (p[e] - omega * v[e]); });
 }
 
 // out = x - a y
 template <typename T>
 __global__ void k_axmy(T* __restrict__ out, const T* __restrict__ x, T a, const T* __restrict__ y, long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    out[t] = x[t] - a * y[t];
+  for_each4(
+      n, aligned16_all(out, x, y),
+      [&](long long q) {
+        const V4<T> b = ld4(x, q), c = ld4(y, q);
+        V4<T> o;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o.v[i] = b.v[i] - a * c.v[i];
+        st4(out, q, o);
+      },
+      [&](long long e) { out[e] = x[e] - a * y[e]; });
 }
 
 // x = x + alpha ph + omega sh
 template <typename T>
 __global__ void k_bicg_x(T* __restrict__ x, const T* __restrict__ ph, const T* __restrict__ sh, T alpha, T omega,
                          long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    x[t] = x[t] + alpha * ph[t] + omega * sh[t];
+  for_each4(
+      n, aligned16_all(x, ph, sh),
+      [&](long long q) {
+        V4<T> a = ld4(x, q);
+        const V4<T> b = ld4(ph, q), c = ld4(sh, q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a.v[i] = a.v[i] + alpha * b.v[i] + omega * c.v[i];
+        st4(x, q, a);
+      },
+      [&](long long e) { x[e] = x[e] + alpha * ph[e] + omega * sh[e]; });
 }
 
 // sum of a*b over float arrays: FP32 products summed in FP32 over runs of
@@ -854,8 +930,12 @@ static bool run_tail(hbf_ctx* c, int l, double beta) {
     tb.pr[q] = &d->pr[q];
   }
   tb.bot = &d->bot;
-  launch(c, kSlotCoarse, k_vcycle_tail<D, T, KIND>, 1, kThreads, tb, lf, 1, (const int*)nullptr, c->cfg.nu1,
-         c->cfg.nu2);
+  if (any_per(c->g))
+    launch(c, kSlotCoarse, k_vcycle_tail<D, T, KIND, true>, 1, kThreads, tb, lf, 1, (const int*)nullptr, c->cfg.nu1,
+           c->cfg.nu2);
+  else
+    launch(c, kSlotCoarse, k_vcycle_tail<D, T, KIND, false>, 1, kThreads, tb, lf, 1, (const int*)nullptr, c->cfg.nu1,
+           c->cfg.nu2);
   return true;
 }
 
@@ -884,14 +964,26 @@ struct ViscProblem : Problem<T> {
       // FP32 finest level: face viscosities from the cell viscosity
       const T* e0 = (const T*)L.feta;
       for (int col = 0; col < 2; ++col)
-        launch3(c, slot, k_visc_smooth_c<D, T, 0, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+        if (any_per(c->g))
+          launch3(c, slot, k_visc_smooth_c<D, T, 0, true, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+                (T)beta, hm);
+        else
+          launch3(c, slot, k_visc_smooth_c<D, T, 0, true, false>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
                 (T)beta, hm);
       for (int col = 0; col < 2; ++col)
-        launch3(c, slot, k_visc_smooth_c<D, T, 1, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+        if (any_per(c->g))
+          launch3(c, slot, k_visc_smooth_c<D, T, 1, true, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+                (T)beta, hm);
+        else
+          launch3(c, slot, k_visc_smooth_c<D, T, 1, true, false>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
                 (T)beta, hm);
       if (D == 3)
         for (int col = 0; col < 2; ++col)
-          launch3(c, slot, k_visc_smooth_c<D, T, 2, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+          if (any_per(c->g))
+            launch3(c, slot, k_visc_smooth_c<D, T, 2, true, true>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
+                  (T)beta, hm);
+          else
+            launch3(c, slot, k_visc_smooth_c<D, T, 2, true, false>, grd, blk, x(l), (const T*)b(l), e0, e0, e0, L.g, col,
                   (T)beta, hm);
       return;
     }
@@ -899,12 +991,22 @@ struct ViscProblem : Problem<T> {
     const T* e1 = View<T>::ef(L, 1);
     const T* e2 = View<T>::ef(L, 2);
     for (int col = 0; col < 2; ++col)
-      launch3(c, slot, k_visc_smooth_c<D, T, 0>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
+      if (any_per(c->g))
+        launch3(c, slot, k_visc_smooth_c<D, T, 0, false, true>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
+      else
+        launch3(c, slot, k_visc_smooth_c<D, T, 0, false, false>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
     for (int col = 0; col < 2; ++col)
-      launch3(c, slot, k_visc_smooth_c<D, T, 1>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
+      if (any_per(c->g))
+        launch3(c, slot, k_visc_smooth_c<D, T, 1, false, true>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
+      else
+        launch3(c, slot, k_visc_smooth_c<D, T, 1, false, false>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta, hm);
     if (D == 3)
       for (int col = 0; col < 2; ++col)
-        launch3(c, slot, k_visc_smooth_c<D, T, 2>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta,
+        if (any_per(c->g))
+          launch3(c, slot, k_visc_smooth_c<D, T, 2, false, true>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta,
+                hm);
+        else
+          launch3(c, slot, k_visc_smooth_c<D, T, 2, false, false>, grd, blk, x(l), (const T*)b(l), e0, e1, e2, L.g, col, (T)beta,
                 hm);
   }
   // the FP32 finest level forms its face viscosities from the cell viscosity
@@ -931,11 +1033,20 @@ struct ViscProblem : Problem<T> {
     const dim3 grd(op3_blocks<D>(L.g), 1, 1);
     if (cell_eta(l)) {
       const T* e0 = (const T*)L.feta;
-      launch3(c, kSlotViscResid, k_visc_op3<D, T, true>, grd, blk, (const T*)x(l), (const T*)b(l), r(l), e0, e0, e0,
+      if (any_per(c->g))
+        launch3(c, kSlotViscResid, k_visc_op3<D, T, true, true>, grd, blk, (const T*)x(l), (const T*)b(l), r(l), e0, e0, e0,
+              L.g, (T)beta, (int)this->hom(l));
+      else
+        launch3(c, kSlotViscResid, k_visc_op3<D, T, true, false>, grd, blk, (const T*)x(l), (const T*)b(l), r(l), e0, e0, e0,
               L.g, (T)beta, (int)this->hom(l));
       return;
     }
-    launch3(c, l == 0 ? kSlotViscResid : kSlotCoarse, k_visc_op3<D, T>, grd, blk, (const T*)x(l), (const T*)b(l), r(l),
+    if (any_per(c->g))
+      launch3(c, l == 0 ? kSlotViscResid : kSlotCoarse, k_visc_op3<D, T, false, true>, grd, blk, (const T*)x(l), (const T*)b(l), r(l),
+            (const T*)View<T>::ef(L, 0), (const T*)View<T>::ef(L, 1), (const T*)View<T>::ef(L, 2), L.g, (T)beta,
+            (int)this->hom(l));
+    else
+      launch3(c, l == 0 ? kSlotViscResid : kSlotCoarse, k_visc_op3<D, T, false, false>, grd, blk, (const T*)x(l), (const T*)b(l), r(l),
             (const T*)View<T>::ef(L, 0), (const T*)View<T>::ef(L, 1), (const T*)View<T>::ef(L, 2), L.g, (T)beta,
             (int)this->hom(l));
   }
@@ -1403,7 +1514,11 @@ static int visc_guess(hbf_ctx* c, double beta, double* x, double* r, double* rn,
   const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
   auto step_along = [&](const float* d, int bit) -> int {
     const float* e0 = L0.feta;
-    launch3(c, kSlotVector, k_visc_op3<D, float, true>, grd, blk, d, (const float*)nullptr, w, e0, e0, e0, L0.g,
+    if (any_per(c->g))
+      launch3(c, kSlotVector, k_visc_op3<D, float, true, true>, grd, blk, d, (const float*)nullptr, w, e0, e0, e0, L0.g,
+            fbeta, 1);
+    else
+      launch3(c, kSlotVector, k_visc_op3<D, float, true, false>, grd, blk, d, (const float*)nullptr, w, e0, e0, e0, L0.g,
             fbeta, 1);
     const double rw = reduce_dot_f(c, cur, w, n, &st);
     if (st) return st;
@@ -1467,7 +1582,11 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
   const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
   auto apply0 = [&](const float* q, float* o) {
     const float* e0 = L0.feta;
-    launch3(c, kSlotViscResid, k_visc_op3<D, float, true>, grd, blk, q, (const float*)nullptr, o, e0, e0, e0, L0.g,
+    if (any_per(c->g))
+      launch3(c, kSlotViscResid, k_visc_op3<D, float, true, true>, grd, blk, q, (const float*)nullptr, o, e0, e0, e0, L0.g,
+            fbeta, 1);
+    else
+      launch3(c, kSlotViscResid, k_visc_op3<D, float, true, false>, grd, blk, q, (const float*)nullptr, o, e0, e0, e0, L0.g,
             fbeta, 1);
   };
   if ((st = cuda_check(c, cudaMemcpyAsync(kb, b_in, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy rhs")))
@@ -1592,7 +1711,11 @@ static int solve_viscous_d(hbf_ctx* c, double beta, const double* b_in, double* 
   auto apply0 = [&](const double* q, double* out_) {
     const dim3 blk(256, 1, 1);
     const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
-    launch3(c, l0slot(), k_visc_op3<D, double>, grd, blk, q, (const double*)nullptr, out_, (const double*)L0.ef[0],
+    if (any_per(c->g))
+      launch3(c, l0slot(), k_visc_op3<D, double, false, true>, grd, blk, q, (const double*)nullptr, out_, (const double*)L0.ef[0],
+            (const double*)L0.ef[1], (const double*)L0.ef[2], L0.g, beta, 1);
+    else
+      launch3(c, l0slot(), k_visc_op3<D, double, false, false>, grd, blk, q, (const double*)nullptr, out_, (const double*)L0.ef[0],
             (const double*)L0.ef[1], (const double*)L0.ef[2], L0.g, beta, 1);
   };
   if ((st = cuda_check(c, cudaMemcpyAsync(kb, b_in, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy rhs")))

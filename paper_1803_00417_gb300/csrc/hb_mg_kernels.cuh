@@ -35,7 +35,10 @@ struct FaceEta {
   const T* const* ef;
   __host__ __device__ T lo(const Geom& g, const Strides& S, int a, const int* p, int id) const;
   __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
-  __host__ __device__ T at(const Geom& g, int a, const int* q) const { return ef[a][fidx(g, a, q[0], q[1], q[2])]; }
+  template <bool PER = true>
+  __host__ __device__ T at(const Geom& g, int a, const int* q) const {
+    return ef[a][fidx(g, a, q[0], q[1], q[2])];
+  }
 };
 
 template <typename T>
@@ -44,9 +47,10 @@ struct CellEta {
   const T* eta;
   __host__ __device__ T lo(const Geom& g, const Strides& S, int a, const int* p, int id) const;
   __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
+  template <bool PER = true>
   __host__ __device__ T at(const Geom& g, int a, const int* q) const {
     int L[3] = {q[0], q[1], q[2]}, R[3] = {q[0], q[1], q[2]};
-    if (g.per[a]) {  // periodic: the two cells across the face, wrapped
+    if (PER && g.per[a]) {  // periodic: the two cells across the face, wrapped
       L[a] = wrap_cell(q[a] - 1, g.n[a]);
       R[a] = wrap_cell(q[a], g.n[a]);
     } else {
@@ -59,11 +63,11 @@ struct CellEta {
 
 // component comp at cell q, which lies inside the domain on every axis but
 // ax: uget with the one reflection test that can apply
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ T uget_axis(const T* __restrict__ uc, const Geom& g, int comp, int i, int j, int k,
                                                 int ax, bool hom) {
   int q[3] = {i, j, k};
-  if (g.per[ax]) {
+  if (PER && g.per[ax]) {
     q[ax] = wrap_cell(q[ax], g.n[ax]);
     return uc[cidx<D>(g, q[0], q[1], q[2])];
   }
@@ -81,29 +85,32 @@ __host__ __device__ __forceinline__ T uget_axis(const T* __restrict__ uc, const 
   return T(2) * ub - v;
 }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
                                   bool hom) {
   // mean of the two cells' central differences, (dL + dR)/2 with dL, dR over 2h;
   // on a wall axis L and L + e_a are inside the domain (a wall face gives 0),
   // on a periodic axis they are wrapped, so only the c offsets can leave it
-  if (!g.per[a] && (L[a] < 0 || L[a] >= g.n[a] - 1)) return T(0);
+  const bool pa = PER && g.per[a];
+  if (!pa && (L[a] < 0 || L[a] >= g.n[a] - 1)) return T(0);
   int p1[3] = {L[0], L[1], L[2]}, p0[3] = {L[0], L[1], L[2]};
-  if (g.per[a]) p1[a] = p0[a] = wrap_cell(L[a], g.n[a]);
+  if (pa) p1[a] = p0[a] = wrap_cell(L[a], g.n[a]);
   p1[c] += 1;
   p0[c] -= 1;
-  T dL = uget_axis<D>(ua, g, a, p1[0], p1[1], p1[2], c, hom) - uget_axis<D>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
-  if (g.per[a]) {
+  T dL = uget_axis<D, T, PER>(ua, g, a, p1[0], p1[1], p1[2], c, hom) -
+         uget_axis<D, T, PER>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
+  if (pa) {
     p1[a] = p0[a] = wrap_cell(L[a] + 1, g.n[a]);
   } else {
     p1[a] += 1;
     p0[a] += 1;
   }
-  T dR = uget_axis<D>(ua, g, a, p1[0], p1[1], p1[2], c, hom) - uget_axis<D>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
+  T dR = uget_axis<D, T, PER>(ua, g, a, p1[0], p1[1], p1[2], c, hom) -
+         uget_axis<D, T, PER>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
   return (dL + dR) * g_q4<T>(g);
 }
 
-template <int D, typename T, typename EF>
+template <int D, typename T, bool PER = true, typename EF>
 __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& ef, const Geom& g, int c,
                                     const int* p, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
@@ -118,13 +125,14 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& 
       L[a] += s - 1;
       int R[3] = {L[0], L[1], L[2]};
       R[a] += 1;
-      T e = ef.at(g, a, R);
+      T e = ef.template at<PER>(g, a, R);
       // L and R differ from the cell p only along a
-      T nrm = (uget_axis<D>(uc, g, c, R[0], R[1], R[2], a, hom) - uget_axis<D>(uc, g, c, L[0], L[1], L[2], a, hom)) * ih;
+      T nrm = (uget_axis<D, T, PER>(uc, g, c, R[0], R[1], R[2], a, hom) -
+               uget_axis<D, T, PER>(uc, g, c, L[0], L[1], L[2], a, hom)) * ih;
       if (a == c)
         flux[s] = e * (T(2) * nrm);
       else
-        flux[s] = e * (nrm + mg_face_cross<D, T>(u + (size_t)a * g.ncell, g, a, c, L, hom));
+        flux[s] = e * (nrm + mg_face_cross<D, T, PER>(u + (size_t)a * g.ncell, g, a, c, L, hom));
     }
     acc += (flux[1] - flux[0]) * ih;
   }
@@ -193,7 +201,7 @@ __host__ __device__ __forceinline__ double rn_fma<double>(double a, double b, do
 }
 
 // Gauss-Seidel update of component c at cell p (all other values frozen)
-template <int D, typename T, typename EF>
+template <int D, typename T, bool PER = true, typename EF>
 __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const EF& ef,
                                   const Geom& g, int c, const int* p, T beta, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
@@ -213,14 +221,15 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
         q[a] += 1;
         fq[a] += 1;
       }
-      T wf = kappa * ef.at(g, a, fq) * ihh;
-      bool wall = !g.per[a] && ((s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1));
+      T wf = kappa * ef.template at<PER>(g, a, fq) * ihh;
+      const bool pa = PER && g.per[a];
+      bool wall = !pa && ((s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1));
       if (wall) {
         T ub = hom ? T(0) : g_wu<T>(g, a, s, c);
         offd = rn_fma(rn_mul(T(2), wf), ub, offd);
         diag = rn_fma(T(2), wf, diag);
       } else {
-        if (g.per[a]) q[a] = wrap_cell(q[a], g.n[a]);
+        if (pa) q[a] = wrap_cell(q[a], g.n[a]);
         offd = rn_fma(wf, uc[cidx<D>(g, q[0], q[1], q[2])], offd);
         diag = rn_add(diag, wf);
       }
@@ -235,8 +244,8 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
     Llo[a] -= 1;
     int fhi[3] = {p[0], p[1], p[2]};
     fhi[a] += 1;
-    T fluxhi = rn_mul(ef.at(g, a, fhi), mg_face_cross<D, T>(ua, g, a, c, p, hom));
-    T fluxlo = rn_mul(ef.at(g, a, p), mg_face_cross<D, T>(ua, g, a, c, Llo, hom));
+    T fluxhi = rn_mul(ef.template at<PER>(g, a, fhi), mg_face_cross<D, T, PER>(ua, g, a, c, p, hom));
+    T fluxlo = rn_mul(ef.template at<PER>(g, a, p), mg_face_cross<D, T, PER>(ua, g, a, c, Llo, hom));
     cross = rn_fma(rn_add(fluxhi, -fluxlo), ih, cross);
   }
   // explicitly rounded (see rn_fma): the same result wherever it is inlined
@@ -426,7 +435,7 @@ __host__ __device__ inline int rb_count(const Geom& g) {
 }
 
 // Gauss-Seidel update of component C at cell p of the current colour
-template <int D, typename T, int C, typename EF>
+template <int D, typename T, int C, bool PER = true, typename EF>
 __host__ __device__ __forceinline__ void visc_smooth_cell(T* __restrict__ u, const T* __restrict__ b, const EF& ef,
                                                           const Geom& g, T beta, int hom, const int* p) {
   T v;
@@ -434,19 +443,19 @@ __host__ __device__ __forceinline__ void visc_smooth_cell(T* __restrict__ u, con
     const Strides S = make_strides(g);
     v = visc_gs_interior<D, T>(u, b, ef, g, S, C, p, beta);
   } else {
-    v = visc_gs_point<D, T>(u, b, ef, g, C, p, beta, hom != 0);
+    v = visc_gs_point<D, T, PER>(u, b, ef, g, C, p, beta, hom != 0);
   }
   u[(size_t)C * g.ncell + cidx<D>(g, p[0], p[1], p[2])] = v;
 }
 
-template <int D, typename T, int C>
+template <int D, typename T, int C, bool PER = true>
 __host__ __device__ __forceinline__ void k_visc_smooth_c_at(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
                                                            const T* ef1, const T* ef2, const Geom& g, int col, T beta,
                                                            int hom, int t) {
   int p[3];
   if (!rb_cell<D>(g, t, col, p)) return;
   const T* ef[3] = {ef0, ef1, ef2};
-  visc_smooth_cell<D, T, C>(u, b, FaceEta<T>{ef}, g, beta, hom, p);
+  visc_smooth_cell<D, T, C, PER>(u, b, FaceEta<T>{ef}, g, beta, hom, p);
 }
 
 // Thread -> cell maps that keep the x-wall cells out of the warps of x-interior
@@ -548,7 +557,7 @@ __host__ __device__ inline bool rbx_cell(const Geom& g, int t, int col, int* p) 
 // time.  (A grid-stride launch of about 24 blocks per SM measured faster than
 // one thread per cell.)  CE: ef0 is the cell viscosity (CellEta), else the
 // face arrays.
-template <int D, typename T, int C, bool CE = false>
+template <int D, typename T, int C, bool CE = false, bool PER = true>
 __global__ void __launch_bounds__(256, CE ? 6 : 8) k_visc_smooth_c(T* __restrict__ u, const T* __restrict__ b, const T* ef0,
                                                       const T* ef1, const T* ef2, const __grid_constant__ Geom g, int col, T beta, int hom) {
   const int nt = rbx_count<D>(g);
@@ -557,16 +566,16 @@ __global__ void __launch_bounds__(256, CE ? 6 : 8) k_visc_smooth_c(T* __restrict
     int p[3];
     if (!rbx_cell<D>(g, t, col, p)) continue;
     if (CE)
-      visc_smooth_cell<D, T, C>(u, b, CellEta<T>{ef0}, g, beta, hom, p);
+      visc_smooth_cell<D, T, C, PER>(u, b, CellEta<T>{ef0}, g, beta, hom, p);
     else
-      visc_smooth_cell<D, T, C>(u, b, FaceEta<T>{ef}, g, beta, hom, p);
+      visc_smooth_cell<D, T, C, PER>(u, b, FaceEta<T>{ef}, g, beta, hom, p);
   }
 }
 
 // out = u - beta L u, or r = b - (u - beta L u) when b != nullptr, for every
 // component of cell p (flat index t).  Interior cells and wall cells are two
 // separate branches (warps are almost always uniform).
-template <int D, typename T, typename EF>
+template <int D, typename T, bool PER = true, typename EF>
 __host__ __device__ __forceinline__ void visc_op_cell(const T* __restrict__ u, const T* __restrict__ b,
                                                      T* __restrict__ out, const EF& ef, const Geom& g, T beta,
                                                      int hom, const int* p, int t) {
@@ -583,27 +592,27 @@ __host__ __device__ __forceinline__ void visc_op_cell(const T* __restrict__ u, c
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       const size_t o = (size_t)c * g.ncell + t;
-      const T Lu = mg_tensor_point<D, T>(u, ef, g, c, p, hom != 0);
+      const T Lu = mg_tensor_point<D, T, PER>(u, ef, g, c, p, hom != 0);
       const T Au = u[o] - beta * Lu;
       out[o] = b ? b[o] - Au : Au;
     }
   }
 }
 
-template <int D, typename T>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ void k_visc_op_at(const T* __restrict__ u, const T* __restrict__ b,
                                                      T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
                                                      const Geom& g, T beta, int hom, int t) {
   const T* ef[3] = {ef0, ef1, ef2};
   int p[3];
   cell_coords<D>(g, t, p[0], p[1], p[2]);
-  visc_op_cell<D, T>(u, b, out, FaceEta<T>{ef}, g, beta, hom, p, t);
+  visc_op_cell<D, T, PER>(u, b, out, FaceEta<T>{ef}, g, beta, hom, p, t);
 }
 
 // out = u - beta L u, or r = b - (u - beta L u) when b != nullptr; one thread
 // per cell, x-interior cells first (xi_cell), op3_blocks(g) blocks of 256.
 // CE: ef0 is the cell viscosity (CellEta), else the face arrays.
-template <int D, typename T, bool CE = false>
+template <int D, typename T, bool CE = false, bool PER = true>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CE ? 4 : 5) : 4) k_visc_op3(const T* __restrict__ u, const T* __restrict__ b,
                                                  T* __restrict__ out, const T* ef0, const T* ef1, const T* ef2,
                                                  const __grid_constant__ Geom g, T beta, int hom) {
@@ -612,9 +621,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CE ? 4 : 5) : 4) k_visc
   if (t >= xi_count<D>(g) || !xi_cell<D>(g, t, p)) return;
   const T* ef[3] = {ef0, ef1, ef2};
   if (CE)
-    visc_op_cell<D, T>(u, b, out, CellEta<T>{ef0}, g, beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
+    visc_op_cell<D, T, PER>(u, b, out, CellEta<T>{ef0}, g, beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
   else
-    visc_op_cell<D, T>(u, b, out, FaceEta<T>{ef}, g, beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
+    visc_op_cell<D, T, PER>(u, b, out, FaceEta<T>{ef}, g, beta, hom, p, cidx<D>(g, p[0], p[1], p[2]));
 }
 
 template <int D>

@@ -111,41 +111,42 @@ struct TailTabs {
 // order as the level-by-level launches; the small levels of all cavities then
 // cost one launch per V-cycle instead of about twenty per level.
 // ---------------------------------------------------------------------------
-template <int D, typename T, int C>
+template <int D, typename T, int C, bool PER>
 __device__ __forceinline__ void tail_visc_colours(const ViscArg<T>& a) {
   const int nt = rb_count<D>(a.g);
   for (int col = 0; col < 2; ++col) {
     for (int t = threadIdx.x; t < nt; t += blockDim.x)
-      k_visc_smooth_c_at<D, T, C>(a.x, a.b, a.ef[0], a.ef[1], a.ef[2], a.g, col, a.beta, a.hom, t);
+      k_visc_smooth_c_at<D, T, C, PER>(a.x, a.b, a.ef[0], a.ef[1], a.ef[2], a.g, col, a.beta, a.hom, t);
     __syncthreads();
   }
 }
 
-template <int D, typename T, int KIND>
+template <int D, typename T, int KIND, bool PER>
 __device__ __forceinline__ void tail_smooth(const TailTabs& tb, int l, int c) {
   if (KIND == kVisc) {
     const ViscArg<T>& a = ((const ViscArg<T>*)tb.lv[l])[c];
-    tail_visc_colours<D, T, 0>(a);
-    tail_visc_colours<D, T, 1>(a);
-    if (D == 3) tail_visc_colours<D, T, (D == 3 ? 2 : 0)>(a);
+    tail_visc_colours<D, T, 0, PER>(a);
+    tail_visc_colours<D, T, 1, PER>(a);
+    if (D == 3) tail_visc_colours<D, T, (D == 3 ? 2 : 0), PER>(a);
   } else if (KIND == kMac) {
     const PoisArg<T>& a = ((const PoisArg<T>*)tb.lv[l])[c];
     const int nt = rb_count<D>(a.g);
     for (int col = 0; col < 2; ++col) {
-      for (int t = threadIdx.x; t < nt; t += blockDim.x) k_cell_smooth_at<D, T>(a.x, a.b, a.g, col, t);
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) k_cell_smooth_at<D, T, PER>(a.x, a.b, a.g, col, t);
       __syncthreads();
     }
   } else {
     const PoisArg<T>& a = ((const PoisArg<T>*)tb.lv[l])[c];
     for (int col = 0; col < (1 << D); ++col) {
       const int nt = mc_count<D>(a.g, col);
-      for (int t = threadIdx.x; t < nt; t += blockDim.x) k_nodal_smooth_at<D, T>(a.x, a.b, a.g, col, t);
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) k_nodal_smooth_at<D, T, PER>(a.x, a.b, a.g, col, t);
       __syncthreads();
     }
   }
 }
 
-template <int D, typename T, int KIND>
+// PER = false: every level of every cavity has walls on every axis
+template <int D, typename T, int KIND, bool PER = true>
 __global__ void __launch_bounds__(256) k_vcycle_tail(TailTabs tb, int lf, int ncav,
                                                            const int* __restrict__ mask, int nu1, int nu2) {
   const int c = blockIdx.x;
@@ -154,23 +155,23 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(TailTabs tb, int lf, int nc
   const int L = bot.level;
   if (L < lf) return;
   for (int l = lf; l < L; ++l) {
-    for (int s = 0; s < nu1; ++s) tail_smooth<D, T, KIND>(tb, l, c);
+    for (int s = 0; s < nu1; ++s) tail_smooth<D, T, KIND, PER>(tb, l, c);
     if (KIND == kVisc) {
       const ViscArg<T>& a = ((const ViscArg<T>*)tb.lv[l])[c];
       for (int t = threadIdx.x; t < a.g.ncell; t += blockDim.x)
-        k_visc_op_at<D, T>(a.x, a.b, a.out, a.ef[0], a.ef[1], a.ef[2], a.g, a.beta, a.hom, t);
+        k_visc_op_at<D, T, PER>(a.x, a.b, a.out, a.ef[0], a.ef[1], a.ef[2], a.g, a.beta, a.hom, t);
     } else {
       const PoisArg<T>& a = ((const PoisArg<T>*)tb.lv[l])[c];
       if (KIND == kMac)
-        for (int t = threadIdx.x; t < a.g.ncell; t += blockDim.x) k_cell_resid_at<D, T>(a.x, a.b, a.r, a.g, t);
+        for (int t = threadIdx.x; t < a.g.ncell; t += blockDim.x) k_cell_resid_at<D, T, PER>(a.x, a.b, a.r, a.g, t);
       else
-        for (int t = threadIdx.x; t < a.g.nnode; t += blockDim.x) k_nodal_resid_at<D, T>(a.x, a.b, a.r, a.g, t);
+        for (int t = threadIdx.x; t < a.g.nnode; t += blockDim.x) k_nodal_resid_at<D, T, PER>(a.x, a.b, a.r, a.g, t);
     }
     __syncthreads();
     const XferArg<T>& r = ((const XferArg<T>*)tb.re[l])[c];
     if (KIND == kNodal) {
       for (int t = threadIdx.x; t < r.gc.nnode; t += blockDim.x) {
-        k_restrict_nodes_at<D, T>(r.src, r.dst, r.gf, r.gc, t);
+        k_restrict_nodes_at<D, T, PER>(r.src, r.dst, r.gf, r.gc, t);
         r.zero[t] = T(0);
       }
     } else {
@@ -190,10 +191,10 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(TailTabs tb, int lf, int nc
     } else {
       const int n = q.ncomp * q.gf.ncell;
       for (int t = threadIdx.x; t < n; t += blockDim.x)
-        k_prolong_cells_add_at<D, T>(q.dst, q.src, q.gf, q.gc, q.ncomp, T(q.sign), t);
+        k_prolong_cells_add_at<D, T, PER>(q.dst, q.src, q.gf, q.gc, q.ncomp, T(q.sign), t);
     }
     __syncthreads();
-    for (int s = 0; s < nu2; ++s) tail_smooth<D, T, KIND>(tb, l, c);
+    for (int s = 0; s < nu2; ++s) tail_smooth<D, T, KIND, PER>(tb, l, c);
   }
 }
 

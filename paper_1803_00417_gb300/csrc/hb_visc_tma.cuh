@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(kThreads) k_visc_smooth_tma(const __grid_const
     if (tid >= kWallRows || row >= n1 * nz) return;
     const int k = z0 + row / n1, j = row - (row / n1) * n1;
     int p[3] = {0, j, k};
-    if (((j + k + col) & 1) == 0) visc_smooth_cell<3, float, C>(u, b, ce, g, beta, hom, p);
+    if (((j + k + col) & 1) == 0) visc_smooth_cell<3, float, C, false>(u, b, ce, g, beta, hom, p);
     p[0] = n0 - 1;
-    if (n0 > 1 && ((n0 - 1 + j + k + col) & 1) == 0) visc_smooth_cell<3, float, C>(u, b, ce, g, beta, hom, p);
+    if (n0 > 1 && ((n0 - 1 + j + k + col) & 1) == 0) visc_smooth_cell<3, float, C, false>(u, b, ce, g, beta, hom, p);
     return;
   }
 
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_visc_smooth_tma(const __grid_const
         if (jr >= TY || j >= n1 || i >= n0 - 1 || i == 0) continue;
         int p[3] = {i, j, k};
         if (j == 0 || j == n1 - 1 || k == 0 || k == n2 - 1) {
-          visc_smooth_cell<3, float, C>(u, b, ce, g, beta, hom, p);
+          visc_smooth_cell<3, float, C, false>(u, b, ce, g, beta, hom, p);
           continue;
         }
         const int sx = i - x0 + kHX, sy = jr + 1;
