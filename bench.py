@@ -96,6 +96,9 @@ def parse():
     ap.add_argument("--staged-sweep", default="0",
                     help="TMA-staged finest-level viscous sweeps: 'TX,TZ' (tile width 64 or 128, planes per block) "
                          "or 0 (hbf_set_staged_sweep)")
+    ap.add_argument("--staged-op", default="0",
+                    help="TMA-staged finest-level viscous operator: 'ROWS,TZ' (tile 64 x ROWS, ROWS 4 or 8, planes "
+                         "per block) or 0 (hbf_set_staged_op)")
     ap.add_argument("--fused-sweeps", action="store_true",
                     help="smooth the 3D FP32 finest level with the one-launch red-black sweep (hbf_set_fused_sweep)")
     ap.add_argument("--breakdown", action="store_true",
@@ -411,6 +414,8 @@ def run_ours(args):
     sim.set_fused_sweep(args.fused_sweeps)
     staged = [int(v) for v in str(args.staged_sweep).split(",")] if args.staged_sweep != "0" else [0, 16]
     sim.set_staged_sweep(staged[0], staged[1] if len(staged) > 1 else 16)
+    sop = [int(v) for v in str(args.staged_op).split(",")] if args.staged_op != "0" else [0, 16]
+    sim.set_staged_op(sop[0], sop[1] if len(sop) > 1 else 16)
     zeros_u = np.zeros(d * ncell)
     zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
     sim.set_field("U", zeros_u)
@@ -619,6 +624,8 @@ def run_ours(args):
                        "viscous_sweeps": ("one-launch fused" if args.fused_sweeps else
                                           f"TMA-staged {staged[0]}x8 tiles, {staged[1]} planes per block"
                                           if staged[0] else "two launches per component, unstaged"),
+                       "viscous_operator": (f"TMA-staged 64x{sop[0]} tiles, {sop[1]} planes per block" if sop[0]
+                                            else "unstaged, one thread per cell"),
                        "cycles_per_step": {k: v / args.steps for k, v in cycles.items()},
                        "converged": bool(converged)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -169,6 +169,16 @@ int hbf_set_fused_sweep(hbf_ctx* ctx, int on);
  * stops updating and the viscous solve returns HBF_ERR_TIMEOUT.
  * HBF_ERR_ARG for another width or tile_z outside [1, 4096]. */
 int hbf_set_staged_sweep(hbf_ctx* ctx, int tile_x, int tile_z);
+/* The 3D FP32 finest-level viscous operator u - beta L_eta u and residual
+ * b - (u - beta L_eta u) of the mixed solve (the BiCGStab products and the
+ * preconditioner's finest residual) with their operands staged the same way:
+ * tiles of 64 x rows cells (rows 4 or 8) and tile_z planes per block.  Every
+ * interior cell's value is the same arithmetic on the same values as in the
+ * unstaged operator (bit for bit).  Taken under the rules of
+ * hbf_set_staged_sweep; rows = 0 disables it.  A block whose bounded wait
+ * gives up stops and the viscous solve returns HBF_ERR_TIMEOUT.  HBF_ERR_ARG
+ * for other rows or tile_z outside [1, 4096]. */
+int hbf_set_staged_op(hbf_ctx* ctx, int rows, int tile_z);
 
 /* Number of doubles of a field (see enum hbf_field), or a negative status. */
 int64_t hbf_field_size(const hbf_ctx* ctx, int which);

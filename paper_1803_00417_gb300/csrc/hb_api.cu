@@ -468,6 +468,15 @@ int hbf_set_staged_sweep(hbf_ctx* c, int tile_x, int tile_z) {
   return HBF_OK;
 }
 
+int hbf_set_staged_op(hbf_ctx* c, int rows, int tile_z) {
+  if (!c) return HBF_ERR_ARG;
+  if ((rows != 0 && rows != 4 && rows != 8) || tile_z < 1 || tile_z > 4096)
+    return fail(c, HBF_ERR_ARG, "staged operator tile: rows 0, 4 or 8, 1 <= planes <= 4096");
+  c->staged_op_rows = rows;
+  c->staged_op_tz = tile_z;
+  return HBF_OK;
+}
+
 int hbf_set_tail(hbf_ctx* c, int max_cells) {
   if (!c) return HBF_ERR_ARG;
   if (max_cells < 0) return fail(c, HBF_ERR_ARG, "negative tail size");

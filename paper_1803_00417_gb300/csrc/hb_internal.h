@@ -101,6 +101,8 @@ struct hbf_ctx {
   int fused_sweep = 0;      // FP32 finest-level viscous sweeps in one launch per component (3D)
   int staged_tx = 0;        // FP32 finest-level viscous sweeps staged by TMA: tile width 64 or 128, 0 off (3D)
   int staged_tz = 16;       // planes per block of the staged sweeps
+  int staged_op_rows = 0;   // FP32 finest-level viscous operator staged by TMA: tile 64 x 4 or 64 x 8, 0 off (3D)
+  int staged_op_tz = 16;    // planes per block of the staged operator
   int* sweep_err = nullptr; // set by a staged sweep whose bounded wait gave up
   double K = 1.0;           // the consistency K as given to hbf_set_rheology
   double theta = 0.5;       // implicit weight of the viscous term (1/2: Crank-Nicolson, Eq. 15)

@@ -939,6 +939,9 @@ static bool run_tail(hbf_ctx* c, int l, double beta) {
   return true;
 }
 
+static bool staged_op(hbf_ctx* c, int slot, const float* u, const float* b, float* out, const float* eta,
+                      const Geom& g, float beta, int hm);
+
 template <int D, typename T>
 struct ViscProblem : Problem<T> {
   using Problem<T>::c;
@@ -1033,6 +1036,8 @@ struct ViscProblem : Problem<T> {
     const dim3 grd(op3_blocks<D>(L.g), 1, 1);
     if (cell_eta(l)) {
       const T* e0 = (const T*)L.feta;
+      if constexpr (std::is_same<T, float>::value)
+        if (staged_op(c, kSlotViscResid, x(l), b(l), r(l), L.feta, L.g, (float)beta, (int)this->hom(l))) return;
       if (any_per(c->g))
         launch3(c, kSlotViscResid, k_visc_op3<D, T, true, true>, grd, blk, (const T*)x(l), (const T*)b(l), r(l), e0, e0, e0,
               L.g, (T)beta, (int)this->hom(l));
@@ -1158,8 +1163,40 @@ bool ViscProblem<D, T>::staged_sweeps(int l, int hm) {
   return false;
 }
 
+// u - beta L u (b == nullptr) or b - (u - beta L u) on the 3D FP32 finest
+// level with the planes staged by TMA (hb_visc_tma.cuh): tile 64 x rows,
+// ring of 4 stages; false (nothing launched) when the staged operator is off,
+// an axis is periodic, or the arrays do not meet the layout rules
+template <int TY>
+static bool staged_op_launch(hbf_ctx* c, int slot, const float* u, const float* b, float* out, const float* eta,
+                             const Geom& g, float beta, int hm) {
+  constexpr int TX = 64, NS = 4;
+  using Lay = tma::Layout<TX, TY, false>;
+  CUtensorMap mu, me;
+  if (!encode_cells(&mu, u, g, 3, Lay::PX, Lay::PY, 3) || !encode_cells(&me, eta, g, 0, Lay::PX, Lay::PY, 1))
+    return false;
+  auto kern = tma::k_visc_op_tma<TX, TY, NS>;
+  static std::atomic<bool> attr{false};
+  const int smem = Lay::smem(NS);
+  if (!attr.load()) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
+    attr.store(true);
+  }
+  const tma::SweepGrid sg = tma::sweep_grid<TX, TY>(g, c->staged_op_tz);
+  launch_smem(c, slot, kern, dim3((unsigned)sg.blocks(), 1, 1), dim3(tma::kThreads, 1, 1), (size_t)smem, mu, me, u, b,
+              out, eta, g, sg, beta, hm, c->sweep_err);
+  return true;
+}
+
+static bool staged_op(hbf_ctx* c, int slot, const float* u, const float* b, float* out, const float* eta,
+                      const Geom& g, float beta, int hm) {
+  if (c->dim != 3 || c->staged_op_rows == 0 || any_per(g) || !c->sweep_err || !eta) return false;
+  if (c->staged_op_rows == 4) return staged_op_launch<4>(c, slot, u, b, out, eta, g, beta, hm);
+  return staged_op_launch<8>(c, slot, u, b, out, eta, g, beta, hm);
+}
+
 static int take_sweep_err(hbf_ctx* c) {
-  if (!c->sweep_err || c->staged_tx == 0) return HBF_OK;
+  if (!c->sweep_err || (c->staged_tx == 0 && c->staged_op_rows == 0)) return HBF_OK;
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, c->sweep_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1514,7 +1551,9 @@ static int visc_guess(hbf_ctx* c, double beta, double* x, double* r, double* rn,
   const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
   auto step_along = [&](const float* d, int bit) -> int {
     const float* e0 = L0.feta;
-    if (any_per(c->g))
+    if (staged_op(c, kSlotVector, d, nullptr, w, e0, L0.g, fbeta, 1))
+      ;
+    else if (any_per(c->g))
       launch3(c, kSlotVector, k_visc_op3<D, float, true, true>, grd, blk, d, (const float*)nullptr, w, e0, e0, e0, L0.g,
             fbeta, 1);
     else
@@ -1582,6 +1621,7 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
   const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
   auto apply0 = [&](const float* q, float* o) {
     const float* e0 = L0.feta;
+    if (staged_op(c, kSlotViscResid, q, nullptr, o, e0, L0.g, fbeta, 1)) return;
     if (any_per(c->g))
       launch3(c, kSlotViscResid, k_visc_op3<D, float, true, true>, grd, blk, q, (const float*)nullptr, o, e0, e0, e0, L0.g,
             fbeta, 1);

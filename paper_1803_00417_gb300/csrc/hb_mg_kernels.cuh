@@ -19,6 +19,67 @@ namespace hb {
 // ---------------------------------------------------------------------------
 // tensor viscous operator pieces (mirrors the explicit-stage operator)
 // ---------------------------------------------------------------------------
+// Explicitly rounded operations (round to nearest): the compiler may not
+// contract or reorder them, so every kernel that inlines the Gauss-Seidel
+// point updates below (visc_gs_point, visc_gs_core) issues the same
+// operations in the same order and gets the same bits.  On the host (the
+// host-built checks) they are the plain operations and an exact fused
+// multiply-add.
+template <typename T>
+__host__ __device__ __forceinline__ T rn_mul(T a, T b);
+template <typename T>
+__host__ __device__ __forceinline__ T rn_add(T a, T b);
+template <typename T>
+__host__ __device__ __forceinline__ T rn_fma(T a, T b, T c);
+template <>
+__host__ __device__ __forceinline__ float rn_mul<float>(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ double rn_mul<double>(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ float rn_add<float>(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ double rn_add<double>(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ float rn_fma<float>(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+template <>
+__host__ __device__ __forceinline__ double rn_fma<double>(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+  return __fma_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+
 struct Strides;
 
 // The face viscosities of a level, stored per face (FaceEta), or, on the
@@ -82,7 +143,7 @@ __host__ __device__ __forceinline__ T uget_axis(const T* __restrict__ uc, const 
   const T v = uc[cidx<D>(g, q[0], q[1], q[2])];
   if (side < 0) return v;
   const T ub = hom ? T(0) : g_wu<T>(g, ax, side, comp);
-  return T(2) * ub - v;
+  return rn_add(rn_mul(T(2), ub), -v);
 }
 
 template <int D, typename T, bool PER = true>
@@ -97,17 +158,17 @@ __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom&
   if (pa) p1[a] = p0[a] = wrap_cell(L[a], g.n[a]);
   p1[c] += 1;
   p0[c] -= 1;
-  T dL = uget_axis<D, T, PER>(ua, g, a, p1[0], p1[1], p1[2], c, hom) -
-         uget_axis<D, T, PER>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
+  T dL = rn_add(uget_axis<D, T, PER>(ua, g, a, p1[0], p1[1], p1[2], c, hom),
+                -uget_axis<D, T, PER>(ua, g, a, p0[0], p0[1], p0[2], c, hom));
   if (pa) {
     p1[a] = p0[a] = wrap_cell(L[a] + 1, g.n[a]);
   } else {
     p1[a] += 1;
     p0[a] += 1;
   }
-  T dR = uget_axis<D, T, PER>(ua, g, a, p1[0], p1[1], p1[2], c, hom) -
-         uget_axis<D, T, PER>(ua, g, a, p0[0], p0[1], p0[2], c, hom);
-  return (dL + dR) * g_q4<T>(g);
+  T dR = rn_add(uget_axis<D, T, PER>(ua, g, a, p1[0], p1[1], p1[2], c, hom),
+                -uget_axis<D, T, PER>(ua, g, a, p0[0], p0[1], p0[2], c, hom));
+  return rn_mul(rn_add(dL, dR), g_q4<T>(g));
 }
 
 template <int D, typename T, bool PER = true, typename EF>
@@ -127,77 +188,17 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& 
       R[a] += 1;
       T e = ef.template at<PER>(g, a, R);
       // L and R differ from the cell p only along a
-      T nrm = (uget_axis<D, T, PER>(uc, g, c, R[0], R[1], R[2], a, hom) -
-               uget_axis<D, T, PER>(uc, g, c, L[0], L[1], L[2], a, hom)) * ih;
+      T nrm = rn_mul(rn_add(uget_axis<D, T, PER>(uc, g, c, R[0], R[1], R[2], a, hom),
+                            -uget_axis<D, T, PER>(uc, g, c, L[0], L[1], L[2], a, hom)),
+                     ih);
       if (a == c)
-        flux[s] = e * (T(2) * nrm);
+        flux[s] = rn_mul(e, rn_mul(T(2), nrm));
       else
-        flux[s] = e * (nrm + mg_face_cross<D, T, PER>(u + (size_t)a * g.ncell, g, a, c, L, hom));
+        flux[s] = rn_mul(e, rn_add(nrm, mg_face_cross<D, T, PER>(u + (size_t)a * g.ncell, g, a, c, L, hom)));
     }
-    acc += (flux[1] - flux[0]) * ih;
+    acc = rn_add(acc, rn_mul(rn_add(flux[1], -flux[0]), ih));
   }
   return acc;
-}
-
-// Explicitly rounded operations (round to nearest): the compiler may not
-// contract or reorder them, so every kernel that inlines the Gauss-Seidel
-// point updates below (visc_gs_point, visc_gs_core) issues the same
-// operations in the same order and gets the same bits.  On the host (the
-// host-built checks) they are the plain operations and an exact fused
-// multiply-add.
-template <typename T>
-__host__ __device__ __forceinline__ T rn_mul(T a, T b);
-template <typename T>
-__host__ __device__ __forceinline__ T rn_add(T a, T b);
-template <typename T>
-__host__ __device__ __forceinline__ T rn_fma(T a, T b, T c);
-template <>
-__host__ __device__ __forceinline__ float rn_mul<float>(float a, float b) {
-#ifdef __CUDA_ARCH__
-  return __fmul_rn(a, b);
-#else
-  return a * b;
-#endif
-}
-template <>
-__host__ __device__ __forceinline__ double rn_mul<double>(double a, double b) {
-#ifdef __CUDA_ARCH__
-  return __dmul_rn(a, b);
-#else
-  return a * b;
-#endif
-}
-template <>
-__host__ __device__ __forceinline__ float rn_add<float>(float a, float b) {
-#ifdef __CUDA_ARCH__
-  return __fadd_rn(a, b);
-#else
-  return a + b;
-#endif
-}
-template <>
-__host__ __device__ __forceinline__ double rn_add<double>(double a, double b) {
-#ifdef __CUDA_ARCH__
-  return __dadd_rn(a, b);
-#else
-  return a + b;
-#endif
-}
-template <>
-__host__ __device__ __forceinline__ float rn_fma<float>(float a, float b, float c) {
-#ifdef __CUDA_ARCH__
-  return __fmaf_rn(a, b, c);
-#else
-  return std::fma(a, b, c);
-#endif
-}
-template <>
-__host__ __device__ __forceinline__ double rn_fma<double>(double a, double b, double c) {
-#ifdef __CUDA_ARCH__
-  return __fma_rn(a, b, c);
-#else
-  return std::fma(a, b, c);
-#endif
 }
 
 // Gauss-Seidel update of component c at cell p (all other values frozen)
@@ -374,38 +375,71 @@ __host__ __device__ __forceinline__ T visc_gs_interior(const T* __restrict__ u, 
   return visc_gs_core<D, T>(c, elo, ehi, ulo, uhi, xa, b[(size_t)c * g.ncell + id], bs);
 }
 
-// (L_eta u)_c for an interior cell: the operator of mg_tensor_point with the
-// 1/h of the differences and of the divergence taken out as one factor 1/h^2
-// (fewer multiplications; the FP64 residuals are bound by GB300's FP64 rate)
+// (L_eta u)_c of an interior cell on gathered values (the names of
+// visc_gs_core; u0 = u_c at the cell): the operator of mg_tensor_point with
+// the 1/h of the differences and of the divergence taken out as one factor
+// 1/h^2 (fewer multiplications; the FP64 residuals are bound by GB300's FP64
+// rate), scaled by sc = 1/h^2 times the accessor's factor.  Explicitly
+// rounded, like visc_gs_core: every caller that gathers the same values gets
+// the same bits.
+template <int D, typename T>
+__host__ __device__ __forceinline__ T tensor_core(int c, T u0, const T* elo, const T* ehi, const T* ulo, const T* uhi,
+                                                  const T (*xa)[6], T sc) {
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const T dlo = rn_add(u0, -ulo[a]);
+    const T dhi = rn_add(uhi[a], -u0);
+    T flo, fhi;
+    if (a == c) {
+      flo = rn_mul(elo[a], rn_mul(T(2), dlo));
+      fhi = rn_mul(ehi[a], rn_mul(T(2), dhi));
+    } else {
+      const T mid = rn_add(xa[a][0], -xa[a][1]);
+      const T xhi = rn_add(mid, rn_add(xa[a][2], -xa[a][3]));
+      const T xlo = rn_add(rn_add(xa[a][4], -xa[a][5]), mid);
+      flo = rn_mul(elo[a], rn_fma(T(0.25), xlo, dlo));
+      fhi = rn_mul(ehi[a], rn_fma(T(0.25), xhi, dhi));
+    }
+    acc = rn_add(acc, rn_add(fhi, -flo));
+  }
+  return rn_mul(acc, sc);
+}
+
+// (L_eta u)_c for an interior cell: direct strided indexing, no ghost logic
 template <int D, typename T, typename EF>
 __host__ __device__ __forceinline__ T tensor_interior(const T* __restrict__ u, const EF& ef, const Geom& g,
                                              const Strides& S, int c, const int* p) {
   const int id = cidx<D>(g, p[0], p[1], p[2]);
   const T* uc = u + (size_t)c * g.ncell;
-  const T u0 = uc[id];
-  T acc = T(0);
+  T elo[3], ehi[3], ulo[3], uhi[3], xa[3][6];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const int sa = S.s[a];
-    const T elo = ef.lo(g, S, a, p, id), ehi = ef.hi(g, S, a, p, id);
-    const T dlo = u0 - uc[id - sa];
-    const T dhi = uc[id + sa] - u0;
-    T flo, fhi;
-    if (a == c) {
-      flo = elo * (T(2) * dlo);
-      fhi = ehi * (T(2) * dhi);
-    } else {
-      const T* ua = u + (size_t)a * g.ncell;
-      const int sc = S.s[c];
-      const T mid = ua[id + sc] - ua[id - sc];
-      const T xhi = mid + (ua[id + sa + sc] - ua[id + sa - sc]);
-      const T xlo = (ua[id - sa + sc] - ua[id - sa - sc]) + mid;
-      flo = elo * (dlo + T(0.25) * xlo);
-      fhi = ehi * (dhi + T(0.25) * xhi);
-    }
-    acc += fhi - flo;
+    elo[a] = ef.lo(g, S, a, p, id);
+    ehi[a] = ef.hi(g, S, a, p, id);
+    ulo[a] = uc[id - S.s[a]];
+    uhi[a] = uc[id + S.s[a]];
   }
-  return acc * (g_ihh<T>(g) * T(EF::kScale));
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (a == c) continue;
+    const T* ua = u + (size_t)a * g.ncell;
+    const int sa = S.s[a], sc = S.s[c];
+    xa[a][0] = ua[id + sc];
+    xa[a][1] = ua[id - sc];
+    xa[a][2] = ua[id + sa + sc];
+    xa[a][3] = ua[id + sa - sc];
+    xa[a][4] = ua[id - sa + sc];
+    xa[a][5] = ua[id - sa - sc];
+  }
+  return tensor_core<D, T>(c, uc[id], elo, ehi, ulo, uhi, xa, g_ihh<T>(g) * T(EF::kScale));
+}
+
+// the operator's output from (L_eta u)_c: u - beta L u, or b - (u - beta L u)
+template <typename T>
+__host__ __device__ __forceinline__ T op_out(T u0, T Lu, T beta, const T* b, size_t o) {
+  const T Au = rn_fma(-beta, Lu, u0);
+  return b ? rn_add(b[o], -Au) : Au;
 }
 
 // thread t -> cell of red-black colour col (x index stride 2)
@@ -585,16 +619,14 @@ __host__ __device__ __forceinline__ void visc_op_cell(const T* __restrict__ u, c
     for (int c = 0; c < D; ++c) {
       const size_t o = (size_t)c * g.ncell + t;
       const T Lu = tensor_interior<D, T>(u, ef, g, S, c, p);
-      const T Au = u[o] - beta * Lu;
-      out[o] = b ? b[o] - Au : Au;
+      out[o] = op_out<T>(u[o], Lu, beta, b, o);
     }
   } else {
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       const size_t o = (size_t)c * g.ncell + t;
       const T Lu = mg_tensor_point<D, T, PER>(u, ef, g, c, p, hom != 0);
-      const T Au = u[o] - beta * Lu;
-      out[o] = b ? b[o] - Au : Au;
+      out[o] = op_out<T>(u[o], Lu, beta, b, o);
     }
   }
 }

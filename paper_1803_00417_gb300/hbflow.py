@@ -103,6 +103,7 @@ SIGNATURES = {
     "hbf_set_tail": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_set_fused_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_set_staged_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hbf_set_staged_op": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hbf_field_size": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "hbf_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -329,6 +330,10 @@ class HBFlow:
     def set_staged_sweep(self, tile_x, tile_z=16):
         """TMA-staged finest-level viscous sweeps (tile_x 64 or 128; 0 off)."""
         self._check(self.lib.hbf_set_staged_sweep(self.ctx, int(tile_x), int(tile_z)))
+
+    def set_staged_op(self, rows, tile_z=16):
+        """TMA-staged finest-level viscous operator (rows 4 or 8; 0 off)."""
+        self._check(self.lib.hbf_set_staged_op(self.ctx, int(rows), int(tile_z)))
 
     def set_tail(self, max_cells):
         """Levels from the first one with at most max_cells cells run as one

@@ -1,5 +1,6 @@
 """The TMA-staged red-black sweeps of the 3D FP32 finest level
-(hbf_set_staged_sweep) against the unstaged two-launch sweeps: from the same
+(hbf_set_staged_sweep) and the TMA-staged viscous operator
+(hbf_set_staged_op) against the unstaged kernels: from the same
 seeded states, cavity steps give the same velocity and pressure bit for bit
 and the same solver iteration counts (every interior update is the same
 arithmetic on the same values; the wall cells take the same global path).
@@ -42,6 +43,33 @@ CASES = [
 
 @pytest.mark.parametrize("n,seed,tx,tz", CASES)
 def test_staged_sweep_matches_unstaged(n, seed, tx, tz):
+    _check_staged(n, seed, lambda s: s.set_staged_sweep(tx, tz), f"sweep {tx}x8x{tz}")
+
+
+OP_CASES = [
+    ((40, 24, 34), 101, 4, 16),
+    ((64, 64, 64), 102, 8, 16),
+    ((136, 36, 24), 103, 8, 5),
+    ((20, 50, 12), 104, 4, 1),
+    ((36, 28, 30), 105, 4, 7),
+    ((18, 30, 12), 106, 8, 16),  # 18 % 4 != 0: unstaged
+]
+
+
+@pytest.mark.parametrize("n,seed,rows,tz", OP_CASES)
+def test_staged_operator_matches_unstaged(n, seed, rows, tz):
+    _check_staged(n, seed, lambda s: s.set_staged_op(rows, tz), f"operator 64x{rows}x{tz}")
+
+
+def test_staged_sweep_and_operator_together():
+    def both(s):
+        s.set_staged_sweep(64, 8)
+        s.set_staged_op(8, 8)
+
+    _check_staged((48, 40, 32), 107, both, "sweep and operator")
+
+
+def _check_staged(n, seed, enable, what):
     from paper_1803_00417_gb300.hbflow import MIXED, HBFlow
 
     cfg = cavity(n, Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)
@@ -51,7 +79,7 @@ def test_staged_sweep_matches_unstaged(n, seed, tx, tz):
         s = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=MIXED)
         s.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
         if staged:
-            s.set_staged_sweep(tx, tz)
+            enable(s)
         s.set_velocity(u)
         s.set_pressure(p)
         sims.append(s)
@@ -62,7 +90,7 @@ def test_staged_sweep_matches_unstaged(n, seed, tx, tz):
             assert st[0][k]["converged"] and st[1][k]["converged"], (k, st[0][k], st[1][k])
         ua, ub = sims[0].get_field("U"), sims[1].get_field("U")
         pa, pb = sims[0].get_field("P"), sims[1].get_field("P")
-        print(f"staged {tx}x8x{tz} vs unstaged {n}: max |du| {np.max(np.abs(ua - ub)):.3e}")
+        print(f"staged {what} vs unstaged {n}: max |du| {np.max(np.abs(ua - ub)):.3e}")
         assert np.array_equal(ua, ub)
         assert np.array_equal(pa, pb)
     g = Grid(cfg["n"], cfg["h"], wall_u=cfg["wall_u"])
@@ -79,7 +107,7 @@ def test_staged_sweep_matches_unstaged(n, seed, tx, tz):
         s.close()
 
 
-def test_staged_sweep_arguments():
+def test_staged_arguments():
     from paper_1803_00417_gb300.hbflow import MIXED, HBFlow, HBFlowError
 
     cfg = cavity((16, 16, 16), Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)
@@ -87,5 +115,9 @@ def test_staged_sweep_arguments():
     for bad in ((32, 16), (128, 0), (64, 5000)):
         with pytest.raises(HBFlowError):
             s.set_staged_sweep(*bad)
+    for bad in ((6, 16), (4, 0), (8, 5000)):
+        with pytest.raises(HBFlowError):
+            s.set_staged_op(*bad)
     s.set_staged_sweep(0)
+    s.set_staged_op(0)
     s.close()
