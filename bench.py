@@ -214,7 +214,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
-SMOOTHER_DRAM_BYTES_PER_CELL = (144.18e6 + 15.14e6) / 192 ** 3  # profiles/k_visc_smooth_cavity192.md
+SMOOTHER_DRAM_BYTES_PER_CELL = (144.20e6 + 15.16e6) / 192 ** 3  # profiles/k_visc_smooth_cavity192.md
 
 
 def visc_smoother_bytes(d, ncell, elem, cell_eta):
