@@ -581,7 +581,10 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     elem = 4 if prec == MIXED else 8
     sm_ms, sm_n = prof["visc_smooth"]
-    stages = {k: v[0] / args.prof_steps for k, v in prof.items() if v[1] > 0}
+    # the guess slot times whole sections whose launches also count in their
+    # own slots: reported beside the stages, not in their sum
+    guess_ms = prof["guess"][0] / args.prof_steps if prof["guess"][1] > 0 else None
+    stages = {k: v[0] / args.prof_steps for k, v in prof.items() if v[1] > 0 and k != "guess"}
     roofline = None
     if sm_n > 0:
         per_launch_s = sm_ms / sm_n / 1e3
@@ -636,6 +639,7 @@ def run_ours(args):
             "protocol": {"develop_steps": args.develop, "develop_seconds": develop_s, "warmup": args.warmup,
                          "timed_steps": args.steps, "instrumentation": "none in the timed steps"},
             "stage_ms_per_step": stages,
+            "learned_guess_ms_per_step": guess_ms,
             "instrumented_pass": {"steps": args.prof_steps, "level": lvl, "ms_per_step": prof_ms,
                                   "stages_sum_ms": sum(stages.values()),
                                   "stages_share": sum(stages.values()) / prof_ms}}

@@ -234,7 +234,9 @@ double hbf_cfl_dt(hbf_ctx* ctx, double cfl);
  *   3 nodal residual, 4 MAC smoother, 5 MAC residual (slots 0-5: finest level
  *   only), 6 explicit stages; with level 2 also 7 coarsest-level solves,
  *   8 transfers and conversions, 9 reductions, 10 Krylov vector updates,
- *   11 smoothing and residuals on coarse levels.
+ *   11 smoothing and residuals on coarse levels, 12 learned-guess sections
+ *   (the network passes, their transfers and the acceptance tests, timed as
+ *   whole regions whose launches also count in their own slots).
  * hbf_profile_enable(ctx, level) synchronises, clears the accumulators and
  * records at that level (0 off, 1 slots 0-6, 2 all); hbf_profile_read
  * synchronises and returns the summed device time in milliseconds and the

@@ -20,6 +20,13 @@ int cuda_check(hbf_ctx* c, cudaError_t e, const char* what) {
   return fail(c, e == cudaErrorMemoryAllocation ? HBF_ERR_OOM : HBF_ERR_CUDA, m);
 }
 
+ProfRegion::ProfRegion(hbf_ctx* ctx, int s) : c(ctx), slot(s), on(prof_wants(ctx->prof, s)) {
+  if (on) prof_mark(c, slot, true);
+}
+ProfRegion::~ProfRegion() {
+  if (on) prof_mark(c, slot, false);
+}
+
 void prof_mark(hbf_ctx* c, int slot, bool start) {
   Prof& P = c->prof;
   if (P.used[slot] + 2 > P.ev[slot].size()) {

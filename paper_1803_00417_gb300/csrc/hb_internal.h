@@ -56,7 +56,10 @@ enum ProfSlot {
   kSlotReduce = 9,
   kSlotVector = 10,
   kSlotCoarse = 11,
-  kSlotCount = 12,
+  // region slot (level 2): a whole learned-guess section, its launches
+  // included (they are also counted in their own slots)
+  kSlotGuess = 12,
+  kSlotCount = 13,
   kSlotNone = -1
 };
 
@@ -190,6 +193,15 @@ inline double visc_beta(double dt, double rho, double theta) {
 }
 
 void prof_mark(hbf_ctx* c, int slot, bool start);
+
+// brackets a whole section with one pair of events of a region slot
+struct ProfRegion {
+  hbf_ctx* c;
+  int slot;
+  bool on;
+  ProfRegion(hbf_ctx* ctx, int s);
+  ~ProfRegion();
+};
 
 // every kernel launch of the library goes through here: counts it and, when
 // profiling is on, brackets finest-level launches of a slot with events

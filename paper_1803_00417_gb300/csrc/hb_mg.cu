@@ -1536,6 +1536,7 @@ __global__ void k_diff_to_f32(float* __restrict__ out, const double* __restrict_
 // (mode 2).  *used: bit 0 the increment, bit 1 the network.
 template <int D>
 static int visc_guess(hbf_ctx* c, double beta, double* x, double* r, double* rn, int* used) {
+  const ProfRegion region(c, kSlotGuess);  // the whole section (regions do not nest)
   Level& L0 = c->lv[0];
   const long long n = (long long)D * L0.g.ncell;
   const int nb = grid_for(n);

@@ -595,6 +595,7 @@ void release_guess(hbf_ctx* c) {
 // argmin |r0 - alpha L delta|_2; kept only if its max-norm residual is smaller.
 int apply_guess(hbf_ctx* c, const double* b, double* p, int* used) {
   (void)b;
+  const ProfRegion region(c, kSlotGuess);
   *used = 0;
   hbf_unet* N = c->guess;
   int st = 0;

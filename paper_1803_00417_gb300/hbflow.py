@@ -498,7 +498,8 @@ class HBFlow:
         return out
 
     PROFILE_SLOTS = dict(visc_smooth=0, visc_resid=1, nodal_smooth=2, nodal_resid=3, mac_smooth=4,
-                         mac_resid=5, explicit=6, bottom=7, transfer=8, reduce=9, vector=10, coarse=11)
+                         mac_resid=5, explicit=6, bottom=7, transfer=8, reduce=9, vector=10, coarse=11,
+                         guess=12)
 
     def profile_enable(self, level=1):
         """0 off, 1 finest-level solver kernels and explicit stages, 2 also
