@@ -19,11 +19,15 @@ namespace hb {
 // ---------------------------------------------------------------------------
 // tensor viscous operator pieces (mirrors the explicit-stage operator)
 // ---------------------------------------------------------------------------
-// Explicitly rounded operations (round to nearest): the compiler may not
+// Explicitly rounded FP32 operations (round to nearest): the compiler may not
 // contract or reorder them, so every kernel that inlines the Gauss-Seidel
-// point updates below (visc_gs_point, visc_gs_core) issues the same
-// operations in the same order and gets the same bits.  On the host (the
-// host-built checks) they are the plain operations and an exact fused
+// point updates and the operator core below (visc_gs_point, visc_gs_core,
+// tensor_core) issues the same FP32 operations in the same order and gets the
+// same bits (the staged and unstaged FP32 kernels are checked against each
+// other bit for bit).  The FP64 forms are the plain operations, which the
+// compiler may fuse: the FP64 kernels are bound by GB300's FP64 issue rate,
+// and none of them has a second implementation to agree with.  On the host
+// (the host-built checks) both are the plain operations and an exact fused
 // multiply-add.
 template <typename T>
 __host__ __device__ __forceinline__ T rn_mul(T a, T b);
@@ -41,11 +45,7 @@ __host__ __device__ __forceinline__ float rn_mul<float>(float a, float b) {
 }
 template <>
 __host__ __device__ __forceinline__ double rn_mul<double>(double a, double b) {
-#ifdef __CUDA_ARCH__
-  return __dmul_rn(a, b);
-#else
   return a * b;
-#endif
 }
 template <>
 __host__ __device__ __forceinline__ float rn_add<float>(float a, float b) {
@@ -57,11 +57,7 @@ __host__ __device__ __forceinline__ float rn_add<float>(float a, float b) {
 }
 template <>
 __host__ __device__ __forceinline__ double rn_add<double>(double a, double b) {
-#ifdef __CUDA_ARCH__
-  return __dadd_rn(a, b);
-#else
   return a + b;
-#endif
 }
 template <>
 __host__ __device__ __forceinline__ float rn_fma<float>(float a, float b, float c) {
@@ -74,7 +70,7 @@ __host__ __device__ __forceinline__ float rn_fma<float>(float a, float b, float 
 template <>
 __host__ __device__ __forceinline__ double rn_fma<double>(double a, double b, double c) {
 #ifdef __CUDA_ARCH__
-  return __fma_rn(a, b, c);
+  return a * b + c;
 #else
   return std::fma(a, b, c);
 #endif
