@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--staged-sweep", default="0",
                     help="TMA-staged finest-level viscous sweeps: 'TX,TZ' (tile width 64 or 128, planes per block) "
                          "or 0 (hbf_set_staged_sweep)")
+    ap.add_argument("--inner-drop", type=float, default=1e-3,
+                    help="residual drop of each FP32 BiCGStab pass of the mixed viscous solve (hbf_set_inner_drop)")
     ap.add_argument("--staged-op", default="0",
                     help="TMA-staged finest-level viscous operator: 'ROWS,TZ' (tile 64 x ROWS, ROWS 4 or 8, planes "
                          "per block) or 0 (hbf_set_staged_op)")
@@ -416,6 +418,8 @@ def run_ours(args):
     sim.set_staged_sweep(staged[0], staged[1] if len(staged) > 1 else 16)
     sop = [int(v) for v in str(args.staged_op).split(",")] if args.staged_op != "0" else [0, 16]
     sim.set_staged_op(sop[0], sop[1] if len(sop) > 1 else 16)
+    if prec == MIXED:
+        sim.set_inner_drop(args.inner_drop)
     zeros_u = np.zeros(d * ncell)
     zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
     sim.set_field("U", zeros_u)
@@ -627,6 +631,7 @@ def run_ours(args):
                        "viscous_sweeps": ("one-launch fused" if args.fused_sweeps else
                                           f"TMA-staged {staged[0]}x8 tiles, {staged[1]} planes per block"
                                           if staged[0] else "two launches per component, unstaged"),
+                       "inner_drop": args.inner_drop if prec == MIXED else None,
                        "viscous_operator": (f"TMA-staged 64x{sop[0]} tiles, {sop[1]} planes per block" if sop[0]
                                             else "unstaged, one thread per cell"),
                        "cycles_per_step": {k: v / args.steps for k, v in cycles.items()},

@@ -140,6 +140,11 @@ int hbf_set_theta(hbf_ctx* ctx, double theta);
  * max_cycles V-cycles; nu1/nu2 pre/post smoothing sweeps; nu_bottom sweeps on
  * the coarsest level.  Defaults 1e-10, 200, 2, 2, 40. */
 int hbf_set_solver(hbf_ctx* ctx, double rtol, int max_cycles, int nu1, int nu2, int nu_bottom);
+/* HBF_MIXED viscous solve (Eq. 16): each pass of the FP64 defect correction
+ * runs the FP32 BiCGStab on A e = r until its residual has dropped by this
+ * factor (or 40 iterations), then recomputes r in FP64.  Default 1e-3; FP32
+ * limits a useful drop to about 1e-6.  HBF_ERR_ARG outside [1e-7, 1). */
+int hbf_set_inner_drop(hbf_ctx* ctx, double drop);
 /* The fused tail of the V-cycles (the multigrid scheme of Sec. III B): from
  * the first level with at most max_cells cells down to the exact bottom solve
  * and back runs as one launch of one thread block, with block barriers

@@ -385,6 +385,13 @@ int hbf_set_solver(hbf_ctx* c, double rtol, int max_cycles, int nu1, int nu2, in
   return HBF_OK;
 }
 
+int hbf_set_inner_drop(hbf_ctx* c, double drop) {
+  if (!c) return HBF_ERR_ARG;
+  if (!(drop >= 1e-7 && drop < 1.0)) return fail(c, HBF_ERR_ARG, "inner drop outside [1e-7, 1)");
+  c->inner_drop = drop;
+  return HBF_OK;
+}
+
 int hbf_set_periodic(hbf_ctx* c, const int periodic[3]) {
   if (!c || !periodic) return HBF_ERR_ARG;
   int per[3] = {0, 0, 0};

@@ -1497,10 +1497,9 @@ static void build_eta_levels(hbf_ctx* c) {
 // it; otherwise restarts from the true residual.  cycles = iterations.
 // Mixed precision: FP64 defect correction (r = b - A x and x += e in FP64)
 // around an FP32 BiCGStab on A e = r, itself preconditioned by FP32 V-cycles,
-// run until its residual drops by kInnerRtol (or kInnerMax iterations).
+// run until its residual drops by inner_drop (or kInnerMax iterations).
 // cycles = total inner iterations.
-constexpr double kInnerRtol = 1e-3;
-constexpr int kInnerMax = 40;
+constexpr int kInnerMax = 40;  // the drop is c->inner_drop (hbf_set_inner_drop, default 1e-3)
 
 // x (FP64) += a d (FP32);  r (FP64) -= a w (FP32)
 __global__ void k_add_scaled_f32(double* __restrict__ x, double a, const float* __restrict__ d, long long n) {
@@ -1655,7 +1654,7 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
     launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, fp, n);
     double in_norm = reduce_max_abs_f(c, fr, n, &st);
     if (st) return st;
-    const double in_tol = kInnerRtol * in_norm;
+    const double in_tol = c->inner_drop * in_norm;
     double rho = 1.0, alpha = 1.0, omega = 1.0;
     // the fused vector kernels need 16-byte aligned vectors (cudaMalloc'd)
     const bool fused = aligned16(fr) && aligned16(fs) && aligned16(ft) && aligned16(frh);

@@ -104,6 +104,7 @@ SIGNATURES = {
     "hbf_set_fused_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_set_staged_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hbf_set_staged_op": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hbf_set_inner_drop": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "hbf_field_size": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "hbf_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -330,6 +331,10 @@ class HBFlow:
     def set_staged_sweep(self, tile_x, tile_z=16):
         """TMA-staged finest-level viscous sweeps (tile_x 64 or 128; 0 off)."""
         self._check(self.lib.hbf_set_staged_sweep(self.ctx, int(tile_x), int(tile_z)))
+
+    def set_inner_drop(self, drop):
+        """Residual drop of each FP32 BiCGStab pass of the mixed viscous solve."""
+        self._check(self.lib.hbf_set_inner_drop(self.ctx, float(drop)))
 
     def set_staged_op(self, rows, tile_z=16):
         """TMA-staged finest-level viscous operator (rows 4 or 8; 0 off)."""
