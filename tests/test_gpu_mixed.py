@@ -113,3 +113,32 @@ def test_fused_tail_matches_level_by_level(precision, n):
         sim.close()
     for other in outs[1:]:
         assert np.linalg.norm(other - outs[0]) <= 1e-12 * np.linalg.norm(outs[0])
+
+
+def test_inner_drop_keeps_the_tolerance():
+    """The residual drop of each FP32 BiCGStab pass (hbf_set_inner_drop) only
+    changes how the FP64 defect correction gets to its tolerance: with drops
+    of 1e-2, 1e-3 (default) and 1e-5 every solve converges and the steps
+    agree to the solve tolerance; drops outside [1e-7, 1) are rejected."""
+    from paper_1803_00417_gb300.hbflow import MIXED, HBFlow, HBFlowError
+
+    cfg = cavity((24, 20, 16), Re=100.0, Bi=10.0, Pa=1e5, nexp=1.5)
+    u, p = random_state(cfg["n"], seed=37)
+    outs = []
+    for drop in (1e-3, 1e-2, 1e-5):
+        sim = HBFlow(cfg["n"], cfg["h"], cfg["wall_u"], precision=MIXED)
+        sim.set_rheology(cfg["K"], cfg["nexp"], cfg["tau_y"], cfg["m"])
+        sim.set_inner_drop(drop)
+        sim.set_velocity(u)
+        sim.set_pressure(p)
+        for _ in range(2):
+            st = sim.step(cfg["dt"])
+            assert all(st[k]["converged"] for k in ("mac", "visc", "nodal")), st
+        outs.append(sim.get_field("U"))
+        if drop == 1e-5:
+            for bad in (0.0, 1.0, 1e-9, float("nan")):
+                with pytest.raises(HBFlowError):
+                    sim.set_inner_drop(bad)
+        sim.close()
+    for other in outs[1:]:
+        assert np.max(np.abs(other - outs[0])) <= 1e-8 * np.max(np.abs(outs[0]))
