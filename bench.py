@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--staged-sweep", default="0",
                     help="TMA-staged finest-level viscous sweeps: 'TX,TZ' (tile width 64 or 128, planes per block) "
                          "or 0 (hbf_set_staged_sweep)")
+    ap.add_argument("--split-layout", type=int, default=1, choices=(0, 1),
+                    help="colour-split layout of the FP32 finest level of the mixed viscous solve (hbf_set_split_layout)")
     ap.add_argument("--inner-drop", type=float, default=1e-3,
                     help="residual drop of each FP32 BiCGStab pass of the mixed viscous solve (hbf_set_inner_drop)")
     ap.add_argument("--staged-op", default="0",
@@ -217,6 +219,19 @@ def run_reference(args):
 # the CUDA path
 # ---------------------------------------------------------------------------
 SMOOTHER_DRAM_BYTES_PER_CELL = (144.20e6 + 15.16e6) / 192 ** 3  # profiles/k_visc_smooth_cavity192.md
+# the colour-split form (profiles/k_visc_smooth_split_cavity192.md)
+SPLIT_SMOOTHER_DRAM_BYTES_PER_CELL = (113.30e6 + 8.67e6) / 192 ** 3
+
+
+def split_applies(args, prec, cfg):
+    """Whether the mixed viscous solve runs its FP32 finest level in the
+    colour-split layout (hbf_set_split_layout): 3D walled grid with an even x
+    extent, neither the fused nor the staged sweep nor the staged operator."""
+    from paper_1803_00417_gb300.hbflow import MIXED
+
+    n = cfg["n"]
+    return (prec == MIXED and args.split_layout == 1 and len(n) == 3 and n[0] % 2 == 0 and not args.fused_sweeps
+            and str(args.staged_sweep) == "0" and str(args.staged_op) == "0")
 
 
 def visc_smoother_bytes(d, ncell, elem, cell_eta):
@@ -420,6 +435,7 @@ def run_ours(args):
     sim.set_staged_op(sop[0], sop[1] if len(sop) > 1 else 16)
     if prec == MIXED:
         sim.set_inner_drop(args.inner_drop)
+        sim.set_split_layout(args.split_layout)
     zeros_u = np.zeros(d * ncell)
     zeros_p = np.zeros(int(np.prod([v + 1 for v in cfg["n"]])))
     sim.set_field("U", zeros_u)
@@ -593,19 +609,22 @@ def run_ours(args):
     if sm_n > 0:
         per_launch_s = sm_ms / sm_n / 1e3
         fused = prec == MIXED and d == 3 and args.fused_sweeps
+        split = split_applies(args, prec, cfg)
         algo = fused_sweep_bytes(d, ncell, elem) if fused else visc_smoother_bytes(d, ncell, elem, prec == MIXED)
         ach = algo / per_launch_s / 1e9
         # DRAM bytes per cell of this kernel from one full ncu capture at 192^3
         # of the current kernel (profiles/k_visc_smooth_cavity192.md), scaled
         # to this grid by the cell count (the kernel reads the same arrays per
         # cell at any size; the 256^3 workload is too large to capture)
-        traffic = SMOOTHER_DRAM_BYTES_PER_CELL * ncell if (prec == MIXED and not fused) else None
+        per_cell = SPLIT_SMOOTHER_DRAM_BYTES_PER_CELL if split else SMOOTHER_DRAM_BYTES_PER_CELL
+        traffic = per_cell * ncell if (prec == MIXED and not fused and per_cell) else None
         roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                     "traffic": traffic,
-                    "traffic_source": "ncu capture of the same kernel at 192^3 (22.5 B/cell), scaled by cells"
+                    "traffic_source": f"ncu capture of the same kernel at 192^3 ({per_cell:.1f} B/cell), scaled by cells"
                     if traffic else None,
                     "kernel": "k_visc_sweep_rb (fused red-black sweep, finest level)" if fused
-                    else "k_visc_smooth (finest level)",
+                    else ("k_visc_smooth_split (finest level, colour-split layout)" if split
+                          else "k_visc_smooth (finest level)"),
                     "launches": sm_n, "avg_launch_us": per_launch_s * 1e6,
                     "algorithmic_bytes_per_launch": algo,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
@@ -632,6 +651,8 @@ def run_ours(args):
                                           f"TMA-staged {staged[0]}x8 tiles, {staged[1]} planes per block"
                                           if staged[0] else "two launches per component, unstaged"),
                        "inner_drop": args.inner_drop if prec == MIXED else None,
+                       "finest_fp32_layout": ("colour-split" if split_applies(args, prec, cfg) else "natural")
+                       if prec == MIXED else None,
                        "viscous_operator": (f"TMA-staged 64x{sop[0]} tiles, {sop[1]} planes per block" if sop[0]
                                             else "unstaged, one thread per cell"),
                        "cycles_per_step": {k: v / args.steps for k, v in cycles.items()},

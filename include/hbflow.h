@@ -145,6 +145,15 @@ int hbf_set_solver(hbf_ctx* ctx, double rtol, int max_cycles, int nu1, int nu2, 
  * factor (or 40 iterations), then recomputes r in FP64.  Default 1e-3; FP32
  * limits a useful drop to about 1e-6.  HBF_ERR_ARG outside [1e-7, 1). */
 int hbf_set_inner_drop(hbf_ctx* ctx, double drop);
+/* HBF_MIXED viscous solve, 3D with walls on every axis and an even x extent:
+ * on = 1 (default) keeps the FP32 finest-level vectors of the solve in the
+ * colour-split layout (the cells with i + j + k even, then the odd ones, each
+ * row-major with n_x / 2 cells per row), so that each red-black sweep reads
+ * and writes unit-stride runs of one colour; on = 0 keeps the natural layout.
+ * The values are the same bit for bit; only the memory traffic differs.  The
+ * TMA-staged and one-launch sweep forms, when enabled, take the natural
+ * layout.  HBF_ERR_ARG unless on is 0 or 1. */
+int hbf_set_split_layout(hbf_ctx* ctx, int on);
 /* The fused tail of the V-cycles (the multigrid scheme of Sec. III B): from
  * the first level with at most max_cells cells down to the exact bottom solve
  * and back runs as one launch of one thread block, with block barriers

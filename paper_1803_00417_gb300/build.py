@@ -13,8 +13,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhbflow.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# a host function reached from device code is an error, not a warning (the
+# device side would otherwise compile to nothing)
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-          "--expt-relaxed-constexpr"]
+          "--expt-relaxed-constexpr", "--diag-error", "20011,20014"]
 # the explicit stages take sign decisions on computed values: no FMA contraction
 UNITS = {
     "hb_api.cu": [],

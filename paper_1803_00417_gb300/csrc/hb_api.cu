@@ -392,6 +392,13 @@ int hbf_set_inner_drop(hbf_ctx* c, double drop) {
   return HBF_OK;
 }
 
+int hbf_set_split_layout(hbf_ctx* c, int on) {
+  if (!c) return HBF_ERR_ARG;
+  if (on != 0 && on != 1) return fail(c, HBF_ERR_ARG, "split layout must be 0 or 1");
+  c->split_layout = on;
+  return HBF_OK;
+}
+
 int hbf_set_periodic(hbf_ctx* c, const int periodic[3]) {
   if (!c || !periodic) return HBF_ERR_ARG;
   int per[3] = {0, 0, 0};

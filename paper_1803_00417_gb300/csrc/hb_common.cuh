@@ -32,6 +32,7 @@ struct Geom {
   unsigned long long m_n0, m_n1, m_e0, m_e1, m_rb, m_mc0[2], m_mc1[2];
   unsigned long long m_rbx, m_xi;    // (n0 - 1) / 2 and n0 - 2: the x-interior cell maps
   unsigned long long m_rbxg, m_xig;  // their row-group sizes 16 M + 32
+  unsigned long long m_sx, m_n1i;    // n0 / 2 - 1 and n1 - 2: the colour-split interior map
 };
 
 // Multiplier M for the exact quotient t / d = floor(t * M / 2^64) of any
@@ -72,6 +73,8 @@ __host__ __device__ inline void geom_finish(Geom& g) {
   g.m_xi = div_magic((unsigned)(g.n[0] > 2 ? g.n[0] - 2 : 0));
   g.m_rbxg = div_magic((unsigned)(16 * ((g.n[0] - 1) / 2) + 32));
   g.m_xig = div_magic((unsigned)(16 * (g.n[0] > 2 ? g.n[0] - 2 : 0) + 32));
+  g.m_sx = div_magic((unsigned)(g.n[0] >= 4 ? g.n[0] / 2 - 1 : 1));
+  g.m_n1i = div_magic((unsigned)(g.n[1] > 2 ? g.n[1] - 2 : 1));
   for (int b = 0; b < 2; ++b) {
     g.m_mc0[b] = div_magic((unsigned)((g.n[0] + 1 - b + 1) / 2));
     g.m_mc1[b] = div_magic((unsigned)((g.n[1] + 1 - b + 1) / 2));
@@ -133,6 +136,20 @@ inline int rheo_e2(double n, int reg_power) {
 template <int D>
 __host__ __device__ inline int cidx(const Geom& g, int i, int j, int k) {
   return i + g.n[0] * (j + g.n[1] * k);
+}
+
+// Cell (i, j, k) of a 3D level with even n0 in the colour-split layout: the
+// cells with i + j + k even first, then the odd ones, each half row-major
+// over (j, k) with n0 / 2 cells per row (cell i at i / 2).  A red-black sweep
+// then reads and writes unit-stride runs of one colour.
+__host__ __device__ inline int sidx(const Geom& g, int i, int j, int k) {
+  return ((i + j + k) & 1) * (g.ncell >> 1) + (j + g.n[1] * k) * (g.n[0] >> 1) + (i >> 1);
+}
+
+// the natural (SP false) or colour-split (SP true, 3D only) cell index
+template <int D, bool SP = false>
+__host__ __device__ inline int lidx(const Geom& g, int i, int j, int k) {
+  return SP ? sidx(g, i, j, k) : cidx<D>(g, i, j, k);
 }
 
 __host__ __device__ inline int nidx(const Geom& g, int i, int j, int k) {

@@ -110,6 +110,8 @@ struct hbf_ctx {
   double K = 1.0;           // the consistency K as given to hbf_set_rheology
   double theta = 0.5;       // implicit weight of the viscous term (1/2: Crank-Nicolson, Eq. 15)
   double inner_drop = 1e-3; // residual drop of each FP32 BiCGStab pass of the mixed viscous solve
+  int split_layout = 1;     // FP32 finest level of the mixed viscous solve in the colour-split layout where it applies
+  int split_last = -1;      // the layout of the last mixed viscous solve (vprev32 is kept in it)
   double t = 0.0;           // time: the sum of the dt of every step taken
   long long nstep = 0;      // steps taken
   int walls_version = 0;    // bumped by hbf_set_walls (batched tables rebuild)

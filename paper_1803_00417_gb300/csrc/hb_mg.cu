@@ -19,6 +19,7 @@
 #include "hb_mg_kernels.cuh"
 #include "hb_vcycle_tail.cuh"
 #include "hb_visc_fused.cuh"
+#include "hb_visc_split.cuh"
 #include "hb_visc_tma.cuh"
 
 #include <cudaTypedefs.h>
@@ -238,6 +239,19 @@ static inline bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // a periodic axis: the Poisson and transfer kernels take their PER = true
 // form (with the wraps); walls on every axis take PER = false
 static inline bool any_per(const Geom& g) { return g.per[0] || g.per[1] || g.per[2]; }
+
+// The FP32 finest level of the mixed viscous solve in the colour-split layout
+// (hb_visc_split.cuh): 3D, walls on every axis, even n0, at least two levels,
+// and none of the opt-in sweep or operator forms that read the natural layout
+// (staged, fused) nor a network on level 0.  Every FP32 level-0 vector of the
+// solve (the BiCGStab vectors, the V-cycle's level-0 arrays, the cell
+// viscosity, the previous increment) is then split; FP64 arrays stay natural.
+static bool split0(const hbf_ctx* c) {
+  const Geom& g = c->g;
+  return c->split_layout && c->dim == 3 && c->precision == HBF_MIXED && !any_per(g) && g.n[0] % 2 == 0 &&
+         g.n[0] >= 4 && g.n[1] >= 3 && g.n[2] >= 3 && c->lv.size() >= 2 && c->lv[0].feta != nullptr &&
+         !c->staged_tx && !c->staged_op_rows && !c->fused_sweep && !(c->vnet && c->vnet_level == 0);
+}
 
 template <int MODE>
 static int reduce_to_device(hbf_ctx* c, const double* x, long long n, double* out) {
@@ -948,7 +962,9 @@ struct ViscProblem : Problem<T> {
   T* x0;
   const T* b0 = nullptr;  // level-0 right-hand side in place of the level's own array (read only)
   double beta;
-  ViscProblem(hbf_ctx* ctx, T* x_in, double bt, bool h0) : Problem<T>(ctx, false, h0), x0(x_in), beta(bt) {}
+  const bool sp;  // level 0 in the colour-split layout (FP32 only)
+  ViscProblem(hbf_ctx* ctx, T* x_in, double bt, bool h0)
+      : Problem<T>(ctx, false, h0), x0(x_in), beta(bt), sp(sizeof(T) == 4 && D == 3 && split0(ctx)) {}
   int kind() const override { return 0; }
   double dense_beta() const override { return beta; }
   bool tail(int l) override { return run_tail<D, T, batch::kVisc>(c, l, beta); }
@@ -962,6 +978,19 @@ struct ViscProblem : Problem<T> {
     const dim3 blk(kThreads, 1, 1);
     const dim3 grd((unsigned)grid_for(rbx_count<D>(L.g), 152 * 24), 1, 1);
     const int hm = (int)this->hom(l);
+    if (l == 0 && sp) {
+      if constexpr (D == 3 && sizeof(T) == 4) {
+        const float* e0 = (const float*)L.feta;
+        const dim3 sg = split_sweep_grid(L.g), sb = split_sweep_block(L.g);
+        for (int col = 0; col < 2; ++col)
+          launch3(c, slot, k_visc_smooth_split<0>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
+        for (int col = 0; col < 2; ++col)
+          launch3(c, slot, k_visc_smooth_split<1>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
+        for (int col = 0; col < 2; ++col)
+          launch3(c, slot, k_visc_smooth_split<2>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
+      }
+      return;
+    }
     if (cell_eta(l) && staged_sweeps(l, hm)) return;
     if (cell_eta(l)) {
       // FP32 finest level: face viscosities from the cell viscosity
@@ -1034,6 +1063,12 @@ struct ViscProblem : Problem<T> {
     Level& L = c->lv[l];
     const dim3 blk(256, 1, 1);
     const dim3 grd(op3_blocks<D>(L.g), 1, 1);
+    if (l == 0 && sp) {
+      if constexpr (D == 3 && sizeof(T) == 4)
+        launch3(c, kSlotViscResid, k_visc_op_split, split_grid(L.g), split_block_dim(L.g, 2), (const T*)x(l),
+                (const T*)b(l), r(l), (const T*)L.feta, L.g, (T)beta, (int)this->hom(l));
+      return;
+    }
     if (cell_eta(l)) {
       const T* e0 = (const T*)L.feta;
       if constexpr (std::is_same<T, float>::value)
@@ -1058,12 +1093,18 @@ struct ViscProblem : Problem<T> {
   void restrict_to(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
     long long n = (long long)D * C.g.ncell;
-    launch(c, kSlotTransfer, k_restrict_cells<D, T>, grid_for(n), kThreads, r(l), b(l + 1), F.g, C.g, D);
+    if (l == 0 && sp)
+      launch(c, kSlotTransfer, k_restrict_cells<D, T, true>, grid_for(n), kThreads, r(l), b(l + 1), F.g, C.g, D);
+    else
+      launch(c, kSlotTransfer, k_restrict_cells<D, T>, grid_for(n), kThreads, r(l), b(l + 1), F.g, C.g, D);
     launch(c, kSlotTransfer, k_zero<T>, grid_for(n), kThreads, x(l + 1), n);
   }
   void prolong_add(int l) override {
     Level &F = c->lv[l], &C = c->lv[l + 1];
-    {
+    if (l == 0 && sp) {
+      launch(c, kSlotTransfer, k_prolong_cells_add_c<D, T, false, true>, grid_for((long long)D * C.g.ncell), kThreads, x(l),
+             x(l + 1), F.g, C.g, D, T(-1));
+    } else {
       if (any_per(c->g))
         launch(c, kSlotTransfer, k_prolong_cells_add_c<D, T, true>, grid_for((long long)D * C.g.ncell), kThreads, x(l), x(l + 1),
            F.g, C.g, D, T(-1));
@@ -1484,8 +1525,12 @@ static void build_eta_levels(hbf_ctx* c) {
     // the finest level of the FP32 V-cycles reads the cell viscosity (the
     // level-0 faces are the means of its cells, wall faces the interior cell)
     Level& L0 = c->lv[0];
-    launch(c, kSlotTransfer, k_convert<float, double>, grid_for(L0.g.ncell), kThreads, L0.feta,
-           (const double*)c->eta, (long long)L0.g.ncell);
+    if (split0(c))
+      launch(c, kSlotTransfer, k_split_from, grid_for(L0.g.ncell / 2), kThreads, L0.feta, (const double*)c->eta,
+             (const double*)nullptr, L0.g, 1);
+    else
+      launch(c, kSlotTransfer, k_convert<float, double>, grid_for(L0.g.ncell), kThreads, L0.feta,
+             (const double*)c->eta, (long long)L0.g.ncell);
   }
 }
 
@@ -1544,14 +1589,22 @@ static int visc_guess(hbf_ctx* c, double beta, double* x, double* r, double* rn,
   float* cur = c->fkr;  // FP32 copy of the current residual
   float* tmp = c->fkt;
   float* w = c->fkv;
-  launch(c, kSlotVector, k_convert<float, double>, nb, kThreads, cur, (const double*)r, n);
+  const bool sp = D == 3 && split0(c);  // the FP32 vectors in the colour-split layout
+  if (sp)
+    launch(c, kSlotVector, k_split_from, grid_for(n / 2), kThreads, cur, (const double*)r, (const double*)nullptr, L0.g,
+           D);
+  else
+    launch(c, kSlotVector, k_convert<float, double>, nb, kThreads, cur, (const double*)r, n);
   double m = reduce_max_abs_f(c, cur, n, &st);
   if (st) return st;
   const dim3 blk(256, 1, 1);
   const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
   auto step_along = [&](const float* d, int bit) -> int {
     const float* e0 = L0.feta;
-    if (staged_op(c, kSlotVector, d, nullptr, w, e0, L0.g, fbeta, 1))
+    if (sp)
+      launch3(c, kSlotVector, k_visc_op_split, split_grid(L0.g), split_block_dim(L0.g, 2), d, (const float*)nullptr, w,
+              e0, L0.g, fbeta, 1);
+    else if (staged_op(c, kSlotVector, d, nullptr, w, e0, L0.g, fbeta, 1))
       ;
     else if (any_per(c->g))
       launch3(c, kSlotVector, k_visc_op3<D, float, true, true>, grd, blk, d, (const float*)nullptr, w, e0, e0, e0, L0.g,
@@ -1569,8 +1622,13 @@ static int visc_guess(hbf_ctx* c, double beta, double* x, double* r, double* rn,
     const double m1 = reduce_max_abs_f(c, tmp, n, &st);
     if (st) return st;
     if (m1 < m) {
-      launch(c, kSlotVector, k_add_scaled_f32, nb, kThreads, x, a, d, n);
-      launch(c, kSlotVector, k_add_scaled_f32, nb, kThreads, r, -a, (const float*)w, n);
+      if (sp) {
+        launch(c, kSlotVector, k_split_add, grid_for(n / 2), kThreads, x, a, d, L0.g, D);
+        launch(c, kSlotVector, k_split_add, grid_for(n / 2), kThreads, r, -a, (const float*)w, L0.g, D);
+      } else {
+        launch(c, kSlotVector, k_add_scaled_f32, nb, kThreads, x, a, d, n);
+        launch(c, kSlotVector, k_add_scaled_f32, nb, kThreads, r, -a, (const float*)w, n);
+      }
       float* t = cur;
       cur = tmp;
       tmp = t;
@@ -1601,6 +1659,9 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
         *fsh = c->fksh, *fe = c->fke;
   ViscProblem<D, double> P(c, x, beta, false);
   const float fbeta = (float)beta;
+  const bool sp = D == 3 && split0(c);  // the FP32 level-0 vectors in the colour-split layout
+  if (c->split_last != (int)sp) c->vprev_ok = false;  // the kept increment is in the other layout
+  c->split_last = (int)sp;
   int st = 0;
   auto true_residual = [&]() -> double {
     cudaMemcpyAsync(L0.vb, kb, bytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -1621,6 +1682,11 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
   const dim3 grd(op3_blocks<D>(L0.g), 1, 1);
   auto apply0 = [&](const float* q, float* o) {
     const float* e0 = L0.feta;
+    if (sp) {
+      launch3(c, kSlotViscResid, k_visc_op_split, split_grid(L0.g), split_block_dim(L0.g, 2), q, (const float*)nullptr, o,
+              e0, L0.g, fbeta, 1);
+      return;
+    }
     if (staged_op(c, kSlotViscResid, q, nullptr, o, e0, L0.g, fbeta, 1)) return;
     if (any_per(c->g))
       launch3(c, kSlotViscResid, k_visc_op3<D, float, true, true>, grd, blk, q, (const float*)nullptr, o, e0, e0, e0, L0.g,
@@ -1647,7 +1713,11 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
   }
   int it = 0;
   while (rn > tol && it < cfg.max_cycles && std::isfinite(rn)) {
-    launch(c, kSlotTransfer, k_convert<float, double>, nb, kThreads, fr, (const double*)r, n);
+    if (sp)
+      launch(c, kSlotTransfer, k_split_from, grid_for(n / 2), kThreads, fr, (const double*)r, (const double*)nullptr,
+             L0.g, D);
+    else
+      launch(c, kSlotTransfer, k_convert<float, double>, nb, kThreads, fr, (const double*)r, n);
     launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, fe, n);
     cudaMemcpyAsync(frh, fr, fbytes, cudaMemcpyDeviceToDevice, c->stream);
     launch(c, kSlotTransfer, k_zero<float>, nb, kThreads, fv, n);
@@ -1702,7 +1772,10 @@ static int solve_viscous_mixed(hbf_ctx* c, double beta, const double* b_in, doub
       ++it;
       if (rr <= in_tol || omega == 0.0 || !std::isfinite(rr)) break;
     }
-    launch(c, kSlotTransfer, k_add_f32, nb, kThreads, x, (const float*)fe, n);
+    if (sp)
+      launch(c, kSlotTransfer, k_split_add, grid_for(n / 2), kThreads, x, 1.0, (const float*)fe, L0.g, D);
+    else
+      launch(c, kSlotTransfer, k_add_f32, nb, kThreads, x, (const float*)fe, n);
     rn = true_residual();
     if (st) return st;
   }
@@ -1887,6 +1960,8 @@ void cell_restrict_f(hbf_ctx* c, int l, const float* fine, float* coarse) {
   const long long n = (long long)c->dim * C.g.ncell;
   if (c->dim == 2)
     launch(c, kSlotTransfer, k_restrict_cells<2, float>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 2);
+  else if (l == 0 && split0(c))  // the FP32 level-0 vectors of the mixed viscous solve
+    launch(c, kSlotTransfer, k_restrict_cells<3, float, true>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3);
   else
     launch(c, kSlotTransfer, k_restrict_cells<3, float>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3);
 }
@@ -1909,6 +1984,9 @@ void cell_prolong_add_f(hbf_ctx* c, int l, float* fine, const float* coarse) {
       launch(c, kSlotTransfer, k_prolong_cells_add_c<2, float, true>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 2, -1.f);
     else
       launch(c, kSlotTransfer, k_prolong_cells_add_c<2, float, false>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 2, -1.f);
+  } else if (l == 0 && split0(c)) {  // the FP32 level-0 vectors of the mixed viscous solve
+    launch(c, kSlotTransfer, k_prolong_cells_add_c<3, float, false, true>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3,
+           -1.f);
   } else {
     if (any_per(c->g))
       launch(c, kSlotTransfer, k_prolong_cells_add_c<3, float, true>, grid_for(n), kThreads, fine, coarse, F.g, C.g, 3, -1.f);
@@ -1920,7 +1998,10 @@ void cell_prolong_add_f(hbf_ctx* c, int l, float* fine, const float* coarse) {
 int visc_after_solve(hbf_ctx* c, const double* ustar, const double* u) {
   const long long n = (long long)c->dim * c->g.ncell;
   if (c->vguess_mode > 0 && c->vprev32) {
-    launch(c, kSlotVector, k_diff_to_f32, grid_for(n), kThreads, c->vprev32, ustar, u, n);
+    if (c->dim == 3 && split0(c))  // kept in the layout of the FP32 vectors of the next solve
+      launch(c, kSlotVector, k_split_from, grid_for(n / 2), kThreads, c->vprev32, ustar, u, c->lv[0].g, 3);
+    else
+      launch(c, kSlotVector, k_diff_to_f32, grid_for(n), kThreads, c->vprev32, ustar, u, n);
     c->vprev_ok = true;
   }
   if (c->vrecord && c->vcorr) launch(c, kSlotVector, k_rsub, grid_for(n), kThreads, ustar, c->vcorr, n);  // u* - start

@@ -105,6 +105,7 @@ SIGNATURES = {
     "hbf_set_staged_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hbf_set_staged_op": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hbf_set_inner_drop": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "hbf_set_split_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_field_size": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
     "hbf_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "hbf_get_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -335,6 +336,11 @@ class HBFlow:
     def set_inner_drop(self, drop):
         """Residual drop of each FP32 BiCGStab pass of the mixed viscous solve."""
         self._check(self.lib.hbf_set_inner_drop(self.ctx, float(drop)))
+
+    def set_split_layout(self, on):
+        """Colour-split layout of the FP32 finest-level vectors of the mixed
+        viscous solve (1, the default where it applies) or the natural one (0)."""
+        self._check(self.lib.hbf_set_split_layout(self.ctx, int(on)))
 
     def set_staged_op(self, rows, tile_z=16):
         """TMA-staged finest-level viscous operator (rows 4 or 8; 0 off)."""
