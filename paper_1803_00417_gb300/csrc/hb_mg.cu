@@ -235,6 +235,7 @@ __global__ void k_dot_partial_v(const double* __restrict__ a, const double* __re
 }
 
 static inline bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+static inline bool aligned8(const void* p) { return ((uintptr_t)p & 7) == 0; }
 
 // a periodic axis: the Poisson and transfer kernels take their PER = true
 // form (with the wraps); walls on every axis take PER = false
@@ -982,12 +983,17 @@ struct ViscProblem : Problem<T> {
       if constexpr (D == 3 && sizeof(T) == 4) {
         const float* e0 = (const float*)L.feta;
         const dim3 sg = split_sweep_grid(L.g), sb = split_sweep_block(L.g);
+        // pairs read by 8-byte loads: even rows (n0 / 2) and 8-byte aligned arrays
+        const bool vec = (L.g.n[0] / 2) % 2 == 0 && aligned8(x(l)) && aligned8(b(l)) && aligned8(e0);
         for (int col = 0; col < 2; ++col)
-          launch3(c, slot, k_visc_smooth_split<0>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
+          vec ? launch3(c, slot, k_visc_smooth_split<0, true>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm)
+              : launch3(c, slot, k_visc_smooth_split<0, false>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
         for (int col = 0; col < 2; ++col)
-          launch3(c, slot, k_visc_smooth_split<1>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
+          vec ? launch3(c, slot, k_visc_smooth_split<1, true>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm)
+              : launch3(c, slot, k_visc_smooth_split<1, false>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
         for (int col = 0; col < 2; ++col)
-          launch3(c, slot, k_visc_smooth_split<2>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
+          vec ? launch3(c, slot, k_visc_smooth_split<2, true>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm)
+              : launch3(c, slot, k_visc_smooth_split<2, false>, sg, sb, x(l), (const T*)b(l), e0, L.g, col, (T)beta, hm);
       }
       return;
     }

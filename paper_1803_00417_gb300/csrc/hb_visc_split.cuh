@@ -266,21 +266,24 @@ __host__ __device__ __forceinline__ void split_smooth_wall(float* __restrict__ u
   u[(size_t)C * g.ncell + (size_t)col * (g.ncell >> 1) + P] = split_gs_wall<C>(u, b, eta, g, col, p, P, beta, hom);
 }
 
-// Thread -> cells map of the sweep: two neighbouring cells of a row per
-// thread (slots m and m + 1, m even, as split_thread numbers them), in 2D
-// blocks of bx threads along the row (a row segment of at most 256 pairs)
-// times R rows, R chosen so that bx R fills whole warps where it can
-// (48 pairs per row: 2 rows, 3 warps).  Block (seg, jb, k) with jb < nb takes
-// rows jb R .. jb R + R - 1 of plane k; the blocks (0, nb + G, k) take the
-// x-wall cells of rows 32 G .. 32 G + 31, one per thread of the first warp.
-// f(p, P, interior, two) for the first cell p at position P and, when two,
-// the next cell of the colour in the row (p[0] + 2, P + 1).
+// Thread -> cells map of the sweep: the cells of the colour at positions
+// i / 2 = 2t and 2t + 1 of a row per thread t (an even first position, so that
+// both can be read with one 8-byte load), in 2D blocks of bx threads along the
+// row (a row segment of at most 256 threads) times R rows, R chosen so that
+// bx R fills whole warps where it can (48 threads per row: 2 rows, 3 warps).
+// Block (seg, jb, k) with jb < nb takes rows jb R .. jb R + R - 1 of plane k:
+// every cell of the row but its x-wall cell (i = 0 or n0 - 1), interior
+// unless j or k is on a wall.  The blocks (0, nb + G, k) take the x-wall cells
+// of rows 32 G .. 32 G + 31, one per thread of the first warp, right after the
+// plane's rows.  f(p, P, interior, a, b) for the first cell p (i / 2 = 2t) at
+// position P; a and b tell which of it and the next cell (p[0] + 2, P + 1)
+// belong to the thread.
 struct SplitSweep {
   int bx, R, nseg, nb;
 };
 
 __host__ __device__ inline SplitSweep split_sweep(const Geom& g) {
-  const int pairs = (g.n[0] >> 1) / 2;  // ceil((n0 / 2 - 1) / 2)
+  const int pairs = ((g.n[0] >> 1) + 1) / 2;
   SplitSweep w;
   w.bx = pairs < 256 ? pairs : 256;
   w.nseg = (pairs + w.bx - 1) / w.bx;
@@ -312,17 +315,17 @@ __host__ __device__ __forceinline__ void split_pair_thread(const Geom& g, int co
   const int hn = g.n[0] >> 1;
   if (jb < w.nb) {
     const int j = jb * w.R + ty;
-    const int m = 2 * (seg * w.bx + tx);
-    if (j >= g.n[1] || m >= hn - 1) return;
-    const int q = (j + k + col) & 1;
-    const int ih = m + 1 - q;
+    const int ih = 2 * (seg * w.bx + tx);
+    if (j >= g.n[1] || ih >= hn) return;
+    const int q = (j + k + col) & 1;  // x parity of the colour's cells in this row
+    // the row's cells but its x-wall cell: i / 2 in [1 - q, hn - 1 - q]
+    const bool a = ih >= 1 - q && ih <= hn - 1 - q, b = ih + 1 <= hn - 1 - q;
     const int p[3] = {2 * ih + q, j, k};
     const int P = (j + g.n[1] * k) * hn + ih;
-    const bool two = m + 1 < hn - 1;
     if (j > 0 && j < g.n[1] - 1 && k > 0 && k < g.n[2] - 1)
-      f(p, P, true, two);
+      f(p, P, true, a, b);
     else
-      f(p, P, false, two);
+      f(p, P, false, a, b);
   } else {
     const int t = ty * w.bx + tx;
     if (seg != 0 || t >= 32) return;
@@ -331,8 +334,94 @@ __host__ __device__ __forceinline__ void split_pair_thread(const Geom& g, int co
     const int q = (j + k + col) & 1;
     const int ih = q ? hn - 1 : 0;
     const int p[3] = {2 * ih + q, j, k};
-    f(p, (j + g.n[1] * k) * hn + ih, false, false);
+    f(p, (j + g.n[1] * k) * hn + ih, false, true, false);
   }
+}
+
+// two floats at an even position of a (8-byte aligned)
+__host__ __device__ __forceinline__ void ld2(const float* __restrict__ a, int pos, float& x0, float& x1) {
+#ifdef __CUDA_ARCH__
+  const float2 v = *reinterpret_cast<const float2*>(a + pos);
+  x0 = v.x;
+  x1 = v.y;
+#else
+  x0 = a[pos];
+  x1 = a[pos + 1];
+#endif
+}
+
+// The Gauss-Seidel values of component C at the two interior cells at
+// positions P0 (even) and P0 + 1 of colour col (x parity q), with the pair's
+// values read by 8-byte loads: a neighbour displaced along y or z sits at
+// P0 + d for the first cell and P0 + d + 1 for the second (one load); along x
+// the two cells need three consecutive positions from P0 + q - 1 or P0 + q
+// (one 8-byte load at the even position and one 4-byte load).  The same
+// values as split_gs_value gathers, into the same visc_gs_core: the same bits.
+template <int C>
+__host__ __device__ __forceinline__ void split_gs_pair(const float* __restrict__ u, const float* __restrict__ b,
+                                                       const float* __restrict__ eta, const Geom& g, int col, int q,
+                                                       int P0, float bs, float& va, float& vb) {
+  const int half = g.ncell >> 1, own = col * half, oth = half - own;
+  const int dr[3] = {0, g.n[0] >> 1, (g.n[0] >> 1) * g.n[1]};
+  // the pair's values of arr at the displacement s1 e_a1 + s2 e_a2 (a2 < 0: none)
+  auto pr = [&](const float* arr, int a1, int s1, int a2, int s2, float& xa, float& xb) {
+    int off = 0, sx = 0;
+    if (a1 == 0)
+      sx = s1;
+    else
+      off += s1 * dr[a1];
+    if (a2 == 0)
+      sx = s2;
+    else if (a2 > 0)
+      off += s2 * dr[a2];
+    const int base = P0 + off;
+    float v0, v1;
+    ld2(arr, base, v0, v1);
+    if (sx > 0) {  // base + q and base + q + 1
+      const float s = arr[base + 2];
+      xa = q ? v1 : v0;
+      xb = q ? s : v1;
+    } else if (sx < 0) {  // base + q - 1 and base + q
+      const float s = arr[base - 1];
+      xa = q ? v0 : s;
+      xb = q ? v1 : v0;
+    } else {
+      xa = v0;
+      xb = v1;
+    }
+  };
+  float elo[2][3], ehi[2][3], ulo[2][3], uhi[2][3], xa[2][3][6];
+  float e0a, e0b;
+  ld2(eta + own, P0, e0a, e0b);
+  const float* uo = u + (size_t)C * g.ncell + oth;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float la, lb, ha, hb;
+    pr(eta + oth, a, -1, -1, 0, la, lb);
+    pr(eta + oth, a, 1, -1, 0, ha, hb);
+    elo[0][a] = la + e0a;
+    elo[1][a] = lb + e0b;
+    ehi[0][a] = e0a + ha;
+    ehi[1][a] = e0b + hb;
+    pr(uo, a, -1, -1, 0, ulo[0][a], ulo[1][a]);
+    pr(uo, a, 1, -1, 0, uhi[0][a], uhi[1][a]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a == C) continue;
+    const float* ao = u + (size_t)a * g.ncell + oth;
+    const float* aw = u + (size_t)a * g.ncell + own;
+    pr(ao, C, 1, -1, 0, xa[0][a][0], xa[1][a][0]);
+    pr(ao, C, -1, -1, 0, xa[0][a][1], xa[1][a][1]);
+    pr(aw, a, 1, C, 1, xa[0][a][2], xa[1][a][2]);
+    pr(aw, a, 1, C, -1, xa[0][a][3], xa[1][a][3]);
+    pr(aw, a, -1, C, 1, xa[0][a][4], xa[1][a][4]);
+    pr(aw, a, -1, C, -1, xa[0][a][5], xa[1][a][5]);
+  }
+  float ba, bb;
+  ld2(b + (size_t)C * g.ncell + own, P0, ba, bb);
+  va = visc_gs_core<3, float>(C, elo[0], ehi[0], ulo[0], uhi[0], xa[0], ba, bs);
+  vb = visc_gs_core<3, float>(C, elo[1], ehi[1], ulo[1], uhi[1], xa[1], bb, bs);
 }
 
 // the Gauss-Seidel value of component C at interior cell s
@@ -346,30 +435,38 @@ __host__ __device__ __forceinline__ float split_gs_value(const float* __restrict
   return visc_gs_core<3, float>(C, elo, ehi, ulo, uhi, xa, b[(size_t)C * g.ncell + s.own + s.P], bs);
 }
 
-// thread (tx, ty) of block (seg, jb, k) of a sweep of colour col: both values of
-// an interior pair are formed before either is stored, so that the loads the
-// two cells share are issued once (the stores, to u_C of colour col, hit no
-// value either cell reads)
-template <int C>
+// thread (tx, ty) of block (seg, jb, k) of a sweep of colour col: both values
+// of an interior pair are formed before either is stored, so that the loads
+// the two cells share are issued once (the stores, to u_C of colour col, hit
+// no value either cell reads).  VEC: the pair read by 8-byte loads
+// (split_gs_pair; n0 / 2 even and 8-byte aligned arrays).
+template <int C, bool VEC>
 __host__ __device__ __forceinline__ void split_smooth_thread(float* __restrict__ u, const float* __restrict__ b,
                                                              const float* __restrict__ eta, const Geom& g, int col,
                                                              float beta, int hom, const SplitSweep& w, int seg, int jb,
                                                              int k, int tx, int ty) {
   const float bs = beta * (g.fihh * 0.5f);  // CellEta's factor 1/2 with 1/h^2
-  split_pair_thread(g, col, w, seg, jb, k, tx, ty, [&](const int* p, int P, bool in, bool two) {
+  split_pair_thread(g, col, w, seg, jb, k, tx, ty, [&](const int* p, int P, bool in, bool ca, bool cb) {
+    const size_t o = (size_t)C * g.ncell + (size_t)col * (g.ncell >> 1) + P;
     if (in) {
-      const SplitCell sa(g, col, p[0] & 1, P);
-      const float va = split_gs_value<C>(u, b, eta, g, sa, bs);
-      const size_t o = (size_t)C * g.ncell + sa.own + P;
-      if (two) {
-        const SplitCell sb(g, col, p[0] & 1, P + 1);
-        const float vb = split_gs_value<C>(u, b, eta, g, sb, bs);
-        u[o + 1] = vb;
+      float va, vb;
+      if (VEC) {
+        split_gs_pair<C>(u, b, eta, g, col, p[0] & 1, P, bs, va, vb);
+      } else {
+        if (ca) va = split_gs_value<C>(u, b, eta, g, SplitCell(g, col, p[0] & 1, P), bs);
+        if (cb) vb = split_gs_value<C>(u, b, eta, g, SplitCell(g, col, p[0] & 1, P + 1), bs);
       }
-      u[o] = va;
+#ifdef __CUDA_ARCH__
+      if (VEC && ca && cb) {
+        *reinterpret_cast<float2*>(u + o) = make_float2(va, vb);
+        return;
+      }
+#endif
+      if (ca) u[o] = va;
+      if (cb) u[o + 1] = vb;
     } else {
-      split_smooth_wall<C>(u, b, eta, g, col, p, P, beta, hom);
-      if (two) {
+      if (ca) split_smooth_wall<C>(u, b, eta, g, col, p, P, beta, hom);
+      if (cb) {
         const int p2[3] = {p[0] + 2, p[1], p[2]};
         split_smooth_wall<C>(u, b, eta, g, col, p2, P + 1, beta, hom);
       }
@@ -379,15 +476,19 @@ __host__ __device__ __forceinline__ void split_smooth_thread(float* __restrict__
 
 // Red-black Gauss-Seidel sweep of component C over the cells of colour col
 // (the update of k_visc_smooth_c with the cell viscosity); grid
-// split_sweep_grid(g), block split_sweep_block(g).
-template <int C>
-__global__ void __launch_bounds__(256, 6) k_visc_smooth_split(float* __restrict__ u, const float* __restrict__ b,
+// split_sweep_grid(g), block split_sweep_block(g).  VEC: see
+// split_smooth_thread; it holds both cells' values at once and runs at 64
+// registers (at 40 or 48 it spilled and was slower than the scalar form; at
+// 64, 72-76 against 75-82 us per 256^3 launch).
+template <int C, bool VEC>
+__global__ void __launch_bounds__(256, VEC ? 4 : 6) k_visc_smooth_split(float* __restrict__ u, const float* __restrict__ b,
                                                                const float* __restrict__ eta,
                                                                const __grid_constant__ Geom g, int col, float beta,
                                                                int hom) {
   // the map's sizes are the launch's (split_sweep(g) on the host)
   const SplitSweep w{(int)blockDim.x, (int)blockDim.y, (int)gridDim.x, (int)gridDim.y - (g.n[1] + 31) / 32};
-  split_smooth_thread<C>(u, b, eta, g, col, beta, hom, w, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y);
+  split_smooth_thread<C, VEC>(u, b, eta, g, col, beta, hom, w, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x,
+                              threadIdx.y);
 }
 
 // the operator at a wall cell

@@ -89,9 +89,9 @@ int main(int argc, char** argv) {
         }
         ++seen[cidx<3>(g, p[0], p[1], p[2])];
       };
-      auto visit2 = [&](const int* p, int P, bool in, bool two) {
-        visit(p, P, col0, in);
-        if (two) {
+      auto visit2 = [&](const int* p, int P, bool in, bool ca, bool cb) {
+        if (ca) visit(p, P, col0, in);
+        if (cb) {
           const int p2[3] = {p[0] + 2, p[1], p[2]};
           visit(p2, P + 1, col0, in);
         }
@@ -141,8 +141,9 @@ int main(int argc, char** argv) {
     if (!same_split(g, out, sout, 3)) return fail(withb ? "operator with b" : "operator");
   }
 
-  // red-black sweeps of the three components in turn
-  {
+  // red-black sweeps of the three components in turn, by the scalar gather
+  // and (rows of even length) by the 8-byte pair gather
+  for (int vec = 0; vec < ((g.n[0] / 2) % 2 == 0 ? 2 : 1); ++vec) {
     std::vector<float> x = u, sx = su0;
     for (int C = 0; C < 3; ++C)
       for (int col = 0; col < 2; ++col) {
@@ -164,11 +165,14 @@ int main(int argc, char** argv) {
             for (int seg = 0; seg < (int)sgr.x; ++seg)
               for (int ty = 0; ty < (int)sbl.y; ++ty)
                 for (int tx = 0; tx < (int)sbl.x; ++tx) {
-                  if (C == 0) split_smooth_thread<0>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
-                  if (C == 1) split_smooth_thread<1>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
-                  if (C == 2) split_smooth_thread<2>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
+                  if (C == 0 && vec) split_smooth_thread<0, true>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
+                  if (C == 0 && !vec) split_smooth_thread<0, false>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
+                  if (C == 1 && vec) split_smooth_thread<1, true>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
+                  if (C == 1 && !vec) split_smooth_thread<1, false>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
+                  if (C == 2 && vec) split_smooth_thread<2, true>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
+                  if (C == 2 && !vec) split_smooth_thread<2, false>(sx.data(), sb.data(), seta.data(), g, col, beta, hom, sw, seg, j, k, tx, ty);
                 }
-        if (!same_split(g, x, sx, 3)) return fail("red-black sweep");
+        if (!same_split(g, x, sx, 3)) return fail(vec ? "red-black sweep (8-byte pairs)" : "red-black sweep");
       }
   }
 

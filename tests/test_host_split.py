@@ -28,12 +28,13 @@ def harness(tmp_path_factory):
 
 # the smallest grid the layout takes, ragged odd y/z extents (no transfers),
 # even grids with the coarse level, both wall conditions, more than 32 rows
-# per plane (several x-wall warps, the last one partial) and rows longer than
-# one block's 256 slots (two segments)
+# per plane (several x-wall warps, the last one partial), rows longer than one
+# block's 256 threads (two segments), and rows of even length n0 / 2, where the
+# sweep's 8-byte pair gather is checked too
 @pytest.mark.parametrize("n,hom,seed", [((4, 3, 3), 0, 1), ((8, 6, 4), 0, 2), ((8, 6, 4), 1, 3),
                                         ((12, 7, 9), 0, 4), ((10, 5, 3), 1, 5), ((16, 16, 16), 0, 6),
                                         ((6, 9, 12), 1, 7), ((20, 8, 6), 0, 8), ((18, 70, 14), 1, 9),
-                                        ((600, 5, 4), 0, 10)])
+                                        ((600, 5, 4), 0, 10), ((24, 10, 8), 1, 15), ((1100, 4, 3), 1, 11)])
 def test_split_layout_matches_natural_bit_for_bit(harness, n, hom, seed):
     r = subprocess.run([harness, *map(str, n), str(hom), str(seed)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
