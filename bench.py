@@ -220,7 +220,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 SMOOTHER_DRAM_BYTES_PER_CELL = (144.20e6 + 15.16e6) / 192 ** 3  # profiles/k_visc_smooth_cavity192.md
 # the colour-split form (profiles/k_visc_smooth_split_cavity192.md)
-SPLIT_SMOOTHER_DRAM_BYTES_PER_CELL = (113.30e6 + 8.67e6) / 192 ** 3
+SPLIT_SMOOTHER_DRAM_BYTES_PER_CELL = (113.29e6 + 8.96e6) / 192 ** 3
 
 
 def split_applies(args, prec, cfg):
