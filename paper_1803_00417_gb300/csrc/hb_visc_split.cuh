@@ -350,21 +350,19 @@ __host__ __device__ __forceinline__ void ld2(const float* __restrict__ a, int po
 #endif
 }
 
-// The Gauss-Seidel values of component C at the two interior cells at
-// positions P0 (even) and P0 + 1 of colour col (x parity q), with the pair's
-// values read by 8-byte loads: a neighbour displaced along y or z sits at
-// P0 + d for the first cell and P0 + d + 1 for the second (one load); along x
-// the two cells need three consecutive positions from P0 + q - 1 or P0 + q
-// (one 8-byte load at the even position and one 4-byte load).  The same
-// values as split_gs_value gathers, into the same visc_gs_core: the same bits.
-template <int C>
-__host__ __device__ __forceinline__ void split_gs_pair(const float* __restrict__ u, const float* __restrict__ b,
-                                                       const float* __restrict__ eta, const Geom& g, int col, int q,
-                                                       int P0, float bs, float& va, float& vb) {
-  const int half = g.ncell >> 1, own = col * half, oth = half - own;
-  const int dr[3] = {0, g.n[0] >> 1, (g.n[0] >> 1) * g.n[1]};
-  // the pair's values of arr at the displacement s1 e_a1 + s2 e_a2 (a2 < 0: none)
-  auto pr = [&](const float* arr, int a1, int s1, int a2, int s2, float& xa, float& xb) {
+// The values two interior cells of colour col at positions P0 (even) and
+// P0 + 1 (x parity q) read, by 8-byte loads: a neighbour displaced along y or
+// z sits at P0 + d for the first cell and P0 + d + 1 for the second (one
+// load); along x the two cells need three consecutive positions from
+// P0 + q - 1 or P0 + q (one 8-byte load at the even position and one 4-byte
+// load).  get(arr, a1, s1, a2, s2): the pair's values of arr (a colour's half)
+// at the displacement s1 e_a1 + s2 e_a2 (a2 < 0: none).
+struct SplitPair {
+  int P0, q, own, oth, dr[3];
+  __host__ __device__ __forceinline__ SplitPair(const Geom& g, int col, int q_, int P0_)
+      : P0(P0_), q(q_), own(col * (g.ncell >> 1)), oth((1 - col) * (g.ncell >> 1)), dr{0, g.n[0] >> 1, (g.n[0] >> 1) * g.n[1]} {}
+  __host__ __device__ __forceinline__ void get(const float* __restrict__ arr, int a1, int s1, int a2, int s2, float& xa,
+                                               float& xb) const {
     int off = 0, sx = 0;
     if (a1 == 0)
       sx = s1;
@@ -389,37 +387,60 @@ __host__ __device__ __forceinline__ void split_gs_pair(const float* __restrict__
       xa = v0;
       xb = v1;
     }
-  };
+  }
+  // CellEta's face sums of the pair (elo / ehi as split_eta forms them)
+  __host__ __device__ __forceinline__ void eta(const float* __restrict__ e, float (*elo)[3], float (*ehi)[3]) const {
+    float e0a, e0b;
+    ld2(e + own, P0, e0a, e0b);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float la, lb, ha, hb;
+      get(e + oth, a, -1, -1, 0, la, lb);
+      get(e + oth, a, 1, -1, 0, ha, hb);
+      elo[0][a] = la + e0a;
+      elo[1][a] = lb + e0b;
+      ehi[0][a] = e0a + ha;
+      ehi[1][a] = e0b + hb;
+    }
+  }
+  // u_c at the face neighbours and, for a != c, the cross term's u_a values
+  // (split_u's) of the pair
+  __host__ __device__ __forceinline__ void stencil(const float* __restrict__ u, const Geom& g, int c, float (*ulo)[3],
+                                                   float (*uhi)[3], float (*xa)[3][6]) const {
+    const float* uo = u + (size_t)c * g.ncell + oth;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      get(uo, a, -1, -1, 0, ulo[0][a], ulo[1][a]);
+      get(uo, a, 1, -1, 0, uhi[0][a], uhi[1][a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == c) continue;
+      const float* ao = u + (size_t)a * g.ncell + oth;
+      const float* aw = u + (size_t)a * g.ncell + own;
+      get(ao, c, 1, -1, 0, xa[0][a][0], xa[1][a][0]);
+      get(ao, c, -1, -1, 0, xa[0][a][1], xa[1][a][1]);
+      get(aw, a, 1, c, 1, xa[0][a][2], xa[1][a][2]);
+      get(aw, a, 1, c, -1, xa[0][a][3], xa[1][a][3]);
+      get(aw, a, -1, c, 1, xa[0][a][4], xa[1][a][4]);
+      get(aw, a, -1, c, -1, xa[0][a][5], xa[1][a][5]);
+    }
+  }
+};
+
+// The Gauss-Seidel values of component C at the pair (SplitPair's cells):
+// the same values as split_gs_value gathers, into the same visc_gs_core, so
+// the same bits
+template <int C>
+__host__ __device__ __forceinline__ void split_gs_pair(const float* __restrict__ u, const float* __restrict__ b,
+                                                       const float* __restrict__ eta, const Geom& g, int col, int q,
+                                                       int P0, float bs, float& va, float& vb) {
+  const SplitPair sp(g, col, q, P0);
   float elo[2][3], ehi[2][3], ulo[2][3], uhi[2][3], xa[2][3][6];
-  float e0a, e0b;
-  ld2(eta + own, P0, e0a, e0b);
-  const float* uo = u + (size_t)C * g.ncell + oth;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float la, lb, ha, hb;
-    pr(eta + oth, a, -1, -1, 0, la, lb);
-    pr(eta + oth, a, 1, -1, 0, ha, hb);
-    elo[0][a] = la + e0a;
-    elo[1][a] = lb + e0b;
-    ehi[0][a] = e0a + ha;
-    ehi[1][a] = e0b + hb;
-    pr(uo, a, -1, -1, 0, ulo[0][a], ulo[1][a]);
-    pr(uo, a, 1, -1, 0, uhi[0][a], uhi[1][a]);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a == C) continue;
-    const float* ao = u + (size_t)a * g.ncell + oth;
-    const float* aw = u + (size_t)a * g.ncell + own;
-    pr(ao, C, 1, -1, 0, xa[0][a][0], xa[1][a][0]);
-    pr(ao, C, -1, -1, 0, xa[0][a][1], xa[1][a][1]);
-    pr(aw, a, 1, C, 1, xa[0][a][2], xa[1][a][2]);
-    pr(aw, a, 1, C, -1, xa[0][a][3], xa[1][a][3]);
-    pr(aw, a, -1, C, 1, xa[0][a][4], xa[1][a][4]);
-    pr(aw, a, -1, C, -1, xa[0][a][5], xa[1][a][5]);
-  }
+  sp.eta(eta, elo, ehi);
+  sp.stencil(u, g, C, ulo, uhi, xa);
   float ba, bb;
-  ld2(b + (size_t)C * g.ncell + own, P0, ba, bb);
+  ld2(b + (size_t)C * g.ncell + sp.own, P0, ba, bb);
   va = visc_gs_core<3, float>(C, elo[0], ehi[0], ulo[0], uhi[0], xa[0], ba, bs);
   vb = visc_gs_core<3, float>(C, elo[1], ehi[1], ulo[1], uhi[1], xa[1], bb, bs);
 }
