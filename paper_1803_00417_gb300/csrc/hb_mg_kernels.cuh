@@ -92,7 +92,7 @@ struct FaceEta {
   const T* const* ef;
   __host__ __device__ T lo(const Geom& g, const Strides& S, int a, const int* p, int id) const;
   __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
-  template <bool PER = true, bool SP = false>
+  template <bool PER = true>
   __host__ __device__ T at(const Geom& g, int a, const int* q) const {
     return ef[a][fidx(g, a, q[0], q[1], q[2])];
   }
@@ -104,7 +104,7 @@ struct CellEta {
   const T* eta;
   __host__ __device__ T lo(const Geom& g, const Strides& S, int a, const int* p, int id) const;
   __host__ __device__ T hi(const Geom& g, const Strides& S, int a, const int* p, int id) const;
-  template <bool PER = true, bool SP = false>
+  template <bool PER = true>
   __host__ __device__ T at(const Geom& g, int a, const int* q) const {
     int L[3] = {q[0], q[1], q[2]}, R[3] = {q[0], q[1], q[2]};
     if (PER && g.per[a]) {  // periodic: the two cells across the face, wrapped
@@ -114,19 +114,19 @@ struct CellEta {
       L[a] = q[a] > 0 ? q[a] - 1 : 0;
       R[a] = q[a] < g.n[a] ? q[a] : g.n[a] - 1;
     }
-    return T(0.5) * (eta[lidx<3, SP>(g, L[0], L[1], L[2])] + eta[lidx<3, SP>(g, R[0], R[1], R[2])]);
+    return T(0.5) * (eta[cidx<3>(g, L[0], L[1], L[2])] + eta[cidx<3>(g, R[0], R[1], R[2])]);
   }
 };
 
 // component comp at cell q, which lies inside the domain on every axis but
 // ax: uget with the one reflection test that can apply
-template <int D, typename T, bool PER = true, bool SP = false>
+template <int D, typename T, bool PER = true>
 __host__ __device__ __forceinline__ T uget_axis(const T* __restrict__ uc, const Geom& g, int comp, int i, int j, int k,
                                                 int ax, bool hom) {
   int q[3] = {i, j, k};
   if (PER && g.per[ax]) {
     q[ax] = wrap_cell(q[ax], g.n[ax]);
-    return uc[lidx<D, SP>(g, q[0], q[1], q[2])];
+    return uc[cidx<D>(g, q[0], q[1], q[2])];
   }
   int side = -1;
   if (q[ax] < 0) {
@@ -136,13 +136,13 @@ __host__ __device__ __forceinline__ T uget_axis(const T* __restrict__ uc, const 
     side = 1;
     q[ax] = 2 * g.n[ax] - 1 - q[ax];
   }
-  const T v = uc[lidx<D, SP>(g, q[0], q[1], q[2])];
+  const T v = uc[cidx<D>(g, q[0], q[1], q[2])];
   if (side < 0) return v;
   const T ub = hom ? T(0) : g_wu<T>(g, ax, side, comp);
   return rn_add(rn_mul(T(2), ub), -v);
 }
 
-template <int D, typename T, bool PER = true, bool SP = false>
+template <int D, typename T, bool PER = true>
 __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom& g, int a, int c, const int* L,
                                   bool hom) {
   // mean of the two cells' central differences, (dL + dR)/2 with dL, dR over 2h;
@@ -154,20 +154,20 @@ __host__ __device__ inline T mg_face_cross(const T* __restrict__ ua, const Geom&
   if (pa) p1[a] = p0[a] = wrap_cell(L[a], g.n[a]);
   p1[c] += 1;
   p0[c] -= 1;
-  T dL = rn_add(uget_axis<D, T, PER, SP>(ua, g, a, p1[0], p1[1], p1[2], c, hom),
-                -uget_axis<D, T, PER, SP>(ua, g, a, p0[0], p0[1], p0[2], c, hom));
+  T dL = rn_add(uget_axis<D, T, PER>(ua, g, a, p1[0], p1[1], p1[2], c, hom),
+                -uget_axis<D, T, PER>(ua, g, a, p0[0], p0[1], p0[2], c, hom));
   if (pa) {
     p1[a] = p0[a] = wrap_cell(L[a] + 1, g.n[a]);
   } else {
     p1[a] += 1;
     p0[a] += 1;
   }
-  T dR = rn_add(uget_axis<D, T, PER, SP>(ua, g, a, p1[0], p1[1], p1[2], c, hom),
-                -uget_axis<D, T, PER, SP>(ua, g, a, p0[0], p0[1], p0[2], c, hom));
+  T dR = rn_add(uget_axis<D, T, PER>(ua, g, a, p1[0], p1[1], p1[2], c, hom),
+                -uget_axis<D, T, PER>(ua, g, a, p0[0], p0[1], p0[2], c, hom));
   return rn_mul(rn_add(dL, dR), g_q4<T>(g));
 }
 
-template <int D, typename T, bool PER = true, bool SP = false, typename EF>
+template <int D, typename T, bool PER = true, typename EF>
 __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& ef, const Geom& g, int c,
                                     const int* p, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
@@ -182,15 +182,15 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& 
       L[a] += s - 1;
       int R[3] = {L[0], L[1], L[2]};
       R[a] += 1;
-      T e = ef.template at<PER, SP>(g, a, R);
+      T e = ef.template at<PER>(g, a, R);
       // L and R differ from the cell p only along a
-      T nrm = rn_mul(rn_add(uget_axis<D, T, PER, SP>(uc, g, c, R[0], R[1], R[2], a, hom),
-                            -uget_axis<D, T, PER, SP>(uc, g, c, L[0], L[1], L[2], a, hom)),
+      T nrm = rn_mul(rn_add(uget_axis<D, T, PER>(uc, g, c, R[0], R[1], R[2], a, hom),
+                            -uget_axis<D, T, PER>(uc, g, c, L[0], L[1], L[2], a, hom)),
                      ih);
       if (a == c)
         flux[s] = rn_mul(e, rn_mul(T(2), nrm));
       else
-        flux[s] = rn_mul(e, rn_add(nrm, mg_face_cross<D, T, PER, SP>(u + (size_t)a * g.ncell, g, a, c, L, hom)));
+        flux[s] = rn_mul(e, rn_add(nrm, mg_face_cross<D, T, PER>(u + (size_t)a * g.ncell, g, a, c, L, hom)));
     }
     acc = rn_add(acc, rn_mul(rn_add(flux[1], -flux[0]), ih));
   }
@@ -198,7 +198,7 @@ __host__ __device__ inline T mg_tensor_point(const T* __restrict__ u, const EF& 
 }
 
 // Gauss-Seidel update of component c at cell p (all other values frozen)
-template <int D, typename T, bool PER = true, bool SP = false, typename EF>
+template <int D, typename T, bool PER = true, typename EF>
 __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __restrict__ b, const EF& ef,
                                   const Geom& g, int c, const int* p, T beta, bool hom) {
   const T* uc = u + (size_t)c * g.ncell;
@@ -218,7 +218,7 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
         q[a] += 1;
         fq[a] += 1;
       }
-      T wf = kappa * ef.template at<PER, SP>(g, a, fq) * ihh;
+      T wf = kappa * ef.template at<PER>(g, a, fq) * ihh;
       const bool pa = PER && g.per[a];
       bool wall = !pa && ((s == 0) ? (p[a] == 0) : (p[a] == g.n[a] - 1));
       if (wall) {
@@ -227,7 +227,7 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
         diag = rn_fma(T(2), wf, diag);
       } else {
         if (pa) q[a] = wrap_cell(q[a], g.n[a]);
-        offd = rn_fma(wf, uc[lidx<D, SP>(g, q[0], q[1], q[2])], offd);
+        offd = rn_fma(wf, uc[cidx<D>(g, q[0], q[1], q[2])], offd);
         diag = rn_add(diag, wf);
       }
     }
@@ -241,12 +241,12 @@ __host__ __device__ inline T visc_gs_point(const T* __restrict__ u, const T* __r
     Llo[a] -= 1;
     int fhi[3] = {p[0], p[1], p[2]};
     fhi[a] += 1;
-    T fluxhi = rn_mul(ef.template at<PER, SP>(g, a, fhi), mg_face_cross<D, T, PER, SP>(ua, g, a, c, p, hom));
-    T fluxlo = rn_mul(ef.template at<PER, SP>(g, a, p), mg_face_cross<D, T, PER, SP>(ua, g, a, c, Llo, hom));
+    T fluxhi = rn_mul(ef.template at<PER>(g, a, fhi), mg_face_cross<D, T, PER>(ua, g, a, c, p, hom));
+    T fluxlo = rn_mul(ef.template at<PER>(g, a, p), mg_face_cross<D, T, PER>(ua, g, a, c, Llo, hom));
     cross = rn_fma(rn_add(fluxhi, -fluxlo), ih, cross);
   }
   // explicitly rounded (see rn_fma): the same result wherever it is inlined
-  return rn_fma(beta, rn_add(offd, cross), b[(size_t)c * g.ncell + lidx<D, SP>(g, p[0], p[1], p[2])]) /
+  return rn_fma(beta, rn_add(offd, cross), b[(size_t)c * g.ncell + cidx<D>(g, p[0], p[1], p[2])]) /
          rn_fma(beta, diag, T(1));
 }
 

@@ -6,8 +6,9 @@
 // colour only: none of the opposite colour's bytes of u_c and b_c that every
 // 32-byte sector of the natural layout carries along.  The arithmetic is that
 // of the natural-layout kernels (visc_gs_core and tensor_core on the same
-// gathered values, the same wall-cell functions through lidx, the same
-// transfers), so both layouts give the same values bit for bit.
+// gathered values; at wall cells visc_gs_point's and mg_tensor_point's
+// operations in the same order; the same transfers through lidx), so both
+// layouts give the same values bit for bit.
 #pragma once
 #include "hb_mg_kernels.cuh"
 
